@@ -1,0 +1,186 @@
+"""Exact signed distance to the extracted surface (Sec. 2.4, Eqs. 29-34).
+
+Distance (Eq. 33): d(q) = min over all triangles T_k of d(q, T_k).  The
+point-to-triangle distance follows the paper's description: project q on the
+triangle's plane; if the projection is inside the triangle, the distance is
+the plane distance; otherwise it is the smallest distance to the three edges
+(segments, which include the vertices).
+
+Search: exact, never approximate.  The upper bound U(q) = distance to the
+nearest triangle centroid (a point of the surface) is found with a k-d tree;
+every triangle within U of q has its centroid within U + rho of q, rho the
+largest centroid-to-vertex radius, so the candidates returned by a ball query
+of radius U + rho contain the minimiser.  Brute force over all triangles is
+kept for the small cross-checks.
+
+Sign (Eq. 30, 34): at grid nodes the surface separates nodes with chi < c
+(inside, sign -1) from the rest (outside, +1) by construction; the paper's
+parity ray cast (Sec. 2.2 crossing-number rule applied to the mesh) is
+implemented here as well, to check that both agree.
+
+Ties between triangles resolve to the smaller distance, then the smaller
+triangle index.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.spatial import cKDTree
+
+
+def _closest_on_segment(p, a, b):
+    ab = b - a
+    L2 = np.sum(ab * ab, axis=-1)
+    t = np.where(L2 > 0, np.sum((p - a) * ab, axis=-1) / np.where(L2 > 0, L2, 1.0), 0.0)
+    t = np.clip(t, 0.0, 1.0)
+    return a + t[..., None] * ab, t
+
+
+def closest_point_triangle(p, a, b, c):
+    """Closest point y on triangle (a,b,c) to p and its barycentrics (wa, wb, wc).
+
+    Arrays broadcast over leading dimensions, last dimension 3.
+    """
+    p, a, b, c = np.broadcast_arrays(p, a, b, c)
+    ab = b - a
+    ac = c - a
+    ap = p - a
+    # projection on the plane: solve [ab.ab ab.ac; ab.ac ac.ac] [v w] = [ab.ap ac.ap]
+    d00 = np.sum(ab * ab, -1)
+    d01 = np.sum(ab * ac, -1)
+    d11 = np.sum(ac * ac, -1)
+    r0 = np.sum(ab * ap, -1)
+    r1 = np.sum(ac * ap, -1)
+    det = d00 * d11 - d01 * d01
+    ok = det > 1e-300
+    sdet = np.where(ok, det, 1.0)
+    v = (d11 * r0 - d01 * r1) / sdet
+    w = (d00 * r1 - d01 * r0) / sdet
+    u = 1.0 - v - w
+    inside = ok & (u >= 0) & (v >= 0) & (w >= 0)
+    y_face = a + v[..., None] * ab + w[..., None] * ac
+    # edges
+    y_ab, t_ab = _closest_on_segment(p, a, b)
+    y_bc, t_bc = _closest_on_segment(p, b, c)
+    y_ca, t_ca = _closest_on_segment(p, c, a)
+    d_ab = np.sum((p - y_ab) ** 2, -1)
+    d_bc = np.sum((p - y_bc) ** 2, -1)
+    d_ca = np.sum((p - y_ca) ** 2, -1)
+    best = np.argmin(np.stack([d_ab, d_bc, d_ca], -1), axis=-1)
+    y_edge = np.where((best == 0)[..., None], y_ab, np.where((best == 1)[..., None], y_bc, y_ca))
+    bary_edge = np.stack([
+        np.where(best == 0, 1 - t_ab, np.where(best == 2, t_ca, 0.0)),
+        np.where(best == 0, t_ab, np.where(best == 1, 1 - t_bc, 0.0)),
+        np.where(best == 1, t_bc, np.where(best == 2, 1 - t_ca, 0.0)),
+    ], -1)
+    y = np.where(inside[..., None], y_face, y_edge)
+    bary = np.where(inside[..., None], np.stack([u, v, w], -1), bary_edge)
+    return y, bary
+
+
+def point_triangle_distance(p, a, b, c):
+    y, _ = closest_point_triangle(p, a, b, c)
+    return np.sqrt(np.sum((p - y) ** 2, -1))
+
+
+def brute_force_distance(nodes, verts):
+    """(d [N], tri [N]) by testing every triangle against every node."""
+    N = nodes.shape[0]
+    d = np.full(N, np.inf)
+    tri = np.full(N, -1, dtype=np.int64)
+    for t in range(verts.shape[0]):
+        dt = point_triangle_distance(nodes, verts[t, 0], verts[t, 1], verts[t, 2])
+        better = dt < d
+        d = np.where(better, dt, d)
+        tri = np.where(better, t, tri)
+    return d, tri
+
+
+def exact_distance(nodes, verts, chunk: int = 16384):
+    """Exact nearest-triangle distance and index for every node (k-d tree pruned)."""
+    N = nodes.shape[0]
+    T = verts.shape[0]
+    d = np.full(N, np.inf)
+    tri = np.full(N, -1, dtype=np.int64)
+    if T == 0 or N == 0:
+        return d, tri
+    cent = verts.mean(axis=1)
+    rho = float(np.max(np.linalg.norm(verts - cent[:, None, :], axis=2)))
+    tree = cKDTree(cent)
+    for s in range(0, N, chunk):
+        q = nodes[s:s + chunk]
+        U, _ = tree.query(q)
+        cands = tree.query_ball_point(q, U * (1 + 1e-12) + rho + 1e-15)
+        lens = np.array([len(cc) for cc in cands])
+        flat = np.concatenate([np.asarray(cc, dtype=np.int64) for cc in cands])
+        owner = np.repeat(np.arange(len(q)), lens)
+        # stable order inside each node: ascending triangle index
+        order = np.lexsort((flat, owner))
+        flat = flat[order]
+        owner = owner[order]
+        dd = point_triangle_distance(q[owner], verts[flat, 0], verts[flat, 1], verts[flat, 2])
+        starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+        mind = np.minimum.reduceat(dd, starts)
+        # smallest triangle index among the minimisers
+        is_min = dd == mind[owner]
+        big = np.where(is_min, flat, np.iinfo(np.int64).max)
+        argt = np.minimum.reduceat(big, starts)
+        d[s:s + chunk] = mind
+        tri[s:s + chunk] = argt
+    return d, tri
+
+
+def node_sign(chi, c):
+    return np.where(chi >= c, 1.0, -1.0)
+
+
+RAY_DIR = np.array([0.5773, 0.5774, 0.5775]) / np.linalg.norm([0.5773, 0.5774, 0.5775])
+
+
+def parity_inside(nodes, verts, direction=RAY_DIR, eps=1e-10):
+    """Crossing-number inside test against the triangle mesh (odd = inside).
+
+    Degenerate hits (on an edge or vertex, or at the origin) are re-cast with a
+    perturbed direction.
+    """
+    out = np.zeros(nodes.shape[0], dtype=bool)
+    a, b, c = verts[:, 0], verts[:, 1], verts[:, 2]
+    e1 = b - a
+    e2 = c - a
+    rng = np.random.default_rng(12345)
+    for i, q in enumerate(nodes):
+        dvec = direction
+        for _attempt in range(20):
+            pvec = np.cross(dvec, e2)
+            det = np.sum(e1 * pvec, axis=1)
+            good = np.abs(det) > 1e-300
+            inv = np.where(good, 1.0 / np.where(good, det, 1.0), 0.0)
+            tvec = q - a
+            u = np.sum(tvec * pvec, axis=1) * inv
+            qvec = np.cross(tvec, e1)
+            v = (qvec @ dvec) * inv
+            t = np.sum(e2 * qvec, axis=1) * inv
+            hit = good & (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 0)
+            near = good & (t > -eps) & (
+                (np.abs(u) < eps) | (np.abs(v) < eps) | (np.abs(1 - u - v) < eps) | (np.abs(t) < eps)
+            ) & (u > -eps) & (v > -eps) & (u + v < 1 + eps)
+            if not near.any():
+                out[i] = bool(hit.sum() % 2)
+                break
+            dvec = dvec + 1e-3 * rng.standard_normal(3)
+            dvec /= np.linalg.norm(dvec)
+    return out
+
+
+def winding_number(points, verts):
+    """Generalised winding number of the oriented mesh at each point."""
+    w = np.zeros(points.shape[0])
+    for i, q in enumerate(points):
+        A = verts[:, 0] - q
+        B = verts[:, 1] - q
+        C = verts[:, 2] - q
+        la, lb, lc = (np.linalg.norm(X, axis=1) for X in (A, B, C))
+        num = np.sum(A * np.cross(B, C), axis=1)
+        den = (la * lb * lc + np.sum(A * B, 1) * lc + np.sum(A * C, 1) * lb
+               + np.sum(B * C, 1) * la)
+        w[i] = np.sum(2.0 * np.arctan2(num, den)) / (4 * np.pi)
+    return w
