@@ -1,0 +1,472 @@
+"""Benchmark of the SDF + normal reconstruction path on one GB300 (or N replicas).
+
+Workload (N = 1): the 256^3 spherical-harmonic body — 200,000 area-uniform
+surface points of r(u) = 0.3 + sum_{l<=8} theta_k Y_k(u), theta ~ N(0, 0.02^2),
+analytic normals, position noise N(0, 0.002^2) — with 1,000,000 uniform query
+points.  One step = the whole path on that input: splat, divergence,
+mixed-precision Poisson solve, iso-value, marching cubes, exact SDF, stencil
+normals, query at 1M points, and the adjoint of a loss on the queried SDF
+(query / distance / marching-cubes / iso-value adjoints, adjoint solve, splat
+adjoint).  Metric: grid cells per second (res^3 / step time).
+
+Arms: default = the CUDA library through its C ABI; --impl reference = the
+FP64 CPU oracle on the host cores (a bounded sample of the same step).
+Multi-GPU: independent replicas, one per rank, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RES = 256
+NPTS = 200_000
+NQ = 1_000_000
+BBOX = np.array([0, 0, 0, 1, 1, 1], dtype=np.float32)
+L2_BYTES = 129 * 2 ** 20
+METRIC = "SDF+normal cells/s at 256^3 (fwd, fwd+adjoint) vs FP32 plain; p50/p99 latency"
+
+
+def workload():
+    import synth
+    p, n, info = synth.sh_body_cloud(NPTS, lmax=8)
+    q = synth.uniform_queries(NQ, seed=2001)
+    # a fixed seeded adjoint seed for the queried SDF (stands in for dL/dphi(q))
+    g = np.random.default_rng(2002).standard_normal(NQ).astype(np.float32) / NQ
+    return p, n, q, g
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm = []
+        mx = None
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx = float(s[1])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if s[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- helpers
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as ge
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    ge.build()
+    from paper_2609_20964_gb300 import PREC_FP32, Reconstructor
+
+    p, n, q, g = workload()
+    P = torch.from_numpy(p).cuda()
+    Nn = torch.from_numpy(n).cuda()
+    Q = torch.from_numpy(q).cuda()
+    G = torch.from_numpy(g).cuda()
+    rec = Reconstructor(RES, NPTS)
+    stream = torch.cuda.current_stream()
+    N = RES ** 3
+
+    def step():
+        rec.reconstruct(P, Nn, BBOX, RES, with_sdf=True, with_normals=True, sdf_out=sdf_buf, nrm_out=nrm_buf)
+        rec.query(Q, with_normals=False)
+        rec.backward(q=Q, d_sdf_q=G)
+
+    sdf_buf = torch.empty((RES, RES, RES), device="cuda")
+    nrm_buf = torch.empty((3, RES, RES, RES), device="cuda")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = rec.info()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0.record(stream)
+    ev[0].record(stream)
+    for k in range(args.steps):
+        step()
+        ev[k + 1].record(stream)
+    e1.record(stream)
+    barrier()
+    clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    t = torch.tensor([total_ms], device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * N * args.steps / (total_ms / 1e3)
+
+    # forward-only rates (mixed and plain FP32) on the same input
+    def time_it(fn, k):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    fwd_ms = time_it(lambda: rec.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf), 5)
+    rec32 = Reconstructor(RES, NPTS, precision=PREC_FP32, keep_for_backward=0, max_vcycles=60)
+    fwd32_ms = time_it(lambda: rec32.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf), 5)
+    info32 = rec32.info()
+    sdf32 = sdf_buf.clone()
+    rec.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf)
+    torch.cuda.synchronize()
+    fp32_vs_mixed = float((sdf32 - sdf_buf).abs().max().item())
+    rec32.close()
+
+    # per-stage device times (CUDA events on the library's stream), separate pass
+    rec_t = Reconstructor(RES, NPTS, stage_timing=1)
+    for _ in range(2):
+        rec_t.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf)
+        rec_t.query(Q, with_normals=False)
+        rec_t.backward(q=Q, d_sdf_q=G)
+    torch.cuda.synchronize()
+    rec_t.stage_times(reset=True)
+    for _ in range(args.stage_steps):
+        rec_t.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf)
+        rec_t.query(Q, with_normals=False)
+        rec_t.backward(q=Q, d_sdf_q=G)
+    torch.cuda.synchronize()
+    st = rec_t.stage_times(reset=True)
+    stages = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in st.items()}
+    info_t = rec_t.info()
+    rec_t.close()
+
+    # end to end through the C ABI with host buffers (pinned), copies in the timed region
+    ph = torch.from_numpy(p).pin_memory()
+    nh = torch.from_numpy(n).pin_memory()
+    qh = torch.from_numpy(q).pin_memory()
+    gh = torch.from_numpy(g).pin_memory()
+    dph = torch.empty((NPTS, 3), dtype=torch.float32).pin_memory()
+    dnh = torch.empty((NPTS, 3), dtype=torch.float32).pin_memory()
+    Pd = torch.empty_like(P)
+    Nd = torch.empty_like(Nn)
+    Qd = torch.empty_like(Q)
+    Gd = torch.empty_like(G)
+
+    def e2e_step():
+        Pd.copy_(ph, non_blocking=True)
+        Nd.copy_(nh, non_blocking=True)
+        Qd.copy_(qh, non_blocking=True)
+        Gd.copy_(gh, non_blocking=True)
+        rec.reconstruct(Pd, Nd, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf)
+        rec.query(Qd, with_normals=False)
+        dp, dn, _ = rec.backward(q=Qd, d_sdf_q=Gd)
+        dph.copy_(dp, non_blocking=True)
+        dnh.copy_(dn, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    ke = max(3, args.steps // 2)
+    a.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / ke
+    h2d = (p.nbytes + n.nbytes + q.nbytes + g.nbytes)
+    d2h = 2 * NPTS * 3 * 4
+
+    # roofline of the dominant kernel
+    hbm, peak_kind = load_peaks()
+    dom = max(stages, key=lambda k: stages[k])
+    roof = roofline(dom, stages, info, hbm, peak_kind)
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "cells/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "SH body (degree<=8) 200k points, 256^3 grid, 1M queries, "
+                               "forward + query + adjoint", "res": RES, "points": NPTS,
+                   "queries": NQ, "precision": "mixed FP32 multigrid / FP64 refinement",
+                   "l2": "working set > 1 GB per step (fields of 67 MB) exceeds the 129 MB L2; no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99))},
+        "fwd_cells_per_s": N / (fwd_ms / 1e3),
+        "fwd_ms": fwd_ms,
+        "fp32_plain_fwd_cells_per_s": N / (fwd32_ms / 1e3),
+        "fp32_plain": {"fwd_ms": fwd32_ms, "vcycles": info32["solver_steps"],
+                       "residual_rel": info32["residual_rel"],
+                       "max_abs_sdf_diff_vs_mixed": fp32_vs_mixed},
+        "points_per_s": NPTS / (ms_per_step / 1e3),
+        "solver": {"steps": info["solver_steps"], "residual_rel": info["residual_rel"],
+                   "bwd_steps": info_t["backward_steps"], "bwd_residual_rel": info_t["backward_residual_rel"]},
+        "triangles": info["n_triangles"],
+        "stage_ms": stages,
+        "e2e": {"value": N / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": None,
+        "roofline": roof,
+        "clocks": clocks.summary(),
+    }
+    out["gpu_launches"] = count_launches_estimate()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_nodes)
+    if rank == 0:
+        print(json.dumps(out))
+    rec.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def count_launches_estimate():
+    """Kernel launches of one step of this build (counted from the launch sequence)."""
+    return None
+
+
+# Algorithmic bytes per cell (minimal traffic of each stage, see the design notes)
+ALG_BYTES = {
+    "splat": 4.0,          # write b
+    "normals": 16.0,       # read phi, write 3 normal planes
+    "query": 0.0,
+}
+
+
+def roofline(dom, stages, info, hbm, peak_kind):
+    N = RES ** 3
+    ms = stages[dom]
+    if dom in ("solve", "bwd_solve"):
+        # per refinement step: FP64 residual (read chi64 8 + b 4, write r 4), correction
+        # update (read e 4 + chi64 8, write chi64 8) and per V-cycle on the fine grid
+        # 2+2 RB sweeps (read x, b + write x: 12 B each) + restriction read (8 B) +
+        # prolongation (read 4 + write 4)
+        steps = max(info["solver_steps"], 1)
+        per_step = 16 + 20 + 2 * (4 * 12 + 8 + 8) * 8 / 7
+        alg = N * per_step * steps
+        return {"bound": "hbm", "kernel": f"{dom} (multigrid + FP64 refinement)",
+                "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": alg / (ms / 1e3) / 1e9 / hbm, "traffic": None,
+                "peak_kind": peak_kind, "alg_bytes_per_launch": alg}
+    if dom == "sdf":
+        return {"bound": "alu", "kernel": "sdf (exact nearest-triangle search)", "achieved": None,
+                "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None, "ms": ms}
+    alg = N * ALG_BYTES.get(dom, 4.0)
+    return {"bound": "hbm", "kernel": dom, "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm,
+            "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / hbm, "traffic": None,
+            "peak_kind": peak_kind}
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_step(p, n, q, g, node_sample: int, rng):
+    """One step of the oracle on the bench workload, with the per-node distance
+    search and the query stages on a random sample; returns (estimated seconds
+    for the full step, detail dict)."""
+    from oracle import divergence as D
+    from oracle import grid as OG
+    from oracle import iso as OI
+    from oracle import mc as OM
+    from oracle import pipeline as OP
+    from oracle import poisson as OPo
+    from oracle import splat as OS
+    N = RES ** 3
+    t = {}
+    t0 = time.perf_counter()
+    lo = OG.grid_lo(BBOX)
+    h = OG.grid_spacing(BBOX, RES)
+    pp = p.astype(np.float64)
+    nn = n.astype(np.float64)
+    bins, fin, _ = OG.bin_points(pp, BBOX, RES)
+    V = OS.splat(pp, nn, bins, fin, lo, h, RES)
+    b = D.divergence(V)
+    t["splat_div"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    chi = OPo.solve(b)
+    t["solve"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    c = OI.isovalue(chi, pp, fin, lo, h, RES)
+    mesh = OM.marching_cubes(chi, c, lo, h)
+    t["iso_mc"] = time.perf_counter() - t0
+    rec = OP.Reconstruction(res=RES, h=h, lo=lo, points=pp, normals_in=nn, bins=bins, finite=fin,
+                            status=0, V=V, b=b, chi=chi, c=c, mesh=mesh)
+    # distance + sign on sampled nodes, extrapolated to all N nodes
+    lin = rng.choice(N, node_sample, replace=False)
+    t0 = time.perf_counter()
+    OP.sdf_at(rec, lin)
+    t["sdf_sample"] = time.perf_counter() - t0
+    t["sdf_est"] = t["sdf_sample"] * N / node_sample
+    # stencil normals cost ~ one more distance per node in the oracle's own form: counted as 0
+    # query + adjoints: adjoint solve (full), splat adjoint (all points), iso adjoint (all points)
+    t0 = time.perf_counter()
+    lam = OPo.solve(chi)          # same operator and cost as the adjoint solve of dL/dchi
+    t["adj_solve"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dV = D.divergence_adjoint(lam)
+    OS.splat_adjoint(pp, nn, bins, fin, lo, h, RES, dV)
+    t["splat_adjoint"] = time.perf_counter() - t0
+    # trilinear query at the 1M points (vectorised, measured on a tenth, scaled)
+    qs = q[: len(q) // 10].astype(np.float64)
+    t0 = time.perf_counter()
+    OI.trilinear(qs, lo, h, RES)
+    t["query_est"] = (time.perf_counter() - t0) * 10
+    total = (t["splat_div"] + t["solve"] + t["iso_mc"] + t["sdf_est"] + t["adj_solve"]
+             + t["splat_adjoint"] + t["query_est"])
+    return total, t
+
+
+def cpu_baseline(node_sample: int):
+    p, n, q, g = workload()
+    rng = np.random.default_rng(7)
+    total, t = oracle_step(p, n, q, g, node_sample, rng)
+    cores = os.cpu_count()
+    return {"value": RES ** 3 / total, "unit": "cells/s", "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle on the same step: splat, divergence, DCT solve, iso-value, "
+                       f"marching cubes, adjoint solve and splat adjoint on the full 256^3 problem; "
+                       f"exact distance on {node_sample} random nodes scaled to all 16.8M; query "
+                       f"interpolation on 100k of the 1M points scaled; est. step {total:.1f} s"),
+            "stage_s": t}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    p, n, q, g = workload()
+    rng = np.random.default_rng(11)
+    times = []
+    for k in range(args.warmup + args.steps):
+        total, t = oracle_step(p, n, q, g, args.cpu_sample_nodes, rng)
+        if k >= args.warmup:
+            times.append(total)
+    ms = 1e3 * float(np.mean(times))
+    value = RES ** 3 / (ms / 1e3)
+    cores = os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "SH body (degree<=8) 200k points, 256^3 grid, 1M queries, "
+                                  "forward + query + adjoint", "res": RES, "points": NPTS, "queries": NQ},
+           "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                            "sample": f"per step: full global stages, distance on "
+                                      f"{args.cpu_sample_nodes} nodes scaled to 256^3"},
+           "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--stage-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample-nodes", type=int, default=3000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

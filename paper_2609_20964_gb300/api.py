@@ -1,0 +1,169 @@
+"""Torch-facing wrapper of the C ABI: tensors in, tensors out, the caller's
+current CUDA stream.  PyTorch only provides device memory and streams; all
+arithmetic runs in libwgeo.so."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor | None, name: str, shape_last=None):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape_last is not None and (t.dim() < 1 or t.shape[-1] != shape_last):
+        raise ValueError(f"{name} must have last dimension {shape_last}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _bbox(bbox) -> C.Array:
+    b = np.asarray(bbox, dtype=np.float32).reshape(6)
+    return (C.c_float * 6)(*b.tolist())
+
+
+class Reconstructor:
+    """One library handle: workspace for grids up to max_res^3 and clouds of up
+    to max_points points, plus the state of its last forward."""
+
+    def __init__(self, max_res: int, max_points: int, device=None, **options):
+        self.lib = L.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.opt = L.default_options(**options)
+        self.max_res = max_res
+        self.max_points = max_points
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.wgeo_create(C.byref(h), max_res, max_points, C.byref(self.opt)),
+                    "wgeo_create")
+        self.h = h
+        self.res = None
+        self.n = 0
+
+    @staticmethod
+    def footprint(max_res: int, max_points: int, **options) -> int:
+        return L.footprint_bytes(max_res, max_points, L.default_options(**options))
+
+    def close(self):
+        if self.h:
+            self.lib.wgeo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reconstruct(self, points: torch.Tensor, normals: torch.Tensor, bbox, res: int,
+                    with_sdf: bool = True, with_normals: bool = True, sdf_out=None, nrm_out=None,
+                    stream=None):
+        n = int(points.shape[0])
+        if normals.shape[0] != n:
+            raise ValueError("points and normals differ in length")
+        if with_sdf and sdf_out is None:
+            sdf_out = torch.empty((res, res, res), device=self.device, dtype=torch.float32)
+        if with_normals and nrm_out is None:
+            nrm_out = torch.empty((3, res, res, res), device=self.device, dtype=torch.float32)
+        rc = self.lib.wgeo_reconstruct(self.h, _dev(points, "points", 3), _dev(normals, "normals", 3),
+                                       n, _bbox(bbox), res, _dev(sdf_out, "sdf_out"),
+                                       _dev(nrm_out, "nrm_out"), C.c_void_p(_stream(stream)))
+        L.check(rc, "wgeo_reconstruct")
+        self.res = res
+        self.n = n
+        return sdf_out, nrm_out
+
+    def query(self, q: torch.Tensor, with_normals: bool = True, stream=None):
+        m = int(q.shape[0])
+        sdf_q = torch.empty((m,), device=self.device, dtype=torch.float32)
+        nrm_q = torch.empty((m, 3), device=self.device, dtype=torch.float32) if with_normals else None
+        rc = self.lib.wgeo_query(self.h, _dev(q, "q", 3), m, _dev(sdf_q, "sdf_q"),
+                                 _dev(nrm_q, "nrm_q"), C.c_void_p(_stream(stream)))
+        L.check(rc, "wgeo_query")
+        return sdf_q, nrm_q
+
+    def backward(self, d_sdf_grid=None, d_nrm_grid=None, q=None, d_sdf_q=None, d_nrm_q=None,
+                 want_dq: bool = False, stream=None):
+        m = int(q.shape[0]) if q is not None else 0
+        d_points = torch.empty((self.n, 3), device=self.device, dtype=torch.float32)
+        d_normals = torch.empty((self.n, 3), device=self.device, dtype=torch.float32)
+        d_q = torch.empty((m, 3), device=self.device, dtype=torch.float32) if (want_dq and m) else None
+        rc = self.lib.wgeo_backward(self.h, _dev(d_sdf_grid, "d_sdf_grid"), _dev(d_nrm_grid, "d_nrm_grid"),
+                                    _dev(q, "q"), _dev(d_sdf_q, "d_sdf_q"), _dev(d_nrm_q, "d_nrm_q"), m,
+                                    _dev(d_points, "d_points"), _dev(d_normals, "d_normals"),
+                                    _dev(d_q, "d_q"), C.c_void_p(_stream(stream)))
+        L.check(rc, "wgeo_backward")
+        return d_points, d_normals, d_q
+
+    def info(self) -> dict:
+        inf = L.Info()
+        L.check(self.lib.wgeo_get_info(self.h, C.byref(inf)), "wgeo_get_info")
+        return {k: getattr(inf, k) for k, _ in L.Info._fields_ if k != "reserved"}
+
+    def field(self, which: str, stream=None) -> torch.Tensor:
+        idx = {"b": 0, "chi": 1, "phi": 2}[which]
+        out = torch.empty((self.res, self.res, self.res), device=self.device, dtype=torch.float32)
+        r = self.lib.wgeo_get_field(self.h, idx, C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream)))
+        if r < 0:
+            L.check(-r, "wgeo_get_field")
+        return out
+
+    def stage_times(self, reset: bool = True) -> dict:
+        """{stage: (total ms, timed calls)} accumulated since the last reset."""
+        ms = np.zeros(len(L.STAGES), dtype=np.float64)
+        cnt = np.zeros(len(L.STAGES), dtype=np.int64)
+        L.check(self.lib.wgeo_stage_times(self.h, ms.ctypes.data, cnt.ctypes.data, int(reset)),
+                "wgeo_stage_times")
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(L.STAGES)}
+
+    def bins(self, stream=None) -> torch.Tensor:
+        out = torch.empty((self.n, 3), device=self.device, dtype=torch.int32)
+        r = self.lib.wgeo_get_bins(self.h, C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream)))
+        if r < 0:
+            L.check(-r, "wgeo_get_bins")
+        return out
+
+    def mesh(self):
+        T = self.lib.wgeo_get_mesh(self.h, None, None, 0)
+        if T < 0:
+            L.check(-T, "wgeo_get_mesh")
+        verts = np.zeros((T, 3, 3), dtype=np.float32)
+        gid = np.zeros((T, 3), dtype=np.int64)
+        if T:
+            self.lib.wgeo_get_mesh(self.h, verts.ctypes.data, gid.ctypes.data, T)
+        return verts, gid
+
+
+def sh_surface(theta: torch.Tensor, dirs: torch.Tensor, base: float = 0.3, centre=None, stream=None):
+    """Points and normals of the SH star body at fixed directions (CUDA)."""
+    lib = L.load()
+    n = int(dirs.shape[0])
+    if centre is None:
+        centre = torch.full((3,), 0.5, device=dirs.device, dtype=torch.float32)
+    pts = torch.empty((n, 3), device=dirs.device, dtype=torch.float32)
+    nrm = torch.empty((n, 3), device=dirs.device, dtype=torch.float32)
+    L.check(lib.wgeo_sh_surface(_dev(theta, "theta"), int(theta.numel()), _dev(dirs, "dirs", 3), n,
+                                float(base), _dev(centre, "centre"), _dev(pts, "pts"), _dev(nrm, "nrm"),
+                                C.c_void_p(_stream(stream))), "wgeo_sh_surface")
+    return pts, nrm
+
+
+def sh_surface_backward(recon: Reconstructor, theta, dirs, d_points, d_normals, base: float = 0.3,
+                        stream=None):
+    lib = L.load()
+    dth = torch.empty_like(theta)
+    L.check(lib.wgeo_sh_surface_backward(recon.h, _dev(theta, "theta"), int(theta.numel()),
+                                         _dev(dirs, "dirs", 3), int(dirs.shape[0]), float(base),
+                                         _dev(d_points, "d_points", 3), _dev(d_normals, "d_normals", 3),
+                                         _dev(dth, "d_theta"), C.c_void_p(_stream(stream))),
+            "wgeo_sh_surface_backward")
+    return dth

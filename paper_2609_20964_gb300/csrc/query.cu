@@ -1,0 +1,517 @@
+// Queries of the grid SDF and the adjoint chain (Sec. 2.5, Eqs. 35-39).
+//
+// Query: trilinear phi and the normalised trilinear stencil normal at q, with
+// q clamped into the node hull [lo + h/2, lo + (res - 1/2) h] per axis.
+//
+// Backward, for the discrete choices of the last forward:
+//   1. dphi: grid seed + scatter of the query adjoints; normal seeds pass
+//      through n = g / |g| (dg = (I - n n^T) dn / |g|) and the transpose of
+//      the gradient stencil.
+//   2. distance: phi_o = s_o |p_o - y_o| with y_o = sum_v beta_v P_v on the
+//      closest triangle -> dP_v = -s_o dphi_o beta_v (p_o - y_o)/|p_o - y_o|;
+//      marching cubes: P = node + eta h e_axis, eta = (c - chi1)/(chi2 - chi1)
+//      -> d chi1, d chi2 and dc, fused in the same pass.
+//   3. iso-value: c = mean_i chi_hat(x_i) -> dchi at the 8 corners, dx_i.
+//   4. adjoint solve L lambda = dchi (L symmetric, Eq. 38), FP64-refined.
+//   5. divergence transpose dV = D^T lambda and the splat adjoint per point:
+//      dn_i = sum_o alpha_oi dV_o, dx_i += sum_o (n_i . dV_o) d alpha_oi / dx_i.
+// Scatters use FP64 atomics into FP64 grids.
+#include "wgeo_internal.cuh"
+
+namespace wgeo {
+
+namespace {
+
+struct QParams {
+  double lo[3];
+  double h;
+  int res;
+};
+
+__device__ __forceinline__ int64_t lin3(int i, int j, int k, int n) {
+  return ((int64_t)k * n + j) * n + i;
+}
+
+// Trilinear cell and weights of a query; dw[c][a] = d w_c / d q_a (0 on clamped axes).
+__device__ __forceinline__ void trilinear(const float* q, const QParams& g, int i0[3], float w[8],
+                                          float dw[8][3]) {
+  float t[3], dt[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double u = ((double)q[a] - g.lo[a]) / g.h - 0.5;
+    const bool cl = (u < 0.0) || (u > (double)(g.res - 1));
+    u = fmin(fmax(u, 0.0), (double)(g.res - 1));
+    int f = (int)floor(u);
+    f = min(f, g.res - 2);
+    i0[a] = f;
+    t[a] = (float)(u - f);
+    dt[a] = cl ? 0.f : (float)(1.0 / g.h);
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+    const float fx = bx ? t[0] : 1.f - t[0], fy = by ? t[1] : 1.f - t[1], fz = bz ? t[2] : 1.f - t[2];
+    const float gx = bx ? dt[0] : -dt[0], gy = by ? dt[1] : -dt[1], gz = bz ? dt[2] : -dt[2];
+    w[c] = fx * fy * fz;
+    dw[c][0] = gx * fy * fz;
+    dw[c][1] = fx * gy * fz;
+    dw[c][2] = fx * fy * gz;
+  }
+}
+
+// Stencil gradient of phi at node (i,j,k) (central inside, one-sided 2nd order at the ends).
+__device__ __forceinline__ void node_grad(const float* __restrict__ phi, int i, int j, int k, int n,
+                                          float inv2h, float g[3]) {
+  const int idx[3] = {i, j, k};
+  const int64_t t = lin3(i, j, k, n);
+  const int64_t st[3] = {1, n, (int64_t)n * n};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float d;
+    if (idx[a] == 0)
+      d = -3.f * phi[t] + 4.f * phi[t + st[a]] - phi[t + 2 * st[a]];
+    else if (idx[a] == n - 1)
+      d = 3.f * phi[t] - 4.f * phi[t - st[a]] + phi[t - 2 * st[a]];
+    else
+      d = phi[t + st[a]] - phi[t - st[a]];
+    g[a] = d * inv2h;
+  }
+}
+
+// Scatter dL/dg at node (i,j,k) through the transpose of the gradient stencil.
+__device__ __forceinline__ void scatter_grad_adjoint(double* __restrict__ dphi, int i, int j, int k,
+                                                     int n, double inv2h, const double dg[3]) {
+  const int idx[3] = {i, j, k};
+  const int64_t t = lin3(i, j, k, n);
+  const int64_t st[3] = {1, n, (int64_t)n * n};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double v = dg[a] * inv2h;
+    if (v == 0.0) continue;
+    if (idx[a] == 0) {
+      atomicAdd(&dphi[t], -3.0 * v);
+      atomicAdd(&dphi[t + st[a]], 4.0 * v);
+      atomicAdd(&dphi[t + 2 * st[a]], -v);
+    } else if (idx[a] == n - 1) {
+      atomicAdd(&dphi[t], 3.0 * v);
+      atomicAdd(&dphi[t - st[a]], -4.0 * v);
+      atomicAdd(&dphi[t - 2 * st[a]], v);
+    } else {
+      atomicAdd(&dphi[t + st[a]], v);
+      atomicAdd(&dphi[t - st[a]], -v);
+    }
+  }
+}
+
+__global__ void query_kernel(const float* __restrict__ q, int64_t m, QParams g,
+                             const float* __restrict__ phi, float* __restrict__ sdf_q,
+                             float* __restrict__ nrm_q) {
+  const int n = g.res;
+  const float inv2h = (float)(0.5 / g.h);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float qq[3] = {q[3 * i], q[3 * i + 1], q[3 * i + 2]};
+    int i0[3];
+    float w[8], dw[8][3];
+    trilinear(qq, g, i0, w, dw);
+    float s = 0.f;
+    float mv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int x = i0[0] + (c & 1), y = i0[1] + ((c >> 1) & 1), z = i0[2] + (c >> 2);
+      s += w[c] * phi[lin3(x, y, z, n)];
+      if (nrm_q) {
+        float gr[3];
+        node_grad(phi, x, y, z, n, inv2h, gr);
+        const float m2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+        const float inv = (isfinite(m2) && m2 > 0.f) ? rsqrtf(m2) : 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) mv[a] += w[c] * gr[a] * inv;
+      }
+    }
+    sdf_q[i] = s;
+    if (nrm_q) {
+      const float m2 = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
+      const float inv = (m2 > 0.f) ? rsqrtf(m2) : 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) nrm_q[3 * i + a] = mv[a] * inv;
+    }
+  }
+}
+
+__global__ void query_adjoint_kernel(const float* __restrict__ q, int64_t m, QParams g,
+                                     const float* __restrict__ phi, const float* __restrict__ dsq,
+                                     const float* __restrict__ dnq, double* __restrict__ dphi,
+                                     float* __restrict__ dq) {
+  const int n = g.res;
+  const float inv2h = (float)(0.5 / g.h);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float qq[3] = {q[3 * i], q[3 * i + 1], q[3 * i + 2]};
+    int i0[3];
+    float w[8], dw[8][3];
+    trilinear(qq, g, i0, w, dw);
+    float dqa[3] = {0.f, 0.f, 0.f};
+    if (dsq) {
+      const float gs = dsq[i];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t o = lin3(i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + (c >> 2), n);
+        if (gs != 0.f) atomicAdd(&dphi[o], (double)(w[c] * gs));
+        const float pv = phi[o];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dqa[a] += dw[c][a] * pv * gs;
+      }
+    }
+    if (dnq) {
+      // recompute the corner normals and the interpolated m
+      float nc[8][3], gm[8];
+      float mv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float gr[3];
+        node_grad(phi, i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + (c >> 2), n, inv2h, gr);
+        const float m2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+        const bool ok = isfinite(m2) && m2 > 0.f;
+        gm[c] = ok ? sqrtf(m2) : 0.f;
+        const float inv = ok ? 1.f / gm[c] : 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          nc[c][a] = gr[a] * inv;
+          mv[a] += w[c] * nc[c][a];
+        }
+      }
+      const float mm = sqrtf(mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2]);
+      if (mm > 0.f) {
+        const float nq[3] = {mv[0] / mm, mv[1] / mm, mv[2] / mm};
+        const float gq[3] = {dnq[3 * i], dnq[3 * i + 1], dnq[3 * i + 2]};
+        const float pr = nq[0] * gq[0] + nq[1] * gq[1] + nq[2] * gq[2];
+        const float dm[3] = {(gq[0] - nq[0] * pr) / mm, (gq[1] - nq[1] * pr) / mm,
+                             (gq[2] - nq[2] * pr) / mm};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float nd = nc[c][0] * dm[0] + nc[c][1] * dm[1] + nc[c][2] * dm[2];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) dqa[a] += dw[c][a] * nd;
+          if (gm[c] > 0.f) {
+            // dn_c = w_c dm ; dg_c = (I - n n^T) dn_c / |g_c|
+            const float wd[3] = {w[c] * dm[0], w[c] * dm[1], w[c] * dm[2]};
+            const float pn = nc[c][0] * wd[0] + nc[c][1] * wd[1] + nc[c][2] * wd[2];
+            const double dg[3] = {(double)((wd[0] - nc[c][0] * pn) / gm[c]),
+                                  (double)((wd[1] - nc[c][1] * pn) / gm[c]),
+                                  (double)((wd[2] - nc[c][2] * pn) / gm[c])};
+            scatter_grad_adjoint(dphi, i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + (c >> 2), n,
+                                 0.5 / g.h, dg);
+          }
+        }
+      }
+    }
+    if (dq) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dq[3 * i + a] = dqa[a];
+    }
+  }
+}
+
+__global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __restrict__ dng,
+                                 const float* __restrict__ phi, QParams g, double* __restrict__ dphi) {
+  const int n = g.res;
+  const int64_t N = (int64_t)n * n * n;
+  const float inv2h = (float)(0.5 / g.h);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (dsg) {
+      const float v = dsg[t];
+      if (v != 0.f) atomicAdd(&dphi[t], (double)v);
+    }
+    if (dng) {
+      const float dn[3] = {dng[t], dng[N + t], dng[2 * N + t]};
+      if (dn[0] == 0.f && dn[1] == 0.f && dn[2] == 0.f) continue;
+      const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
+      float gr[3];
+      node_grad(phi, i, j, k, n, inv2h, gr);
+      const float m2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+      if (!(isfinite(m2) && m2 > 0.f)) continue;
+      const float gm = sqrtf(m2);
+      const float nv[3] = {gr[0] / gm, gr[1] / gm, gr[2] / gm};
+      const float pn = nv[0] * dn[0] + nv[1] * dn[1] + nv[2] * dn[2];
+      const double dg[3] = {(double)((dn[0] - nv[0] * pn) / gm), (double)((dn[1] - nv[1] * pn) / gm),
+                            (double)((dn[2] - nv[2] * pn) / gm)};
+      scatter_grad_adjoint(dphi, i, j, k, n, 0.5 / g.h, dg);
+    }
+  }
+}
+
+// Distance + marching-cubes adjoint, one thread per node with a nonzero dphi.
+__global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int* __restrict__ ctri,
+                                      const float* __restrict__ chi, const DevState* __restrict__ st,
+                                      const Tri* __restrict__ tris, QParams g,
+                                      double* __restrict__ dchi, double* __restrict__ partials) {
+  __shared__ double red[32];
+  const int n = g.res;
+  const int64_t N = (int64_t)n * n * n;
+  const double c = st->c;
+  double dcacc = 0.0;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const double gphi = dphi[o];
+    if (gphi == 0.0) continue;
+    const int t = ctri[o];
+    if (t < 0) continue;
+    const int i = (int)(o % n), j = (int)((o / n) % n), k = (int)(o / ((int64_t)n * n));
+    const float3 p = make_float3((float)(g.lo[0] + (i + 0.5) * g.h), (float)(g.lo[1] + (j + 0.5) * g.h),
+                                 (float)(g.lo[2] + (k + 0.5) * g.h));
+    const Tri tr = tris[t];
+    float bw[3];
+    const float d2 = tri_closest(p, f3(tr.a), f3(tr.b), f3(tr.c), &bw[0], &bw[1], &bw[2]);
+    if (!(d2 > 0.f)) continue;
+    const float3 y = make_float3(bw[0] * tr.a.x + bw[1] * tr.b.x + bw[2] * tr.c.x,
+                                 bw[0] * tr.a.y + bw[1] * tr.b.y + bw[2] * tr.c.y,
+                                 bw[0] * tr.a.z + bw[1] * tr.b.z + bw[2] * tr.c.z);
+    const double d = sqrt((double)d2);
+    const double sgn = ((double)chi[o] >= c) ? 1.0 : -1.0;
+    const double u[3] = {(p.x - y.x) / d, (p.y - y.y) / d, (p.z - y.z) / d};
+    const float4 vv[3] = {tr.a, tr.b, tr.c};
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      if (bw[v] == 0.f) continue;
+      const int gid = __float_as_int(vv[v].w);
+      const int ax = gid % 3;
+      const int64_t pl = gid / 3;
+      const int64_t stv = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+      const double c1 = (double)chi[pl], c2 = (double)chi[pl + stv];
+      const double den = c2 - c1;
+      const double eta = (c - c1) / den;
+      // dL/dP_v[ax] = -s dphi beta_v u[ax];  dP/deta = h e_ax
+      const double deta = -sgn * gphi * (double)bw[v] * u[ax] * g.h;
+      atomicAdd(&dchi[pl], deta * (eta - 1.0) / den);
+      atomicAdd(&dchi[pl + stv], -deta * eta / den);
+      dcacc += deta / den;
+    }
+  }
+  dcacc = block_sum<256>(dcacc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = dcacc;
+}
+
+__global__ void dc_finalize_kernel(const double* __restrict__ partials, int nblocks, DevState* st) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += partials[i];
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) st->dc = s;
+}
+
+// Iso-value adjoint: dchi += dc/N_p * w at the 8 corners; d_points = dc/N_p * sum dw chi.
+__global__ void iso_adjoint_kernel(const int* __restrict__ pcell, const float4* __restrict__ pfrac,
+                                   int64_t np, const float* __restrict__ chi,
+                                   const DevState* __restrict__ st, QParams g,
+                                   double* __restrict__ dchi, float* __restrict__ dpts) {
+  const int n = g.res;
+  const double scale = st->npts > 0 ? st->dc / (double)st->npts : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int pc = pcell[i];
+    if (pc < 0 || scale == 0.0) {
+      dpts[3 * i] = 0.f;
+      dpts[3 * i + 1] = 0.f;
+      dpts[3 * i + 2] = 0.f;
+      continue;
+    }
+    const float4 fr = pfrac[i];
+    const int b[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
+    const float f[3] = {fr.x, fr.y, fr.z};
+    int i0[3];
+    double t[3], dt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double u = (double)b[a] + (double)f[a] - 0.5;
+      const bool cl = (u < 0.0) || (u > (double)(n - 1));
+      u = fmin(fmax(u, 0.0), (double)(n - 1));
+      int fl = (int)floor(u);
+      fl = min(fl, n - 2);
+      i0[a] = fl;
+      t[a] = u - fl;
+      dt[a] = cl ? 0.0 : 1.0 / g.h;
+    }
+    double dx[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+      const double fx = bx ? t[0] : 1 - t[0], fy = by ? t[1] : 1 - t[1], fz = bz ? t[2] : 1 - t[2];
+      const double gx = bx ? dt[0] : -dt[0], gy = by ? dt[1] : -dt[1], gz = bz ? dt[2] : -dt[2];
+      const int64_t o = lin3(i0[0] + bx, i0[1] + by, i0[2] + bz, n);
+      atomicAdd(&dchi[o], scale * fx * fy * fz);
+      const double cv = (double)chi[o];
+      dx[0] += gx * fy * fz * cv;
+      dx[1] += fx * gy * fz * cv;
+      dx[2] += fx * fy * gz * cv;
+    }
+    dpts[3 * i] = (float)(scale * dx[0]);
+    dpts[3 * i + 1] = (float)(scale * dx[1]);
+    dpts[3 * i + 2] = (float)(scale * dx[2]);
+  }
+}
+
+// dV_o = D^T lambda at cell (x,y,z): 1/2 (lambda_o - lambda_{o+e}) on interior
+// faces o+1/2 plus 1/2 (lambda_{o-e} - lambda_o) on interior faces o-1/2.
+__device__ __forceinline__ void dV_at(const double* __restrict__ lam, int x, int y, int z, int n,
+                                      double dv[3]) {
+  const int idx[3] = {x, y, z};
+  const int64_t o = lin3(x, y, z, n);
+  const int64_t st[3] = {1, n, (int64_t)n * n};
+  const double lo = lam[o];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double v = 0.0;
+    if (idx[a] + 1 < n) v += 0.5 * (lo - lam[o + st[a]]);
+    if (idx[a] - 1 >= 0) v += 0.5 * (lam[o - st[a]] - lo);
+    dv[a] = v;
+  }
+}
+
+__global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4* __restrict__ pfrac,
+                                     const float4* __restrict__ pnrm, int64_t np,
+                                     const double* __restrict__ lam, QParams g,
+                                     float* __restrict__ dpts, float* __restrict__ dnrm) {
+  const int n = g.res;
+  const double inv2h = 0.5 / g.h;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int pc = pcell[i];
+    if (pc < 0) {
+      dnrm[3 * i] = 0.f;
+      dnrm[3 * i + 1] = 0.f;
+      dnrm[3 * i + 2] = 0.f;
+      continue;
+    }
+    const float4 fr = pfrac[i];
+    const float4 nv = pnrm[i];
+    const int b[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
+    const double f[3] = {fr.x, fr.y, fr.z};
+    const double nn[3] = {nv.x, nv.y, nv.z};
+    double fac[3][3], dfac[3][3];
+    bool ing[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double s = f[a] - 0.5 - (double)(d - 1);   // (x - c_o) / h
+        const double t = fabs(s);
+        const double arg = 1.0 - 0.5 * t;
+        fac[a][d] = 0.5 * fmax(0.0, arg);
+        dfac[a][d] = (arg > 0.0) ? -0.5 * ((s > 0.0) - (s < 0.0)) * inv2h : 0.0;
+        const int o = b[a] + d - 1;
+        ing[a][d] = (o >= 0) && (o < n);
+      }
+    }
+    double S = 0.0, dS[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < 27; ++q) {
+      const int dx = q % 3, dy = (q / 3) % 3, dz = q / 9;
+      if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
+      if (q == 13) {
+        S += 0.5;
+        continue;
+      }
+      S += fac[0][dx] * fac[1][dy] * fac[2][dz];
+      dS[0] += dfac[0][dx] * fac[1][dy] * fac[2][dz];
+      dS[1] += fac[0][dx] * dfac[1][dy] * fac[2][dz];
+      dS[2] += fac[0][dx] * fac[1][dy] * dfac[2][dz];
+    }
+    double gdn[3] = {0.0, 0.0, 0.0}, gdx[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < 27; ++q) {
+      const int dx = q % 3, dy = (q / 3) % 3, dz = q / 9;
+      if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
+      double dv[3];
+      dV_at(lam, b[0] + dx - 1, b[1] + dy - 1, b[2] + dz - 1, n, dv);
+      double a, da[3];
+      if (q == 13) {
+        a = 0.5;
+        da[0] = da[1] = da[2] = 0.0;
+      } else {
+        a = fac[0][dx] * fac[1][dy] * fac[2][dz];
+        da[0] = dfac[0][dx] * fac[1][dy] * fac[2][dz];
+        da[1] = fac[0][dx] * dfac[1][dy] * fac[2][dz];
+        da[2] = fac[0][dx] * fac[1][dy] * dfac[2][dz];
+      }
+      const double alpha = a / S;
+      const double wdot = nn[0] * dv[0] + nn[1] * dv[1] + nn[2] * dv[2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        gdn[c] += alpha * dv[c];
+        gdx[c] += wdot * (da[c] - alpha * dS[c]) / S;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dnrm[3 * i + c] = (float)gdn[c];
+      dpts[3 * i + c] = dpts[3 * i + c] + (float)gdx[c];
+    }
+  }
+}
+
+QParams qparams(const wgeo_handle* h) {
+  QParams g;
+  for (int a = 0; a < 3; ++a) g.lo[a] = h->lo[a];
+  g.h = h->h;
+  g.res = h->res;
+  return g;
+}
+
+}  // namespace
+
+int launch_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s) {
+  if (m == 0) return WGEO_OK;
+  query_kernel<<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, qparams(h), h->phi, sdf_q, nrm_q);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
+                    const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,
+                    float* d_normals, float* d_q, cudaStream_t s) {
+  const int res = h->res;
+  const int64_t N = (int64_t)res * res * res;
+  const QParams g = qparams(h);
+  int slot = stage_begin(h, kStBwdSeed, s);
+  WGEO_CUDA_TRY(cudaMemsetAsync(h->dphi64, 0, sizeof(double) * N, s));
+  WGEO_CUDA_TRY(cudaMemsetAsync(h->dchi64, 0, sizeof(double) * N, s));
+  if (d_sdf_grid || d_nrm_grid) {
+    grid_seed_kernel<<<grid_blocks(N, 256, 152 * 32), 256, 0, s>>>(d_sdf_grid, d_nrm_grid, h->phi, g,
+                                                                   h->dphi64);
+    WGEO_LAUNCH_CHECK();
+  }
+  if (m > 0 && q && (d_sdf_q || d_nrm_q || d_q)) {
+    query_adjoint_kernel<<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, g, h->phi, d_sdf_q, d_nrm_q,
+                                                                       h->dphi64, d_q);
+    WGEO_LAUNCH_CHECK();
+  }
+  stage_end(h, kStBwdSeed, slot, s);
+  slot = stage_begin(h, kStBwdSurf, s);
+  const int nb = grid_blocks(N, 256, kPartials);
+  sdf_mc_adjoint_kernel<<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, g,
+                                           h->dchi64, h->partials);
+  WGEO_LAUNCH_CHECK();
+  dc_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, nb, h->dstate);
+  WGEO_LAUNCH_CHECK();
+  if (h->npts > 0) {
+    iso_adjoint_kernel<<<grid_blocks(h->npts, 256, 152 * 32), 256, 0, s>>>(
+        h->pcell, h->pfrac, h->npts, h->chi32, h->dstate, g, h->dchi64, d_points);
+    WGEO_LAUNCH_CHECK();
+  }
+  stage_end(h, kStBwdSurf, slot, s);
+  slot = stage_begin(h, kStBwdSolve, s);
+  WGEO_CUDA_TRY(cudaMemsetAsync(h->lam64, 0, sizeof(double) * N, s));
+  int rc = launch_solve(h, res, 1, s);
+  if (rc) return rc;
+  stage_end(h, kStBwdSolve, slot, s);
+  slot = stage_begin(h, kStBwdSplat, s);
+  if (h->npts > 0) {
+    splat_adjoint_kernel<<<grid_blocks(h->npts, 128, 152 * 64), 128, 0, s>>>(
+        h->pcell, h->pfrac, h->pnrm, h->npts, h->lam64, g, d_points, d_normals);
+    WGEO_LAUNCH_CHECK();
+  }
+  stage_end(h, kStBwdSplat, slot, s);
+  return WGEO_OK;
+}
+
+}  // namespace wgeo

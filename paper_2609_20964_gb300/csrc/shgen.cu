@@ -1,0 +1,238 @@
+// Differentiable shape parameterisation (Sec. 2.5 last paragraph, Sec. 3.3):
+// a star body r(u) = base + sum_k theta_k Y_k(u) with orthonormal real
+// spherical harmonics (no Condon-Shortley phase, k = l*l + l + m), sampled at
+// fixed unit directions u_i:  x_i = centre + r(u_i) u_i and the outward normal
+// n_i = m_i / |m_i|, m_i = u_i - P_perp grad r / r.
+//
+// SH are evaluated in Cartesian form: Y_lm = sqrt(2) K_lm Q_l^m(z) Re/Im (x+iy)^m
+// (K_l0 Q_l^0 for m = 0) with Q_l^m the polynomial part of P_l^m, so the
+// Cartesian gradient of the polynomial extension has no pole singularity.
+//
+// The adjoint reduces sum_i over points per coefficient with warp shuffles,
+// per-warp shared slots and a fixed-order final pass (deterministic).
+#include <math.h>
+
+#include "wgeo_internal.cuh"
+
+namespace wgeo {
+
+namespace {
+
+constexpr int kLmax = 8;
+constexpr int kK = (kLmax + 1) * (kLmax + 1);
+constexpr int kShThreads = 128;
+constexpr int kShBlocks = 256;
+
+struct ShConsts {
+  float K[kLmax + 1][kLmax + 1];  // K_lm
+  int lmax;
+};
+
+// Y_k and the Cartesian gradient of the polynomial extension, for all k.
+__device__ __forceinline__ void eval_sh(const float u[3], const ShConsts& cs, float* Y, float (*dY)[3]) {
+  const float x = u[0], y = u[1], z = u[2];
+  float C[kLmax + 1], S[kLmax + 1];
+  C[0] = 1.f;
+  S[0] = 0.f;
+  for (int m = 1; m <= cs.lmax; ++m) {
+    C[m] = x * C[m - 1] - y * S[m - 1];
+    S[m] = x * S[m - 1] + y * C[m - 1];
+  }
+  for (int m = 0; m <= cs.lmax; ++m) {
+    float dfact = 1.f;
+    for (int j = 1; j < 2 * m; j += 2) dfact *= (float)j;
+    float q2 = 0.f, dq2 = 0.f;          // Q_{l-2}
+    float q1 = dfact, dq1 = 0.f;        // Q_{l-1} (starts at l = m)
+    for (int l = m; l <= cs.lmax; ++l) {
+      float q, dq;
+      if (l == m) {
+        q = dfact;
+        dq = 0.f;
+      } else if (l == m + 1) {
+        q = (2 * m + 1) * z * q1;
+        dq = (2 * m + 1) * (q1 + z * dq1);
+      } else {
+        q = ((2 * l - 1) * z * q1 - (l + m - 1) * q2) / (float)(l - m);
+        dq = ((2 * l - 1) * (q1 + z * dq1) - (l + m - 1) * dq2) / (float)(l - m);
+      }
+      if (l > m) {
+        q2 = q1;
+        dq2 = dq1;
+        q1 = q;
+        dq1 = dq;
+      }
+      const float K = cs.K[l][m];
+      if (m == 0) {
+        const int k = l * l + l;
+        Y[k] = K * q;
+        dY[k][0] = 0.f;
+        dY[k][1] = 0.f;
+        dY[k][2] = K * dq;
+      } else {
+        const float s2 = 1.41421356237309515f * K;
+        const int kc = l * l + l + m, ks = l * l + l - m;
+        Y[kc] = s2 * q * C[m];
+        Y[ks] = s2 * q * S[m];
+        dY[kc][0] = s2 * q * m * C[m - 1];
+        dY[kc][1] = -s2 * q * m * S[m - 1];
+        dY[kc][2] = s2 * dq * C[m];
+        dY[ks][0] = s2 * q * m * S[m - 1];
+        dY[ks][1] = s2 * q * m * C[m - 1];
+        dY[ks][2] = s2 * dq * S[m];
+      }
+    }
+  }
+}
+
+struct Surf {
+  float r;
+  float gt[3];  // tangential gradient of r
+  float m[3];
+  float mn;     // |m|
+  float n[3];
+};
+
+__device__ __forceinline__ Surf surface_at(const float u[3], const float* __restrict__ theta, int K,
+                                           float base, const float* Y, const float (*dY)[3]) {
+  Surf s;
+  float r = base, g[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k < K; ++k) {
+    const float t = theta[k];
+    r += t * Y[k];
+    g[0] += t * dY[k][0];
+    g[1] += t * dY[k][1];
+    g[2] += t * dY[k][2];
+  }
+  const float gu = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+  for (int a = 0; a < 3; ++a) s.gt[a] = g[a] - gu * u[a];
+  for (int a = 0; a < 3; ++a) s.m[a] = u[a] - s.gt[a] / r;
+  s.mn = sqrtf(s.m[0] * s.m[0] + s.m[1] * s.m[1] + s.m[2] * s.m[2]);
+  for (int a = 0; a < 3; ++a) s.n[a] = s.m[a] / s.mn;
+  s.r = r;
+  return s;
+}
+
+__global__ void sh_surface_kernel(const float* __restrict__ theta, int K, ShConsts cs,
+                                  const float* __restrict__ dirs, int64_t n, float base,
+                                  const float* __restrict__ centre, float* __restrict__ pts,
+                                  float* __restrict__ nrm) {
+  float Y[kK], dY[kK][3];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float u[3] = {dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2]};
+    eval_sh(u, cs, Y, dY);
+    const Surf s = surface_at(u, theta, K, base, Y, dY);
+    for (int a = 0; a < 3; ++a) {
+      pts[3 * i + a] = centre[a] + s.r * u[a];
+      nrm[3 * i + a] = s.n[a];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kShThreads) sh_backward_kernel(
+    const float* __restrict__ theta, int K, ShConsts cs, const float* __restrict__ dirs, int64_t n,
+    float base, const float* __restrict__ dpts, const float* __restrict__ dnrm,
+    double* __restrict__ partials) {
+  __shared__ double acc[kK][kShThreads / 32];
+  for (int t = threadIdx.x; t < kK * (kShThreads / 32); t += blockDim.x) (&acc[0][0])[t] = 0.0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float Y[kK], dY[kK][3];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (n + stride - 1) / stride;
+  for (int64_t it = 0; it < iters; ++it) {
+    const int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool act = i < n;
+    float A = 0.f, B[3] = {0.f, 0.f, 0.f}, Cc = 0.f, u[3] = {0.f, 0.f, 1.f};
+    if (act) {
+      u[0] = dirs[3 * i];
+      u[1] = dirs[3 * i + 1];
+      u[2] = dirs[3 * i + 2];
+      eval_sh(u, cs, Y, dY);
+      const Surf s = surface_at(u, theta, K, base, Y, dY);
+      const float dp[3] = {dpts[3 * i], dpts[3 * i + 1], dpts[3 * i + 2]};
+      const float dn[3] = {dnrm[3 * i], dnrm[3 * i + 1], dnrm[3 * i + 2]};
+      A = dp[0] * u[0] + dp[1] * u[1] + dp[2] * u[2];
+      const float pr = s.n[0] * dn[0] + s.n[1] * dn[1] + s.n[2] * dn[2];
+      float dm[3];
+      for (int a = 0; a < 3; ++a) dm[a] = (dn[a] - s.n[a] * pr) / s.mn;
+      for (int a = 0; a < 3; ++a) B[a] = dm[a] / s.r;
+      Cc = (dm[0] * s.gt[0] + dm[1] * s.gt[1] + dm[2] * s.gt[2]) / (s.r * s.r);
+    }
+    const float uB = u[0] * B[0] + u[1] * B[1] + u[2] * B[2];
+    for (int k = 0; k < K; ++k) {
+      double v = 0.0;
+      if (act) {
+        const float dyb = dY[k][0] * B[0] + dY[k][1] * B[1] + dY[k][2] * B[2];
+        const float dyu = dY[k][0] * u[0] + dY[k][1] * u[1] + dY[k][2] * u[2];
+        v = (double)(Y[k] * (A + Cc)) - (double)(dyb - dyu * uB);
+      }
+      v = warp_sum(v);
+      if (lane == 0) acc[k][w] += v;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < kShThreads / 32; ++q) s += acc[k][q];
+    partials[(int64_t)blockIdx.x * K + k] = s;
+  }
+}
+
+__global__ void sh_finalize_kernel(const double* __restrict__ partials, int nblocks, int K,
+                                   float* __restrict__ dtheta) {
+  const int k = threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * K + k];
+  dtheta[k] = (float)s;
+}
+
+ShConsts make_consts(int K) {
+  ShConsts cs;
+  cs.lmax = (int)lround(sqrt((double)K)) - 1;
+  for (int l = 0; l <= kLmax; ++l)
+    for (int m = 0; m <= kLmax; ++m) {
+      if (m > l) {
+        cs.K[l][m] = 0.f;
+        continue;
+      }
+      double r = 1.0;
+      for (int j = l - m + 1; j <= l + m; ++j) r /= (double)j;   // (l-m)!/(l+m)!
+      cs.K[l][m] = (float)sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * r);
+    }
+  return cs;
+}
+
+}  // namespace
+
+int launch_sh_surface(const float* theta, int K, const float* dirs, int64_t n, float base,
+                      const float* centre, float* points, float* normals, cudaStream_t s) {
+  if (n == 0) return WGEO_OK;
+  sh_surface_kernel<<<grid_blocks(n, 128, 152 * 16), 128, 0, s>>>(theta, K, make_consts(K), dirs, n, base,
+                                                                 centre, points, normals);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+int launch_sh_backward(wgeo_handle* h, const float* theta, int K, const float* dirs, int64_t n,
+                       float base, const float* dpts, const float* dnrm, float* dtheta, cudaStream_t s) {
+  const int nb = (n == 0) ? 1 : grid_blocks(n, kShThreads, kShBlocks);
+  if (n == 0) {
+    WGEO_CUDA_TRY(cudaMemsetAsync(dtheta, 0, sizeof(float) * K, s));
+    return WGEO_OK;
+  }
+  sh_backward_kernel<<<nb, kShThreads, 0, s>>>(theta, K, make_consts(K), dirs, n, base, dpts, dnrm,
+                                               h->partials);
+  WGEO_LAUNCH_CHECK();
+  sh_finalize_kernel<<<1, 128, 0, s>>>(h->partials, nb, K, dtheta);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+int sh_valid_K(int K) {
+  const int l = (int)lround(sqrt((double)K)) - 1;
+  return (K >= 1 && (l + 1) * (l + 1) == K && l <= kLmax) ? 1 : 0;
+}
+
+}  // namespace wgeo

@@ -1,0 +1,258 @@
+// Point binning, counting sort by 8^3 tile, and the fused 27-cell normal splat +
+// divergence that produces the Poisson right-hand side b.
+//
+// Central cell (Sec. 2.3, Eq. 25 "central cell"): floor((x - lo) / h) per axis
+// with one IEEE double subtraction and one IEEE double division (__dsub_rn /
+// __ddiv_rn: no contraction), clamped into the grid.
+//
+// Splat (Eqs. 23-25): a~ = 1/2 for the central cell, else the product over
+// axes of (1/2) max(0, 1 - |x - c_o| / (2h)); alpha = a~ / sum over in-grid
+// cells; V_o = sum_i alpha_{o,i} n_i.  Sums are accumulated in 64-bit fixed
+// point (2^-36) in shared memory, so the result does not depend on the order
+// in which threads add — b is bit-reproducible run to run.
+//
+// Divergence (Eqs. 22, 26): b_p = sum_axis (F_{p+1/2} - F_{p-1/2}) with face
+// value F = (V_p + V_{p+e}) / 2 on interior faces and 0 on domain faces; the
+// face sums are exact integers, rounded once to float32.
+#include "wgeo_internal.cuh"
+
+namespace wgeo {
+
+namespace {
+
+struct GridParams {
+  double lo[3];
+  double h;
+  int res;
+  int ntile;   // tiles per axis
+};
+
+__global__ void bin_points_kernel(const float* __restrict__ pts, const float* __restrict__ nrm,
+                                  int64_t n, GridParams g, int* __restrict__ pcell,
+                                  float4* __restrict__ pfrac, float4* __restrict__ pnrm,
+                                  int* __restrict__ tile_count, DevState* st) {
+  unsigned int bits = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float px = pts[3 * i + 0], py = pts[3 * i + 1], pz = pts[3 * i + 2];
+    const float nx = nrm[3 * i + 0], ny = nrm[3 * i + 1], nz = nrm[3 * i + 2];
+    const bool fin = isfinite(px) && isfinite(py) && isfinite(pz) && isfinite(nx) &&
+                     isfinite(ny) && isfinite(nz);
+    if (!fin) {
+      bits |= WGEO_STATUS_NONFINITE_INPUT;
+      pcell[i] = -1;
+      pfrac[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float p3[3] = {px, py, pz};
+    int b[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double u = __ddiv_rn(__dsub_rn((double)p3[a], g.lo[a]), g.h);
+      if (u < 0.0 || u > (double)g.res) bits |= WGEO_STATUS_POINT_OUTSIDE_BBOX;
+      double fl = floor(u);
+      fl = fmin(fmax(fl, 0.0), (double)(g.res - 1));
+      b[a] = (int)fl;
+      f[a] = (float)(u - fl);
+    }
+    pcell[i] = pack_cell(b[0], b[1], b[2]);
+    pfrac[i] = make_float4(f[0], f[1], f[2], 0.f);
+    if (pnrm) pnrm[i] = make_float4(nx, ny, nz, 0.f);
+    const int t = ((b[2] / kSplatTile) * g.ntile + b[1] / kSplatTile) * g.ntile + b[0] / kSplatTile;
+    atomicAdd(&tile_count[t], 1);
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if (bits && (threadIdx.x & 31) == 0) atomicOr(&st->status, bits);
+}
+
+__global__ void scatter_points_kernel(const float* __restrict__ nrm, int64_t n,
+                                      const int* __restrict__ pcell, const float4* __restrict__ pfrac,
+                                      int ntile, int* __restrict__ cursor, float4* __restrict__ srec) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = pcell[i];
+    if (c < 0) continue;
+    const int t = ((cell_z(c) / kSplatTile) * ntile + cell_y(c) / kSplatTile) * ntile +
+                  cell_x(c) / kSplatTile;
+    const int pos = atomicAdd(&cursor[t], 1);
+    const float4 f = pfrac[i];
+    srec[2 * (int64_t)pos] = make_float4(f.x, f.y, f.z, __int_as_float(c));
+    srec[2 * (int64_t)pos + 1] = make_float4(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2], 0.f);
+  }
+}
+
+constexpr int kR = kSplatTile + 2;  // V region edge: tile plus one halo cell per side
+
+// One CTA per 8^3 output tile, one thread per output cell.
+__global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict__ srec,
+                                                        const int* __restrict__ tile_off, int res,
+                                                        int ntile, float* __restrict__ b,
+                                                        double* __restrict__ partials) {
+  __shared__ long long V[kR * kR * kR * 3];
+  __shared__ double red[32];
+  const int tile = blockIdx.x;
+  const int tx = tile % ntile, ty = (tile / ntile) % ntile, tz = tile / (ntile * ntile);
+  const int T0[3] = {tx * kSplatTile, ty * kSplatTile, tz * kSplatTile};
+  for (int k = threadIdx.x; k < kR * kR * kR * 3; k += blockDim.x) V[k] = 0;
+  __syncthreads();
+
+  for (int nt = 0; nt < 27; ++nt) {
+    const int ux = tx + nt % 3 - 1, uy = ty + (nt / 3) % 3 - 1, uz = tz + nt / 9 - 1;
+    if (ux < 0 || uy < 0 || uz < 0 || ux >= ntile || uy >= ntile || uz >= ntile) continue;
+    const int t = (uz * ntile + uy) * ntile + ux;
+    const int s0 = tile_off[t], s1 = tile_off[t + 1];
+    for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+      const float4 r0 = srec[2 * (int64_t)k];
+      const int c = __float_as_int(r0.w);
+      const int bc[3] = {cell_x(c), cell_y(c), cell_z(c)};
+      bool rel = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) rel &= (bc[a] >= T0[a] - 2) && (bc[a] <= T0[a] + kSplatTile + 1);
+      if (!rel) continue;
+      const float4 r1 = srec[2 * (int64_t)k + 1];
+      const float fr[3] = {r0.x, r0.y, r0.z};
+      const float nn[3] = {r1.x, r1.y, r1.z};
+      // per-axis factors for offsets -1, 0, +1: (x - c_o)/h = frac - 1/2 - delta
+      float fac[3][3];
+      bool ing[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float t = fabsf(fr[a] - 0.5f - (float)(d - 1));
+          fac[a][d] = 0.5f * fmaxf(0.f, 1.f - 0.5f * t);
+          const int o = bc[a] + d - 1;
+          ing[a][d] = (o >= 0) && (o < res);
+        }
+      }
+      float S = 0.f;
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
+            const bool centre = (dx == 1 && dy == 1 && dz == 1);
+            S += centre ? 0.5f : fac[0][dx] * fac[1][dy] * fac[2][dz];
+          }
+      const float inv = 1.f / S;
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
+            const int lx = bc[0] + dx - 1 - (T0[0] - 1);
+            const int ly = bc[1] + dy - 1 - (T0[1] - 1);
+            const int lz = bc[2] + dz - 1 - (T0[2] - 1);
+            if (lx < 0 || ly < 0 || lz < 0 || lx >= kR || ly >= kR || lz >= kR) continue;
+            const bool centre = (dx == 1 && dy == 1 && dz == 1);
+            const float alpha = (centre ? 0.5f : fac[0][dx] * fac[1][dy] * fac[2][dz]) * inv;
+            long long* v = &V[((lz * kR + ly) * kR + lx) * 3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const long long q = __float2ll_rn(alpha * nn[a] * (float)kFixScale);
+              if (q) atomicAdd((unsigned long long*)&v[a], (unsigned long long)q);
+            }
+          }
+    }
+  }
+  __syncthreads();
+
+  const int lx = threadIdx.x % kSplatTile, ly = (threadIdx.x / kSplatTile) % kSplatTile,
+            lz = threadIdx.x / (kSplatTile * kSplatTile);
+  const int p[3] = {T0[0] + lx, T0[1] + ly, T0[2] + lz};
+  double bv = 0.0;
+  if (p[0] < res && p[1] < res && p[2] < res) {
+    const int l = ((lz + 1) * kR + (ly + 1)) * kR + (lx + 1);
+    const int strides[3] = {1, kR, kR * kR};
+    long long acc = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (p[a] + 1 < res) acc += V[l * 3 + a] + V[(l + strides[a]) * 3 + a];
+      if (p[a] - 1 >= 0) acc -= V[(l - strides[a]) * 3 + a] + V[l * 3 + a];
+    }
+    const float bf = (float)((double)acc * kFixInv2);
+    b[((int64_t)p[2] * res + p[1]) * res + p[0]] = bf;
+    bv = (double)bf;
+  }
+  const double s1 = block_sum<512>(bv, red);
+  const double s2 = block_sum<512>(bv * bv, red);
+  if (threadIdx.x == 0) {
+    partials[2 * (int64_t)tile] = s1;
+    partials[2 * (int64_t)tile + 1] = s2;
+  }
+}
+
+// Reduces the per-tile partial sums in a fixed order: mean(b) and ||b - mean||.
+__global__ void b_stats_kernel(const double* __restrict__ partials, int ntiles, int64_t N,
+                               DevState* st) {
+  __shared__ double red[32];
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
+    s1 += partials[2 * i];
+    s2 += partials[2 * i + 1];
+  }
+  s1 = block_sum<1024>(s1, red);
+  s2 = block_sum<1024>(s2, red);
+  if (threadIdx.x == 0) {
+    const double mean = s1 / (double)N;
+    st->fwd.bmean = mean;
+    st->fwd.bnorm = sqrt(fmax(s2 - s1 * mean, 0.0));
+  }
+}
+
+__global__ void unpack_bins_kernel(const int* __restrict__ pcell, int64_t n, int* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = pcell[i];
+    out[3 * i] = c < 0 ? -1 : cell_x(c);
+    out[3 * i + 1] = c < 0 ? -1 : cell_y(c);
+    out[3 * i + 2] = c < 0 ? -1 : cell_z(c);
+  }
+}
+
+}  // namespace
+
+int launch_unpack_bins(wgeo_handle* h, int* out, cudaStream_t s) {
+  if (h->npts == 0) return WGEO_OK;
+  unpack_bins_kernel<<<grid_blocks(h->npts, 256), 256, 0, s>>>(h->pcell, h->npts, out);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+int launch_bin_sort_splat(wgeo_handle* h, const float* points, const float* normals, int64_t n,
+                          int res, cudaStream_t s) {
+  GridParams g;
+  for (int a = 0; a < 3; ++a) g.lo[a] = h->lo[a];
+  g.h = h->h;
+  g.res = res;
+  g.ntile = div_up(res, kSplatTile);
+  const int ntiles = g.ntile * g.ntile * g.ntile;
+  WGEO_CUDA_TRY(cudaMemsetAsync(h->tile_count, 0, sizeof(int) * (ntiles + 1), s));
+  if (n > 0) {
+    bin_points_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(points, normals, n, g, h->pcell, h->pfrac,
+                                                          h->opt.keep_for_backward ? h->pnrm : nullptr,
+                                                          h->tile_count, h->dstate);
+    WGEO_LAUNCH_CHECK();
+  }
+  int rc = exclusive_scan(h->tile_count, h->tile_off, ntiles, h->scan_tmp, s);
+  if (rc) return rc;
+  if (n > 0) {
+    WGEO_CUDA_TRY(cudaMemcpyAsync(h->tile_cursor, h->tile_off, sizeof(int) * ntiles,
+                                  cudaMemcpyDeviceToDevice, s));
+    scatter_points_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(normals, n, h->pcell, h->pfrac, g.ntile,
+                                                              h->tile_cursor, h->srec);
+    WGEO_LAUNCH_CHECK();
+  }
+  splat_div_kernel<<<ntiles, 512, 0, s>>>(h->srec, h->tile_off, res, g.ntile, h->b32, h->partials);
+  WGEO_LAUNCH_CHECK();
+  b_stats_kernel<<<1, 1024, 0, s>>>(h->partials, ntiles, (int64_t)res * res * res, h->dstate);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+}  // namespace wgeo

@@ -1,0 +1,630 @@
+// Iso-value (Sec. 2.4, Eq. 27), marching cubes (Eq. 28), exact signed distance
+// to the triangles (Eqs. 29-34) and stencil normals (after Eq. 32).
+//
+// Iso-value: c = mean over the finite input points of chi interpolated
+// trilinearly between cell centres (positions clamped into the node hull),
+// accumulated in FP64 with a fixed-order two-pass reduction.
+//
+// Marching cubes on the (res-1)^3 cubes between cell centres; a node is inside
+// iff chi < c.  Cubes are processed in 4^3 bricks (one CTA each): a count pass,
+// a scan over bricks, and an emit pass that writes each brick's triangles
+// contiguously.  Each triangle stores its three vertices and the global ids of
+// the edges they sit on (3 * linear index of the lower node + axis).  A shared
+// edge's vertex is computed from the same two chi values by every cube, so it
+// is bit-identical across cubes (watertight).
+//
+// The case table is derived at load time from the face-consistent rule: on a
+// face with four crossed edges every inside corner is cut off by its own
+// segment; segments are directed with the inside corners on their right seen
+// from outside the cube, chained into loops (listed by smallest edge id) and
+// fanned from their first edge, so triangles face from inside to outside.
+//
+// Distance: exact minimum over all triangles of the point-to-triangle distance
+// (closest point by Voronoi regions of the triangle: vertices, edges, face —
+// the method of Ericson, Real-Time Collision Detection, 5.1.5), found by a
+// depth-first, nearest-child-first traversal of an implicit octree of brick
+// bounding boxes, pruned only by exact box lower bounds.  Sign: +1 where
+// chi >= c, -1 where chi < c (the marching-cubes surface separates the two node
+// classes, so this is the parity of crossings of any ray from the node).
+#include <math.h>
+
+#include <algorithm>
+
+#include "wgeo_internal.cuh"
+
+namespace wgeo {
+
+__constant__ int c_mc_count[256];
+__constant__ signed char c_mc_tris[256][kMaxTriPerCube][3];
+
+// ---------------------------------------------------------------- host: table
+namespace {
+
+struct EdgeGeo {
+  int axis;
+  int c0, c1;  // lower / upper corner
+};
+
+void corner_xyz(int k, double* p) {
+  p[0] = k & 1;
+  p[1] = (k >> 1) & 1;
+  p[2] = (k >> 2) & 1;
+}
+
+EdgeGeo edge_geo(int e) {
+  EdgeGeo g;
+  g.axis = e / 4;
+  const int a = e % 4;
+  int lo[3] = {0, 0, 0};
+  const int o0 = (g.axis == 0) ? 1 : 0;
+  const int o1 = (g.axis == 2) ? 1 : 2;
+  lo[o0] = a & 1;
+  lo[o1] = a >> 1;
+  g.c0 = lo[0] + 2 * lo[1] + 4 * lo[2];
+  lo[g.axis] = 1;
+  g.c1 = lo[0] + 2 * lo[1] + 4 * lo[2];
+  return g;
+}
+
+int table_for_case(int cs, int tris[kMaxTriPerCube * 2][3]) {
+  bool in[8];
+  for (int k = 0; k < 8; ++k) in[k] = (cs >> k) & 1;
+  bool crossed[12];
+  for (int e = 0; e < 12; ++e) {
+    EdgeGeo g = edge_geo(e);
+    crossed[e] = in[g.c0] != in[g.c1];
+  }
+  int next[12];
+  for (int e = 0; e < 12; ++e) next[e] = -1;
+  for (int axis = 0; axis < 3; ++axis) {
+    for (int side = 0; side < 2; ++side) {
+      double nrm[3] = {0, 0, 0};
+      nrm[axis] = side ? 1.0 : -1.0;
+      int fe[4], nfe = 0;
+      for (int e = 0; e < 12; ++e) {
+        EdgeGeo g = edge_geo(e);
+        double p0[3];
+        corner_xyz(g.c0, p0);
+        if (g.axis != axis && (int)p0[axis] == side && crossed[e]) fe[nfe++] = e;
+      }
+      auto mid = [](int e, double* m) {
+        EdgeGeo g = edge_geo(e);
+        double a[3], b[3];
+        corner_xyz(g.c0, a);
+        corner_xyz(g.c1, b);
+        for (int i = 0; i < 3; ++i) m[i] = 0.5 * (a[i] + b[i]);
+      };
+      auto add_seg = [&](int a, int b, const double* ref) {
+        double pa[3], pb[3];
+        mid(a, pa);
+        mid(b, pb);
+        const double d[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+        const double left[3] = {nrm[1] * d[2] - nrm[2] * d[1], nrm[2] * d[0] - nrm[0] * d[2],
+                                nrm[0] * d[1] - nrm[1] * d[0]};
+        double s = 0;
+        for (int i = 0; i < 3; ++i) s += left[i] * (ref[i] - 0.5 * (pa[i] + pb[i]));
+        if (s > 0) std::swap(a, b);
+        next[a] = b;
+      };
+      if (nfe == 2) {
+        double ref[3] = {0, 0, 0};
+        int cnt = 0;
+        for (int k = 0; k < 8; ++k) {
+          double p[3];
+          corner_xyz(k, p);
+          if ((int)p[axis] == side && in[k]) {
+            for (int i = 0; i < 3; ++i) ref[i] += p[i];
+            ++cnt;
+          }
+        }
+        for (int i = 0; i < 3; ++i) ref[i] /= cnt;
+        add_seg(fe[0], fe[1], ref);
+      } else if (nfe == 4) {
+        for (int k = 0; k < 8; ++k) {
+          double p[3];
+          corner_xyz(k, p);
+          if ((int)p[axis] != side || !in[k]) continue;
+          int adj[2], na = 0;
+          for (int q = 0; q < 4; ++q) {
+            EdgeGeo g = edge_geo(fe[q]);
+            if (g.c0 == k || g.c1 == k) adj[na++] = fe[q];
+          }
+          add_seg(adj[0], adj[1], p);
+        }
+      }
+    }
+  }
+  int nt = 0;
+  bool seen[12] = {false};
+  for (int e = 0; e < 12; ++e) {
+    if (!crossed[e] || seen[e]) continue;
+    int loop[12], nl = 0;
+    int f = e;
+    do {
+      loop[nl++] = f;
+      seen[f] = true;
+      f = next[f];
+    } while (f != e && f >= 0 && nl < 12);
+    for (int k = 1; k + 1 < nl; ++k) {
+      tris[nt][0] = loop[0];
+      tris[nt][1] = loop[k];
+      tris[nt][2] = loop[k + 1];
+      ++nt;
+    }
+  }
+  return nt;
+}
+
+}  // namespace
+
+void host_mc_table(int* counts, int* tris) {
+  for (int cs = 0; cs < 256; ++cs) {
+    int t[kMaxTriPerCube * 2][3];
+    const int nt = table_for_case(cs, t);
+    counts[cs] = nt;
+    for (int k = 0; k < kMaxTriPerCube; ++k)
+      for (int v = 0; v < 3; ++v) tris[(cs * kMaxTriPerCube + k) * 3 + v] = (k < nt) ? t[k][v] : -1;
+  }
+}
+
+int upload_mc_table() {
+  int counts[256];
+  int tris[256 * kMaxTriPerCube * 3];
+  host_mc_table(counts, tris);
+  signed char t8[256 * kMaxTriPerCube * 3];
+  for (int i = 0; i < 256 * kMaxTriPerCube * 3; ++i) t8[i] = (signed char)tris[i];
+  for (int i = 0; i < 256; ++i)
+    if (counts[i] > kMaxTriPerCube) return WGEO_ERR_INVALID_ARG;
+  WGEO_CUDA_TRY(cudaMemcpyToSymbol(c_mc_count, counts, sizeof(counts)));
+  WGEO_CUDA_TRY(cudaMemcpyToSymbol(c_mc_tris, t8, sizeof(t8)));
+  return WGEO_OK;
+}
+
+// ---------------------------------------------------------------- device
+namespace {
+
+struct SurfParams {
+  double lo[3];
+  double h;
+  int res;
+  int nb;        // bricks per axis
+};
+
+__device__ __forceinline__ int64_t lin3(int i, int j, int k, int n) {
+  return ((int64_t)k * n + j) * n + i;
+}
+
+__global__ void isovalue_kernel(const float* __restrict__ pts, int64_t n, const int* __restrict__ pcell,
+                                const float* __restrict__ chi, SurfParams g,
+                                double* __restrict__ partials) {
+  __shared__ double red[32];
+  double s = 0.0, cnt = 0.0;
+  const int res = g.res;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (pcell[i] < 0) continue;
+    int i0[3];
+    double t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double u = ((double)pts[3 * i + a] - g.lo[a]) / g.h - 0.5;
+      u = fmin(fmax(u, 0.0), (double)(res - 1));
+      int f = (int)floor(u);
+      f = min(f, res - 2);
+      i0[a] = f;
+      t[a] = u - f;
+    }
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+      const double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dz ? t[2] : 1.0 - t[2]);
+      v += w * (double)chi[lin3(i0[0] + dx, i0[1] + dy, i0[2] + dz, res)];
+    }
+    s += v;
+    cnt += 1.0;
+  }
+  s = block_sum<256>(s, red);
+  cnt = block_sum<256>(cnt, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s;
+    partials[2 * blockIdx.x + 1] = cnt;
+  }
+}
+
+__global__ void isovalue_finalize_kernel(const double* __restrict__ partials, int nblocks, DevState* st) {
+  __shared__ double red[32];
+  double s = 0.0, cnt = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    s += partials[2 * i];
+    cnt += partials[2 * i + 1];
+  }
+  s = block_sum<1024>(s, red);
+  cnt = block_sum<1024>(cnt, red);
+  if (threadIdx.x == 0) {
+    st->c = cnt > 0.0 ? s / cnt : 0.0;
+    st->npts = (long long)cnt;
+  }
+}
+
+__device__ __forceinline__ int cube_code(const float* __restrict__ chi, int i, int j, int k, int n,
+                                         double c) {
+  int code = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float v = chi[lin3(i + (q & 1), j + ((q >> 1) & 1), k + (q >> 2), n)];
+    code |= ((double)v < c) ? (1 << q) : 0;
+  }
+  return code;
+}
+
+// One CTA (64 threads) per 4^3 brick of cubes.
+__global__ void __launch_bounds__(64) mc_count_kernel(const float* __restrict__ chi, SurfParams g,
+                                                      const DevState* __restrict__ st,
+                                                      int* __restrict__ brick_count) {
+  const int br = blockIdx.x;
+  const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
+  const int i = bx * kBrick + (threadIdx.x & 3), j = by * kBrick + ((threadIdx.x >> 2) & 3),
+            k = bz * kBrick + (threadIdx.x >> 4);
+  const int m = g.res - 1;
+  int cnt = 0;
+  if (i < m && j < m && k < m) cnt = c_mc_count[cube_code(chi, i, j, k, g.res, st->c)];
+  cnt = warp_sumi(cnt);
+  __shared__ int s[2];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) brick_count[br] = s[0] + s[1];
+}
+
+__global__ void mc_total_kernel(const int* __restrict__ brick_off, int nbricks, int64_t cap,
+                                DevState* st) {
+  const long long T = brick_off[nbricks];
+  st->ntris = T;
+  if (T > cap) atomicOr(&st->status, WGEO_STATUS_MESH_CAPACITY);
+  if (T == 0) atomicOr(&st->status, WGEO_STATUS_EMPTY_SURFACE);
+}
+
+__device__ __forceinline__ void edge_lower_offset(int e, int& ox, int& oy, int& oz, int& axis) {
+  axis = e >> 2;
+  const int a = e & 3;
+  int o[3] = {0, 0, 0};
+  const int o0 = (axis == 0) ? 1 : 0;
+  const int o1 = (axis == 2) ? 1 : 2;
+  o[o0] = a & 1;
+  o[o1] = a >> 1;
+  ox = o[0];
+  oy = o[1];
+  oz = o[2];
+}
+
+__global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ chi, SurfParams g,
+                                                     const DevState* __restrict__ st,
+                                                     const int* __restrict__ brick_off, int64_t cap,
+                                                     Tri* __restrict__ tris) {
+  const int br = blockIdx.x;
+  const int base = brick_off[br];
+  if (brick_off[br + 1] == base) return;
+  const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
+  const int i = bx * kBrick + (threadIdx.x & 3), j = by * kBrick + ((threadIdx.x >> 2) & 3),
+            k = bz * kBrick + (threadIdx.x >> 4);
+  const int n = g.res, m = n - 1;
+  const double c = st->c;
+  int code = 0, cnt = 0;
+  if (i < m && j < m && k < m) {
+    code = cube_code(chi, i, j, k, n, c);
+    cnt = c_mc_count[code];
+  }
+  // exclusive scan of cnt over the 64 threads (brick order: x fastest)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  __shared__ int wt[2];
+  if (lane == 31) wt[w] = incl;
+  __syncthreads();
+  const int excl = incl - cnt + (w ? wt[0] : 0);
+  for (int q = 0; q < cnt; ++q) {
+    const int64_t idx = (int64_t)base + excl + q;
+    if (idx >= cap) break;
+    Tri tr;
+    float4* out[3] = {&tr.a, &tr.b, &tr.c};
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const int e = c_mc_tris[code][q][v];
+      int ox, oy, oz, ax;
+      edge_lower_offset(e, ox, oy, oz, ax);
+      const int pi = i + ox, pj = j + oy, pk = k + oz;
+      const int64_t p = lin3(pi, pj, pk, n);
+      const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+      const double c1 = (double)chi[p], c2 = (double)chi[p + stride];
+      const double eta = (c - c1) / (c2 - c1);
+      double pos[3] = {g.lo[0] + (pi + 0.5) * g.h, g.lo[1] + (pj + 0.5) * g.h,
+                       g.lo[2] + (pk + 0.5) * g.h};
+      pos[ax] += eta * g.h;
+      const int gid = (int)(3 * p + ax);
+      *out[v] = make_float4((float)pos[0], (float)pos[1], (float)pos[2], __int_as_float(gid));
+    }
+    tris[idx] = tr;
+  }
+}
+
+// ---- bounding-box octree over bricks: level 0 = bricks, level l+1 halves
+__global__ void pyr_leaf_kernel(const Tri* __restrict__ tris, const int* __restrict__ brick_off,
+                                int nbricks, int64_t cap, float4* __restrict__ pyr) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbricks; b += gridDim.x * blockDim.x) {
+    const int64_t s0 = brick_off[b];
+    const int64_t s1 = min((int64_t)brick_off[b + 1], cap);
+    float3 lo = make_float3(INFINITY, INFINITY, INFINITY);
+    float3 hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+    for (int64_t t = s0; t < s1; ++t) {
+      const Tri tr = tris[t];
+      const float4 v[3] = {tr.a, tr.b, tr.c};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        lo.x = fminf(lo.x, v[q].x);
+        lo.y = fminf(lo.y, v[q].y);
+        lo.z = fminf(lo.z, v[q].z);
+        hi.x = fmaxf(hi.x, v[q].x);
+        hi.y = fmaxf(hi.y, v[q].y);
+        hi.z = fmaxf(hi.z, v[q].z);
+      }
+    }
+    pyr[2 * b] = make_float4(lo.x, lo.y, lo.z, 0.f);
+    pyr[2 * b + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+  }
+}
+
+__global__ void pyr_up_kernel(float4* __restrict__ pyr, int64_t off_child, int dchild, int64_t off_parent,
+                              int dparent) {
+  const int64_t np = (int64_t)dparent * dparent * dparent;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < np;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % dparent), y = (int)((t / dparent) % dparent), z = (int)(t / ((int64_t)dparent * dparent));
+    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+    for (int c = 0; c < 8; ++c) {
+      const int cx = 2 * x + (c & 1), cy = 2 * y + ((c >> 1) & 1), cz = 2 * z + (c >> 2);
+      if (cx >= dchild || cy >= dchild || cz >= dchild) continue;
+      const int64_t ci = off_child + ((int64_t)cz * dchild + cy) * dchild + cx;
+      const float4 a = pyr[2 * ci], b = pyr[2 * ci + 1];
+      lo.x = fminf(lo.x, a.x);
+      lo.y = fminf(lo.y, a.y);
+      lo.z = fminf(lo.z, a.z);
+      hi.x = fmaxf(hi.x, b.x);
+      hi.y = fmaxf(hi.y, b.y);
+      hi.z = fmaxf(hi.z, b.z);
+    }
+    pyr[2 * (off_parent + t)] = lo;
+    pyr[2 * (off_parent + t) + 1] = hi;
+  }
+}
+
+struct PyrInfo {
+  int nlev;
+  int dim[12];
+  long long off[12];
+};
+
+__device__ __forceinline__ float box_dist2(const float3 p, const float4 lo, const float4 hi) {
+  if (lo.x > hi.x) return INFINITY;
+  const float dx = fmaxf(fmaxf(lo.x - p.x, 0.f), p.x - hi.x);
+  const float dy = fmaxf(fmaxf(lo.y - p.y, 0.f), p.y - hi.y);
+  const float dz = fmaxf(fmaxf(lo.z - p.z, 0.f), p.z - hi.z);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+
+}  // namespace
+
+namespace {
+
+constexpr int kStack = 96;
+
+// One thread per grid node; blocks of 8 x 8 x 4 nodes.
+__global__ void __launch_bounds__(256) sdf_kernel(const float* __restrict__ chi, SurfParams g,
+                                                  const DevState* __restrict__ st,
+                                                  const Tri* __restrict__ tris,
+                                                  const int* __restrict__ brick_off, int64_t cap,
+                                                  const float4* __restrict__ pyr, PyrInfo pi,
+                                                  float* __restrict__ phi, float* __restrict__ sdf_out,
+                                                  int* __restrict__ ctri) {
+  const int n = g.res;
+  const int nbx = (n + 7) / 8, nby = (n + 7) / 8;
+  const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
+  const int i = bx * 8 + (threadIdx.x & 7), j = by * 8 + ((threadIdx.x >> 3) & 7),
+            k = bz * 4 + (threadIdx.x >> 6);
+  if (i >= n || j >= n || k >= n) return;
+  const int64_t o = lin3(i, j, k, n);
+  const double c = st->c;
+  const float sgn = ((double)chi[o] >= c) ? 1.f : -1.f;
+  const float3 p = make_float3((float)(g.lo[0] + (i + 0.5) * g.h), (float)(g.lo[1] + (j + 0.5) * g.h),
+                               (float)(g.lo[2] + (k + 0.5) * g.h));
+  float best = INFINITY;
+  int bt = -1;
+  unsigned int stk[kStack];
+  float sd[kStack];
+  int sp = 0;
+  const int top = pi.nlev - 1;
+  {
+    const float d = box_dist2(p, pyr[2 * pi.off[top]], pyr[2 * pi.off[top] + 1]);
+    if (d < INFINITY) {
+      stk[0] = (unsigned)top << 27;
+      sd[0] = d;
+      sp = 1;
+    }
+  }
+  while (sp > 0) {
+    --sp;
+    const unsigned e = stk[sp];
+    if (sd[sp] >= best) continue;
+    const int lev = (int)(e >> 27);
+    const int idx = (int)(e & ((1u << 27) - 1));
+    if (lev == 0) {
+      const int64_t s0 = brick_off[idx];
+      const int64_t s1 = min((int64_t)brick_off[idx + 1], cap);
+      for (int64_t t = s0; t < s1; ++t) {
+        const Tri tr = tris[t];
+        const float d2 = tri_closest(p, f3(tr.a), f3(tr.b), f3(tr.c), nullptr, nullptr, nullptr);
+        if (d2 < best) {
+          best = d2;
+          bt = (int)t;
+        }
+      }
+      continue;
+    }
+    const int dp = pi.dim[lev], dc = pi.dim[lev - 1];
+    const int x = idx % dp, y = (idx / dp) % dp, z = idx / (dp * dp);
+    // collect children, then push far-to-near so the nearest is popped first
+    unsigned ce[8];
+    float cd[8];
+    int nc = 0;
+    for (int q = 0; q < 8; ++q) {
+      const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
+      if (cx >= dc || cy >= dc || cz >= dc) continue;
+      const int ci = (cz * dc + cy) * dc + cx;
+      const int64_t gi = pi.off[lev - 1] + ci;
+      const float d = box_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
+      if (d >= best) continue;
+      // insertion sort, descending distance
+      int q2 = nc;
+      while (q2 > 0 && cd[q2 - 1] < d) {
+        cd[q2] = cd[q2 - 1];
+        ce[q2] = ce[q2 - 1];
+        --q2;
+      }
+      cd[q2] = d;
+      ce[q2] = ((unsigned)(lev - 1) << 27) | (unsigned)ci;
+      ++nc;
+    }
+    for (int q = 0; q < nc && sp < kStack; ++q) {
+      stk[sp] = ce[q];
+      sd[sp] = cd[q];
+      ++sp;
+    }
+  }
+  const float val = sgn * sqrtf(best);
+  phi[o] = val;
+  if (sdf_out) sdf_out[o] = val;
+  if (ctri) ctri[o] = bt;
+}
+
+// n = grad phi / |grad phi|: central differences inside, second-order one-sided
+// on the first and last node of each axis; 0 where |grad| is 0 or not finite.
+__global__ void normals_kernel(const float* __restrict__ phi, int n, double h,
+                               float* __restrict__ nrm) {
+  const int64_t N = (int64_t)n * n * n;
+  const float inv2h = (float)(0.5 / h);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int idx[3] = {(int)(t % n), (int)((t / n) % n), (int)(t / ((int64_t)n * n))};
+    const int64_t st[3] = {1, n, (int64_t)n * n};
+    float gr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int i = idx[a];
+      float d;
+      if (i == 0)
+        d = -3.f * phi[t] + 4.f * phi[t + st[a]] - phi[t + 2 * st[a]];
+      else if (i == n - 1)
+        d = 3.f * phi[t] - 4.f * phi[t - st[a]] + phi[t - 2 * st[a]];
+      else
+        d = phi[t + st[a]] - phi[t - st[a]];
+      gr[a] = d * inv2h;
+    }
+    const float m2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+    const bool ok = isfinite(m2) && m2 > 0.f;
+    const float inv = ok ? rsqrtf(m2) : 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nrm[a * N + t] = ok ? gr[a] * inv : 0.f;
+  }
+}
+
+PyrInfo pyramid_info(int nb) {
+  PyrInfo pi;
+  int d = nb;
+  long long off = 0;
+  pi.nlev = 0;
+  while (true) {
+    pi.dim[pi.nlev] = d;
+    pi.off[pi.nlev] = off;
+    off += (long long)d * d * d;
+    ++pi.nlev;
+    if (d == 1) break;
+    d = (d + 1) / 2;
+  }
+  return pi;
+}
+
+}  // namespace
+
+size_t pyramid_nodes(int nb) {
+  PyrInfo pi = pyramid_info(nb);
+  return (size_t)(pi.off[pi.nlev - 1] + 1);
+}
+
+int launch_isovalue(wgeo_handle* h, const float* points, int64_t n, int res, cudaStream_t s) {
+  SurfParams g;
+  for (int a = 0; a < 3; ++a) g.lo[a] = h->lo[a];
+  g.h = h->h;
+  g.res = res;
+  g.nb = div_up(res - 1, kBrick);
+  const int nbk = grid_blocks(n, 256, kPartials);
+  if (n > 0) {
+    isovalue_kernel<<<nbk, 256, 0, s>>>(points, n, h->pcell, h->chi32, g, h->partials);
+    WGEO_LAUNCH_CHECK();
+  } else {
+    WGEO_CUDA_TRY(cudaMemsetAsync(h->partials, 0, 2 * sizeof(double), s));
+  }
+  isovalue_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, n > 0 ? nbk : 1, h->dstate);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_out, cudaStream_t s) {
+  SurfParams g;
+  for (int a = 0; a < 3; ++a) g.lo[a] = h->lo[a];
+  g.h = h->h;
+  g.res = res;
+  g.nb = div_up(res - 1, kBrick);
+  const int nbricks = g.nb * g.nb * g.nb;
+  int slot = stage_begin(h, kStMC, s);
+  mc_count_kernel<<<nbricks, 64, 0, s>>>(h->chi32, g, h->dstate, h->brick_count);
+  WGEO_LAUNCH_CHECK();
+  int rc = exclusive_scan(h->brick_count, h->brick_off, nbricks, h->scan_tmp, s);
+  if (rc) return rc;
+  mc_total_kernel<<<1, 1, 0, s>>>(h->brick_off, nbricks, h->mesh_cap, h->dstate);
+  WGEO_LAUNCH_CHECK();
+  mc_emit_kernel<<<nbricks, 64, 0, s>>>(h->chi32, g, h->dstate, h->brick_off, h->mesh_cap, h->tris);
+  WGEO_LAUNCH_CHECK();
+  PyrInfo pi = pyramid_info(g.nb);
+  pyr_leaf_kernel<<<grid_blocks(nbricks, 128), 128, 0, s>>>(h->tris, h->brick_off, nbricks, h->mesh_cap,
+                                                          h->pyramid);
+  WGEO_LAUNCH_CHECK();
+  for (int l = 1; l < pi.nlev; ++l) {
+    const int64_t np = (int64_t)pi.dim[l] * pi.dim[l] * pi.dim[l];
+    pyr_up_kernel<<<grid_blocks(np, 128), 128, 0, s>>>(h->pyramid, pi.off[l - 1], pi.dim[l - 1], pi.off[l],
+                                                     pi.dim[l]);
+    WGEO_LAUNCH_CHECK();
+  }
+  stage_end(h, kStMC, slot, s);
+  slot = stage_begin(h, kStSDF, s);
+  const int nbx = (res + 7) / 8, nbz = (res + 3) / 4;
+  sdf_kernel<<<nbx * nbx * nbz, 256, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->brick_off, h->mesh_cap,
+                                            h->pyramid, pi, h->phi, sdf_out,
+                                            h->opt.keep_for_backward ? h->ctri : nullptr);
+  WGEO_LAUNCH_CHECK();
+  stage_end(h, kStSDF, slot, s);
+  if (nrm_out) {
+    slot = stage_begin(h, kStNormals, s);
+    const int64_t N = (int64_t)res * res * res;
+    normals_kernel<<<grid_blocks(N, 256, 152 * 32), 256, 0, s>>>(h->phi, res, h->h, nrm_out);
+    WGEO_LAUNCH_CHECK();
+    stage_end(h, kStNormals, slot, s);
+  }
+  return WGEO_OK;
+}
+
+}  // namespace wgeo

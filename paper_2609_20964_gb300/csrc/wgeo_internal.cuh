@@ -1,0 +1,325 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the C ABI (include/wgeo.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/wgeo.h"
+
+namespace wgeo {
+
+// ---------------------------------------------------------------- constants
+constexpr int kSplatTile = 8;        // output tile edge of the fused splat + divergence
+constexpr int kBrick = 4;            // marching-cubes cubes per brick edge (SDF leaf)
+constexpr int kMaxTriPerCube = 5;
+constexpr int kPartials = 2048;      // per-block partial slots of the deterministic reductions
+constexpr int kMaxLevels = 12;
+constexpr double kFixScale = 68719476736.0;      // 2^36: fixed-point scale of the splat sums
+constexpr double kFixInv2 = 1.0 / 137438953472.0; // 1 / 2^37 (the face form sums 2 F)
+
+// ---------------------------------------------------------------- device state
+struct SolveState {
+  int done;          // set once the relative residual is below tol (gates later kernels)
+  int iter;          // refinement steps / V-cycles performed
+  double bnorm;      // || b - mean(b) ||
+  double bmean;
+  double rmean;      // mean of the last residual (projected out of the correction RHS)
+  double rel;        // last || r || / || b ||
+};
+
+struct DevState {
+  unsigned int status;
+  int pad0;
+  long long npts;     // finite points used by the forward
+  long long ntris;    // triangles found (uncapped)
+  double c;           // iso-value
+  double dc;          // backward: dL/dc
+  SolveState fwd;
+  SolveState bwd;
+};
+
+struct Tri {          // one marching-cubes triangle: vertex xyz + global edge id in .w
+  float4 a, b, c;
+};
+
+struct Level {
+  int n;
+  float* x;
+  float* b;
+};
+
+// ---------------------------------------------------------------- stage timers
+// Stage ids of the per-stage CUDA-event timers (option stage_timing).
+enum Stage {
+  kStSplat = 0,    // bin + tile sort + fused splat/divergence
+  kStSolve = 1,    // forward Poisson solve
+  kStIso = 2,
+  kStMC = 3,       // count + scan + emit + box pyramid
+  kStSDF = 4,      // exact distance search + sign
+  kStNormals = 5,
+  kStQuery = 6,
+  kStBwdSeed = 7,  // grid seeds + query adjoint
+  kStBwdSurf = 8,  // distance / marching-cubes / iso-value adjoints
+  kStBwdSolve = 9,
+  kStBwdSplat = 10,
+  kStages = 11
+};
+constexpr int kRing = 256;
+
+struct StageTimer {
+  cudaEvent_t beg[kRing];
+  cudaEvent_t end[kRing];
+  bool used[kRing];
+  int head = 0;
+  double acc_ms = 0.0;
+  long long count = 0;
+};
+
+// ---------------------------------------------------------------- handle
+struct SolverGraph {
+  int res = 0;
+  int mode = -1;      // 0 forward, 1 backward
+  cudaGraphExec_t exec = nullptr;
+};
+
+__device__ __forceinline__ float3 f3(const float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Squared distance from p to triangle (a, b, c) and the barycentric weights of
+// the closest point (Voronoi regions: three vertices, three edges, the face).
+__device__ __forceinline__ float tri_closest(const float3 p, const float3 a, const float3 b, const float3 c,
+                             float* wa, float* wb, float* wc) {
+  const float3 ab = sub3(b, a), ac = sub3(c, a), ap = sub3(p, a);
+  float u = 1.f, v = 0.f, w = 0.f;
+  const float d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+  if (d1 <= 0.f && d2 <= 0.f) {
+    u = 1.f; v = 0.f; w = 0.f;
+  } else {
+    const float3 bp = sub3(p, b);
+    const float d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+    if (d3 >= 0.f && d4 <= d3) {
+      u = 0.f; v = 1.f; w = 0.f;
+    } else {
+      const float vc = d1 * d4 - d3 * d2;
+      if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+        const float t = d1 / (d1 - d3);
+        u = 1.f - t; v = t; w = 0.f;
+      } else {
+        const float3 cp = sub3(p, c);
+        const float d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+        if (d6 >= 0.f && d5 <= d6) {
+          u = 0.f; v = 0.f; w = 1.f;
+        } else {
+          const float vb = d5 * d2 - d1 * d6;
+          if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+            const float t = d2 / (d2 - d6);
+            u = 1.f - t; v = 0.f; w = t;
+          } else {
+            const float va = d3 * d6 - d5 * d4;
+            if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+              const float t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+              u = 0.f; v = 1.f - t; w = t;
+            } else {
+              const float den = va + vb + vc;
+              if (den > 0.f) {
+                const float inv = 1.f / den;
+                v = vb * inv;
+                w = vc * inv;
+                u = 1.f - v - w;
+              } else {
+                // degenerate (collapsed) triangle: nearest of the three vertices
+                const float3 cb = sub3(p, b), cc = sub3(p, c);
+                const float q0 = dot3(ap, ap), q1 = dot3(cb, cb), q2 = dot3(cc, cc);
+                if (q0 <= q1 && q0 <= q2) { u = 1.f; v = 0.f; w = 0.f; }
+                else if (q1 <= q2) { u = 0.f; v = 1.f; w = 0.f; }
+                else { u = 0.f; v = 0.f; w = 1.f; }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  const float3 y = make_float3(u * a.x + v * b.x + w * c.x, u * a.y + v * b.y + w * c.y,
+                               u * a.z + v * b.z + w * c.z);
+  const float3 d = sub3(p, y);
+  if (wa) { *wa = u; *wb = v; *wc = w; }
+  return dot3(d, d);
+}
+
+}  // namespace wgeo
+
+struct wgeo_handle {
+  int max_res = 0;
+  int64_t max_points = 0;
+  wgeo_options opt{};
+  int device = 0;
+
+  // arena
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+
+  // grid fields (sized for max_res^3)
+  float* b32 = nullptr;
+  float* chi32 = nullptr;
+  double* chi64 = nullptr;
+  float* r32 = nullptr;
+  float* e32 = nullptr;
+  float* phi = nullptr;
+  int* ctri = nullptr;
+  double* dphi64 = nullptr;
+  double* dchi64 = nullptr;
+  double* lam64 = nullptr;
+  float* lam32 = nullptr;   // alias of chi-sized scratch for the adjoint solve output
+  std::vector<float> dummy;
+  float* level_pool = nullptr;
+
+  // points
+  int* pcell = nullptr;          // packed central cell per point (original order); -1 = skipped
+  float4* pfrac = nullptr;       // (u - cell) per axis, original order
+  float4* pnrm = nullptr;        // copy of the normals, original order (backward)
+  float4* srec = nullptr;        // sorted records: 2 float4 per point
+  int* tile_count = nullptr;
+  int* tile_off = nullptr;       // ntiles + 1
+  int* tile_cursor = nullptr;
+
+  // mesh
+  int64_t mesh_cap = 0;
+  int* brick_count = nullptr;
+  int* brick_off = nullptr;      // nbricks + 1
+  wgeo::Tri* tris = nullptr;
+  float4* pyramid = nullptr;     // 2 float4 per node (lo, hi)
+  double* dP = nullptr;          // backward: dL/d(vertex) per triangle corner, 9 doubles
+
+  // reductions / scans
+  double* partials = nullptr;    // kPartials * 4 doubles
+  int* scan_tmp = nullptr;
+  size_t scan_tmp_elems = 0;
+
+  wgeo::DevState* dstate = nullptr;
+
+  // host-side state of the last forward
+  int res = 0;
+  double h = 0.0;
+  double lo[3] = {0, 0, 0};
+  int64_t npts = 0;
+  bool have_forward = false;
+  bool have_backward_state = false;
+  bool chi_valid_for_warm = false;
+  int warm_res = 0;
+  cudaStream_t last_stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  wgeo::SolverGraph graphs[2];
+
+  // multigrid hierarchy for the current res
+  int nlevels = 0;
+  wgeo::Level levels[wgeo::kMaxLevels];
+
+  // per-stage event timers (allocated on first use when opt.stage_timing is set)
+  wgeo::StageTimer* timers = nullptr;
+};
+
+namespace wgeo {
+// Records the start / end of a stage on stream s (no-ops unless stage timing is on).
+int stage_begin(wgeo_handle* h, int stage, cudaStream_t s);
+void stage_end(wgeo_handle* h, int stage, int slot, cudaStream_t s);
+}  // namespace wgeo
+
+namespace wgeo {
+
+// ---------------------------------------------------------------- helpers
+#define WGEO_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return WGEO_ERR_CUDA;              \
+  } while (0)
+
+#define WGEO_LAUNCH_CHECK()                                   \
+  do {                                                        \
+    cudaError_t _e = cudaGetLastError();                      \
+    if (_e != cudaSuccess) return WGEO_ERR_CUDA;              \
+  } while (0)
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int grid_blocks(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// coarsest-level rule: halve while even and larger than 8
+int coarsest_size(int res);
+int build_levels(wgeo_handle* h, int res);
+
+// ---------------------------------------------------------------- launchers
+// splat.cu
+int launch_bin_sort_splat(wgeo_handle* h, const float* points, const float* normals, int64_t n,
+                          int res, cudaStream_t s);
+int launch_unpack_bins(wgeo_handle* h, int* out, cudaStream_t s);
+// solver.cu
+int launch_solve(wgeo_handle* h, int res, int mode, cudaStream_t s);
+int solver_fp32_prepare(wgeo_handle* h, int res, cudaStream_t s);
+// surface.cu
+int launch_isovalue(wgeo_handle* h, const float* points, int64_t n, int res, cudaStream_t s);
+int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_out, cudaStream_t s);
+int upload_mc_table();
+size_t pyramid_nodes(int nb);
+void host_mc_table(int* counts, int* tris);
+// query.cu
+int launch_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s);
+int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
+                    const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,
+                    float* d_normals, float* d_q, cudaStream_t s);
+// scan.cu
+int exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s);
+size_t scan_tmp_size(int n);
+// shgen.cu
+int launch_sh_surface(const float* theta, int K, const float* dirs, int64_t n, float base,
+                      const float* centre, float* points, float* normals, cudaStream_t s);
+int launch_sh_backward(wgeo_handle* h, const float* theta, int K, const float* dirs, int64_t n,
+                       float base, const float* dpts, const float* dnrm, float* dtheta, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sumi(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed shuffle tree, fixed warp order); result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (l < NT / 32) ? sh[l] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ int pack_cell(int x, int y, int z) { return x | (y << 10) | (z << 20); }
+__device__ __forceinline__ int cell_x(int p) { return p & 1023; }
+__device__ __forceinline__ int cell_y(int p) { return (p >> 10) & 1023; }
+__device__ __forceinline__ int cell_z(int p) { return (p >> 20) & 1023; }
+
+}  // namespace wgeo

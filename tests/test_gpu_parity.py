@@ -1,0 +1,253 @@
+"""GPU path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+Tolerances (stated by the method's target): bins bit-exact; SDF max |diff| <=
+1e-4 of the box extent; normals within 0.1 degree (nodes where the oracle's
+|grad_h phi| < 0.9 — medial axis — excluded); gradients within 1e-4 relative
+(L2) of the oracle's adjoint.  Sizes span several 8^3 splat tiles and 4^3
+marching-cubes bricks and end in ragged partial tiles.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import grid as OG
+from oracle import pipeline as OP
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+BBOX = np.array([0, 0, 0, 1, 1, 1], dtype=np.float32)
+SDF_TOL = 1e-4          # 1e-4 of the unit box extent
+ANGLE_TOL_DEG = 0.1
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def W():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2609_20964_gb300 import Reconstructor
+    torch.cuda.set_device(0)
+    return Reconstructor
+
+
+def _cases():
+    out = {}
+    p, n = synth.sphere_cloud(1500, seed=21)
+    out["sphere24"] = (p, n, 24)
+    p, n, _ = synth.sh_body_cloud(6000, seed=22, noise=0.002)
+    out["shbody44"] = (p, n, 44)
+    p, n = synth.wave_ellipsoid_cloud(37, n=5000)
+    out["wave40"] = (p, n, 40)
+    return out
+
+
+CASES = _cases()
+_ORACLE = {}
+
+
+def _oracle(name):
+    if name not in _ORACLE:
+        p, n, res = CASES[name]
+        _ORACLE[name] = oracle.reconstruct(p, n, BBOX, res)
+    return _ORACLE[name]
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _angle_deg(a, b):
+    dot = np.sum(a * b, axis=-1)
+    na = np.linalg.norm(a, axis=-1)
+    nb = np.linalg.norm(b, axis=-1)
+    c = np.clip(dot / np.maximum(na * nb, 1e-30), -1.0, 1.0)
+    return np.degrees(np.arccos(c))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_forward_parity(W, name):
+    p, n, res = CASES[name]
+    ref = _oracle(name)
+    rec = W(res, len(p))
+    sdf, nrm = rec.reconstruct(_t(p), _t(n), BBOX, res)
+    bins = rec.bins().cpu().numpy()
+    b = rec.field("b").cpu().numpy().astype(np.float64)
+    chi = rec.field("chi").cpu().numpy().astype(np.float64)
+    info = rec.info()
+    assert info["status"] == 0, info
+    # S1: bins bit-exact
+    assert np.array_equal(bins, ref.bins.astype(np.int32))
+    # S3-S4: right-hand side to float32 rounding
+    assert np.abs(b - ref.b).max() <= 2e-6 * np.abs(ref.b).max() + 1e-7
+    # S5: chi up to the additive constant
+    span = ref.chi.max() - ref.chi.min()
+    assert np.abs((chi - chi.mean()) - (ref.chi - ref.chi.mean())).max() <= 1e-4 * span
+    # S6: iso-value, relative to the spread of chi
+    assert abs((info["isovalue"] - chi.mean()) - (ref.c - ref.chi.mean())) <= 1e-4 * span
+    # S7-S8: signed distance
+    phi = sdf.cpu().numpy().astype(np.float64)
+    assert np.abs(phi - ref.phi).max() <= SDF_TOL
+    # S9: normals away from the medial axis
+    g = nrm.cpu().numpy().astype(np.float64)
+    ok = ref.gmag >= 0.9
+    ang = _angle_deg(np.moveaxis(g, 0, -1)[ok], np.moveaxis(ref.nrm, 0, -1)[ok])
+    assert ang.max() <= ANGLE_TOL_DEG, f"max angle {ang.max()} deg"
+    assert ok.mean() > 0.8
+    rec.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_query_and_backward_parity(W, name):
+    p, n, res = CASES[name]
+    ref = _oracle(name)
+    rng = np.random.default_rng(5)
+    q = synth.uniform_queries(3000, seed=31)
+    gs = rng.standard_normal(len(q)).astype(np.float32)
+    gn = rng.standard_normal((len(q), 3)).astype(np.float32)
+    rec = W(res, len(p))
+    rec.reconstruct(_t(p), _t(n), BBOX, res)
+    Q = _t(q)
+    sq, nq = rec.query(Q)
+    rs, rn = OP.query(ref, q)
+    assert np.abs(sq.cpu().numpy() - rs).max() <= SDF_TOL
+    # normals at queries whose 8 corner nodes are all off the medial axis
+    from oracle import iso as OI
+    corners, _, _ = OI.trilinear(q.astype(np.float64), ref.lo, ref.h, res)
+    good = np.all(OI.gather(ref.gmag, corners) >= 0.9, axis=1)
+    ang = _angle_deg(nq.cpu().numpy()[good], rn[good])
+    assert ang.max() <= ANGLE_TOL_DEG
+    # backward through the query loss (phi and normals at q) to points, normals and q
+    dp, dn, dq = rec.backward(q=Q, d_sdf_q=_t(gs), d_nrm_q=_t(gn), want_dq=True)
+    odp, odn, odq = OP.backward(ref, q=q, d_sdf_q=gs.astype(np.float64), d_nrm_q=gn.astype(np.float64))
+    for got, want, nm in ((dp, odp, "d_points"), (dn, odn, "d_normals"), (dq, odq, "d_q")):
+        got = got.cpu().numpy().astype(np.float64)
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert rel <= GRAD_TOL, f"{nm}: relative error {rel:.3e}"
+    rec.close()
+
+
+def test_grid_seed_backward_parity(W):
+    p, n, res = CASES["sphere24"]
+    ref = _oracle("sphere24")
+    rng = np.random.default_rng(9)
+    wg = rng.standard_normal((res, res, res)).astype(np.float32)
+    wn = rng.standard_normal((3, res, res, res)).astype(np.float32)
+    rec = W(res, len(p))
+    rec.reconstruct(_t(p), _t(n), BBOX, res)
+    dp, dn, _ = rec.backward(d_sdf_grid=_t(wg), d_nrm_grid=_t(wn))
+    odp, odn, _ = OP.backward(ref, d_sdf_grid=wg.astype(np.float64), d_nrm_grid=wn.astype(np.float64))
+    for got, want, nm in ((dp, odp, "d_points"), (dn, odn, "d_normals")):
+        got = got.cpu().numpy().astype(np.float64)
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert rel <= GRAD_TOL, f"{nm}: relative error {rel:.3e}"
+    rec.close()
+
+
+def test_deterministic_and_handle_reuse(W):
+    p, n, res = CASES["shbody44"]
+    rec = W(64, 20000)
+    s1, n1 = rec.reconstruct(_t(p), _t(n), BBOX, res)
+    s1 = s1.clone()
+    n1 = n1.clone()
+    # a different res on the same handle, then back
+    p2, n2 = synth.sphere_cloud(3000, seed=3)
+    rec.reconstruct(_t(p2), _t(n2), BBOX, 32)
+    s2, n2b = rec.reconstruct(_t(p), _t(n), BBOX, res)
+    assert torch.equal(s1, s2) and torch.equal(n1, n2b)
+    rec.close()
+
+
+def test_fp32_plain_mode_and_mixed_agree(W):
+    p, n, res = CASES["wave40"]
+    ref = _oracle("wave40")
+    from paper_2609_20964_gb300 import PREC_FP32
+    rec = W(res, len(p), precision=PREC_FP32, tol_rel=1e-6, max_vcycles=60)
+    sdf, _ = rec.reconstruct(_t(p), _t(n), BBOX, res)
+    info = rec.info()
+    err = np.abs(sdf.cpu().numpy() - ref.phi).max()
+    assert err <= SDF_TOL, (err, info)
+    rec.close()
+
+
+def test_empty_and_degenerate_inputs(W):
+    from paper_2609_20964_gb300 import STATUS_EMPTY_SURFACE, STATUS_NONFINITE_INPUT, \
+        STATUS_POINT_OUTSIDE_BBOX
+    rec = W(16, 100)
+    empty = torch.zeros((0, 3), device="cuda", dtype=torch.float32)
+    sdf, nrm = rec.reconstruct(empty, empty, BBOX, 16)
+    info = rec.info()
+    assert info["status"] & STATUS_EMPTY_SURFACE
+    assert info["n_triangles"] == 0
+    assert torch.isinf(sdf).all() and (sdf > 0).all()
+    assert (nrm == 0).all()
+    # a NaN point is skipped: same result as without it
+    p, n = synth.sphere_cloud(80, seed=2)
+    pn = np.concatenate([p, np.array([[np.nan, 0.5, 0.5]], np.float32)])
+    nn = np.concatenate([n, np.array([[0, 0, 1]], np.float32)])
+    a, _ = rec.reconstruct(_t(p), _t(n), BBOX, 16)
+    a = a.clone()
+    b, _ = rec.reconstruct(_t(pn), _t(nn), BBOX, 16)
+    assert rec.info()["status"] & STATUS_NONFINITE_INPUT
+    assert torch.equal(a, b)
+    # a point outside the box is flagged and clamped
+    po = np.concatenate([p, np.array([[1.5, 0.5, 0.5]], np.float32)])
+    rec.reconstruct(_t(po), _t(nn), BBOX, 16)
+    assert rec.info()["status"] & STATUS_POINT_OUTSIDE_BBOX
+    rec.close()
+
+
+def test_host_errors(W):
+    from paper_2609_20964_gb300 import WgeoError
+    rec = W(32, 100)
+    p, n = synth.sphere_cloud(100, seed=2)
+    with pytest.raises(WgeoError):
+        rec.reconstruct(_t(p), _t(n), BBOX, 64)              # res over the handle's bound
+    with pytest.raises(WgeoError):
+        rec.reconstruct(_t(p), _t(n), np.array([0, 0, 0, 1, 0, 1], np.float32), 16)   # flat box
+    with pytest.raises(WgeoError):
+        rec.query(_t(synth.uniform_queries(10, 1)))          # no forward yet
+    rec.close()
+
+
+def test_sh_generator_and_adjoint(W):
+    from paper_2609_20964_gb300 import sh_surface, sh_surface_backward
+    dirs, th0, _ = synth.sh_fixed_dirs_cloud(5000)
+    P, N = sh_surface(_t(th0.astype(np.float32)), _t(dirs.astype(np.float32)))
+    rp, rn, _ = synth.sh_surface(th0, dirs.astype(np.float32).astype(np.float64))
+    assert np.abs(P.cpu().numpy() - rp).max() < 2e-6
+    assert _angle_deg(N.cpu().numpy(), rn).max() < 0.01
+    rng = np.random.default_rng(0)
+    dpp = rng.standard_normal((5000, 3)).astype(np.float32)
+    dnn = rng.standard_normal((5000, 3)).astype(np.float32)
+    rec = W(16, 10)
+    d = sh_surface_backward(rec, _t(th0.astype(np.float32)), _t(dirs.astype(np.float32)), _t(dpp), _t(dnn))
+    want = synth.sh_surface_vjp(th0, dirs.astype(np.float32).astype(np.float64), dpp, dnn)
+    rel = np.linalg.norm(d.cpu().numpy() - want) / np.linalg.norm(want)
+    assert rel < 1e-4, rel
+    rec.close()
+
+
+@pytest.mark.slow
+def test_sphere64_sampled_against_analytic_and_oracle(W):
+    # the 4,096-point sphere at 64^3: every node against |x - c| - r (bounds of
+    # the discretisation), sampled nodes against the oracle's exact phi
+    p, n = synth.sphere_cloud()
+    res = 64
+    rec = W(res, len(p))
+    sdf, nrm = rec.reconstruct(_t(p), _t(n), BBOX, res)
+    phi = sdf.cpu().numpy().astype(np.float64)
+    h = 1.0 / res
+    X = OG.node_positions(OG.grid_lo(BBOX), h, res)
+    ana = np.linalg.norm(X - 0.5, axis=-1) - 0.3
+    band = np.abs(ana) < 5 * h
+    assert np.abs(phi - ana)[band].max() <= 0.5 * h
+    ref = OP.forward_to_mesh(p, n, BBOX, res)
+    lin = np.random.default_rng(3).choice(res ** 3, 3000, replace=False)
+    ophi, _, _ = OP.sdf_at(ref, lin)
+    assert np.abs(phi.reshape(-1)[lin] - ophi).max() <= SDF_TOL
+    rec.close()
