@@ -80,7 +80,8 @@ typedef struct {
   int64_t mesh_capacity;     /* maximum triangles; 0 = default 16 * max_res^2 */
   int32_t use_graphs;        /* record the solver's fixed launch sequence once as a CUDA graph (default 1) */
   int32_t stage_timing;      /* bracket each stage with CUDA events on the call's stream (default 0) */
-  int32_t reserved[6];
+  int32_t reserved[5];
+  double  tol_rel_adjoint;   /* adjoint solve: stop when ||g - A lambda|| <= tol * ||g|| (default 1e-9) */
 } wgeo_options;
 
 /* Stage ids reported by wgeo_stage_times. */

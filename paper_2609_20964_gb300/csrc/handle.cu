@@ -22,7 +22,7 @@ struct Layout {
   size_t total = 0;
   size_t off_b32, off_chi32, off_chi64, off_r32, off_e32, off_phi, off_ctri, off_dphi64, off_dchi64,
       off_lam64, off_lam32, off_levels, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
-      off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_tris, off_pyr, off_partials,
+      off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_pyr, off_partials,
       off_scan, off_state;
   size_t n_partials, n_scan;
   int64_t cap;
@@ -44,17 +44,17 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   size_t c = 0;
   L.off_b32 = take(c, 4 * N);
   L.off_chi32 = take(c, 4 * N);
-  L.off_chi64 = take(c, 8 * N);
+  L.off_chi64 = take(c, 16 * N);                       // two FP64 buffers
   L.off_r32 = take(c, 4 * N);
   L.off_e32 = take(c, 4 * N);
   L.off_phi = take(c, 4 * N);
   L.off_ctri = take(c, keep ? 4 * N : 0);
   L.off_dphi64 = take(c, keep ? 8 * N : 0);
   L.off_dchi64 = take(c, keep ? 8 * N : 0);
-  L.off_lam64 = take(c, keep ? 8 * N : 0);
+  L.off_lam64 = take(c, keep ? 16 * N : 0);
   L.off_lam32 = take(c, keep ? 4 * N : 0);
   const size_t half = (size_t)(R / 2 + 1);
-  const size_t lev = 2 * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);
+  const size_t lev = 3 * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);
   L.off_levels = take(c, 4 * lev);
   const size_t Pp = (size_t)(P > 0 ? P : 1);
   L.off_pcell = take(c, 4 * Pp);
@@ -70,6 +70,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   const size_t nbricks = (size_t)nb * nb * nb;
   L.off_brick_count = take(c, 4 * (nbricks + 1));
   L.off_brick_off = take(c, 4 * (nbricks + 2));
+  L.off_leaf_off = take(c, 4 * (8 * nbricks + 2));
   int64_t cap = opt.mesh_capacity > 0 ? opt.mesh_capacity : (int64_t)16 * R * R;
   if (cap < 4096) cap = 4096;
   L.cap = cap;
@@ -85,7 +86,8 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
 }
 
 bool valid_opt(const wgeo_options& o) {
-  return o.tol_rel >= 0.0 && o.max_vcycles >= 0 && o.max_vcycles <= 1000 && o.max_refine >= 0 &&
+  return o.tol_rel >= 0.0 && o.tol_rel_adjoint >= 0.0 && o.max_vcycles >= 0 && o.max_vcycles <= 1000 &&
+         o.max_refine >= 0 &&
          o.max_refine <= 200 && o.vcycles_per_refine >= 1 && o.vcycles_per_refine <= 20 &&
          (o.precision == WGEO_PREC_MIXED || o.precision == WGEO_PREC_FP32) && o.mesh_capacity >= 0 &&
          o.mesh_capacity < (int64_t)1 << 31;
@@ -170,6 +172,7 @@ int wgeo_default_options(wgeo_options* opt) {
   opt->keep_for_backward = 1;
   opt->mesh_capacity = 0;
   opt->use_graphs = 1;
+  opt->tol_rel_adjoint = 1e-9;
   return WGEO_OK;
 }
 
@@ -208,16 +211,19 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->arena_bytes = L.total;
   char* a = h->arena;
   const bool keep = o.keep_for_backward != 0;
+  const size_t N = (size_t)max_res * max_res * max_res;
   h->b32 = (float*)(a + L.off_b32);
   h->chi32 = (float*)(a + L.off_chi32);
-  h->chi64 = (double*)(a + L.off_chi64);
+  h->chi64[0] = (double*)(a + L.off_chi64);
+  h->chi64[1] = h->chi64[0] + N;
   h->r32 = (float*)(a + L.off_r32);
   h->e32 = (float*)(a + L.off_e32);
   h->phi = (float*)(a + L.off_phi);
   h->ctri = keep ? (int*)(a + L.off_ctri) : nullptr;
   h->dphi64 = keep ? (double*)(a + L.off_dphi64) : nullptr;
   h->dchi64 = keep ? (double*)(a + L.off_dchi64) : nullptr;
-  h->lam64 = keep ? (double*)(a + L.off_lam64) : nullptr;
+  h->lam64[0] = keep ? (double*)(a + L.off_lam64) : nullptr;
+  h->lam64[1] = keep ? h->lam64[0] + N : nullptr;
   h->lam32 = keep ? (float*)(a + L.off_lam32) : nullptr;
   h->level_pool = (float*)(a + L.off_levels);
   h->pcell = (int*)(a + L.off_pcell);
@@ -229,6 +235,7 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->tile_cursor = (int*)(a + L.off_tile_cursor);
   h->brick_count = (int*)(a + L.off_brick_count);
   h->brick_off = (int*)(a + L.off_brick_off);
+  h->leaf_off = (int*)(a + L.off_leaf_off);
   h->mesh_cap = L.cap;
   h->tris = (Tri*)(a + L.off_tris);
   h->pyramid = (float4*)(a + L.off_pyr);
@@ -237,7 +244,7 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->scan_tmp_elems = L.n_scan;
   h->dstate = (DevState*)(a + L.off_state);
   if (upload_mc_table() != WGEO_OK || cudaMemset(h->dstate, 0, sizeof(DevState)) != cudaSuccess ||
-      cudaMemset(h->chi64, 0, 8 * (size_t)max_res * max_res * max_res) != cudaSuccess) {
+      cudaMemset(h->chi64[0], 0, 16 * N) != cudaSuccess) {
     cudaFree(h->arena);
     delete h;
     return WGEO_ERR_CUDA;
@@ -291,18 +298,13 @@ int wgeo_reconstruct(wgeo_handle* h, const float* points, const float* normals, 
   reset_status_kernel<<<1, 1, 0, s>>>(h->dstate);
   WGEO_LAUNCH_CHECK();
   const bool warm = h->opt.warm_start && h->chi_valid_for_warm && h->warm_res == res;
-  if (!warm) {
-    if (h->opt.precision == WGEO_PREC_FP32)
-      WGEO_CUDA_TRY(cudaMemsetAsync(h->chi32, 0, 4 * N, s));
-    else
-      WGEO_CUDA_TRY(cudaMemsetAsync(h->chi64, 0, 8 * N, s));
-  }
+  if (!warm && h->opt.precision == WGEO_PREC_FP32) WGEO_CUDA_TRY(cudaMemsetAsync(h->chi32, 0, 4 * N, s));
   int slot = stage_begin(h, kStSplat, s);
   int rc = launch_bin_sort_splat(h, points, normals, n, res, s);
   if (rc) return rc;
   stage_end(h, kStSplat, slot, s);
   slot = stage_begin(h, kStSolve, s);
-  rc = launch_solve(h, res, 0, s);
+  rc = launch_solve(h, res, 0, !warm, s);
   if (rc) return rc;
   stage_end(h, kStSolve, slot, s);
   slot = stage_begin(h, kStIso, s);

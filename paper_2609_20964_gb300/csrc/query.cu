@@ -371,8 +371,10 @@ __device__ __forceinline__ void dV_at(const double* __restrict__ lam, int x, int
 
 __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4* __restrict__ pfrac,
                                      const float4* __restrict__ pnrm, int64_t np,
-                                     const double* __restrict__ lam, QParams g,
+                                     const double* __restrict__ lam0, const double* __restrict__ lam1,
+                                     const int* __restrict__ lam_idx, QParams g,
                                      float* __restrict__ dpts, float* __restrict__ dnrm) {
+  const double* __restrict__ lam = (*lam_idx) ? lam1 : lam0;
   const int n = g.res;
   const double inv2h = 0.5 / g.h;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
@@ -500,14 +502,14 @@ int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_
   }
   stage_end(h, kStBwdSurf, slot, s);
   slot = stage_begin(h, kStBwdSolve, s);
-  WGEO_CUDA_TRY(cudaMemsetAsync(h->lam64, 0, sizeof(double) * N, s));
-  int rc = launch_solve(h, res, 1, s);
+  int rc = launch_solve(h, res, 1, true, s);
   if (rc) return rc;
   stage_end(h, kStBwdSolve, slot, s);
   slot = stage_begin(h, kStBwdSplat, s);
   if (h->npts > 0) {
     splat_adjoint_kernel<<<grid_blocks(h->npts, 128, 152 * 64), 128, 0, s>>>(
-        h->pcell, h->pfrac, h->pnrm, h->npts, h->lam64, g, d_points, d_normals);
+        h->pcell, h->pfrac, h->pnrm, h->npts, h->lam64[0], h->lam64[1], &h->dstate->bwd.xidx, g,
+        d_points, d_normals);
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStBwdSplat, slot, s);

@@ -7,20 +7,30 @@
 // mean out of the right-hand side; chi is defined up to an additive constant.
 //
 // Mixed precision (default): FP64 iterative refinement around FP32 multigrid.
-//   r = b - L x64 in FP64 (block partial sums of r and r^2 in FP64, reduced in
-//   a fixed order), convergence test ||r - mean r|| <= tol ||b - mean b||,
-//   then V-cycles in FP32 on L e = r - mean(r), x64 += e.
+//   One fused FP64 pass per refinement step adds the last FP32 correction to
+//   x64 (ping-pong buffers selected by a device-side index, so early exit
+//   needs no host decision), writes the FP32 copy and the residual
+//   r = b - L x64, and sums r and r^2 per block in FP64; a one-block kernel
+//   reduces the sums in a fixed order and tests ||r - mean r|| <= tol ||b||.
+//   The correction solves L e = r - mean(r) with V-cycles in FP32.
 // Plain FP32 (comparator): V-cycles directly on x32 with an FP32 residual.
 //
-// Multigrid: cell-centred, halving while the grid is even and larger than 8;
-// red-black Gauss-Seidel (2 pre, 2 post sweeps), residual restricted by
-// summing the 8 children with weight 1/2 (average times H^2/h^2 = 4 for the
-// unit-free operator), trilinear prolongation with mirrored Neumann edges,
-// coarsest grid (<= 16^3) solved by Gauss-Seidel sweeps in one CTA.
+// Multigrid: cell-centred, halving while even and larger than 8; red-black
+// Gauss-Seidel, 2 pre- and 2 post-sweeps; residual restricted with weight 1/2
+// on the 8 children (average x H^2/h^2 for the unit-free operator); trilinear
+// prolongation (3/4, 1/4 per axis, mirrored at the walls).  Levels larger than
+// 16^3 use two fused z-marching kernels per V-cycle: a CTA owns a 32 x 16
+// column tile and a 32-plane z chunk, keeps a ring of planes in shared memory
+// and pipelines the four half-sweeps (half-sweep s works s planes behind the
+// newest), which reproduces global red-black Gauss-Seidel exactly while each
+// field is read from HBM once; the pre-smoothing kernel also forms the
+// residual and restricts it, the post-smoothing kernel adds the prolonged
+// coarse correction while loading.  Grids of at most 16^3 run a whole
+// V-cycle hierarchy in one CTA's shared memory.
 //
-// Every kernel after the first convergence test reads the solve's `done` flag
-// and returns at once when it is set, so the fixed launch sequence (recorded
-// once as a CUDA graph) stops doing work as soon as the tolerance is met.
+// Every kernel of the fixed launch sequence reads the solve's `done` flag and
+// returns at once when it is set, so the sequence (recorded once as a CUDA
+// graph) stops doing work as soon as the tolerance is met.
 #include "wgeo_internal.cuh"
 
 namespace wgeo {
@@ -28,32 +38,51 @@ namespace wgeo {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kNu1 = 2, kNu2 = 2;
+constexpr int kNu = 2;              // red-black sweeps before and after the coarse correction
+constexpr int kTX = 32, kTY = 16, kZC = 32;
+constexpr int kSmThreads = 512;
+constexpr int kSmallN = 16;         // levels up to 16^3 are solved in one CTA
 
 __device__ __forceinline__ int64_t lin(int i, int j, int k, int n) {
   return ((int64_t)k * n + j) * n + i;
 }
 
+struct Pair64 {
+  double* buf[2];
+};
+
+// ---------------------------------------------------------------- FP64 refinement
+// x64_new = x64 + e (e may be null: no correction this step; cold: x64 := 0),
+// x32 = (float) x64_new, r32 = b - L x64_new, per-block sums of r and r^2.
 template <typename TB>
-__global__ void residual64_kernel(const double* __restrict__ x, const TB* __restrict__ b, int n,
-                                  float* __restrict__ r32, double* __restrict__ partials,
-                                  const int* __restrict__ gate) {
-  if (*gate) return;
+__global__ void update_residual_kernel(Pair64 xp, const float* __restrict__ e, const TB* __restrict__ b,
+                                       int n, float* __restrict__ r32, float* __restrict__ x32,
+                                       double* __restrict__ partials, SolveState* ss) {
+  if (ss->done) return;
   __shared__ double red[32];
+  const int cur = ss->xidx;
+  const bool cold = ss->cold != 0;
+  const double* __restrict__ xin = xp.buf[cur];
+  double* __restrict__ xout = xp.buf[e ? cur ^ 1 : cur];
   const int64_t N = (int64_t)n * n * n;
   double s1 = 0.0, s2 = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
-    const double xc = x[t];
-    double acc = 0.0;
-    if (i > 0) acc += x[t - 1] - xc;
-    if (i < n - 1) acc += x[t + 1] - xc;
-    if (j > 0) acc += x[t - n] - xc;
-    if (j < n - 1) acc += x[t + n] - xc;
-    if (k > 0) acc += x[t - (int64_t)n * n] - xc;
-    if (k < n - 1) acc += x[t + (int64_t)n * n] - xc;
+    double xc = 0.0, acc = 0.0;
+    if (!cold) {
+      xc = xin[t] + (e ? (double)e[t] : 0.0);
+      auto nb = [&](int64_t q) { return xin[q] + (e ? (double)e[q] : 0.0); };
+      if (i > 0) acc += nb(t - 1) - xc;
+      if (i < n - 1) acc += nb(t + 1) - xc;
+      if (j > 0) acc += nb(t - n) - xc;
+      if (j < n - 1) acc += nb(t + n) - xc;
+      if (k > 0) acc += nb(t - (int64_t)n * n) - xc;
+      if (k < n - 1) acc += nb(t + (int64_t)n * n) - xc;
+    }
     const double r = (double)b[t] - acc;
+    if (e || cold) xout[t] = xc;
+    x32[t] = (float)xc;
     r32[t] = (float)r;
     s1 += r;
     s2 += r * r;
@@ -92,9 +121,7 @@ __global__ void residual32_kernel(const float* __restrict__ x, const float* __re
   s1 = warp_sumf(s1);
   s2 = warp_sumf(s2);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    red[w] = s1;
-  }
+  if (l == 0) red[w] = s1;
   __syncthreads();
   float t1 = 0.f;
   if (threadIdx.x < 32) t1 = warp_sumf(l < kThreads / 32 ? red[l] : 0.f);
@@ -110,10 +137,11 @@ __global__ void residual32_kernel(const float* __restrict__ x, const float* __re
 }
 
 // Fixed-order reduction of the residual partials and the convergence test.
-// fp32 != 0: sums in float (the plain FP32 comparator's dots).
+// fp32 != 0: sums in float (the plain FP32 comparator's dots).  flip != 0:
+// this step wrote the corrected x64 into the other buffer.
 __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks, int64_t N,
-                                SolveState* ss, DevState* st, double tol, int step, int last,
-                                int fp32) {
+                                SolveState* ss, DevState* st, double tol, int step, int last, int fp32,
+                                int flip) {
   if (ss->done) return;
   __shared__ double red[32];
   double s1 = 0.0, s2 = 0.0;
@@ -136,6 +164,8 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks
     s2 = block_sum<1024>(s2, red);
   }
   if (threadIdx.x == 0) {
+    if (flip) ss->xidx ^= 1;
+    ss->cold = 0;
     const double mean = s1 / (double)N;
     const double rn = sqrt(fmax(s2 - s1 * mean, 0.0));
     ss->rmean = mean;
@@ -152,161 +182,288 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks
   }
 }
 
-__global__ void solve_begin_kernel(SolveState* ss) {
+__global__ void solve_begin_kernel(SolveState* ss, int cold) {
   ss->done = 0;
   ss->iter = 0;
   ss->rel = 0.0;
   ss->rmean = 0.0;
+  ss->cold = cold;
 }
 
-__global__ void zero_kernel(float* __restrict__ x, int64_t N, const int* __restrict__ gate) {
-  if (*gate) return;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x)
-    x[t] = 0.f;
+// ---------------------------------------------------------------- fused smoothers
+template <bool PRE>
+struct SmGeom {
+  static constexpr int H = PRE ? 2 * kNu + 1 : 2 * kNu;   // halo of the loaded tile
+  static constexpr int WX = kTX + 2 * H, WY = kTY + 2 * H, P = WX * WY;
+  static constexpr int RX = PRE ? 2 * kNu + 3 : 2 * kNu + 2;   // x plane ring
+  static constexpr int RB = PRE ? 2 * kNu + 2 : 2 * kNu + 1;   // b plane ring
+  static constexpr size_t smem = sizeof(float) * ((size_t)(RX + RB) * P + (PRE ? (kTX / 2) * (kTY / 2) : 0));
+};
+
+__device__ __forceinline__ float prolong_at(const float* __restrict__ xc, int nc, int gx, int gy, int gz) {
+  const int I = gx >> 1, J = gy >> 1, K = gz >> 1;
+  const int I2 = min(max((gx & 1) ? I + 1 : I - 1, 0), nc - 1);
+  const int J2 = min(max((gy & 1) ? J + 1 : J - 1, 0), nc - 1);
+  const int K2 = min(max((gz & 1) ? K + 1 : K - 1, 0), nc - 1);
+  const float a = 0.75f, c = 0.25f;
+  return a * a * a * xc[lin(I, J, K, nc)] + c * a * a * xc[lin(I2, J, K, nc)] +
+         a * c * a * xc[lin(I, J2, K, nc)] + a * a * c * xc[lin(I, J, K2, nc)] +
+         c * c * a * xc[lin(I2, J2, K, nc)] + c * a * c * xc[lin(I2, J, K2, nc)] +
+         a * c * c * xc[lin(I, J2, K2, nc)] + c * c * c * xc[lin(I2, J2, K2, nc)];
 }
 
-// One colour of red-black Gauss-Seidel; colour of (i,j,k) is (i+j+k) & 1.
-__global__ void rbgs_kernel(float* __restrict__ x, const float* __restrict__ b,
-                            const double* __restrict__ shift, int n, int color,
-                            const int* __restrict__ gate) {
+// PRE: x_out = 2 red-black sweeps (red first) of x_in (or of 0 when ZERO), and
+//      bc = 1/2 * sum of the children residuals b - L x_out.
+// POST: x_out = 2 sweeps (black first) of x_in + P xc.
+template <bool PRE, bool ZERO>
+__global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restrict__ xin,
+                                                            float* __restrict__ xout,
+                                                            const float* __restrict__ b,
+                                                            const double* __restrict__ shift, int n,
+                                                            const float* __restrict__ xc,
+                                                            float* __restrict__ bc,
+                                                            const int* __restrict__ gate) {
   if (*gate) return;
-  const int half = n >> 1;
-  const int64_t M = (int64_t)half * n * n;
+  using G = SmGeom<PRE>;
+  extern __shared__ float sm[];
+  float* xs = sm;                       // RX planes
+  float* bs = sm + G::RX * G::P;        // RB planes
+  float* cacc = bs + G::RB * G::P;      // coarse accumulator (PRE)
+  const int X0 = blockIdx.x * kTX, Y0 = blockIdx.y * kTY, z0 = blockIdx.z * kZC;
+  const int z1 = min(z0 + kZC, n);
+  const int ax = max(X0 - G::H, 0), bx = min(X0 + kTX + G::H, n);
+  const int ay = max(Y0 - G::H, 0), by = min(Y0 + kTY + G::H, n);
+  const int zlo = max(z0 - G::H, 0), zhi = min(z1 + G::H, n);
   const float sh = shift ? (float)*shift : 0.f;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int ih = (int)(t % half);
-    const int64_t row = t / half;
-    const int j = (int)(row % n), k = (int)(row / n);
-    const int i = 2 * ih + ((j + k + color) & 1);
-    const int64_t p = lin(i, j, k, n);
-    float s = 0.f;
-    int cnt = 0;
-    if (i > 0) { s += x[p - 1]; ++cnt; }
-    if (i < n - 1) { s += x[p + 1]; ++cnt; }
-    if (j > 0) { s += x[p - n]; ++cnt; }
-    if (j < n - 1) { s += x[p + n]; ++cnt; }
-    if (k > 0) { s += x[p - (int64_t)n * n]; ++cnt; }
-    if (k < n - 1) { s += x[p + (int64_t)n * n]; ++cnt; }
-    x[p] = (s - (b[p] - sh)) / (float)cnt;
-  }
-}
-
-// bc(I,J,K) = 1/2 * sum over the 8 children of (b - shift - L x).
-__global__ void resid_restrict_kernel(const float* __restrict__ x, const float* __restrict__ b,
-                                      const double* __restrict__ shift, int n,
-                                      float* __restrict__ bc, const int* __restrict__ gate) {
-  if (*gate) return;
   const int nc = n >> 1;
-  const int64_t Mc = (int64_t)nc * nc * nc;
-  const float sh = shift ? (float)*shift : 0.f;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Mc;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int I = (int)(t % nc), J = (int)((t / nc) % nc), K = (int)(t / ((int64_t)nc * nc));
-    float acc = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
-      const int64_t p = lin(i, j, k, n);
-      const float xc = x[p];
-      float lx = 0.f;
-      if (i > 0) lx += x[p - 1] - xc;
-      if (i < n - 1) lx += x[p + 1] - xc;
-      if (j > 0) lx += x[p - n] - xc;
-      if (j < n - 1) lx += x[p + n] - xc;
-      if (k > 0) lx += x[p - (int64_t)n * n] - xc;
-      if (k < n - 1) lx += x[p + (int64_t)n * n] - xc;
-      acc += (b[p] - sh) - lx;
+  const int c0 = PRE ? 0 : 1;           // colour of the first half-sweep
+  const int zend = zhi + 2 * kNu + (PRE ? 1 : 0);
+  for (int zin = zlo; zin < zend; ++zin) {
+    if (zin < zhi) {
+      float* xp = xs + (zin % G::RX) * G::P;
+      float* bp = bs + (zin % G::RB) * G::P;
+      for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
+        const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
+        const bool in = gx >= ax && gx < bx && gy >= ay && gy < by;
+        float xv = 0.f, bv = 0.f;
+        if (in) {
+          const int64_t g = lin(gx, gy, zin, n);
+          if (!ZERO) xv = xin[g];
+          if (!PRE) xv += prolong_at(xc, nc, gx, gy, zin);
+          bv = b[g] - sh;
+        }
+        xp[c] = xv;
+        bp[c] = bv;
+      }
     }
-    bc[t] = 0.5f * acc;
-  }
-}
-
-// x_fine += P x_coarse (trilinear between coarse cell centres, 3/4-1/4 per axis,
-// the outside neighbour mirrored onto the edge cell).
-__global__ void prolong_kernel(const float* __restrict__ xc, float* __restrict__ x, int n,
-                               const int* __restrict__ gate) {
-  if (*gate) return;
-  const int nc = n >> 1;
-  const int64_t N = (int64_t)n * n * n;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    int I2 = (i & 1) ? I + 1 : I - 1;
-    int J2 = (j & 1) ? J + 1 : J - 1;
-    int K2 = (k & 1) ? K + 1 : K - 1;
-    I2 = min(max(I2, 0), nc - 1);
-    J2 = min(max(J2, 0), nc - 1);
-    K2 = min(max(K2, 0), nc - 1);
-    const float a = 0.75f, c = 0.25f;
-    const float v =
-        a * a * a * xc[lin(I, J, K, nc)] + c * a * a * xc[lin(I2, J, K, nc)] +
-        a * c * a * xc[lin(I, J2, K, nc)] + a * a * c * xc[lin(I, J, K2, nc)] +
-        c * c * a * xc[lin(I2, J2, K, nc)] + c * a * c * xc[lin(I2, J, K2, nc)] +
-        a * c * c * xc[lin(I, J2, K2, nc)] + c * c * c * xc[lin(I2, J2, K2, nc)];
-    x[t] += v;
-  }
-}
-
-// Coarsest grid (n^3 <= 4096): mean-projected right-hand side, Gauss-Seidel
-// sweeps in shared memory by one CTA.
-__global__ void __launch_bounds__(1024) coarse_kernel(float* __restrict__ x,
-                                                      const float* __restrict__ b,
-                                                      const double* __restrict__ shift, int n,
-                                                      int sweeps, const int* __restrict__ gate) {
-  if (*gate) return;
-  __shared__ float xs[4096];
-  __shared__ float bs[4096];
-  __shared__ double red[32];
-  const int N = n * n * n;
-  const float sh = shift ? (float)*shift : 0.f;
-  double s = 0.0;
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    bs[t] = b[t] - sh;
-    xs[t] = 0.f;
-    s += bs[t];
-  }
-  s = block_sum<1024>(s, red);
-  __shared__ float meanb;
-  if (threadIdx.x == 0) meanb = (float)(s / N);
-  __syncthreads();
-  for (int t = threadIdx.x; t < N; t += blockDim.x) bs[t] -= meanb;
-  __syncthreads();
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int color = 0; color < 2; ++color) {
-      for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        const int i = t % n, j = (t / n) % n, k = t / (n * n);
-        if (((i + j + k) & 1) != color) continue;
-        float acc = 0.f;
-        int cnt = 0;
-        if (i > 0) { acc += xs[t - 1]; ++cnt; }
-        if (i < n - 1) { acc += xs[t + 1]; ++cnt; }
-        if (j > 0) { acc += xs[t - n]; ++cnt; }
-        if (j < n - 1) { acc += xs[t + n]; ++cnt; }
-        if (k > 0) { acc += xs[t - n * n]; ++cnt; }
-        if (k < n - 1) { acc += xs[t + n * n]; ++cnt; }
-        xs[t] = cnt ? (acc - bs[t]) / (float)cnt : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int s = 1; s <= 2 * kNu; ++s) {
+      const int p = zin - s;
+      const int plo = zlo + (zlo > 0 ? s : 0), phi = zhi - (zhi < n ? s : 0);
+      if (p >= plo && p < phi) {
+        const int xlo = ax + (ax > 0 ? s : 0), xhi = bx - (bx < n ? s : 0);
+        const int ylo = ay + (ay > 0 ? s : 0), yhi = by - (by < n ? s : 0);
+        const int colour = c0 ^ ((s - 1) & 1);
+        float* xp = xs + (p % G::RX) * G::P;
+        const float* xm = (p > 0) ? xs + ((p - 1) % G::RX) * G::P : nullptr;
+        const float* xq = (p < n - 1) ? xs + ((p + 1) % G::RX) * G::P : nullptr;
+        const float* bp = bs + (p % G::RB) * G::P;
+        for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
+          const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
+          if (gx < xlo || gx >= xhi || gy < ylo || gy >= yhi || ((gx + gy + p) & 1) != colour) continue;
+          float acc = 0.f;
+          int cnt = 0;
+          if (gx > 0) { acc += xp[c - 1]; ++cnt; }
+          if (gx < n - 1) { acc += xp[c + 1]; ++cnt; }
+          if (gy > 0) { acc += xp[c - G::WX]; ++cnt; }
+          if (gy < n - 1) { acc += xp[c + G::WX]; ++cnt; }
+          if (xm) { acc += xm[c]; ++cnt; }
+          if (xq) { acc += xq[c]; ++cnt; }
+          xp[c] = (acc - bp[c]) / (float)cnt;
+        }
+      }
+      __syncthreads();
+    }
+    if (PRE) {
+      const int q = zin - 2 * kNu - 1;
+      if (q >= z0 && q < z1) {
+        const float* xp = xs + (q % G::RX) * G::P;
+        const float* xm = (q > 0) ? xs + ((q - 1) % G::RX) * G::P : nullptr;
+        const float* xq = (q < n - 1) ? xs + ((q + 1) % G::RX) * G::P : nullptr;
+        const float* bp = bs + (q % G::RB) * G::P;
+        for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
+          const int gx = X0 + c % kTX, gy = Y0 + c / kTX;
+          if (gx < n && gy < n) {
+            const int lc = (gy - Y0 + G::H) * G::WX + (gx - X0 + G::H);
+            xout[lin(gx, gy, q, n)] = xp[lc];
+          }
+        }
+        // one thread per coarse cell of this plane: residual of its 4 children, fixed order
+        for (int c = threadIdx.x; c < (kTX / 2) * (kTY / 2); c += blockDim.x) {
+          const int cx = c % (kTX / 2), cy = c / (kTX / 2);
+          float r = 0.f;
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) {
+            const int gx = X0 + 2 * cx + (ch & 1), gy = Y0 + 2 * cy + (ch >> 1);
+            if (gx >= n || gy >= n) continue;
+            const int lc = (gy - Y0 + G::H) * G::WX + (gx - X0 + G::H);
+            const float xv = xp[lc];
+            float lx = 0.f;
+            if (gx > 0) lx += xp[lc - 1] - xv;
+            if (gx < n - 1) lx += xp[lc + 1] - xv;
+            if (gy > 0) lx += xp[lc - G::WX] - xv;
+            if (gy < n - 1) lx += xp[lc + G::WX] - xv;
+            if (xm) lx += xm[lc] - xv;
+            if (xq) lx += xq[lc] - xv;
+            r += bp[lc] - lx;
+          }
+          if ((q & 1) == 0) {
+            cacc[c] = r;
+          } else {
+            const int gcx = (X0 >> 1) + cx, gcy = (Y0 >> 1) + cy;
+            if (gcx < nc && gcy < nc) bc[lin(gcx, gcy, q >> 1, nc)] = 0.5f * (cacc[c] + r);
+          }
+        }
+      }
+      __syncthreads();
+    } else {
+      const int p = zin - 2 * kNu;
+      if (p >= z0 && p < z1) {
+        const float* xp = xs + (p % G::RX) * G::P;
+        for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
+          const int gx = X0 + c % kTX, gy = Y0 + c / kTX;
+          if (gx < n && gy < n) {
+            const int lc = (gy - Y0 + G::H) * G::WX + (gx - X0 + G::H);
+            xout[lin(gx, gy, p, n)] = xp[lc];
+          }
+        }
       }
       __syncthreads();
     }
   }
-  for (int t = threadIdx.x; t < N; t += blockDim.x) x[t] = xs[t];
 }
 
-__global__ void update64_kernel(double* __restrict__ x64, const float* __restrict__ e, int64_t N,
-                                const int* __restrict__ gate) {
+// ---------------------------------------------------------------- small grids
+// A whole V-cycle hierarchy for n <= 16 in one CTA's shared memory: solves
+// L x = b - shift - mean approximately (2 V-cycles from zero), writes x.
+constexpr int kSmallCap = 4096 + 512 + 64 + 27 + 8;
+
+__device__ void small_rbgs(float* x, const float* b, int n, int color) {
+  const int N = n * n * n;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const int i = t % n, j = (t / n) % n, k = t / (n * n);
+    if (((i + j + k) & 1) != color) continue;
+    float acc = 0.f;
+    int cnt = 0;
+    if (i > 0) { acc += x[t - 1]; ++cnt; }
+    if (i < n - 1) { acc += x[t + 1]; ++cnt; }
+    if (j > 0) { acc += x[t - n]; ++cnt; }
+    if (j < n - 1) { acc += x[t + n]; ++cnt; }
+    if (k > 0) { acc += x[t - n * n]; ++cnt; }
+    if (k < n - 1) { acc += x[t + n * n]; ++cnt; }
+    x[t] = cnt ? (acc - b[t]) / (float)cnt : 0.f;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) small_vcycle_kernel(float* __restrict__ xg, const float* __restrict__ bg,
+                                                            const double* __restrict__ shift, int n0,
+                                                            const int* __restrict__ gate) {
   if (*gate) return;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x)
-    x64[t] += (double)e[t];
-}
-
-__global__ void to_f32_kernel(const double* __restrict__ x64, float* __restrict__ x32, int64_t N) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x)
-    x32[t] = (float)x64[t];
+  __shared__ float xs[kSmallCap];
+  __shared__ float bsm[kSmallCap];
+  __shared__ double red[32];
+  __shared__ float meanb;
+  int ns[8], off[8], L = 0;
+  {
+    int n = n0, o = 0;
+    while (true) {
+      ns[L] = n;
+      off[L] = o;
+      o += n * n * n;
+      ++L;
+      if ((n % 2) != 0 || n <= 4 || L == 8) break;
+      n /= 2;
+    }
+  }
+  const int N0 = n0 * n0 * n0;
+  const float sh = shift ? (float)*shift : 0.f;
+  double s = 0.0;
+  for (int t = threadIdx.x; t < N0; t += blockDim.x) {
+    const float v = bg[t] - sh;
+    bsm[t] = v;
+    xs[t] = 0.f;
+    s += v;
+  }
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) meanb = (float)(s / N0);
+  __syncthreads();
+  for (int t = threadIdx.x; t < N0; t += blockDim.x) bsm[t] -= meanb;
+  __syncthreads();
+  for (int cyc = 0; cyc < 2; ++cyc) {
+    // down
+    for (int l = 0; l < L - 1; ++l) {
+      const int n = ns[l];
+      float* x = xs + off[l];
+      const float* b = bsm + off[l];
+      for (int sw = 0; sw < kNu; ++sw) {
+        small_rbgs(x, b, n, 0);
+        small_rbgs(x, b, n, 1);
+      }
+      const int nc = ns[l + 1];
+      float* xcn = xs + off[l + 1];
+      float* bcn = bsm + off[l + 1];
+      for (int t = threadIdx.x; t < nc * nc * nc; t += blockDim.x) {
+        const int I = t % nc, J = (t / nc) % nc, K = t / (nc * nc);
+        float acc = 0.f;
+        for (int ch = 0; ch < 8; ++ch) {
+          const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+          const int p = (k * n + j) * n + i;
+          const float xv = x[p];
+          float lx = 0.f;
+          if (i > 0) lx += x[p - 1] - xv;
+          if (i < n - 1) lx += x[p + 1] - xv;
+          if (j > 0) lx += x[p - n] - xv;
+          if (j < n - 1) lx += x[p + n] - xv;
+          if (k > 0) lx += x[p - n * n] - xv;
+          if (k < n - 1) lx += x[p + n * n] - xv;
+          acc += b[p] - lx;
+        }
+        bcn[t] = 0.5f * acc;
+        xcn[t] = 0.f;
+      }
+      __syncthreads();
+    }
+    // coarsest
+    {
+      const int n = ns[L - 1];
+      float* x = xs + off[L - 1];
+      const float* b = bsm + off[L - 1];
+      const int sweeps = 2 * n * n + 16;
+      for (int sw = 0; sw < sweeps; ++sw) {
+        small_rbgs(x, b, n, 0);
+        small_rbgs(x, b, n, 1);
+      }
+    }
+    // up
+    for (int l = L - 2; l >= 0; --l) {
+      const int n = ns[l], nc = ns[l + 1];
+      float* x = xs + off[l];
+      const float* b = bsm + off[l];
+      const float* xcn = xs + off[l + 1];
+      for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
+        const int i = t % n, j = (t / n) % n, k = t / (n * n);
+        x[t] += prolong_at(xcn, nc, i, j, k);
+      }
+      __syncthreads();
+      for (int sw = 0; sw < kNu; ++sw) {
+        small_rbgs(x, b, n, 1);
+        small_rbgs(x, b, n, 0);
+      }
+    }
+  }
+  for (int t = threadIdx.x; t < N0; t += blockDim.x) xg[t] = xs[t];
 }
 
 __global__ void rhs_stats64_kernel(const double* __restrict__ b, int64_t N,
@@ -344,44 +501,34 @@ __global__ void rhs_stats_finalize_kernel(const double* __restrict__ partials, i
   }
 }
 
-int coarse_sweeps(int n) { return 2 * n * n + 16; }
-
-int vcycle(wgeo_handle* h, int l, float* x0, const float* b0, const double* shift0,
+// One V-cycle on level l.  x0 / x0b: level-0 iterate and its ping-pong
+// partner; b0, shift0: level-0 right-hand side.  zero0: level-0 x is zero.
+int vcycle(wgeo_handle* h, int l, float* x0, float* x0b, const float* b0, const double* shift0, bool zero0,
            const int* gate, cudaStream_t s) {
   const int n = h->levels[l].n;
   float* x = (l == 0) ? x0 : h->levels[l].x;
+  float* xb = (l == 0) ? x0b : h->levels[l].x2;
   const float* b = (l == 0) ? b0 : h->levels[l].b;
   const double* shift = (l == 0) ? shift0 : nullptr;
-  if (l == h->nlevels - 1) {
-    coarse_kernel<<<1, 1024, 0, s>>>(x, b, shift, n, coarse_sweeps(n), gate);
+  if (n <= kSmallN || l == h->nlevels - 1) {
+    small_vcycle_kernel<<<1, 1024, 0, s>>>(x, b, shift, n, gate);
     WGEO_LAUNCH_CHECK();
     return WGEO_OK;
   }
-  const int64_t N = (int64_t)n * n * n;
-  const int gb = grid_blocks(N / 2, kThreads, 152 * 32);
-  for (int sw = 0; sw < kNu1; ++sw)
-    for (int c = 0; c < 2; ++c) {
-      rbgs_kernel<<<gb, kThreads, 0, s>>>(x, b, shift, n, c, gate);
-      WGEO_LAUNCH_CHECK();
-    }
-  const int nc = n >> 1;
-  const int64_t Nc = (int64_t)nc * nc * nc;
-  resid_restrict_kernel<<<grid_blocks(Nc, kThreads, 152 * 32), kThreads, 0, s>>>(
-      x, b, shift, n, h->levels[l + 1].b, gate);
+  const dim3 grid(div_up(n, kTX), div_up(n, kTY), div_up(n, kZC));
+  const bool zero = (l == 0) ? zero0 : true;
+  if (zero)
+    smooth_kernel<true, true><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, nullptr,
+                                                                           h->levels[l + 1].b, gate);
+  else
+    smooth_kernel<true, false><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, nullptr,
+                                                                            h->levels[l + 1].b, gate);
   WGEO_LAUNCH_CHECK();
-  if (l + 1 != h->nlevels - 1) {
-    zero_kernel<<<grid_blocks(Nc, kThreads, 152 * 32), kThreads, 0, s>>>(h->levels[l + 1].x, Nc, gate);
-    WGEO_LAUNCH_CHECK();
-  }
-  int rc = vcycle(h, l + 1, x0, b0, shift0, gate, s);
+  int rc = vcycle(h, l + 1, x0, x0b, b0, shift0, zero0, gate, s);
   if (rc) return rc;
-  prolong_kernel<<<grid_blocks(N, kThreads, 152 * 32), kThreads, 0, s>>>(h->levels[l + 1].x, x, n, gate);
+  smooth_kernel<false, false><<<grid, kSmThreads, SmGeom<false>::smem, s>>>(xb, x, b, shift, n,
+                                                                            h->levels[l + 1].x, nullptr, gate);
   WGEO_LAUNCH_CHECK();
-  for (int sw = 0; sw < kNu2; ++sw)
-    for (int c = 1; c >= 0; --c) {
-      rbgs_kernel<<<gb, kThreads, 0, s>>>(x, b, shift, n, c, gate);
-      WGEO_LAUNCH_CHECK();
-    }
   return WGEO_OK;
 }
 
@@ -392,46 +539,44 @@ int enqueue_solve(wgeo_handle* h, int res, int mode, cudaStream_t s) {
   const int* gate = &ss->done;
   const bool fp32 = (mode == 0 && h->opt.precision == WGEO_PREC_FP32);
   const int rb = grid_blocks(N, kThreads, kPartials);
-  const double tol = h->opt.tol_rel;
-  solve_begin_kernel<<<1, 1, 0, s>>>(ss);
-  WGEO_LAUNCH_CHECK();
   if (fp32) {
+    const double tol = h->opt.tol_rel;
     const int maxv = h->opt.max_vcycles;
     for (int it = 0; it <= maxv; ++it) {
       residual32_kernel<<<rb, kThreads, 0, s>>>(h->chi32, h->b32, &ss->bmean, res, h->partials, gate);
       WGEO_LAUNCH_CHECK();
-      finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, tol, it, it == maxv, 1);
+      finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, tol, it, it == maxv, 1, 0);
       WGEO_LAUNCH_CHECK();
       if (it == maxv) break;
-      int rc = vcycle(h, 0, h->chi32, h->b32, &ss->bmean, gate, s);
+      int rc = vcycle(h, 0, h->chi32, h->r32, h->b32, &ss->bmean, false, gate, s);
       if (rc) return rc;
     }
     return WGEO_OK;
   }
-  double* x64 = mode == 0 ? h->chi64 : h->lam64;
+  const double tol = mode == 0 ? h->opt.tol_rel : h->opt.tol_rel_adjoint;
+  Pair64 xp;
+  xp.buf[0] = mode == 0 ? h->chi64[0] : h->lam64[0];
+  xp.buf[1] = mode == 0 ? h->chi64[1] : h->lam64[1];
   float* x32 = mode == 0 ? h->chi32 : h->lam32;
   const int maxr = h->opt.max_refine;
   const int nv = h->opt.vcycles_per_refine;
   for (int it = 0; it <= maxr; ++it) {
+    const float* e = it == 0 ? nullptr : h->e32;
     if (mode == 0)
-      residual64_kernel<float><<<rb, kThreads, 0, s>>>(x64, h->b32, res, h->r32, h->partials, gate);
+      update_residual_kernel<float><<<rb, kThreads, 0, s>>>(xp, e, h->b32, res, h->r32, x32, h->partials, ss);
     else
-      residual64_kernel<double><<<rb, kThreads, 0, s>>>(x64, h->dchi64, res, h->r32, h->partials, gate);
+      update_residual_kernel<double><<<rb, kThreads, 0, s>>>(xp, e, h->dchi64, res, h->r32, x32, h->partials, ss);
     WGEO_LAUNCH_CHECK();
-    finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, tol, it, it == maxr, 0);
+    finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, tol, it, it == maxr, 0, e ? 1 : 0);
     WGEO_LAUNCH_CHECK();
     if (it == maxr) break;
-    zero_kernel<<<grid_blocks(N, kThreads, 152 * 32), kThreads, 0, s>>>(h->e32, N, gate);
-    WGEO_LAUNCH_CHECK();
+    // correction: V-cycles on L e = r - mean(r); the FP32 copy x32 serves as the
+    // ping-pong partner (it is rewritten by the next refinement pass)
     for (int v = 0; v < nv; ++v) {
-      int rc = vcycle(h, 0, h->e32, h->r32, &ss->rmean, gate, s);
+      int rc = vcycle(h, 0, h->e32, x32, h->r32, &ss->rmean, v == 0, gate, s);
       if (rc) return rc;
     }
-    update64_kernel<<<grid_blocks(N, kThreads, 152 * 32), kThreads, 0, s>>>(x64, h->e32, N, gate);
-    WGEO_LAUNCH_CHECK();
   }
-  to_f32_kernel<<<grid_blocks(N, kThreads, 152 * 32), kThreads, 0, s>>>(x64, x32, N);
-  WGEO_LAUNCH_CHECK();
   return WGEO_OK;
 }
 
@@ -444,22 +589,34 @@ int coarsest_size(int res) {
 }
 
 int build_levels(wgeo_handle* h, int res) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(smooth_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SmGeom<true>::smem);
+    cudaFuncSetAttribute(smooth_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SmGeom<true>::smem);
+    cudaFuncSetAttribute(smooth_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SmGeom<false>::smem);
+    attr_done = true;
+  }
   int n = res;
   int l = 0;
   float* pool = h->level_pool;
   h->levels[0].n = n;
   h->levels[0].x = nullptr;
+  h->levels[0].x2 = nullptr;
   h->levels[0].b = nullptr;
   while ((n % 2) == 0 && n > 8) {
     n /= 2;
     ++l;
     if (l >= kMaxLevels) return WGEO_ERR_INVALID_ARG;
     const int64_t M = (int64_t)n * n * n;
+    const int64_t Ma = (M + 63) / 64 * 64;
     h->levels[l].n = n;
     h->levels[l].x = pool;
-    pool += (M + 63) / 64 * 64;
-    h->levels[l].b = pool;
-    pool += (M + 63) / 64 * 64;
+    h->levels[l].x2 = pool + Ma;
+    h->levels[l].b = pool + 2 * Ma;
+    pool += 3 * Ma;
   }
   if (n > 16) return WGEO_ERR_INVALID_ARG;
   h->nlevels = l + 1;
@@ -470,15 +627,18 @@ int build_levels(wgeo_handle* h, int res) {
 // options), and every pointer it uses is owned by the handle, so it is
 // recorded once as a CUDA graph and replayed; while the caller's stream is
 // itself being captured the kernels are enqueued directly instead.
-int launch_solve(wgeo_handle* h, int res, int mode, cudaStream_t s) {
+int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
   const int64_t N = (int64_t)res * res * res;
+  SolveState* ss = mode == 0 ? &h->dstate->fwd : &h->dstate->bwd;
   if (mode == 1) {
     const int rb = grid_blocks(N, kThreads, kPartials);
     rhs_stats64_kernel<<<rb, kThreads, 0, s>>>(h->dchi64, N, h->partials);
     WGEO_LAUNCH_CHECK();
-    rhs_stats_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, &h->dstate->bwd);
+    rhs_stats_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss);
     WGEO_LAUNCH_CHECK();
   }
+  solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0);
+  WGEO_LAUNCH_CHECK();
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   WGEO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
   if (!h->opt.use_graphs || cap != cudaStreamCaptureStatusNone) return enqueue_solve(h, res, mode, s);

@@ -258,14 +258,24 @@ __device__ __forceinline__ int cube_code(const float* __restrict__ chi, int i, i
   return code;
 }
 
+// Cube (i,j,k) of a 4^3 brick handled by thread t: Morton order inside the
+// brick, so the 8 cubes of each 2^3 sub-brick (an octree leaf) are the
+// contiguous threads 8k..8k+7 and their triangles are contiguous in memory.
+__device__ __forceinline__ void brick_cube(int t, int& lx, int& ly, int& lz) {
+  lx = (t & 1) | (((t >> 3) & 1) << 1);
+  ly = ((t >> 1) & 1) | (((t >> 4) & 1) << 1);
+  lz = ((t >> 2) & 1) | (((t >> 5) & 1) << 1);
+}
+
 // One CTA (64 threads) per 4^3 brick of cubes.
 __global__ void __launch_bounds__(64) mc_count_kernel(const float* __restrict__ chi, SurfParams g,
                                                       const DevState* __restrict__ st,
                                                       int* __restrict__ brick_count) {
   const int br = blockIdx.x;
   const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
-  const int i = bx * kBrick + (threadIdx.x & 3), j = by * kBrick + ((threadIdx.x >> 2) & 3),
-            k = bz * kBrick + (threadIdx.x >> 4);
+  int lx, ly, lz;
+  brick_cube(threadIdx.x, lx, ly, lz);
+  const int i = bx * kBrick + lx, j = by * kBrick + ly, k = bz * kBrick + lz;
   const int m = g.res - 1;
   int cnt = 0;
   if (i < m && j < m && k < m) cnt = c_mc_count[cube_code(chi, i, j, k, g.res, st->c)];
@@ -277,9 +287,10 @@ __global__ void __launch_bounds__(64) mc_count_kernel(const float* __restrict__ 
 }
 
 __global__ void mc_total_kernel(const int* __restrict__ brick_off, int nbricks, int64_t cap,
-                                DevState* st) {
+                                int* __restrict__ leaf_off, DevState* st) {
   const long long T = brick_off[nbricks];
   st->ntris = T;
+  leaf_off[8 * (int64_t)nbricks] = brick_off[nbricks];
   if (T > cap) atomicOr(&st->status, WGEO_STATUS_MESH_CAPACITY);
   if (T == 0) atomicOr(&st->status, WGEO_STATUS_EMPTY_SURFACE);
 }
@@ -297,16 +308,22 @@ __device__ __forceinline__ void edge_lower_offset(int e, int& ox, int& oy, int& 
   oz = o[2];
 }
 
+// Emits each brick's triangles contiguously (Morton cube order) and the
+// triangle offset of each of its 8 sub-bricks (octree leaves).
 __global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ chi, SurfParams g,
                                                      const DevState* __restrict__ st,
                                                      const int* __restrict__ brick_off, int64_t cap,
-                                                     Tri* __restrict__ tris) {
+                                                     Tri* __restrict__ tris, int* __restrict__ leaf_off) {
   const int br = blockIdx.x;
   const int base = brick_off[br];
-  if (brick_off[br + 1] == base) return;
+  if (brick_off[br + 1] == base) {
+    if (threadIdx.x < 8) leaf_off[8 * (int64_t)br + threadIdx.x] = base;
+    return;
+  }
   const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
-  const int i = bx * kBrick + (threadIdx.x & 3), j = by * kBrick + ((threadIdx.x >> 2) & 3),
-            k = bz * kBrick + (threadIdx.x >> 4);
+  int lx, ly, lz;
+  brick_cube(threadIdx.x, lx, ly, lz);
+  const int i = bx * kBrick + lx, j = by * kBrick + ly, k = bz * kBrick + lz;
   const int n = g.res, m = n - 1;
   const double c = st->c;
   int code = 0, cnt = 0;
@@ -314,7 +331,6 @@ __global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ c
     code = cube_code(chi, i, j, k, n, c);
     cnt = c_mc_count[code];
   }
-  // exclusive scan of cnt over the 64 threads (brick order: x fastest)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int incl = cnt;
 #pragma unroll
@@ -326,6 +342,7 @@ __global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ c
   if (lane == 31) wt[w] = incl;
   __syncthreads();
   const int excl = incl - cnt + (w ? wt[0] : 0);
+  if ((threadIdx.x & 7) == 0) leaf_off[8 * (int64_t)br + (threadIdx.x >> 3)] = base + excl;
   for (int q = 0; q < cnt; ++q) {
     const int64_t idx = (int64_t)base + excl + q;
     if (idx >= cap) break;
@@ -351,120 +368,201 @@ __global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ c
   }
 }
 
-// ---- bounding-box octree over bricks: level 0 = bricks, level l+1 halves
-__global__ void pyr_leaf_kernel(const Tri* __restrict__ tris, const int* __restrict__ brick_off,
-                                int nbricks, int64_t cap, float4* __restrict__ pyr) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbricks; b += gridDim.x * blockDim.x) {
-    const int64_t s0 = brick_off[b];
-    const int64_t s1 = min((int64_t)brick_off[b + 1], cap);
-    float3 lo = make_float3(INFINITY, INFINITY, INFINITY);
-    float3 hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
-    for (int64_t t = s0; t < s1; ++t) {
-      const Tri tr = tris[t];
-      const float4 v[3] = {tr.a, tr.b, tr.c};
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        lo.x = fminf(lo.x, v[q].x);
-        lo.y = fminf(lo.y, v[q].y);
-        lo.z = fminf(lo.z, v[q].z);
-        hi.x = fmaxf(hi.x, v[q].x);
-        hi.y = fmaxf(hi.y, v[q].y);
-        hi.z = fmaxf(hi.z, v[q].z);
-      }
-    }
-    pyr[2 * b] = make_float4(lo.x, lo.y, lo.z, 0.f);
-    pyr[2 * b + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
-  }
-}
-
-__global__ void pyr_up_kernel(float4* __restrict__ pyr, int64_t off_child, int dchild, int64_t off_parent,
-                              int dparent) {
-  const int64_t np = (int64_t)dparent * dparent * dparent;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < np;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % dparent), y = (int)((t / dparent) % dparent), z = (int)(t / ((int64_t)dparent * dparent));
-    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-    for (int c = 0; c < 8; ++c) {
-      const int cx = 2 * x + (c & 1), cy = 2 * y + ((c >> 1) & 1), cz = 2 * z + (c >> 2);
-      if (cx >= dchild || cy >= dchild || cz >= dchild) continue;
-      const int64_t ci = off_child + ((int64_t)cz * dchild + cy) * dchild + cx;
-      const float4 a = pyr[2 * ci], b = pyr[2 * ci + 1];
-      lo.x = fminf(lo.x, a.x);
-      lo.y = fminf(lo.y, a.y);
-      lo.z = fminf(lo.z, a.z);
-      hi.x = fmaxf(hi.x, b.x);
-      hi.y = fmaxf(hi.y, b.y);
-      hi.z = fmaxf(hi.z, b.z);
-    }
-    pyr[2 * (off_parent + t)] = lo;
-    pyr[2 * (off_parent + t) + 1] = hi;
-  }
-}
-
+// ---- octree of "pucks" over the leaves (2^3-cube sub-bricks).  A puck is a
+// solid cylinder (centre c, unit axis n, radius r, half-thickness t) holding
+// every vertex of the node's triangles, hence (by convexity) the triangles
+// themselves; its exact distance is a lower bound on their distance.  For a
+// smooth patch the cylinder is thin and oriented along the surface normal, so
+// the bound stays tight even for far, oblique queries.  Empty node: r < 0.
 struct PyrInfo {
   int nlev;
   int dim[12];
   long long off[12];
 };
 
-__device__ __forceinline__ float box_dist2(const float3 p, const float4 lo, const float4 hi) {
-  if (lo.x > hi.x) return INFINITY;
-  const float dx = fmaxf(fmaxf(lo.x - p.x, 0.f), p.x - hi.x);
-  const float dy = fmaxf(fmaxf(lo.y - p.y, 0.f), p.y - hi.y);
-  const float dz = fmaxf(fmaxf(lo.z - p.z, 0.f), p.z - hi.z);
-  return dx * dx + dy * dy + dz * dz;
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
+__device__ __forceinline__ int leaf_index(int lx, int ly, int lz, int nb) {
+  const int br = ((lz >> 1) * nb + (ly >> 1)) * nb + (lx >> 1);
+  return 8 * br + ((lx & 1) | ((ly & 1) << 1) | ((lz & 1) << 2));
+}
+
+constexpr float kPuckPad = 1e-5f;   // relative inflation: rounding of the bound stays conservative
+
+__global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const int* __restrict__ leaf_off, int nb,
+                                 int64_t cap, float4* __restrict__ pyr) {
+  const int nl = 2 * nb;
+  const int64_t nleaf = (int64_t)nl * nl * nl;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int lx = (int)(t % nl), ly = (int)((t / nl) % nl), lz = (int)(t / ((int64_t)nl * nl));
+    const int li = leaf_index(lx, ly, lz, nb);
+    const int64_t s0 = leaf_off[li];
+    const int64_t s1 = min((int64_t)leaf_off[li + 1], cap);
+    if (s1 <= s0) {
+      pyr[2 * t] = make_float4(0.f, 0.f, 0.f, -1.f);
+      pyr[2 * t + 1] = make_float4(0.f, 0.f, 1.f, 0.f);
+      continue;
+    }
+    float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
+    for (int64_t q = s0; q < s1; ++q) {
+      const Tri tr = tris[q];
+      const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
+      cs.x += a.x + b.x + c.x;
+      cs.y += a.y + b.y + c.y;
+      cs.z += a.z + b.z + c.z;
+      const float3 cr = cross3(sub3(b, a), sub3(c, a));
+      ns.x += cr.x;
+      ns.y += cr.y;
+      ns.z += cr.z;
+    }
+    const float inv = 1.f / (3.f * (float)(s1 - s0));
+    const float3 cc = make_float3(cs.x * inv, cs.y * inv, cs.z * inv);
+    const float nn = sqrtf(dot3(ns, ns));
+    const float3 nv = nn > 0.f ? make_float3(ns.x / nn, ns.y / nn, ns.z / nn) : make_float3(0.f, 0.f, 1.f);
+    float r = 0.f, th = 0.f;
+    for (int64_t q = s0; q < s1; ++q) {
+      const Tri tr = tris[q];
+      const float4 vv[3] = {tr.a, tr.b, tr.c};
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const float3 d = sub3(f3(vv[v]), cc);
+        const float z = dot3(d, nv);
+        const float rho2 = fmaxf(dot3(d, d) - z * z, 0.f);
+        th = fmaxf(th, fabsf(z));
+        r = fmaxf(r, sqrtf(rho2));
+      }
+    }
+    const float pad = kPuckPad * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cc.z) + r + th) + 1e-7f;
+    pyr[2 * t] = make_float4(cc.x, cc.y, cc.z, r * (1.f + kPuckPad) + pad);
+    pyr[2 * t + 1] = make_float4(nv.x, nv.y, nv.z, th * (1.f + kPuckPad) + pad);
+  }
+}
+
+// Parent puck from its (up to 8) children: axis = normalised sum of child axes
+// weighted by r^2, centre = weighted mean of child centres, then radius and
+// half-thickness that bound every child cylinder in the parent's frame.
+__global__ void puck_up_kernel(float4* __restrict__ pyr, int64_t off_child, int dchild, int64_t off_parent,
+                               int dparent) {
+  const int64_t np = (int64_t)dparent * dparent * dparent;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < np;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % dparent), y = (int)((t / dparent) % dparent), z = (int)(t / ((int64_t)dparent * dparent));
+    float4 A[8], B[8];
+    int nc = 0;
+    float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
+    float ws = 0.f;
+    for (int c = 0; c < 8; ++c) {
+      const int cx = 2 * x + (c & 1), cy = 2 * y + ((c >> 1) & 1), cz = 2 * z + (c >> 2);
+      if (cx >= dchild || cy >= dchild || cz >= dchild) continue;
+      const int64_t ci = off_child + ((int64_t)cz * dchild + cy) * dchild + cx;
+      const float4 a = pyr[2 * ci], b = pyr[2 * ci + 1];
+      if (a.w < 0.f) continue;
+      A[nc] = a;
+      B[nc] = b;
+      const float w = a.w * a.w + b.w * b.w + 1e-20f;
+      cs.x += w * a.x;
+      cs.y += w * a.y;
+      cs.z += w * a.z;
+      ns.x += w * b.x;
+      ns.y += w * b.y;
+      ns.z += w * b.z;
+      ws += w;
+      ++nc;
+    }
+    if (nc == 0) {
+      pyr[2 * (off_parent + t)] = make_float4(0.f, 0.f, 0.f, -1.f);
+      pyr[2 * (off_parent + t) + 1] = make_float4(0.f, 0.f, 1.f, 0.f);
+      continue;
+    }
+    const float3 cc = make_float3(cs.x / ws, cs.y / ws, cs.z / ws);
+    const float nn = sqrtf(dot3(ns, ns));
+    const float3 nv = nn > 1e-12f ? make_float3(ns.x / nn, ns.y / nn, ns.z / nn) : make_float3(0.f, 0.f, 1.f);
+    float r = 0.f, th = 0.f;
+    for (int q = 0; q < nc; ++q) {
+      const float3 d = sub3(make_float3(A[q].x, A[q].y, A[q].z), cc);
+      const float3 ni = make_float3(B[q].x, B[q].y, B[q].z);
+      const float cz = dot3(d, nv);
+      const float crho = sqrtf(fmaxf(dot3(d, d) - cz * cz, 0.f));
+      const float cosi = fminf(fabsf(dot3(nv, ni)), 1.f);
+      const float sini = sqrtf(fmaxf(1.f - cosi * cosi, 0.f));
+      th = fmaxf(th, fabsf(cz) + A[q].w * sini + B[q].w * cosi);
+      r = fmaxf(r, crho + A[q].w + B[q].w * sini);
+    }
+    const float pad = kPuckPad * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cc.z) + r + th) + 1e-7f;
+    pyr[2 * (off_parent + t)] = make_float4(cc.x, cc.y, cc.z, r * (1.f + kPuckPad) + pad);
+    pyr[2 * (off_parent + t) + 1] = make_float4(nv.x, nv.y, nv.z, th * (1.f + kPuckPad) + pad);
+  }
+}
+
+// Squared distance from p to the solid cylinder of a puck (INF when empty).
+__device__ __forceinline__ float puck_dist2(const float3 p, const float4 A, const float4 B) {
+  if (A.w < 0.f) return INFINITY;
+  const float3 d = make_float3(p.x - A.x, p.y - A.y, p.z - A.z);
+  const float z = d.x * B.x + d.y * B.y + d.z * B.z;
+  const float rho = sqrtf(fmaxf(d.x * d.x + d.y * d.y + d.z * d.z - z * z, 0.f));
+  const float dz = fmaxf(fabsf(z) - B.w, 0.f);
+  const float dr = fmaxf(rho - A.w, 0.f);
+  return dz * dz + dr * dr;
+}
 
 }  // namespace
 
 namespace {
 
-constexpr int kStack = 96;
+constexpr int kWarps = 4;          // warps per CTA
+constexpr int kStack = 96;         // per-warp traversal stack
 
-// One thread per grid node; blocks of 8 x 8 x 4 nodes.
-__global__ void __launch_bounds__(256) sdf_kernel(const float* __restrict__ chi, SurfParams g,
-                                                  const DevState* __restrict__ st,
-                                                  const Tri* __restrict__ tris,
-                                                  const int* __restrict__ brick_off, int64_t cap,
-                                                  const float4* __restrict__ pyr, PyrInfo pi,
-                                                  float* __restrict__ phi, float* __restrict__ sdf_out,
-                                                  int* __restrict__ ctri) {
+// Warp-cooperative exact distance search: a warp owns a 4 x 4 x 2 patch of
+// nodes and walks the octree once for all of them (a subtree is entered when
+// its bound beats the current best of at least one lane); leaves are tested
+// by every lane against its own node with the same (broadcast) triangle.
+__global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restrict__ chi, SurfParams g,
+                                                          const DevState* __restrict__ st,
+                                                          const Tri* __restrict__ tris,
+                                                          const int* __restrict__ leaf_off, int64_t cap,
+                                                          const float4* __restrict__ pyr, PyrInfo pi,
+                                                          float* __restrict__ phi, float* __restrict__ sdf_out,
+                                                          int* __restrict__ ctri) {
+  __shared__ unsigned int s_node[kWarps][kStack];
   const int n = g.res;
-  const int nbx = (n + 7) / 8, nby = (n + 7) / 8;
-  const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
-  const int i = bx * 8 + (threadIdx.x & 7), j = by * 8 + ((threadIdx.x >> 3) & 7),
-            k = bz * 4 + (threadIdx.x >> 6);
-  if (i >= n || j >= n || k >= n) return;
-  const int64_t o = lin3(i, j, k, n);
-  const double c = st->c;
-  const float sgn = ((double)chi[o] >= c) ? 1.f : -1.f;
-  const float3 p = make_float3((float)(g.lo[0] + (i + 0.5) * g.h), (float)(g.lo[1] + (j + 0.5) * g.h),
-                               (float)(g.lo[2] + (k + 0.5) * g.h));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // CTA covers 8 x 8 x 2 nodes: warp w -> (4 (w & 1), 4 (w >> 1)) in x, y
+  const int ntx = (n + 7) / 8, nty = (n + 7) / 8;
+  const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
+  const int i = bx * 8 + 4 * (w & 1) + (lane & 3);
+  const int j = by * 8 + 4 * (w >> 1) + ((lane >> 2) & 3);
+  const int k = bz * 2 + (lane >> 4);
+  const bool valid = (i < n) && (j < n) && (k < n);
+  const int ic = min(i, n - 1), jc = min(j, n - 1), kc = min(k, n - 1);
+  const float3 p = make_float3((float)(g.lo[0] + (ic + 0.5) * g.h), (float)(g.lo[1] + (jc + 0.5) * g.h),
+                               (float)(g.lo[2] + (kc + 0.5) * g.h));
   float best = INFINITY;
   int bt = -1;
-  unsigned int stk[kStack];
-  float sd[kStack];
+  unsigned int* stk = s_node[w];
   int sp = 0;
   const int top = pi.nlev - 1;
-  {
-    const float d = box_dist2(p, pyr[2 * pi.off[top]], pyr[2 * pi.off[top] + 1]);
-    if (d < INFINITY) {
-      stk[0] = (unsigned)top << 27;
-      sd[0] = d;
-      sp = 1;
-    }
-  }
+  const int nb = (pi.dim[0] + 1) / 2;
+  if (lane == 0) stk[0] = (unsigned)top << 27;
+  sp = 1;
+  __syncwarp();
   while (sp > 0) {
     --sp;
     const unsigned e = stk[sp];
-    if (sd[sp] >= best) continue;
+    __syncwarp();
     const int lev = (int)(e >> 27);
     const int idx = (int)(e & ((1u << 27) - 1));
+    const int64_t gi = pi.off[lev] + idx;
+    const float lb = puck_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
+    if (!__any_sync(0xffffffffu, lb < best)) continue;
     if (lev == 0) {
-      const int64_t s0 = brick_off[idx];
-      const int64_t s1 = min((int64_t)brick_off[idx + 1], cap);
+      const int dl = pi.dim[0];
+      const int lx = idx % dl, ly = (idx / dl) % dl, lz = idx / (dl * dl);
+      const int li = leaf_index(lx, ly, lz, nb);
+      const int64_t s0 = leaf_off[li];
+      const int64_t s1 = min((int64_t)leaf_off[li + 1], cap);
       for (int64_t t = s0; t < s1; ++t) {
         const Tri tr = tris[t];
         const float d2 = tri_closest(p, f3(tr.a), f3(tr.b), f3(tr.c), nullptr, nullptr, nullptr);
@@ -477,34 +575,44 @@ __global__ void __launch_bounds__(256) sdf_kernel(const float* __restrict__ chi,
     }
     const int dp = pi.dim[lev], dc = pi.dim[lev - 1];
     const int x = idx % dp, y = (idx / dp) % dp, z = idx / (dp * dp);
-    // collect children, then push far-to-near so the nearest is popped first
-    unsigned ce[8];
-    float cd[8];
+    // children: visit if any lane may improve; order nearest-first by the warp's
+    // smallest bound (pushed far-to-near)
+    float key[8];
+    unsigned ent[8];
     int nc = 0;
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
       if (cx >= dc || cy >= dc || cz >= dc) continue;
       const int ci = (cz * dc + cy) * dc + cx;
-      const int64_t gi = pi.off[lev - 1] + ci;
-      const float d = box_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
-      if (d >= best) continue;
-      // insertion sort, descending distance
+      const int64_t cg = pi.off[lev - 1] + ci;
+      const float4 A = pyr[2 * cg];
+      if (A.w < 0.f) continue;
+      const float d = puck_dist2(p, A, pyr[2 * cg + 1]);
+      if (!__any_sync(0xffffffffu, d < best)) continue;
+      float dm = d;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dm = fminf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
       int q2 = nc;
-      while (q2 > 0 && cd[q2 - 1] < d) {
-        cd[q2] = cd[q2 - 1];
-        ce[q2] = ce[q2 - 1];
+      while (q2 > 0 && key[q2 - 1] < dm) {
+        key[q2] = key[q2 - 1];
+        ent[q2] = ent[q2 - 1];
         --q2;
       }
-      cd[q2] = d;
-      ce[q2] = ((unsigned)(lev - 1) << 27) | (unsigned)ci;
+      key[q2] = dm;
+      ent[q2] = ((unsigned)(lev - 1) << 27) | (unsigned)ci;
       ++nc;
     }
-    for (int q = 0; q < nc && sp < kStack; ++q) {
-      stk[sp] = ce[q];
-      sd[sp] = cd[q];
-      ++sp;
+    if (lane == 0) {
+      for (int q = 0; q < nc && sp + q < kStack; ++q) stk[sp + q] = ent[q];
     }
+    sp = min(sp + nc, kStack);
+    __syncwarp();
   }
+  if (!valid) return;
+  const int64_t o = lin3(i, j, k, n);
+  const double c = st->c;
+  const float sgn = ((double)chi[o] >= c) ? 1.f : -1.f;
   const float val = sgn * sqrtf(best);
   phi[o] = val;
   if (sdf_out) sdf_out[o] = val;
@@ -542,9 +650,9 @@ __global__ void normals_kernel(const float* __restrict__ phi, int n, double h,
   }
 }
 
-PyrInfo pyramid_info(int nb) {
+PyrInfo pyramid_info(int nl) {
   PyrInfo pi;
-  int d = nb;
+  int d = nl;
   long long off = 0;
   pi.nlev = 0;
   while (true) {
@@ -560,8 +668,9 @@ PyrInfo pyramid_info(int nb) {
 
 }  // namespace
 
+// nb = bricks per axis; the octree's leaves are the 2 nb sub-bricks per axis
 size_t pyramid_nodes(int nb) {
-  PyrInfo pi = pyramid_info(nb);
+  PyrInfo pi = pyramid_info(2 * nb);
   return (size_t)(pi.off[pi.nlev - 1] + 1);
 }
 
@@ -595,26 +704,28 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   WGEO_LAUNCH_CHECK();
   int rc = exclusive_scan(h->brick_count, h->brick_off, nbricks, h->scan_tmp, s);
   if (rc) return rc;
-  mc_total_kernel<<<1, 1, 0, s>>>(h->brick_off, nbricks, h->mesh_cap, h->dstate);
+  mc_total_kernel<<<1, 1, 0, s>>>(h->brick_off, nbricks, h->mesh_cap, h->leaf_off, h->dstate);
   WGEO_LAUNCH_CHECK();
-  mc_emit_kernel<<<nbricks, 64, 0, s>>>(h->chi32, g, h->dstate, h->brick_off, h->mesh_cap, h->tris);
+  mc_emit_kernel<<<nbricks, 64, 0, s>>>(h->chi32, g, h->dstate, h->brick_off, h->mesh_cap, h->tris,
+                                        h->leaf_off);
   WGEO_LAUNCH_CHECK();
-  PyrInfo pi = pyramid_info(g.nb);
-  pyr_leaf_kernel<<<grid_blocks(nbricks, 128), 128, 0, s>>>(h->tris, h->brick_off, nbricks, h->mesh_cap,
-                                                          h->pyramid);
+  const PyrInfo pi = pyramid_info(2 * g.nb);
+  const int64_t nleaf = (int64_t)pi.dim[0] * pi.dim[0] * pi.dim[0];
+  puck_leaf_kernel<<<grid_blocks(nleaf, 256, 152 * 16), 256, 0, s>>>(h->tris, h->leaf_off, g.nb,
+                                                                      h->mesh_cap, h->pyramid);
   WGEO_LAUNCH_CHECK();
   for (int l = 1; l < pi.nlev; ++l) {
     const int64_t np = (int64_t)pi.dim[l] * pi.dim[l] * pi.dim[l];
-    pyr_up_kernel<<<grid_blocks(np, 128), 128, 0, s>>>(h->pyramid, pi.off[l - 1], pi.dim[l - 1], pi.off[l],
-                                                     pi.dim[l]);
+    puck_up_kernel<<<grid_blocks(np, 128, 152 * 16), 128, 0, s>>>(h->pyramid, pi.off[l - 1], pi.dim[l - 1],
+                                                                  pi.off[l], pi.dim[l]);
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStMC, slot, s);
   slot = stage_begin(h, kStSDF, s);
-  const int nbx = (res + 7) / 8, nbz = (res + 3) / 4;
-  sdf_kernel<<<nbx * nbx * nbz, 256, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->brick_off, h->mesh_cap,
-                                            h->pyramid, pi, h->phi, sdf_out,
-                                            h->opt.keep_for_backward ? h->ctri : nullptr);
+  const int ntx = (res + 7) / 8, ntz = (res + 1) / 2;
+  sdf_kernel<<<ntx * ntx * ntz, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
+                                                    h->mesh_cap, h->pyramid, pi, h->phi, sdf_out,
+                                                    h->opt.keep_for_backward ? h->ctri : nullptr);
   WGEO_LAUNCH_CHECK();
   stage_end(h, kStSDF, slot, s);
   if (nrm_out) {

@@ -24,6 +24,8 @@ constexpr double kFixInv2 = 1.0 / 137438953472.0; // 1 / 2^37 (the face form sum
 struct SolveState {
   int done;          // set once the relative residual is below tol (gates later kernels)
   int iter;          // refinement steps / V-cycles performed
+  int xidx;          // which of the two FP64 buffers holds the current iterate
+  int cold;          // 1: start from x = 0 (the first refinement pass writes zeros)
   double bnorm;      // || b - mean(b) ||
   double bmean;
   double rmean;      // mean of the last residual (projected out of the correction RHS)
@@ -48,6 +50,7 @@ struct Tri {          // one marching-cubes triangle: vertex xyz + global edge i
 struct Level {
   int n;
   float* x;
+  float* x2;   // ping-pong partner of x for the fused smoothers
   float* b;
 };
 
@@ -166,16 +169,15 @@ struct wgeo_handle {
   // grid fields (sized for max_res^3)
   float* b32 = nullptr;
   float* chi32 = nullptr;
-  double* chi64 = nullptr;
+  double* chi64[2] = {nullptr, nullptr};   // FP64 iterate, ping-pong (index on the device)
   float* r32 = nullptr;
   float* e32 = nullptr;
   float* phi = nullptr;
   int* ctri = nullptr;
   double* dphi64 = nullptr;
   double* dchi64 = nullptr;
-  double* lam64 = nullptr;
-  float* lam32 = nullptr;   // alias of chi-sized scratch for the adjoint solve output
-  std::vector<float> dummy;
+  double* lam64[2] = {nullptr, nullptr};   // adjoint solution, ping-pong like chi64
+  float* lam32 = nullptr;
   float* level_pool = nullptr;
 
   // points
@@ -191,6 +193,7 @@ struct wgeo_handle {
   int64_t mesh_cap = 0;
   int* brick_count = nullptr;
   int* brick_off = nullptr;      // nbricks + 1
+  int* leaf_off = nullptr;       // 8 * nbricks + 1: triangle offset of each 2^3 sub-brick
   wgeo::Tri* tris = nullptr;
   float4* pyramid = nullptr;     // 2 float4 per node (lo, hi)
   double* dP = nullptr;          // backward: dL/d(vertex) per triangle corner, 9 doubles
@@ -262,8 +265,7 @@ int launch_bin_sort_splat(wgeo_handle* h, const float* points, const float* norm
                           int res, cudaStream_t s);
 int launch_unpack_bins(wgeo_handle* h, int* out, cudaStream_t s);
 // solver.cu
-int launch_solve(wgeo_handle* h, int res, int mode, cudaStream_t s);
-int solver_fp32_prepare(wgeo_handle* h, int res, cudaStream_t s);
+int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s);
 // surface.cu
 int launch_isovalue(wgeo_handle* h, const float* points, int64_t n, int res, cudaStream_t s);
 int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_out, cudaStream_t s);
