@@ -211,7 +211,7 @@ def run_ours(args):
     rec32.close()
 
     # per-stage device times (CUDA events on the library's stream), separate pass
-    rec_t = Reconstructor(RES, NPTS, stage_timing=1)
+    rec_t = Reconstructor(RES, NPTS, stage_timing=2)
     for _ in range(2):
         rec_t.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf)
         rec_t.query(Q, with_normals=False)
@@ -300,6 +300,10 @@ def run_ours(args):
         "solver": {"steps": info["solver_steps"], "residual_rel": info["residual_rel"],
                    "bwd_steps": info_t["backward_steps"], "bwd_residual_rel": info_t["backward_residual_rel"]},
         "triangles": info["n_triangles"],
+        "sdf_search": {"node_visits_per_warp_launch": info_t["sdf_node_visits"],
+                       "leaf_visits": info_t["sdf_leaf_visits"],
+                       "tri_tests": info_t["sdf_tri_tests"],
+                       "tri_tests_per_node": info_t["sdf_tri_tests"] / N},
         "stage_ms": stages,
         "e2e": {"value": N / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -109,7 +109,10 @@ typedef struct {
   int64_t  n_triangles;      /* triangles extracted by the last forward */
   int64_t  n_points_used;    /* finite points used by the last forward */
   double   h;                /* cell size of the last forward */
-  int64_t  reserved[6];
+  int64_t  sdf_node_visits;  /* with stage_timing = 2: octree nodes entered by the distance search (per warp) */
+  int64_t  sdf_leaf_visits;  /* ... leaves entered (per warp) */
+  int64_t  sdf_tri_tests;    /* ... point-triangle distance evaluations (per node, i.e. per lane) */
+  int64_t  reserved[3];
 } wgeo_info;
 
 /* Fills `opt` with the defaults listed above.  Never fails for non-null opt. */

@@ -98,6 +98,9 @@ __global__ void reset_status_kernel(DevState* st) {
   st->ntris = 0;
   st->c = 0.0;
   st->npts = 0;
+  st->sdf_cnt[0] = 0;
+  st->sdf_cnt[1] = 0;
+  st->sdf_cnt[2] = 0;
 }
 
 void accumulate_slot(StageTimer& t, int slot) {
@@ -364,6 +367,9 @@ int wgeo_get_info(wgeo_handle* h, wgeo_info* out) {
   out->n_triangles = st.ntris;
   out->n_points_used = st.npts;
   out->h = h->h;
+  out->sdf_node_visits = (int64_t)st.sdf_cnt[0];
+  out->sdf_leaf_visits = (int64_t)st.sdf_cnt[1];
+  out->sdf_tri_tests = (int64_t)st.sdf_cnt[2];
   return WGEO_OK;
 }
 

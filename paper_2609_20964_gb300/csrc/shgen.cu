@@ -24,36 +24,37 @@ constexpr int kShThreads = 128;
 constexpr int kShBlocks = 256;
 
 struct ShConsts {
-  float K[kLmax + 1][kLmax + 1];  // K_lm
+  double K[kLmax + 1][kLmax + 1];  // K_lm
   int lmax;
 };
 
 // Y_k and the Cartesian gradient of the polynomial extension, for all k.
 __device__ __forceinline__ void eval_sh(const float u[3], const ShConsts& cs, float* Y, float (*dY)[3]) {
-  const float x = u[0], y = u[1], z = u[2];
-  float C[kLmax + 1], S[kLmax + 1];
-  C[0] = 1.f;
-  S[0] = 0.f;
+  // recurrences in FP64 (the three-term Legendre recurrence cancels), stored as float
+  const double x = u[0], y = u[1], z = u[2];
+  double C[kLmax + 1], S[kLmax + 1];
+  C[0] = 1.0;
+  S[0] = 0.0;
   for (int m = 1; m <= cs.lmax; ++m) {
     C[m] = x * C[m - 1] - y * S[m - 1];
     S[m] = x * S[m - 1] + y * C[m - 1];
   }
   for (int m = 0; m <= cs.lmax; ++m) {
-    float dfact = 1.f;
-    for (int j = 1; j < 2 * m; j += 2) dfact *= (float)j;
-    float q2 = 0.f, dq2 = 0.f;          // Q_{l-2}
-    float q1 = dfact, dq1 = 0.f;        // Q_{l-1} (starts at l = m)
+    double dfact = 1.0;
+    for (int j = 1; j < 2 * m; j += 2) dfact *= (double)j;
+    double q2 = 0.0, dq2 = 0.0;         // Q_{l-2}
+    double q1 = dfact, dq1 = 0.0;       // Q_{l-1} (starts at l = m)
     for (int l = m; l <= cs.lmax; ++l) {
-      float q, dq;
+      double q, dq;
       if (l == m) {
         q = dfact;
-        dq = 0.f;
+        dq = 0.0;
       } else if (l == m + 1) {
         q = (2 * m + 1) * z * q1;
         dq = (2 * m + 1) * (q1 + z * dq1);
       } else {
-        q = ((2 * l - 1) * z * q1 - (l + m - 1) * q2) / (float)(l - m);
-        dq = ((2 * l - 1) * (q1 + z * dq1) - (l + m - 1) * dq2) / (float)(l - m);
+        q = ((2 * l - 1) * z * q1 - (l + m - 1) * q2) / (double)(l - m);
+        dq = ((2 * l - 1) * (q1 + z * dq1) - (l + m - 1) * dq2) / (double)(l - m);
       }
       if (l > m) {
         q2 = q1;
@@ -61,24 +62,24 @@ __device__ __forceinline__ void eval_sh(const float u[3], const ShConsts& cs, fl
         q1 = q;
         dq1 = dq;
       }
-      const float K = cs.K[l][m];
+      const double K = cs.K[l][m];
       if (m == 0) {
         const int k = l * l + l;
-        Y[k] = K * q;
+        Y[k] = (float)(K * q);
         dY[k][0] = 0.f;
         dY[k][1] = 0.f;
-        dY[k][2] = K * dq;
+        dY[k][2] = (float)(K * dq);
       } else {
-        const float s2 = 1.41421356237309515f * K;
+        const double s2 = 1.4142135623730951 * K;
         const int kc = l * l + l + m, ks = l * l + l - m;
-        Y[kc] = s2 * q * C[m];
-        Y[ks] = s2 * q * S[m];
-        dY[kc][0] = s2 * q * m * C[m - 1];
-        dY[kc][1] = -s2 * q * m * S[m - 1];
-        dY[kc][2] = s2 * dq * C[m];
-        dY[ks][0] = s2 * q * m * S[m - 1];
-        dY[ks][1] = s2 * q * m * C[m - 1];
-        dY[ks][2] = s2 * dq * S[m];
+        Y[kc] = (float)(s2 * q * C[m]);
+        Y[ks] = (float)(s2 * q * S[m]);
+        dY[kc][0] = (float)(s2 * q * m * C[m - 1]);
+        dY[kc][1] = (float)(-s2 * q * m * S[m - 1]);
+        dY[kc][2] = (float)(s2 * dq * C[m]);
+        dY[ks][0] = (float)(s2 * q * m * S[m - 1]);
+        dY[ks][1] = (float)(s2 * q * m * C[m - 1]);
+        dY[ks][2] = (float)(s2 * dq * S[m]);
       }
     }
   }
@@ -94,21 +95,31 @@ struct Surf {
 
 __device__ __forceinline__ Surf surface_at(const float u[3], const float* __restrict__ theta, int K,
                                            float base, const float* Y, const float (*dY)[3]) {
+  // r and grad r accumulate up to 81 terms with |grad Y| ~ 20 and cancellation:
+  // FP64 here keeps the normals at float32 accuracy
   Surf s;
-  float r = base, g[3] = {0.f, 0.f, 0.f};
+  double r = base, g[3] = {0.0, 0.0, 0.0};
   for (int k = 0; k < K; ++k) {
-    const float t = theta[k];
+    const double t = theta[k];
     r += t * Y[k];
     g[0] += t * dY[k][0];
     g[1] += t * dY[k][1];
     g[2] += t * dY[k][2];
   }
-  const float gu = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
-  for (int a = 0; a < 3; ++a) s.gt[a] = g[a] - gu * u[a];
-  for (int a = 0; a < 3; ++a) s.m[a] = u[a] - s.gt[a] / r;
-  s.mn = sqrtf(s.m[0] * s.m[0] + s.m[1] * s.m[1] + s.m[2] * s.m[2]);
-  for (int a = 0; a < 3; ++a) s.n[a] = s.m[a] / s.mn;
-  s.r = r;
+  const double gu = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+  double m[3];
+  for (int a = 0; a < 3; ++a) {
+    const double gt = g[a] - gu * u[a];
+    s.gt[a] = (float)gt;
+    m[a] = u[a] - gt / r;
+  }
+  const double mn = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  for (int a = 0; a < 3; ++a) {
+    s.m[a] = (float)m[a];
+    s.n[a] = (float)(m[a] / mn);
+  }
+  s.mn = (float)mn;
+  s.r = (float)r;
   return s;
 }
 
@@ -194,12 +205,12 @@ ShConsts make_consts(int K) {
   for (int l = 0; l <= kLmax; ++l)
     for (int m = 0; m <= kLmax; ++m) {
       if (m > l) {
-        cs.K[l][m] = 0.f;
+        cs.K[l][m] = 0.0;
         continue;
       }
       double r = 1.0;
       for (int j = l - m + 1; j <= l + m; ++j) r /= (double)j;   // (l-m)!/(l+m)!
-      cs.K[l][m] = (float)sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * r);
+      cs.K[l][m] = sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * r);
     }
   return cs;
 }

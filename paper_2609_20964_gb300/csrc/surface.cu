@@ -519,8 +519,9 @@ constexpr int kStack = 96;         // per-warp traversal stack
 // nodes and walks the octree once for all of them (a subtree is entered when
 // its bound beats the current best of at least one lane); leaves are tested
 // by every lane against its own node with the same (broadcast) triangle.
+template <bool COUNT>
 __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restrict__ chi, SurfParams g,
-                                                          const DevState* __restrict__ st,
+                                                          DevState* __restrict__ st,
                                                           const Tri* __restrict__ tris,
                                                           const int* __restrict__ leaf_off, int64_t cap,
                                                           const float4* __restrict__ pyr, PyrInfo pi,
@@ -547,6 +548,7 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
   const int nb = (pi.dim[0] + 1) / 2;
   if (lane == 0) stk[0] = (unsigned)top << 27;
   sp = 1;
+  unsigned long long c_nodes = 0, c_leaves = 0, c_tests = 0;
   __syncwarp();
   while (sp > 0) {
     --sp;
@@ -557,12 +559,17 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
     const int64_t gi = pi.off[lev] + idx;
     const float lb = puck_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
     if (!__any_sync(0xffffffffu, lb < best)) continue;
+    if (COUNT) ++c_nodes;
     if (lev == 0) {
       const int dl = pi.dim[0];
       const int lx = idx % dl, ly = (idx / dl) % dl, lz = idx / (dl * dl);
       const int li = leaf_index(lx, ly, lz, nb);
       const int64_t s0 = leaf_off[li];
       const int64_t s1 = min((int64_t)leaf_off[li + 1], cap);
+      if (COUNT) {
+        ++c_leaves;
+        c_tests += 32ull * (unsigned long long)(s1 > s0 ? s1 - s0 : 0);
+      }
       for (int64_t t = s0; t < s1; ++t) {
         const Tri tr = tris[t];
         const float d2 = tri_closest(p, f3(tr.a), f3(tr.b), f3(tr.c), nullptr, nullptr, nullptr);
@@ -608,6 +615,11 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
     }
     sp = min(sp + nc, kStack);
     __syncwarp();
+  }
+  if (COUNT && lane == 0) {
+    atomicAdd(&st->sdf_cnt[0], c_nodes);
+    atomicAdd(&st->sdf_cnt[1], c_leaves);
+    atomicAdd(&st->sdf_cnt[2], c_tests);
   }
   if (!valid) return;
   const int64_t o = lin3(i, j, k, n);
@@ -723,9 +735,14 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   stage_end(h, kStMC, slot, s);
   slot = stage_begin(h, kStSDF, s);
   const int ntx = (res + 7) / 8, ntz = (res + 1) / 2;
-  sdf_kernel<<<ntx * ntx * ntz, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
-                                                    h->mesh_cap, h->pyramid, pi, h->phi, sdf_out,
-                                                    h->opt.keep_for_backward ? h->ctri : nullptr);
+  if (h->opt.stage_timing == 2)
+    sdf_kernel<true><<<ntx * ntx * ntz, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
+                                                            h->mesh_cap, h->pyramid, pi, h->phi, sdf_out,
+                                                            h->opt.keep_for_backward ? h->ctri : nullptr);
+  else
+    sdf_kernel<false><<<ntx * ntx * ntz, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
+                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out,
+                                                             h->opt.keep_for_backward ? h->ctri : nullptr);
   WGEO_LAUNCH_CHECK();
   stage_end(h, kStSDF, slot, s);
   if (nrm_out) {

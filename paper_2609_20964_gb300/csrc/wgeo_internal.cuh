@@ -41,6 +41,7 @@ struct DevState {
   double dc;          // backward: dL/dc
   SolveState fwd;
   SolveState bwd;
+  unsigned long long sdf_cnt[3];   // octree nodes entered, leaves entered, lane point-triangle tests
 };
 
 struct Tri {          // one marching-cubes triangle: vertex xyz + global edge id in .w

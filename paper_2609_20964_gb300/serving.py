@@ -1,0 +1,207 @@
+"""Request loop with continuous batching of reconstructions of differing grid
+sizes and point counts.
+
+* A request carries a point cloud (host or device) with normals, a box, a grid
+  size, optional query points and an optional adjoint seed at the queries
+  (then the point/normal gradients are returned too).
+* Admission: a request runs when a stream slot is free and its handle fits
+  the device-memory budget.  Handles (library workspaces, sized by
+  ``wgeo_footprint_bytes``) are pooled per grid size and reused, so grids
+  and the warm-start solution stay resident; idle handles are evicted when a
+  new size needs room.
+* Requests that arrive while others are on the GPU are admitted as soon as a
+  slot and memory free up; each runs on its own CUDA stream, so the kernels of
+  different requests overlap on the device.
+* Completion is detected with CUDA events (host polling, no device spin);
+  latency = completion - arrival, reported as p50 / p99.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .api import Reconstructor
+
+
+@dataclass
+class Request:
+    points: object                 # [n,3] float32 (numpy or torch)
+    normals: object
+    res: int
+    bbox: tuple = (0.0, 0.0, 0.0, 1.0, 1.0, 1.0)
+    queries: object = None         # [m,3] float32 or None
+    d_sdf_q: object = None         # [m] adjoint seed at the queries (gradients requested)
+    want_grid: bool = False        # return the SDF grid (device tensor)
+    arrival: float = field(default_factory=time.perf_counter)
+    rid: int = 0
+
+
+@dataclass
+class Result:
+    rid: int
+    sdf_q: np.ndarray | None
+    d_points: np.ndarray | None
+    d_normals: np.ndarray | None
+    sdf_grid: torch.Tensor | None
+    info: dict
+    latency_s: float
+
+
+class _Slot:
+    def __init__(self, device):
+        self.stream = torch.cuda.Stream(device=device)
+        self.busy = False
+
+
+class Server:
+    def __init__(self, budget_bytes: int, n_streams: int = 4, max_points: int = 500_000,
+                 device=None, **options):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.budget = int(budget_bytes)
+        self.max_points = max_points
+        self.options = options
+        self.slots = [_Slot(self.device) for _ in range(n_streams)]
+        self.free_handles = collections.defaultdict(list)   # res -> [Reconstructor]
+        self.used_bytes = 0
+        self.pending = collections.deque()
+        self.inflight = []
+        self.latencies = []
+        self.completed = 0
+        self.lock = threading.Condition()
+        self.stop_flag = False
+        self.worker = threading.Thread(target=self._run, daemon=True)
+        self.worker.start()
+
+    # ---------------------------------------------------------------- public
+    def submit(self, req: Request) -> Future:
+        fut = Future()
+        if self.footprint(req.res) > self.budget:
+            fut.set_exception(MemoryError(
+                f"a {req.res}^3 workspace needs {self.footprint(req.res)} bytes, budget is {self.budget}"))
+            return fut
+        with self.lock:
+            self.pending.append((req, fut))
+            self.lock.notify()
+        return fut
+
+    def close(self):
+        with self.lock:
+            self.stop_flag = True
+            self.lock.notify()
+        self.worker.join()
+        for hs in self.free_handles.values():
+            for h in hs:
+                h.close()
+        self.free_handles.clear()
+
+    def stats(self) -> dict:
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        return {"completed": self.completed, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "used_bytes": self.used_bytes}
+
+    # ---------------------------------------------------------------- internals
+    def footprint(self, res: int) -> int:
+        return Reconstructor.footprint(res, self.max_points, **self.options)
+
+    def _take_handle(self, res: int):
+        if self.free_handles[res]:
+            return self.free_handles[res].pop()
+        need = self.footprint(res)
+        # evict idle handles of other sizes until the new one fits
+        while self.used_bytes + need > self.budget:
+            victim = None
+            for r, hs in self.free_handles.items():
+                if hs:
+                    victim = (r, hs.pop())
+                    break
+            if victim is None:
+                return None
+            victim[1].close()
+            self.used_bytes -= self.footprint(victim[0])
+        with torch.cuda.device(self.device):
+            h = Reconstructor(res, self.max_points, device=self.device.index, **self.options)
+        self.used_bytes += need
+        return h
+
+    def _launch(self, req: Request, fut: Future, slot: _Slot, h: Reconstructor):
+        dev = self.device
+        with torch.cuda.stream(slot.stream):
+            def to_dev(a):
+                if a is None:
+                    return None
+                t = torch.as_tensor(a)
+                return t.to(dev, non_blocking=True).contiguous() if t.device != dev else t.contiguous()
+            P = to_dev(req.points)
+            N = to_dev(req.normals)
+            Q = to_dev(req.queries)
+            G = to_dev(req.d_sdf_q)
+            sdf, _ = h.reconstruct(P, N, req.bbox, req.res, with_sdf=req.want_grid, with_normals=False,
+                                   stream=slot.stream)
+            out = {"sdf_grid": sdf}
+            if Q is not None:
+                sq, _ = h.query(Q, with_normals=False, stream=slot.stream)
+                out["sdf_q"] = sq.to("cpu", non_blocking=True) if Q is not None else None
+                if G is not None:
+                    dp, dn, _ = h.backward(q=Q, d_sdf_q=G, stream=slot.stream)
+                    out["d_points"] = dp.to("cpu", non_blocking=True)
+                    out["d_normals"] = dn.to("cpu", non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+            keep = (P, N, Q, G)          # inputs stay alive until the stream has used them
+        self.inflight.append((req, fut, slot, h, ev, out, keep))
+
+    def _poll(self):
+        done = []
+        for item in self.inflight:
+            if item[4].query():
+                done.append(item)
+        for item in done:
+            self.inflight.remove(item)
+            req, fut, slot, h, ev, out, _ = item
+            info = h.info()
+            lat = time.perf_counter() - req.arrival
+            self.latencies.append(lat)
+            self.completed += 1
+            res = Result(rid=req.rid,
+                         sdf_q=out["sdf_q"].numpy() if out.get("sdf_q") is not None else None,
+                         d_points=out["d_points"].numpy() if "d_points" in out else None,
+                         d_normals=out["d_normals"].numpy() if "d_normals" in out else None,
+                         sdf_grid=out["sdf_grid"], info=info, latency_s=lat)
+            slot.busy = False
+            self.free_handles[req.res].append(h)
+            fut.set_result(res)
+        return bool(done)
+
+    def _run(self):
+        torch.cuda.set_device(self.device)
+        while True:
+            with self.lock:
+                if self.stop_flag and not self.pending and not self.inflight:
+                    return
+            progressed = self._poll()
+            with self.lock:
+                while self.pending:
+                    slot = next((s for s in self.slots if not s.busy), None)
+                    if slot is None:
+                        break
+                    req, fut = self.pending[0]
+                    h = self._take_handle(req.res)
+                    if h is None:
+                        break           # memory: wait for a running request to finish
+                    self.pending.popleft()
+                    slot.busy = True
+                    try:
+                        self._launch(req, fut, slot, h)
+                    except Exception as exc:  # noqa: BLE001
+                        slot.busy = False
+                        self.free_handles[req.res].append(h)
+                        fut.set_exception(exc)
+                    progressed = True
+                if not progressed:
+                    self.lock.wait(timeout=0.0005)
