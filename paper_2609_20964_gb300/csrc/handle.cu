@@ -44,7 +44,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   size_t c = 0;
   L.off_b32 = take(c, 4 * N);
   L.off_chi32 = take(c, 4 * N);
-  L.off_chi64 = take(c, 16 * N);                       // two FP64 buffers
+  L.off_chi64 = take(c, 16 * N);                       // two float-float buffers
   L.off_r32 = take(c, 4 * N);
   L.off_e32 = take(c, 4 * N);
   L.off_phi = take(c, 4 * N);
@@ -217,16 +217,16 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   const size_t N = (size_t)max_res * max_res * max_res;
   h->b32 = (float*)(a + L.off_b32);
   h->chi32 = (float*)(a + L.off_chi32);
-  h->chi64[0] = (double*)(a + L.off_chi64);
-  h->chi64[1] = h->chi64[0] + N;
+  h->chiff[0] = (float2*)(a + L.off_chi64);
+  h->chiff[1] = h->chiff[0] + N;
   h->r32 = (float*)(a + L.off_r32);
   h->e32 = (float*)(a + L.off_e32);
   h->phi = (float*)(a + L.off_phi);
   h->ctri = keep ? (int*)(a + L.off_ctri) : nullptr;
   h->dphi64 = keep ? (double*)(a + L.off_dphi64) : nullptr;
   h->dchi64 = keep ? (double*)(a + L.off_dchi64) : nullptr;
-  h->lam64[0] = keep ? (double*)(a + L.off_lam64) : nullptr;
-  h->lam64[1] = keep ? h->lam64[0] + N : nullptr;
+  h->lamff[0] = keep ? (float2*)(a + L.off_lam64) : nullptr;
+  h->lamff[1] = keep ? h->lamff[0] + N : nullptr;
   h->lam32 = keep ? (float*)(a + L.off_lam32) : nullptr;
   h->level_pool = (float*)(a + L.off_levels);
   h->pcell = (int*)(a + L.off_pcell);
@@ -247,7 +247,7 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->scan_tmp_elems = L.n_scan;
   h->dstate = (DevState*)(a + L.off_state);
   if (upload_mc_table() != WGEO_OK || cudaMemset(h->dstate, 0, sizeof(DevState)) != cudaSuccess ||
-      cudaMemset(h->chi64[0], 0, 16 * N) != cudaSuccess) {
+      cudaMemset(h->chiff[0], 0, 16 * N) != cudaSuccess) {
     cudaFree(h->arena);
     delete h;
     return WGEO_ERR_CUDA;

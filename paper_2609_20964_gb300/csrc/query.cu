@@ -243,6 +243,7 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
 }
 
 // Distance + marching-cubes adjoint, one thread per node with a nonzero dphi.
+// FP32 arithmetic per node; FP64 only in the scatter (atomics) and the dc sum.
 __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int* __restrict__ ctri,
                                       const float* __restrict__ chi, const DevState* __restrict__ st,
                                       const Tri* __restrict__ tris, QParams g,
@@ -251,13 +252,15 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
   const int n = g.res;
   const int64_t N = (int64_t)n * n * n;
   const double c = st->c;
-  double dcacc = 0.0;
+  const float hf = (float)g.h;
+  float dcacc = 0.f;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N;
        o += (int64_t)gridDim.x * blockDim.x) {
-    const double gphi = dphi[o];
-    if (gphi == 0.0) continue;
+    const double gphi64 = dphi[o];
+    if (gphi64 == 0.0) continue;
     const int t = ctri[o];
     if (t < 0) continue;
+    const float gphi = (float)gphi64;
     const int i = (int)(o % n), j = (int)((o / n) % n), k = (int)(o / ((int64_t)n * n));
     const float3 p = make_float3((float)(g.lo[0] + (i + 0.5) * g.h), (float)(g.lo[1] + (j + 0.5) * g.h),
                                  (float)(g.lo[2] + (k + 0.5) * g.h));
@@ -268,9 +271,9 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
     const float3 y = make_float3(bw[0] * tr.a.x + bw[1] * tr.b.x + bw[2] * tr.c.x,
                                  bw[0] * tr.a.y + bw[1] * tr.b.y + bw[2] * tr.c.y,
                                  bw[0] * tr.a.z + bw[1] * tr.b.z + bw[2] * tr.c.z);
-    const double d = sqrt((double)d2);
-    const double sgn = ((double)chi[o] >= c) ? 1.0 : -1.0;
-    const double u[3] = {(p.x - y.x) / d, (p.y - y.y) / d, (p.z - y.z) / d};
+    const float invd = rsqrtf(d2);
+    const float sgn = ((double)chi[o] >= c) ? 1.f : -1.f;
+    const float u[3] = {(p.x - y.x) * invd, (p.y - y.y) * invd, (p.z - y.z) * invd};
     const float4 vv[3] = {tr.a, tr.b, tr.c};
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
@@ -279,18 +282,20 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
       const int ax = gid % 3;
       const int64_t pl = gid / 3;
       const int64_t stv = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
-      const double c1 = (double)chi[pl], c2 = (double)chi[pl + stv];
-      const double den = c2 - c1;
-      const double eta = (c - c1) / den;
+      const float c1 = chi[pl], c2 = chi[pl + stv];
+      const float den = c2 - c1;                       // neighbouring values: exact
+      const float cm = (float)(c - (double)c1);        // c - chi1 without losing c's low bits
+      const float eta = cm / den;
       // dL/dP_v[ax] = -s dphi beta_v u[ax];  dP/deta = h e_ax
-      const double deta = -sgn * gphi * (double)bw[v] * u[ax] * g.h;
-      atomicAdd(&dchi[pl], deta * (eta - 1.0) / den);
-      atomicAdd(&dchi[pl + stv], -deta * eta / den);
-      dcacc += deta / den;
+      const float deta = -sgn * gphi * bw[v] * u[ax] * hf;
+      const float w = deta / den;
+      atomicAdd(&dchi[pl], (double)(w * (eta - 1.f)));
+      atomicAdd(&dchi[pl + stv], (double)(-w * eta));
+      dcacc += w;
     }
   }
-  dcacc = block_sum<256>(dcacc, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = dcacc;
+  const double s = block_sum<256>((double)dcacc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 __global__ void dc_finalize_kernel(const double* __restrict__ partials, int nblocks, DevState* st) {
@@ -353,30 +358,37 @@ __global__ void iso_adjoint_kernel(const int* __restrict__ pcell, const float4* 
 }
 
 // dV_o = D^T lambda at cell (x,y,z): 1/2 (lambda_o - lambda_{o+e}) on interior
-// faces o+1/2 plus 1/2 (lambda_{o-e} - lambda_o) on interior faces o-1/2.
-__device__ __forceinline__ void dV_at(const double* __restrict__ lam, int x, int y, int z, int n,
-                                      double dv[3]) {
+// faces o+1/2 plus 1/2 (lambda_{o-e} - lambda_o) on interior faces o-1/2;
+// lambda is float-float, the differences are formed exactly.
+__device__ __forceinline__ void dV_at(const float2* __restrict__ lam, int x, int y, int z, int n,
+                                      float dv[3]) {
   const int idx[3] = {x, y, z};
   const int64_t o = lin3(x, y, z, n);
   const int64_t st[3] = {1, n, (int64_t)n * n};
-  const double lo = lam[o];
+  const float2 lo = lam[o];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double v = 0.0;
-    if (idx[a] + 1 < n) v += 0.5 * (lo - lam[o + st[a]]);
-    if (idx[a] - 1 >= 0) v += 0.5 * (lam[o - st[a]] - lo);
+    float v = 0.f;
+    if (idx[a] + 1 < n) {
+      const float2 d = ff_sub(lo, lam[o + st[a]]);
+      v += 0.5f * (d.x + d.y);
+    }
+    if (idx[a] - 1 >= 0) {
+      const float2 d = ff_sub(lam[o - st[a]], lo);
+      v += 0.5f * (d.x + d.y);
+    }
     dv[a] = v;
   }
 }
 
 __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4* __restrict__ pfrac,
                                      const float4* __restrict__ pnrm, int64_t np,
-                                     const double* __restrict__ lam0, const double* __restrict__ lam1,
+                                     const float2* __restrict__ lam0, const float2* __restrict__ lam1,
                                      const int* __restrict__ lam_idx, QParams g,
                                      float* __restrict__ dpts, float* __restrict__ dnrm) {
-  const double* __restrict__ lam = (*lam_idx) ? lam1 : lam0;
+  const float2* __restrict__ lam = (*lam_idx) ? lam1 : lam0;
   const int n = g.res;
-  const double inv2h = 0.5 / g.h;
+  const float inv2h = (float)(0.5 / g.h);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int pc = pcell[i];
@@ -389,29 +401,28 @@ __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4
     const float4 fr = pfrac[i];
     const float4 nv = pnrm[i];
     const int b[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
-    const double f[3] = {fr.x, fr.y, fr.z};
-    const double nn[3] = {nv.x, nv.y, nv.z};
-    double fac[3][3], dfac[3][3];
+    const float f[3] = {fr.x, fr.y, fr.z};
+    const float nn[3] = {nv.x, nv.y, nv.z};
+    float fac[3][3], dfac[3][3];
     bool ing[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const double s = f[a] - 0.5 - (double)(d - 1);   // (x - c_o) / h
-        const double t = fabs(s);
-        const double arg = 1.0 - 0.5 * t;
-        fac[a][d] = 0.5 * fmax(0.0, arg);
-        dfac[a][d] = (arg > 0.0) ? -0.5 * ((s > 0.0) - (s < 0.0)) * inv2h : 0.0;
+        const float s = f[a] - 0.5f - (float)(d - 1);   // (x - c_o) / h
+        const float arg = 1.f - 0.5f * fabsf(s);
+        fac[a][d] = 0.5f * fmaxf(0.f, arg);
+        dfac[a][d] = (arg > 0.f) ? -0.5f * (float)((s > 0.f) - (s < 0.f)) * inv2h : 0.f;
         const int o = b[a] + d - 1;
         ing[a][d] = (o >= 0) && (o < n);
       }
     }
-    double S = 0.0, dS[3] = {0.0, 0.0, 0.0};
+    float S = 0.f, dS[3] = {0.f, 0.f, 0.f};
     for (int q = 0; q < 27; ++q) {
       const int dx = q % 3, dy = (q / 3) % 3, dz = q / 9;
       if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
       if (q == 13) {
-        S += 0.5;
+        S += 0.5f;
         continue;
       }
       S += fac[0][dx] * fac[1][dy] * fac[2][dz];
@@ -419,37 +430,39 @@ __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4
       dS[1] += fac[0][dx] * dfac[1][dy] * fac[2][dz];
       dS[2] += fac[0][dx] * fac[1][dy] * dfac[2][dz];
     }
-    double gdn[3] = {0.0, 0.0, 0.0}, gdx[3] = {0.0, 0.0, 0.0};
+    const float invS = 1.f / S;
+    float gdn[3] = {0.f, 0.f, 0.f}, gdx[3] = {0.f, 0.f, 0.f};
     for (int q = 0; q < 27; ++q) {
       const int dx = q % 3, dy = (q / 3) % 3, dz = q / 9;
       if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
-      double dv[3];
+      float dv[3];
       dV_at(lam, b[0] + dx - 1, b[1] + dy - 1, b[2] + dz - 1, n, dv);
-      double a, da[3];
+      float a, da[3];
       if (q == 13) {
-        a = 0.5;
-        da[0] = da[1] = da[2] = 0.0;
+        a = 0.5f;
+        da[0] = da[1] = da[2] = 0.f;
       } else {
         a = fac[0][dx] * fac[1][dy] * fac[2][dz];
         da[0] = dfac[0][dx] * fac[1][dy] * fac[2][dz];
         da[1] = fac[0][dx] * dfac[1][dy] * fac[2][dz];
         da[2] = fac[0][dx] * fac[1][dy] * dfac[2][dz];
       }
-      const double alpha = a / S;
-      const double wdot = nn[0] * dv[0] + nn[1] * dv[1] + nn[2] * dv[2];
+      const float alpha = a * invS;
+      const float wdot = nn[0] * dv[0] + nn[1] * dv[1] + nn[2] * dv[2];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         gdn[c] += alpha * dv[c];
-        gdx[c] += wdot * (da[c] - alpha * dS[c]) / S;
+        gdx[c] += wdot * (da[c] - alpha * dS[c]) * invS;
       }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      dnrm[3 * i + c] = (float)gdn[c];
-      dpts[3 * i + c] = dpts[3 * i + c] + (float)gdx[c];
+      dnrm[3 * i + c] = gdn[c];
+      dpts[3 * i + c] = dpts[3 * i + c] + gdx[c];
     }
   }
 }
+
 
 QParams qparams(const wgeo_handle* h) {
   QParams g;
@@ -508,7 +521,7 @@ int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_
   slot = stage_begin(h, kStBwdSplat, s);
   if (h->npts > 0) {
     splat_adjoint_kernel<<<grid_blocks(h->npts, 128, 152 * 64), 128, 0, s>>>(
-        h->pcell, h->pfrac, h->pnrm, h->npts, h->lam64[0], h->lam64[1], &h->dstate->bwd.xidx, g,
+        h->pcell, h->pfrac, h->pnrm, h->npts, h->lamff[0], h->lamff[1], &h->dstate->bwd.xidx, g,
         d_points, d_normals);
     WGEO_LAUNCH_CHECK();
   }

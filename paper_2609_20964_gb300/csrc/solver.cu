@@ -6,27 +6,32 @@
 // h).  The system is singular (constants) and consistent after projecting the
 // mean out of the right-hand side; chi is defined up to an additive constant.
 //
-// Mixed precision (default): FP64 iterative refinement around FP32 multigrid.
-//   One fused FP64 pass per refinement step adds the last FP32 correction to
-//   x64 (ping-pong buffers selected by a device-side index, so early exit
-//   needs no host decision), writes the FP32 copy and the residual
-//   r = b - L x64, and sums r and r^2 per block in FP64; a one-block kernel
-//   reduces the sums in a fixed order and tests ||r - mean r|| <= tol ||b||.
-//   The correction solves L e = r - mean(r) with V-cycles in FP32.
+// Mixed precision (default): iterative refinement in double-float around FP32
+//   multigrid.  The iterate is a float-float pair (hi + lo, ~48-bit
+//   significand, error-free two-sum arithmetic on the FP32 pipe; this GPU's
+//   FP64 pipe made a native FP64 residual pass ~12x slower than its memory
+//   traffic).  One fused pass per refinement step adds the last FP32
+//   correction (ping-pong buffers selected by a device-side index, so early
+//   exit needs no host decision), writes the FP32 copy and the residual
+//   r = b - L x, and sums r and r^2 (FP64 across threads and blocks); a
+//   one-block kernel reduces the sums in a fixed order and tests
+//   ||r - mean r|| <= tol ||b - mean b||.  The correction solves
+//   L e = r - mean(r) with FP32 V-cycles.
 // Plain FP32 (comparator): V-cycles directly on x32 with an FP32 residual.
 //
 // Multigrid: cell-centred, halving while even and larger than 8; red-black
 // Gauss-Seidel, 2 pre- and 2 post-sweeps; residual restricted with weight 1/2
 // on the 8 children (average x H^2/h^2 for the unit-free operator); trilinear
-// prolongation (3/4, 1/4 per axis, mirrored at the walls).  Levels larger than
-// 16^3 use two fused z-marching kernels per V-cycle: a CTA owns a 32 x 16
-// column tile and a 32-plane z chunk, keeps a ring of planes in shared memory
-// and pipelines the four half-sweeps (half-sweep s works s planes behind the
-// newest), which reproduces global red-black Gauss-Seidel exactly while each
-// field is read from HBM once; the pre-smoothing kernel also forms the
-// residual and restricts it, the post-smoothing kernel adds the prolonged
-// coarse correction while loading.  Grids of at most 16^3 run a whole
-// V-cycle hierarchy in one CTA's shared memory.
+// prolongation (3/4, 1/4 per axis, mirrored at the walls).  Levels with
+// n >= 128 use two fused z-marching kernels per V-cycle: a CTA owns a 64 x 16
+// column tile and a 16-plane z chunk, keeps a ring of planes in shared memory
+// (next plane prefetched with cp.async) and pipelines the four half-sweeps
+// (half-sweep s works s planes behind the newest), which reproduces global
+// red-black Gauss-Seidel exactly while x is read from HBM once; the
+// pre-smoothing kernel also forms the residual and restricts it, the
+// post-smoothing kernel adds the prolonged coarse correction while loading.
+// Mid-size levels use one launch per half-sweep; grids of at most 16^3 run a
+// whole V-cycle hierarchy in one CTA's shared memory.
 //
 // Every kernel of the fixed launch sequence reads the solve's `done` flag and
 // returns at once when it is set, so the sequence (recorded once as a CUDA
@@ -39,7 +44,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kNu = 2;              // red-black sweeps before and after the coarse correction
-constexpr int kTX = 32, kTY = 16, kZC = 32;
+constexpr int kTX = 64, kTY = 16;
 constexpr int kSmThreads = 512;
 constexpr int kSmallN = 16;         // levels up to 16^3 are solved in one CTA
 
@@ -47,51 +52,72 @@ __device__ __forceinline__ int64_t lin(int i, int j, int k, int n) {
   return ((int64_t)k * n + j) * n + i;
 }
 
-struct Pair64 {
-  double* buf[2];
+struct PairFF {
+  float2* buf[2];
 };
 
-// ---------------------------------------------------------------- FP64 refinement
-// x64_new = x64 + e (e may be null: no correction this step; cold: x64 := 0),
-// x32 = (float) x64_new, r32 = b - L x64_new, per-block sums of r and r^2.
+__device__ __forceinline__ float rhs_hi(const float* b, int64_t t, float& lo) {
+  lo = 0.f;
+  return b[t];
+}
+__device__ __forceinline__ float rhs_hi(const double* b, int64_t t, float& lo) {
+  const double v = b[t];
+  const float hi = (float)v;
+  lo = (float)(v - (double)hi);
+  return hi;
+}
+
+// ---------------------------------------------------------------- refinement pass
+// The refinement iterate is kept in float-float (hi + lo, ~48-bit significand):
+// on this GPU the FP64 pipe made an FP64 stencil pass about 12x slower than its
+// memory traffic, while the error-free sums below run on the FP32 pipe.
+//   x_new = x + e (e may be null: no correction this step; cold: x := 0),
+//   x32 = hi(x_new), r32 = b - L x_new (each neighbour difference formed
+//   exactly), per-thread sums of r and r^2 in FP32, per-block sums in FP64.
 template <typename TB>
-__global__ void update_residual_kernel(Pair64 xp, const float* __restrict__ e, const TB* __restrict__ b,
+__global__ void update_residual_kernel(PairFF xp, const float* __restrict__ e, const TB* __restrict__ b,
                                        int n, float* __restrict__ r32, float* __restrict__ x32,
                                        double* __restrict__ partials, SolveState* ss) {
   if (ss->done) return;
   __shared__ double red[32];
   const int cur = ss->xidx;
   const bool cold = ss->cold != 0;
-  const double* __restrict__ xin = xp.buf[cur];
-  double* __restrict__ xout = xp.buf[e ? cur ^ 1 : cur];
+  const float2* __restrict__ xin = xp.buf[cur];
+  float2* __restrict__ xout = xp.buf[e ? cur ^ 1 : cur];
   const int64_t N = (int64_t)n * n * n;
-  double s1 = 0.0, s2 = 0.0;
+  float s1 = 0.f, s2 = 0.f;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
-    double xc = 0.0, acc = 0.0;
+    float2 xc = make_float2(0.f, 0.f), acc = make_float2(0.f, 0.f);
     if (!cold) {
-      xc = xin[t] + (e ? (double)e[t] : 0.0);
-      auto nb = [&](int64_t q) { return xin[q] + (e ? (double)e[q] : 0.0); };
-      if (i > 0) acc += nb(t - 1) - xc;
-      if (i < n - 1) acc += nb(t + 1) - xc;
-      if (j > 0) acc += nb(t - n) - xc;
-      if (j < n - 1) acc += nb(t + n) - xc;
-      if (k > 0) acc += nb(t - (int64_t)n * n) - xc;
-      if (k < n - 1) acc += nb(t + (int64_t)n * n) - xc;
+      auto val = [&](int64_t q) {
+        const float2 v = xin[q];
+        return e ? ff_add_f(v, e[q]) : v;
+      };
+      xc = val(t);
+      if (i > 0) acc = ff_add(acc, ff_sub(val(t - 1), xc));
+      if (i < n - 1) acc = ff_add(acc, ff_sub(val(t + 1), xc));
+      if (j > 0) acc = ff_add(acc, ff_sub(val(t - n), xc));
+      if (j < n - 1) acc = ff_add(acc, ff_sub(val(t + n), xc));
+      if (k > 0) acc = ff_add(acc, ff_sub(val(t - (int64_t)n * n), xc));
+      if (k < n - 1) acc = ff_add(acc, ff_sub(val(t + (int64_t)n * n), xc));
     }
-    const double r = (double)b[t] - acc;
+    float blo;
+    const float bhi = rhs_hi(b, t, blo);
+    const float2 r = ff_sub(make_float2(bhi, blo), acc);
     if (e || cold) xout[t] = xc;
-    x32[t] = (float)xc;
-    r32[t] = (float)r;
-    s1 += r;
-    s2 += r * r;
+    x32[t] = xc.x;
+    const float rf = r.x + r.y;
+    r32[t] = rf;
+    s1 += rf;
+    s2 += rf * rf;
   }
-  s1 = block_sum<kThreads>(s1, red);
-  s2 = block_sum<kThreads>(s2, red);
+  double d1 = block_sum<kThreads>((double)s1, red);
+  double d2 = block_sum<kThreads>((double)s2, red);
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = s1;
-    partials[2 * blockIdx.x + 1] = s2;
+    partials[2 * blockIdx.x] = d1;
+    partials[2 * blockIdx.x + 1] = d2;
   }
 }
 
@@ -191,13 +217,20 @@ __global__ void solve_begin_kernel(SolveState* ss, int cold) {
 }
 
 // ---------------------------------------------------------------- fused smoothers
+// Levels with n >= kFusedMin.  A CTA owns a kTX x kTY column tile and a
+// kZC-plane z chunk and walks z, keeping a ring of x planes (with halo) in
+// shared memory; the next plane is prefetched with cp.async while the current
+// one is processed.  Half-sweep s of the pipeline works s planes behind the
+// newest plane, so every update sees exactly the neighbour values a global
+// red-black Gauss-Seidel sweep would.  b is read through the L1/L2 caches.
+constexpr int kFusedMin = 128;
+
 template <bool PRE>
 struct SmGeom {
   static constexpr int H = PRE ? 2 * kNu + 1 : 2 * kNu;   // halo of the loaded tile
   static constexpr int WX = kTX + 2 * H, WY = kTY + 2 * H, P = WX * WY;
-  static constexpr int RX = PRE ? 2 * kNu + 3 : 2 * kNu + 2;   // x plane ring
-  static constexpr int RB = PRE ? 2 * kNu + 2 : 2 * kNu + 1;   // b plane ring
-  static constexpr size_t smem = sizeof(float) * ((size_t)(RX + RB) * P + (PRE ? (kTX / 2) * (kTY / 2) : 0));
+  static constexpr int RX = PRE ? 2 * kNu + 4 : 2 * kNu + 3; // planes alive + 1 prefetch slot
+  static constexpr size_t smem = sizeof(float) * ((size_t)RX * P + (PRE ? (kTX / 2) * (kTY / 2) : 0));
 };
 
 __device__ __forceinline__ float prolong_at(const float* __restrict__ xc, int nc, int gx, int gy, int gz) {
@@ -212,6 +245,13 @@ __device__ __forceinline__ float prolong_at(const float* __restrict__ xc, int nc
          a * c * c * xc[lin(I, J2, K2, nc)] + c * c * c * xc[lin(I2, J2, K2, nc)];
 }
 
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // PRE: x_out = 2 red-black sweeps (red first) of x_in (or of 0 when ZERO), and
 //      bc = 1/2 * sum of the children residuals b - L x_out.
 // POST: x_out = 2 sweeps (black first) of x_in + P xc.
@@ -219,7 +259,7 @@ template <bool PRE, bool ZERO>
 __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restrict__ xin,
                                                             float* __restrict__ xout,
                                                             const float* __restrict__ b,
-                                                            const double* __restrict__ shift, int n,
+                                                            const double* __restrict__ shift, int n, int zc,
                                                             const float* __restrict__ xc,
                                                             float* __restrict__ bc,
                                                             const int* __restrict__ gate) {
@@ -227,10 +267,9 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
   using G = SmGeom<PRE>;
   extern __shared__ float sm[];
   float* xs = sm;                       // RX planes
-  float* bs = sm + G::RX * G::P;        // RB planes
-  float* cacc = bs + G::RB * G::P;      // coarse accumulator (PRE)
-  const int X0 = blockIdx.x * kTX, Y0 = blockIdx.y * kTY, z0 = blockIdx.z * kZC;
-  const int z1 = min(z0 + kZC, n);
+  float* cacc = sm + G::RX * G::P;      // coarse accumulator (PRE)
+  const int X0 = blockIdx.x * kTX, Y0 = blockIdx.y * kTY, z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, n);
   const int ax = max(X0 - G::H, 0), bx = min(X0 + kTX + G::H, n);
   const int ay = max(Y0 - G::H, 0), by = min(Y0 + kTY + G::H, n);
   const int zlo = max(z0 - G::H, 0), zhi = min(z1 + G::H, n);
@@ -238,22 +277,30 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
   const int nc = n >> 1;
   const int c0 = PRE ? 0 : 1;           // colour of the first half-sweep
   const int zend = zhi + 2 * kNu + (PRE ? 1 : 0);
+
+  auto issue = [&](int z) {             // start loading plane z into its ring slot
+    float* xp = xs + (z % G::RX) * G::P;
+    for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
+      const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
+      const bool in = gx >= ax && gx < bx && gy >= ay && gy < by;
+      if (in && !ZERO)
+        cp_async4(xp + c, xin + lin(gx, gy, z, n));
+      else
+        xp[c] = 0.f;
+    }
+  };
+
+  issue(zlo);
+  cp_async_commit();
   for (int zin = zlo; zin < zend; ++zin) {
-    if (zin < zhi) {
+    if (zin + 1 < zhi) issue(zin + 1);
+    cp_async_commit();
+    cp_async_wait1();                   // plane zin has landed (this thread's copies)
+    if (!PRE && zin < zhi) {
       float* xp = xs + (zin % G::RX) * G::P;
-      float* bp = bs + (zin % G::RB) * G::P;
       for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
         const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
-        const bool in = gx >= ax && gx < bx && gy >= ay && gy < by;
-        float xv = 0.f, bv = 0.f;
-        if (in) {
-          const int64_t g = lin(gx, gy, zin, n);
-          if (!ZERO) xv = xin[g];
-          if (!PRE) xv += prolong_at(xc, nc, gx, gy, zin);
-          bv = b[g] - sh;
-        }
-        xp[c] = xv;
-        bp[c] = bv;
+        if (gx >= ax && gx < bx && gy >= ay && gy < by) xp[c] += prolong_at(xc, nc, gx, gy, zin);
       }
     }
     __syncthreads();
@@ -268,10 +315,14 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
         float* xp = xs + (p % G::RX) * G::P;
         const float* xm = (p > 0) ? xs + ((p - 1) % G::RX) * G::P : nullptr;
         const float* xq = (p < n - 1) ? xs + ((p + 1) % G::RX) * G::P : nullptr;
-        const float* bp = bs + (p % G::RB) * G::P;
-        for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
-          const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
-          if (gx < xlo || gx >= xhi || gy < ylo || gy >= yhi || ((gx + gy + p) & 1) != colour) continue;
+        // only the cells of this colour: row ly, pair j -> lx = 2j + parity
+        for (int k = threadIdx.x; k < G::WY * (G::WX / 2); k += blockDim.x) {
+          const int ly = k / (G::WX / 2), j = k % (G::WX / 2);
+          const int gy = Y0 - G::H + ly;
+          const int lx = 2 * j + ((colour + gy + p + X0 + G::H) & 1);
+          const int gx = X0 - G::H + lx;
+          if (gx < xlo || gx >= xhi || gy < ylo || gy >= yhi) continue;
+          const int c = ly * G::WX + lx;
           float acc = 0.f;
           int cnt = 0;
           if (gx > 0) { acc += xp[c - 1]; ++cnt; }
@@ -280,7 +331,7 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
           if (gy < n - 1) { acc += xp[c + G::WX]; ++cnt; }
           if (xm) { acc += xm[c]; ++cnt; }
           if (xq) { acc += xq[c]; ++cnt; }
-          xp[c] = (acc - bp[c]) / (float)cnt;
+          xp[c] = (acc - (__ldg(b + lin(gx, gy, p, n)) - sh)) / (float)cnt;
         }
       }
       __syncthreads();
@@ -291,7 +342,6 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
         const float* xp = xs + (q % G::RX) * G::P;
         const float* xm = (q > 0) ? xs + ((q - 1) % G::RX) * G::P : nullptr;
         const float* xq = (q < n - 1) ? xs + ((q + 1) % G::RX) * G::P : nullptr;
-        const float* bp = bs + (q % G::RB) * G::P;
         for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
           const int gx = X0 + c % kTX, gy = Y0 + c / kTX;
           if (gx < n && gy < n) {
@@ -316,7 +366,7 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
             if (gy < n - 1) lx += xp[lc + G::WX] - xv;
             if (xm) lx += xm[lc] - xv;
             if (xq) lx += xq[lc] - xv;
-            r += bp[lc] - lx;
+            r += (__ldg(b + lin(gx, gy, q, n)) - sh) - lx;
           }
           if ((q & 1) == 0) {
             cacc[c] = r;
@@ -343,6 +393,84 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
     }
   }
 }
+
+// ---------------------------------------------------------------- mid-size levels
+// 16 < n < kFusedMin: one launch per half-sweep (launch-latency regime, the
+// level is L2-resident).  In place on x.
+__global__ void zero_kernel(float* __restrict__ x, int64_t N, const int* __restrict__ gate) {
+  if (*gate) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x)
+    x[t] = 0.f;
+}
+
+__global__ void rbgs_kernel(float* __restrict__ x, const float* __restrict__ b,
+                            const double* __restrict__ shift, int n, int color,
+                            const int* __restrict__ gate) {
+  if (*gate) return;
+  const int half = n >> 1;
+  const int64_t M = (int64_t)half * n * n;
+  const float sh = shift ? (float)*shift : 0.f;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int ih = (int)(t % half);
+    const int64_t row = t / half;
+    const int j = (int)(row % n), k = (int)(row / n);
+    const int i = 2 * ih + ((j + k + color) & 1);
+    const int64_t p = lin(i, j, k, n);
+    float s = 0.f;
+    int cnt = 0;
+    if (i > 0) { s += x[p - 1]; ++cnt; }
+    if (i < n - 1) { s += x[p + 1]; ++cnt; }
+    if (j > 0) { s += x[p - n]; ++cnt; }
+    if (j < n - 1) { s += x[p + n]; ++cnt; }
+    if (k > 0) { s += x[p - (int64_t)n * n]; ++cnt; }
+    if (k < n - 1) { s += x[p + (int64_t)n * n]; ++cnt; }
+    x[p] = (s - (b[p] - sh)) / (float)cnt;
+  }
+}
+
+__global__ void resid_restrict_kernel(const float* __restrict__ x, const float* __restrict__ b,
+                                      const double* __restrict__ shift, int n,
+                                      float* __restrict__ bc, const int* __restrict__ gate) {
+  if (*gate) return;
+  const int nc = n >> 1;
+  const int64_t Mc = (int64_t)nc * nc * nc;
+  const float sh = shift ? (float)*shift : 0.f;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Mc;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(t % nc), J = (int)((t / nc) % nc), K = (int)(t / ((int64_t)nc * nc));
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
+      const int64_t p = lin(i, j, k, n);
+      const float xc = x[p];
+      float lx = 0.f;
+      if (i > 0) lx += x[p - 1] - xc;
+      if (i < n - 1) lx += x[p + 1] - xc;
+      if (j > 0) lx += x[p - n] - xc;
+      if (j < n - 1) lx += x[p + n] - xc;
+      if (k > 0) lx += x[p - (int64_t)n * n] - xc;
+      if (k < n - 1) lx += x[p + (int64_t)n * n] - xc;
+      acc += (b[p] - sh) - lx;
+    }
+    bc[t] = 0.5f * acc;
+  }
+}
+
+__global__ void prolong_kernel(const float* __restrict__ xc, float* __restrict__ x, int n,
+                               const int* __restrict__ gate) {
+  if (*gate) return;
+  const int nc = n >> 1;
+  const int64_t N = (int64_t)n * n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
+    x[t] += prolong_at(xc, nc, i, j, k);
+  }
+}
+
 
 // ---------------------------------------------------------------- small grids
 // A whole V-cycle hierarchy for n <= 16 in one CTA's shared memory: solves
@@ -515,18 +643,47 @@ int vcycle(wgeo_handle* h, int l, float* x0, float* x0b, const float* b0, const 
     WGEO_LAUNCH_CHECK();
     return WGEO_OK;
   }
-  const dim3 grid(div_up(n, kTX), div_up(n, kTY), div_up(n, kZC));
   const bool zero = (l == 0) ? zero0 : true;
+  const int nc = n >> 1;
+  const int64_t N = (int64_t)n * n * n, Nc = (int64_t)nc * nc * nc;
+  if (n < kFusedMin) {
+    // mid-size level: in place, one launch per half-sweep
+    const int gb = grid_blocks(N / 2, kThreads, 152 * 32);
+    if (zero) {
+      zero_kernel<<<grid_blocks(N, kThreads, 152 * 32), kThreads, 0, s>>>(x, N, gate);
+      WGEO_LAUNCH_CHECK();
+    }
+    for (int sw = 0; sw < kNu; ++sw)
+      for (int c = 0; c < 2; ++c) {
+        rbgs_kernel<<<gb, kThreads, 0, s>>>(x, b, shift, n, c, gate);
+        WGEO_LAUNCH_CHECK();
+      }
+    resid_restrict_kernel<<<grid_blocks(Nc, kThreads, 152 * 32), kThreads, 0, s>>>(x, b, shift, n,
+                                                                                  h->levels[l + 1].b, gate);
+    WGEO_LAUNCH_CHECK();
+    int rc = vcycle(h, l + 1, x0, x0b, b0, shift0, zero0, gate, s);
+    if (rc) return rc;
+    prolong_kernel<<<grid_blocks(N, kThreads, 152 * 32), kThreads, 0, s>>>(h->levels[l + 1].x, x, n, gate);
+    WGEO_LAUNCH_CHECK();
+    for (int sw = 0; sw < kNu; ++sw)
+      for (int c = 1; c >= 0; --c) {
+        rbgs_kernel<<<gb, kThreads, 0, s>>>(x, b, shift, n, c, gate);
+        WGEO_LAUNCH_CHECK();
+      }
+    return WGEO_OK;
+  }
+  const int zc = 16;
+  const dim3 grid(div_up(n, kTX), div_up(n, kTY), div_up(n, zc));
   if (zero)
-    smooth_kernel<true, true><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, nullptr,
+    smooth_kernel<true, true><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, zc, nullptr,
                                                                            h->levels[l + 1].b, gate);
   else
-    smooth_kernel<true, false><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, nullptr,
+    smooth_kernel<true, false><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, zc, nullptr,
                                                                             h->levels[l + 1].b, gate);
   WGEO_LAUNCH_CHECK();
   int rc = vcycle(h, l + 1, x0, x0b, b0, shift0, zero0, gate, s);
   if (rc) return rc;
-  smooth_kernel<false, false><<<grid, kSmThreads, SmGeom<false>::smem, s>>>(xb, x, b, shift, n,
+  smooth_kernel<false, false><<<grid, kSmThreads, SmGeom<false>::smem, s>>>(xb, x, b, shift, n, zc,
                                                                             h->levels[l + 1].x, nullptr, gate);
   WGEO_LAUNCH_CHECK();
   return WGEO_OK;
@@ -554,9 +711,9 @@ int enqueue_solve(wgeo_handle* h, int res, int mode, cudaStream_t s) {
     return WGEO_OK;
   }
   const double tol = mode == 0 ? h->opt.tol_rel : h->opt.tol_rel_adjoint;
-  Pair64 xp;
-  xp.buf[0] = mode == 0 ? h->chi64[0] : h->lam64[0];
-  xp.buf[1] = mode == 0 ? h->chi64[1] : h->lam64[1];
+  PairFF xp;
+  xp.buf[0] = mode == 0 ? h->chiff[0] : h->lamff[0];
+  xp.buf[1] = mode == 0 ? h->chiff[1] : h->lamff[1];
   float* x32 = mode == 0 ? h->chi32 : h->lam32;
   const int maxr = h->opt.max_refine;
   const int nv = h->opt.vcycles_per_refine;

@@ -89,6 +89,32 @@ struct SolverGraph {
   cudaGraphExec_t exec = nullptr;
 };
 
+// ---- float-float arithmetic (value = x + y, |y| <= ulp(x)/2).  Knuth's
+// two-sum and Dekker's fast two-sum give the exact rounding error of one
+// addition; the __f*_rn intrinsics keep the compiler from contracting or
+// reordering them.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, err);
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {   // needs |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  const float2 t = two_sum(a.y, b.y);
+  const float2 r = fast_two_sum(s.x, __fadd_rn(s.y, t.x));
+  return fast_two_sum(r.x, __fadd_rn(r.y, t.y));
+}
+__device__ __forceinline__ float2 ff_sub(float2 a, float2 b) { return ff_add(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 ff_add_f(float2 a, float b) {
+  const float2 s = two_sum(a.x, b);
+  return fast_two_sum(s.x, __fadd_rn(s.y, a.y));
+}
+
 __device__ __forceinline__ float3 f3(const float4 v) { return make_float3(v.x, v.y, v.z); }
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
@@ -170,14 +196,14 @@ struct wgeo_handle {
   // grid fields (sized for max_res^3)
   float* b32 = nullptr;
   float* chi32 = nullptr;
-  double* chi64[2] = {nullptr, nullptr};   // FP64 iterate, ping-pong (index on the device)
+  float2* chiff[2] = {nullptr, nullptr};   // float-float iterate, ping-pong (index on the device)
   float* r32 = nullptr;
   float* e32 = nullptr;
   float* phi = nullptr;
   int* ctri = nullptr;
   double* dphi64 = nullptr;
   double* dchi64 = nullptr;
-  double* lam64[2] = {nullptr, nullptr};   // adjoint solution, ping-pong like chi64
+  float2* lamff[2] = {nullptr, nullptr};   // adjoint solution, ping-pong like chiff
   float* lam32 = nullptr;
   float* level_pool = nullptr;
 
