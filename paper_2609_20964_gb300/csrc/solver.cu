@@ -86,9 +86,11 @@ __global__ void update_residual_kernel(PairFF xp, const float* __restrict__ e, c
   float2* __restrict__ xout = xp.buf[e ? cur ^ 1 : cur];
   const int64_t N = (int64_t)n * n * n;
   float s1 = 0.f, s2 = 0.f;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
+  (void)N;
+  for (int row = blockIdx.x; row < n * n; row += gridDim.x) {     // rows (j, k), x along threads
+   const int j = row % n, k = row / n;
+   for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t t = (int64_t)row * n + i;
     float2 xc = make_float2(0.f, 0.f), acc = make_float2(0.f, 0.f);
     if (!cold) {
       auto val = [&](int64_t q) {
@@ -112,6 +114,7 @@ __global__ void update_residual_kernel(PairFF xp, const float* __restrict__ e, c
     r32[t] = rf;
     s1 += rf;
     s2 += rf * rf;
+   }
   }
   double d1 = block_sum<kThreads>((double)s1, red);
   double d2 = block_sum<kThreads>((double)s2, red);
@@ -230,7 +233,9 @@ struct SmGeom {
   static constexpr int H = PRE ? 2 * kNu + 1 : 2 * kNu;   // halo of the loaded tile
   static constexpr int WX = kTX + 2 * H, WY = kTY + 2 * H, P = WX * WY;
   static constexpr int RX = PRE ? 2 * kNu + 4 : 2 * kNu + 3; // planes alive + 1 prefetch slot
-  static constexpr size_t smem = sizeof(float) * ((size_t)RX * P + (PRE ? (kTX / 2) * (kTY / 2) : 0));
+  static constexpr int CW = WX / 2 + 3, CH = WY / 2 + 3;       // coarse staging window (POST)
+  static constexpr size_t smem =
+      sizeof(float) * ((size_t)RX * P + (PRE ? (kTX / 2) * (kTY / 2) : CW * CH));
 };
 
 __device__ __forceinline__ float prolong_at(const float* __restrict__ xc, int nc, int gx, int gy, int gz) {
@@ -297,10 +302,29 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
     cp_async_commit();
     cp_async_wait1();                   // plane zin has landed (this thread's copies)
     if (!PRE && zin < zhi) {
+      // prolongation, separably: the coarse window interpolated in z into shared
+      // memory (2 reads per coarse cell), then bilinear in x, y from there
+      float* cz = cacc;
+      const int K = zin >> 1;
+      const int K2 = min(max((zin & 1) ? K + 1 : K - 1, 0), nc - 1);
+      const int cI0 = ((X0 - G::H) >> 1) - 1, cJ0 = ((Y0 - G::H) >> 1) - 1;
+      for (int c = threadIdx.x; c < G::CW * G::CH; c += blockDim.x) {
+        const int ci = min(max(cI0 + c % G::CW, 0), nc - 1);
+        const int cj = min(max(cJ0 + c / G::CW, 0), nc - 1);
+        cz[c] = 0.75f * xc[lin(ci, cj, K, nc)] + 0.25f * xc[lin(ci, cj, K2, nc)];
+      }
+      __syncthreads();
       float* xp = xs + (zin % G::RX) * G::P;
       for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
         const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
-        if (gx >= ax && gx < bx && gy >= ay && gy < by) xp[c] += prolong_at(xc, nc, gx, gy, zin);
+        if (gx >= ax && gx < bx && gy >= ay && gy < by) {
+          const int I = gx >> 1, J = gy >> 1;
+          const int I2 = min(max((gx & 1) ? I + 1 : I - 1, 0), nc - 1);
+          const int J2 = min(max((gy & 1) ? J + 1 : J - 1, 0), nc - 1);
+          const int r1 = (J - cJ0) * G::CW, r2 = (J2 - cJ0) * G::CW;
+          xp[c] += 0.5625f * cz[r1 + I - cI0] + 0.1875f * cz[r1 + I2 - cI0] +
+                   0.1875f * cz[r2 + I - cI0] + 0.0625f * cz[r2 + I2 - cI0];
+        }
       }
     }
     __syncthreads();

@@ -497,6 +497,69 @@ __global__ void puck_up_kernel(float4* __restrict__ pyr, int64_t off_child, int 
   }
 }
 
+// Tight puck of an internal node at level l >= 1 (dim d_l; level 1 = bricks):
+// axis and centre from its own triangles, radius and half-thickness from
+// their vertices (two passes over the bricks it covers).
+__global__ void puck_tight_kernel(const Tri* __restrict__ tris, const int* __restrict__ brick_off, int nb,
+                                  int64_t cap, int level, int dim, float4* __restrict__ out) {
+  const int64_t np = (int64_t)dim * dim * dim;
+  const int span = 1 << (level - 1);        // bricks per axis under one node
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < np;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % dim), y = (int)((t / dim) % dim), z = (int)(t / ((int64_t)dim * dim));
+    float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
+    int64_t cnt = 0;
+    for (int bz = z * span; bz < min((z + 1) * span, nb); ++bz)
+      for (int by = y * span; by < min((y + 1) * span, nb); ++by)
+        for (int bx = x * span; bx < min((x + 1) * span, nb); ++bx) {
+          const int br = (bz * nb + by) * nb + bx;
+          const int64_t s1 = min((int64_t)brick_off[br + 1], cap);
+          for (int64_t q = brick_off[br]; q < s1; ++q) {
+            const Tri tr = tris[q];
+            const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
+            cs.x += a.x + b.x + c.x;
+            cs.y += a.y + b.y + c.y;
+            cs.z += a.z + b.z + c.z;
+            const float3 cr = cross3(sub3(b, a), sub3(c, a));
+            ns.x += cr.x;
+            ns.y += cr.y;
+            ns.z += cr.z;
+            ++cnt;
+          }
+        }
+    if (cnt == 0) {
+      out[2 * t] = make_float4(0.f, 0.f, 0.f, -1.f);
+      out[2 * t + 1] = make_float4(0.f, 0.f, 1.f, 0.f);
+      continue;
+    }
+    const float inv = 1.f / (3.f * (float)cnt);
+    const float3 cc = make_float3(cs.x * inv, cs.y * inv, cs.z * inv);
+    const float nn = sqrtf(dot3(ns, ns));
+    const float3 nv = nn > 0.f ? make_float3(ns.x / nn, ns.y / nn, ns.z / nn) : make_float3(0.f, 0.f, 1.f);
+    float r = 0.f, th = 0.f;
+    for (int bz = z * span; bz < min((z + 1) * span, nb); ++bz)
+      for (int by = y * span; by < min((y + 1) * span, nb); ++by)
+        for (int bx = x * span; bx < min((x + 1) * span, nb); ++bx) {
+          const int br = (bz * nb + by) * nb + bx;
+          const int64_t s1 = min((int64_t)brick_off[br + 1], cap);
+          for (int64_t q = brick_off[br]; q < s1; ++q) {
+            const Tri tr = tris[q];
+            const float4 vv[3] = {tr.a, tr.b, tr.c};
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+              const float3 d = sub3(f3(vv[v]), cc);
+              const float zz = dot3(d, nv);
+              th = fmaxf(th, fabsf(zz));
+              r = fmaxf(r, sqrtf(fmaxf(dot3(d, d) - zz * zz, 0.f)));
+            }
+          }
+        }
+    const float pad = kPuckPad * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cc.z) + r + th) + 1e-7f;
+    out[2 * t] = make_float4(cc.x, cc.y, cc.z, r * (1.f + kPuckPad) + pad);
+    out[2 * t + 1] = make_float4(nv.x, nv.y, nv.z, th * (1.f + kPuckPad) + pad);
+  }
+}
+
 // Squared distance from p to the solid cylinder of a puck (INF when empty).
 __device__ __forceinline__ float puck_dist2(const float3 p, const float4 A, const float4 B) {
   if (A.w < 0.f) return INFINITY;
@@ -597,9 +660,7 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
       if (A.w < 0.f) continue;
       const float d = puck_dist2(p, A, pyr[2 * cg + 1]);
       if (!__any_sync(0xffffffffu, d < best)) continue;
-      float dm = d;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dm = fminf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+      const float dm = __shfl_sync(0xffffffffu, d, 0);   // ordering key: the first lane's bound
       int q2 = nc;
       while (q2 > 0 && key[q2 - 1] < dm) {
         key[q2] = key[q2 - 1];
@@ -728,8 +789,12 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   WGEO_LAUNCH_CHECK();
   for (int l = 1; l < pi.nlev; ++l) {
     const int64_t np = (int64_t)pi.dim[l] * pi.dim[l] * pi.dim[l];
-    puck_up_kernel<<<grid_blocks(np, 128, 152 * 16), 128, 0, s>>>(h->pyramid, pi.off[l - 1], pi.dim[l - 1],
-                                                                  pi.off[l], pi.dim[l]);
+    if (l <= 4)   // fitted to the subtree's vertices (at most 8^3 bricks per node)
+      puck_tight_kernel<<<grid_blocks(np, 64, 152 * 32), 64, 0, s>>>(h->tris, h->brick_off, g.nb, h->mesh_cap,
+                                                                     l, pi.dim[l], h->pyramid + 2 * pi.off[l]);
+    else          // merged conservatively from the children
+      puck_up_kernel<<<grid_blocks(np, 128, 152 * 16), 128, 0, s>>>(h->pyramid, pi.off[l - 1], pi.dim[l - 1],
+                                                                    pi.off[l], pi.dim[l]);
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStMC, slot, s);

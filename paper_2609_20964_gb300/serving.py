@@ -29,7 +29,7 @@ import torch
 from .api import Reconstructor
 
 
-@dataclass
+@dataclass(eq=False)
 class Request:
     points: object                 # [n,3] float32 (numpy or torch)
     normals: object
@@ -161,8 +161,9 @@ class Server:
         for item in self.inflight:
             if item[4].query():
                 done.append(item)
+        gone = {id(item) for item in done}
+        self.inflight = [item for item in self.inflight if id(item) not in gone]
         for item in done:
-            self.inflight.remove(item)
             req, fut, slot, h, ev, out, _ = item
             info = h.info()
             lat = time.perf_counter() - req.arrival
