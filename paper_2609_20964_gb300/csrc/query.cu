@@ -253,7 +253,7 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
   const int64_t N = (int64_t)n * n * n;
   const double c = st->c;
   const float hf = (float)g.h;
-  float dcacc = 0.f;
+  double dcacc = 0.0;    // dL/dc: terms of both signs that nearly cancel -> FP64
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N;
        o += (int64_t)gridDim.x * blockDim.x) {
     const double gphi64 = dphi[o];
@@ -291,10 +291,10 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
       const float w = deta / den;
       atomicAdd(&dchi[pl], (double)(w * (eta - 1.f)));
       atomicAdd(&dchi[pl + stv], (double)(-w * eta));
-      dcacc += w;
+      dcacc += (double)w;
     }
   }
-  const double s = block_sum<256>((double)dcacc, red);
+  const double s = block_sum<256>(dcacc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 

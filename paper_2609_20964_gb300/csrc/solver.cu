@@ -261,18 +261,20 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 //      bc = 1/2 * sum of the children residuals b - L x_out.
 // POST: x_out = 2 sweeps (black first) of x_in + P xc.
 template <bool PRE, bool ZERO>
-__global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restrict__ xin,
-                                                            float* __restrict__ xout,
-                                                            const float* __restrict__ b,
-                                                            const double* __restrict__ shift, int n, int zc,
-                                                            const float* __restrict__ xc,
-                                                            float* __restrict__ bc,
-                                                            const int* __restrict__ gate) {
+__global__ void __launch_bounds__(kSmThreads, 2) smooth_kernel(const float* __restrict__ xin,
+                                                               float* __restrict__ xout,
+                                                               const float* __restrict__ b,
+                                                               const double* __restrict__ shift, int n, int zc,
+                                                               const float* __restrict__ xc,
+                                                               float* __restrict__ bc,
+                                                               const int* __restrict__ gate) {
   if (*gate) return;
   using G = SmGeom<PRE>;
+  constexpr int NPAIR = G::P / 2;                               // cell pairs per plane (WX even)
+  constexpr int SLOTS = (NPAIR + kSmThreads - 1) / kSmThreads;  // pairs per thread
   extern __shared__ float sm[];
   float* xs = sm;                       // RX planes
-  float* cacc = sm + G::RX * G::P;      // coarse accumulator (PRE)
+  float* cacc = sm + G::RX * G::P;      // coarse accumulator (PRE) / coarse staging (POST)
   const int X0 = blockIdx.x * kTX, Y0 = blockIdx.y * kTY, z0 = blockIdx.z * zc;
   const int z1 = min(z0 + zc, n);
   const int ax = max(X0 - G::H, 0), bx = min(X0 + kTX + G::H, n);
@@ -280,16 +282,47 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
   const int zlo = max(z0 - G::H, 0), zhi = min(z1 + G::H, n);
   const float sh = shift ? (float)*shift : 0.f;
   const int nc = n >> 1;
+  const int64_t nn = (int64_t)n * n;
   const int c0 = PRE ? 0 : 1;           // colour of the first half-sweep
   const int zend = zhi + 2 * kNu + (PRE ? 1 : 0);
 
+  // Per-thread cell table, built once.  Within one z step every half-sweep s
+  // works on plane zin - s with colour c0 ^ (s-1), so the cell of a pair that
+  // has the right colour depends only on (row, zin): phase = rowph ^ (zin & 1).
+  int cloc[SLOTS][2], boff[SLOTS][2], info[SLOTS][2];   // info: depth | neighbour mask << 8
+  int rowph[SLOTS];
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) {
+    const int pr = threadIdx.x + k * kSmThreads;
+    const int ly = pr / (G::WX / 2), j = pr % (G::WX / 2);
+    const int gy = Y0 - G::H + ly;
+    rowph[k] = (c0 - 1 + gy + X0 + G::H) & 1;
+#pragma unroll
+    for (int ph = 0; ph < 2; ++ph) {
+      const int lx = 2 * j + ph, gx = X0 - G::H + lx;
+      cloc[k][ph] = ly * G::WX + lx;
+      boff[k][ph] = gy * n + gx;
+      int depth = -1;
+      if (pr < NPAIR && gx >= ax && gx < bx && gy >= ay && gy < by) {
+        depth = 2 * kNu;
+        if (ax > 0) depth = min(depth, gx - ax);
+        if (bx < n) depth = min(depth, bx - 1 - gx);
+        if (ay > 0) depth = min(depth, gy - ay);
+        if (by < n) depth = min(depth, by - 1 - gy);
+      }
+      const int mask = (gx > 0 ? 1 : 0) | (gx < n - 1 ? 2 : 0) | (gy > 0 ? 4 : 0) | (gy < n - 1 ? 8 : 0);
+      info[k][ph] = depth | (mask << 8);
+    }
+  }
+
   auto issue = [&](int z) {             // start loading plane z into its ring slot
     float* xp = xs + (z % G::RX) * G::P;
+    const float* src = xin + (int64_t)z * nn;
     for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
       const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
       const bool in = gx >= ax && gx < bx && gy >= ay && gy < by;
       if (in && !ZERO)
-        cp_async4(xp + c, xin + lin(gx, gy, z, n));
+        cp_async4(xp + c, src + gy * n + gx);
       else
         xp[c] = 0.f;
     }
@@ -308,10 +341,12 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
       const int K = zin >> 1;
       const int K2 = min(max((zin & 1) ? K + 1 : K - 1, 0), nc - 1);
       const int cI0 = ((X0 - G::H) >> 1) - 1, cJ0 = ((Y0 - G::H) >> 1) - 1;
+      const float* xk = xc + (int64_t)K * nc * nc;
+      const float* xk2 = xc + (int64_t)K2 * nc * nc;
       for (int c = threadIdx.x; c < G::CW * G::CH; c += blockDim.x) {
         const int ci = min(max(cI0 + c % G::CW, 0), nc - 1);
         const int cj = min(max(cJ0 + c / G::CW, 0), nc - 1);
-        cz[c] = 0.75f * xc[lin(ci, cj, K, nc)] + 0.25f * xc[lin(ci, cj, K2, nc)];
+        cz[c] = 0.75f * xk[cj * nc + ci] + 0.25f * xk2[cj * nc + ci];
       }
       __syncthreads();
       float* xp = xs + (zin % G::RX) * G::P;
@@ -328,34 +363,35 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
       }
     }
     __syncthreads();
+    const int zph = zin & 1;
 #pragma unroll
     for (int s = 1; s <= 2 * kNu; ++s) {
       const int p = zin - s;
       const int plo = zlo + (zlo > 0 ? s : 0), phi = zhi - (zhi < n ? s : 0);
       if (p >= plo && p < phi) {
-        const int xlo = ax + (ax > 0 ? s : 0), xhi = bx - (bx < n ? s : 0);
-        const int ylo = ay + (ay > 0 ? s : 0), yhi = by - (by < n ? s : 0);
-        const int colour = c0 ^ ((s - 1) & 1);
         float* xp = xs + (p % G::RX) * G::P;
-        const float* xm = (p > 0) ? xs + ((p - 1) % G::RX) * G::P : nullptr;
-        const float* xq = (p < n - 1) ? xs + ((p + 1) % G::RX) * G::P : nullptr;
-        // only the cells of this colour: row ly, pair j -> lx = 2j + parity
-        for (int k = threadIdx.x; k < G::WY * (G::WX / 2); k += blockDim.x) {
-          const int ly = k / (G::WX / 2), j = k % (G::WX / 2);
-          const int gy = Y0 - G::H + ly;
-          const int lx = 2 * j + ((colour + gy + p + X0 + G::H) & 1);
-          const int gx = X0 - G::H + lx;
-          if (gx < xlo || gx >= xhi || gy < ylo || gy >= yhi) continue;
-          const int c = ly * G::WX + lx;
+        const float* xm = xs + ((p + G::RX - 1) % G::RX) * G::P;
+        const float* xq = xs + ((p + 1) % G::RX) * G::P;
+        const bool hm = p > 0, hq = p < n - 1;
+        const float* bp = b + (int64_t)p * nn;
+        const int zcnt = (hm ? 1 : 0) + (hq ? 1 : 0);
+#pragma unroll
+        for (int k = 0; k < SLOTS; ++k) {
+          const int ph = rowph[k] ^ zph;
+          const int inf = ph ? info[k][1] : info[k][0];     // selects keep the tables in registers
+          if ((inf & 0xff) < s || (inf & 0x80)) continue;   // outside this stage's region / domain
+          const int c = ph ? cloc[k][1] : cloc[k][0];
+          const int bo = ph ? boff[k][1] : boff[k][0];
+          const int m = inf >> 8;
           float acc = 0.f;
-          int cnt = 0;
-          if (gx > 0) { acc += xp[c - 1]; ++cnt; }
-          if (gx < n - 1) { acc += xp[c + 1]; ++cnt; }
-          if (gy > 0) { acc += xp[c - G::WX]; ++cnt; }
-          if (gy < n - 1) { acc += xp[c + G::WX]; ++cnt; }
-          if (xm) { acc += xm[c]; ++cnt; }
-          if (xq) { acc += xq[c]; ++cnt; }
-          xp[c] = (acc - (__ldg(b + lin(gx, gy, p, n)) - sh)) / (float)cnt;
+          int cnt = zcnt;
+          if (m & 1) { acc += xp[c - 1]; ++cnt; }
+          if (m & 2) { acc += xp[c + 1]; ++cnt; }
+          if (m & 4) { acc += xp[c - G::WX]; ++cnt; }
+          if (m & 8) { acc += xp[c + G::WX]; ++cnt; }
+          if (hm) acc += xm[c];
+          if (hq) acc += xq[c];
+          xp[c] = __fdividef(acc - (__ldg(bp + bo) - sh), (float)cnt);
         }
       }
       __syncthreads();
@@ -364,14 +400,14 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
       const int q = zin - 2 * kNu - 1;
       if (q >= z0 && q < z1) {
         const float* xp = xs + (q % G::RX) * G::P;
-        const float* xm = (q > 0) ? xs + ((q - 1) % G::RX) * G::P : nullptr;
-        const float* xq = (q < n - 1) ? xs + ((q + 1) % G::RX) * G::P : nullptr;
+        const float* xm = xs + ((q + G::RX - 1) % G::RX) * G::P;
+        const float* xq = xs + ((q + 1) % G::RX) * G::P;
+        const bool hm = q > 0, hq = q < n - 1;
+        float* out = xout + (int64_t)q * nn;
+        const float* bq = b + (int64_t)q * nn;
         for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
           const int gx = X0 + c % kTX, gy = Y0 + c / kTX;
-          if (gx < n && gy < n) {
-            const int lc = (gy - Y0 + G::H) * G::WX + (gx - X0 + G::H);
-            xout[lin(gx, gy, q, n)] = xp[lc];
-          }
+          if (gx < n && gy < n) out[gy * n + gx] = xp[(gy - Y0 + G::H) * G::WX + (gx - X0 + G::H)];
         }
         // one thread per coarse cell of this plane: residual of its 4 children, fixed order
         for (int c = threadIdx.x; c < (kTX / 2) * (kTY / 2); c += blockDim.x) {
@@ -388,9 +424,9 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
             if (gx < n - 1) lx += xp[lc + 1] - xv;
             if (gy > 0) lx += xp[lc - G::WX] - xv;
             if (gy < n - 1) lx += xp[lc + G::WX] - xv;
-            if (xm) lx += xm[lc] - xv;
-            if (xq) lx += xq[lc] - xv;
-            r += (__ldg(b + lin(gx, gy, q, n)) - sh) - lx;
+            if (hm) lx += xm[lc] - xv;
+            if (hq) lx += xq[lc] - xv;
+            r += (__ldg(bq + gy * n + gx) - sh) - lx;
           }
           if ((q & 1) == 0) {
             cacc[c] = r;
@@ -405,18 +441,17 @@ __global__ void __launch_bounds__(kSmThreads) smooth_kernel(const float* __restr
       const int p = zin - 2 * kNu;
       if (p >= z0 && p < z1) {
         const float* xp = xs + (p % G::RX) * G::P;
+        float* out = xout + (int64_t)p * nn;
         for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
           const int gx = X0 + c % kTX, gy = Y0 + c / kTX;
-          if (gx < n && gy < n) {
-            const int lc = (gy - Y0 + G::H) * G::WX + (gx - X0 + G::H);
-            xout[lin(gx, gy, p, n)] = xp[lc];
-          }
+          if (gx < n && gy < n) out[gy * n + gx] = xp[(gy - Y0 + G::H) * G::WX + (gx - X0 + G::H)];
         }
       }
       __syncthreads();
     }
   }
 }
+
 
 // ---------------------------------------------------------------- mid-size levels
 // 16 < n < kFusedMin: one launch per half-sweep (launch-latency regime, the

@@ -74,11 +74,12 @@ def _smooth_nodes(ref):
 
 
 def _angle_deg(a, b):
-    dot = np.sum(a * b, axis=-1)
-    na = np.linalg.norm(a, axis=-1)
-    nb = np.linalg.norm(b, axis=-1)
-    c = np.clip(dot / np.maximum(na * nb, 1e-30), -1.0, 1.0)
-    return np.degrees(np.arccos(c))
+    # float64 and atan2(|a x b|, a . b): arccos of a float32-normalised dot
+    # product near 1 would itself carry ~0.02 degrees of rounding
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    cr = np.linalg.norm(np.cross(a, b), axis=-1)
+    return np.degrees(np.arctan2(cr, np.sum(a * b, axis=-1)))
 
 
 @pytest.mark.parametrize("name", list(CASES))
