@@ -165,10 +165,11 @@ int wgeo_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_gr
  * status into *out. */
 int wgeo_get_info(wgeo_handle* h, wgeo_info* out);
 
-/* Copies internal fields of the last forward into caller DEVICE buffers
- * (test and warm-start export): which = 0 b [res^3], 1 chi [res^3] (float32),
- * 2 phi [res^3]; enqueued on `stream`.  Returns the element count written or
- * a negative wgeo_status. */
+/* Copies internal fields into caller DEVICE float32 buffers [res^3] (stage-by-
+ * stage tests, warm-start export), enqueued on `stream`: which = 0 b, 1 chi,
+ * 2 phi (last forward); 3 dL/dphi, 4 dL/dchi, 5 lambda (adjoint solution) of
+ * the last backward (rounded to float32).  Returns the element count written
+ * or a negative wgeo_status. */
 int64_t wgeo_get_field(wgeo_handle* h, int32_t which, float* out, void* stream);
 
 /* Central cell of every point of the last forward (Sec. 2.3, Eq. 25): writes

@@ -376,9 +376,14 @@ int wgeo_get_info(wgeo_handle* h, wgeo_info* out) {
 int64_t wgeo_get_field(wgeo_handle* h, int32_t which, float* out, void* stream) {
   if (!h || !out) return -WGEO_ERR_INVALID_ARG;
   if (!h->have_forward) return -WGEO_ERR_NO_FORWARD;
+  const int64_t N = (int64_t)h->res * h->res * h->res;
+  if (which >= 3 && which <= 5) {
+    if (!h->opt.keep_for_backward) return -WGEO_ERR_NO_FORWARD;
+    const int rc = launch_export_adjoint(h, which, out, (cudaStream_t)stream);
+    return rc ? -rc : N;
+  }
   const float* src = which == 0 ? h->b32 : which == 1 ? h->chi32 : which == 2 ? h->phi : nullptr;
   if (!src) return -WGEO_ERR_INVALID_ARG;
-  const int64_t N = (int64_t)h->res * h->res * h->res;
   if (cudaMemcpyAsync(out, src, 4 * N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
     return -WGEO_ERR_CUDA;
   return N;

@@ -530,3 +530,39 @@ int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_
 }
 
 }  // namespace wgeo
+
+namespace wgeo {
+
+namespace {
+
+__global__ void export_f64_kernel(const double* __restrict__ src, int64_t N, float* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (float)src[t];
+}
+
+__global__ void export_ff_kernel(const float2* __restrict__ a, const float2* __restrict__ b,
+                                 const int* __restrict__ idx, int64_t N, float* __restrict__ out) {
+  const float2* __restrict__ src = (*idx) ? b : a;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = src[t].x + src[t].y;
+}
+
+}  // namespace
+
+// Backward intermediates as float32: 3 dL/dphi, 4 dL/dchi, 5 lambda.
+int launch_export_adjoint(wgeo_handle* h, int which, float* out, cudaStream_t s) {
+  const int64_t N = (int64_t)h->res * h->res * h->res;
+  const int gb = grid_blocks(N, 256, 152 * 32);
+  if (which == 3)
+    export_f64_kernel<<<gb, 256, 0, s>>>(h->dphi64, N, out);
+  else if (which == 4)
+    export_f64_kernel<<<gb, 256, 0, s>>>(h->dchi64, N, out);
+  else
+    export_ff_kernel<<<gb, 256, 0, s>>>(h->lamff[0], h->lamff[1], &h->dstate->bwd.xidx, N, out);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+}  // namespace wgeo

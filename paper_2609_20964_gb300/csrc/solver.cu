@@ -731,7 +731,23 @@ int vcycle(wgeo_handle* h, int l, float* x0, float* x0b, const float* b0, const 
       }
     return WGEO_OK;
   }
-  const int zc = 16;
+  // z chunk: a CTA's pipeline costs ~ (zc + 3 * 2 kNu) plane steps and runs in
+  // ceil(CTAs / resident CTAs) waves; take the chunk with the lowest product
+  int zc = 16;
+  {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int slots = 2 * sms;
+    long best = -1;
+    for (int cand = 16; cand <= 64; cand *= 2) {
+      const long ctas = (long)div_up(n, kTX) * div_up(n, kTY) * div_up(n, cand);
+      const long cost = ((ctas + slots - 1) / slots) * (cand + 6 * kNu);
+      if (best < 0 || cost < best) {
+        best = cost;
+        zc = cand;
+      }
+    }
+  }
   const dim3 grid(div_up(n, kTX), div_up(n, kTY), div_up(n, zc));
   if (zero)
     smooth_kernel<true, true><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, zc, nullptr,

@@ -789,7 +789,7 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   WGEO_LAUNCH_CHECK();
   for (int l = 1; l < pi.nlev; ++l) {
     const int64_t np = (int64_t)pi.dim[l] * pi.dim[l] * pi.dim[l];
-    if (l <= 4)   // fitted to the subtree's vertices (at most 8^3 bricks per node)
+    if (l <= 2)   // fitted to the subtree's vertices (at most 2^3 bricks per node)
       puck_tight_kernel<<<grid_blocks(np, 64, 152 * 32), 64, 0, s>>>(h->tris, h->brick_off, g.nb, h->mesh_cap,
                                                                      l, pi.dim[l], h->pyramid + 2 * pi.off[l]);
     else          // merged conservatively from the children

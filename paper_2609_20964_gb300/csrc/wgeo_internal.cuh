@@ -301,6 +301,7 @@ size_t pyramid_nodes(int nb);
 void host_mc_table(int* counts, int* tris);
 // query.cu
 int launch_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s);
+int launch_export_adjoint(wgeo_handle* h, int which, float* out, cudaStream_t s);
 int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
                     const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,
                     float* d_normals, float* d_q, cudaStream_t s);
