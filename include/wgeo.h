@@ -112,7 +112,8 @@ typedef struct {
   int64_t  sdf_node_visits;  /* with stage_timing = 2: octree nodes entered by the distance search (per warp) */
   int64_t  sdf_leaf_visits;  /* ... leaves entered (per warp) */
   int64_t  sdf_tri_tests;    /* ... point-triangle distance evaluations (per node, i.e. per lane) */
-  int64_t  reserved[3];
+  double   backward_dc;      /* dL/dc of the last backward */
+  int64_t  reserved[2];
 } wgeo_info;
 
 /* Fills `opt` with the defaults listed above.  Never fails for non-null opt. */

@@ -370,6 +370,7 @@ int wgeo_get_info(wgeo_handle* h, wgeo_info* out) {
   out->sdf_node_visits = (int64_t)st.sdf_cnt[0];
   out->sdf_leaf_visits = (int64_t)st.sdf_cnt[1];
   out->sdf_tri_tests = (int64_t)st.sdf_cnt[2];
+  out->backward_dc = st.dc;
   return WGEO_OK;
 }
 
