@@ -113,7 +113,9 @@ typedef struct {
   int64_t  sdf_leaf_visits;  /* ... leaves entered (per warp) */
   int64_t  sdf_tri_tests;    /* ... point-triangle distance evaluations (per node, i.e. per lane) */
   double   backward_dc;      /* dL/dc of the last backward */
-  int64_t  reserved[2];
+  int64_t  sdf_tie_nodes;    /* with stage_timing = 2: nodes whose nearest triangle was a float32
+                                near-tie, re-decided in float64 */
+  int64_t  reserved[1];
 } wgeo_info;
 
 /* Fills `opt` with the defaults listed above.  Never fails for non-null opt. */
@@ -166,11 +168,13 @@ int wgeo_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_gr
  * status into *out. */
 int wgeo_get_info(wgeo_handle* h, wgeo_info* out);
 
-/* Copies internal fields into caller DEVICE float32 buffers [res^3] (stage-by-
- * stage tests, warm-start export), enqueued on `stream`: which = 0 b, 1 chi,
- * 2 phi (last forward); 3 dL/dphi, 4 dL/dchi, 5 lambda (adjoint solution) of
- * the last backward (rounded to float32).  Returns the element count written
- * or a negative wgeo_status. */
+/* Copies internal fields into caller DEVICE buffers of 4-byte elements
+ * [res^3] (stage-by-stage tests, warm-start export), enqueued on `stream`:
+ * which = 0 b, 1 chi, 2 phi (last forward, float32); 3 dL/dphi, 4 dL/dchi,
+ * 5 lambda (adjoint solution) of the last backward (rounded to float32);
+ * 6 the index of each node's closest triangle (Eq. 33) in the order of
+ * wgeo_get_mesh, as int32 (-1 for an empty surface; needs keep_for_backward).
+ * Returns the element count written or a negative wgeo_status. */
 int64_t wgeo_get_field(wgeo_handle* h, int32_t which, float* out, void* stream);
 
 /* Central cell of every point of the last forward (Sec. 2.3, Eq. 25): writes

@@ -184,3 +184,50 @@ def winding_number(points, verts):
                + np.sum(B * C, 1) * la)
         w[i] = np.sum(2.0 * np.arctan2(num, den)) / (4 * np.pi)
     return w
+
+
+def closest_point_ambiguous(nodes, verts, d, delta, sep, chunk: int = 2048):
+    """True where the closest surface point of a node is not unique.
+
+    A node is ambiguous when some triangle lies within ``delta`` of the
+    minimum distance ``d`` (Eq. 33) but its closest point is more than ``sep``
+    away from the closest point of the minimising triangle.  There the
+    distance is not differentiable in the vertices (the node sits on, or
+    within rounding of, the medial axis of the mesh), so two exact
+    implementations may legitimately pick different triangles and obtain
+    different vertex gradients.  Triangles sharing the closest edge or vertex
+    give the same point and do not count.  Exact, k-d tree pruned: a triangle
+    with centroid m and centroid radius r_t can only be within d + delta of q
+    if |q - m| <= d + delta + r_t.
+    """
+    N = nodes.shape[0]
+    amb = np.zeros(N, dtype=bool)
+    if verts.shape[0] == 0 or N == 0:
+        return amb
+    cent = verts.mean(axis=1)
+    rad = np.max(np.linalg.norm(verts - cent[:, None, :], axis=2), axis=1)
+    rho = float(rad.max())
+    tree = cKDTree(cent)
+    for s in range(0, N, chunk):
+        q = nodes[s:s + chunk]
+        dq = d[s:s + chunk]
+        cands = tree.query_ball_point(q, dq + delta + rho + 1e-15)
+        lens = np.array([len(cc) for cc in cands])
+        if lens.sum() == 0:
+            continue
+        flat = np.concatenate([np.asarray(cc, dtype=np.int64) for cc in cands])
+        owner = np.repeat(np.arange(len(q)), lens)
+        keep = np.linalg.norm(q[owner] - cent[flat], axis=1) <= dq[owner] + delta + rad[flat] + 1e-15
+        flat, owner = flat[keep], owner[keep]
+        y, _ = closest_point_triangle(q[owner], verts[flat, 0], verts[flat, 1], verts[flat, 2])
+        dd = np.sqrt(np.sum((q[owner] - y) ** 2, -1))
+        near = dd <= dq[owner] + delta
+        # the closest point of the minimiser, per node
+        best = np.full(len(q), np.inf)
+        np.minimum.at(best, owner, dd)
+        is_best = dd == best[owner]
+        ybest = np.zeros((len(q), 3))
+        ybest[owner[is_best]] = y[is_best]
+        far = near & (np.linalg.norm(y - ybest[owner], axis=1) > sep)
+        amb[s:s + chunk] |= np.bincount(owner[far], minlength=len(q)).astype(bool)
+    return amb

@@ -50,7 +50,7 @@ class Info(C.Structure):
                 ("backward_residual_rel", C.c_double), ("isovalue", C.c_double),
                 ("n_triangles", _i64), ("n_points_used", _i64), ("h", C.c_double),
                 ("sdf_node_visits", _i64), ("sdf_leaf_visits", _i64), ("sdf_tri_tests", _i64),
-                ("backward_dc", C.c_double), ("reserved", _i64 * 2)]
+                ("backward_dc", C.c_double), ("sdf_tie_nodes", _i64), ("reserved", _i64 * 1)]
 
 
 SIGNATURES = {

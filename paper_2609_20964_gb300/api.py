@@ -110,8 +110,9 @@ class Reconstructor:
         return {k: getattr(inf, k) for k, _ in L.Info._fields_ if k != "reserved"}
 
     def field(self, which: str, stream=None) -> torch.Tensor:
-        idx = {"b": 0, "chi": 1, "phi": 2, "dphi": 3, "dchi": 4, "lambda": 5}[which]
-        out = torch.empty((self.res, self.res, self.res), device=self.device, dtype=torch.float32)
+        idx = {"b": 0, "chi": 1, "phi": 2, "dphi": 3, "dchi": 4, "lambda": 5, "closest": 6}[which]
+        dt = torch.int32 if which == "closest" else torch.float32
+        out = torch.empty((self.res, self.res, self.res), device=self.device, dtype=dt)
         r = self.lib.wgeo_get_field(self.h, idx, C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream)))
         if r < 0:
             L.check(-r, "wgeo_get_field")

@@ -101,6 +101,7 @@ __global__ void reset_status_kernel(DevState* st) {
   st->sdf_cnt[0] = 0;
   st->sdf_cnt[1] = 0;
   st->sdf_cnt[2] = 0;
+  st->sdf_cnt[3] = 0;
 }
 
 void accumulate_slot(StageTimer& t, int slot) {
@@ -370,6 +371,7 @@ int wgeo_get_info(wgeo_handle* h, wgeo_info* out) {
   out->sdf_node_visits = (int64_t)st.sdf_cnt[0];
   out->sdf_leaf_visits = (int64_t)st.sdf_cnt[1];
   out->sdf_tri_tests = (int64_t)st.sdf_cnt[2];
+  out->sdf_tie_nodes = (int64_t)st.sdf_cnt[3];
   out->backward_dc = st.dc;
   return WGEO_OK;
 }
@@ -378,12 +380,15 @@ int64_t wgeo_get_field(wgeo_handle* h, int32_t which, float* out, void* stream) 
   if (!h || !out) return -WGEO_ERR_INVALID_ARG;
   if (!h->have_forward) return -WGEO_ERR_NO_FORWARD;
   const int64_t N = (int64_t)h->res * h->res * h->res;
+  if (cudaSetDevice(h->device) != cudaSuccess) return -WGEO_ERR_CUDA;
   if (which >= 3 && which <= 5) {
     if (!h->opt.keep_for_backward) return -WGEO_ERR_NO_FORWARD;
     const int rc = launch_export_adjoint(h, which, out, (cudaStream_t)stream);
     return rc ? -rc : N;
   }
-  const float* src = which == 0 ? h->b32 : which == 1 ? h->chi32 : which == 2 ? h->phi : nullptr;
+  if (which == 6 && !h->opt.keep_for_backward) return -WGEO_ERR_NO_FORWARD;
+  const void* src = which == 0 ? (const void*)h->b32 : which == 1 ? (const void*)h->chi32
+                  : which == 2 ? (const void*)h->phi : which == 6 ? (const void*)h->ctri : nullptr;
   if (!src) return -WGEO_ERR_INVALID_ARG;
   if (cudaMemcpyAsync(out, src, 4 * N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
     return -WGEO_ERR_CUDA;

@@ -578,18 +578,42 @@ namespace {
 constexpr int kWarps = 4;          // warps per CTA
 constexpr int kStack = 96;         // per-warp traversal stack
 
+// Float32 rounding of one point-triangle distance, as a bound used to detect
+// near-ties: relative to the distance, plus an absolute part for the rounding
+// of the node and vertex coordinates (of magnitude up to the coordinate scale).
+constexpr float kTieRel = 4e-7f;
+constexpr float kTieAbs = 1.5e-7f;
+constexpr int kCand = 4;           // smallest float32 distances kept per node
+
+struct TieSlots {
+  int2* p[2];   // the two float-float iterate buffers; the one not current is free
+};
+
 // Warp-cooperative exact distance search: a warp owns a 4 x 4 x 2 patch of
 // nodes and walks the octree once for all of them (a subtree is entered when
-// its bound beats the current best of at least one lane); leaves are tested
+// its bound beats the current cut of at least one lane); leaves are tested
 // by every lane against its own node with the same (broadcast) triangle.
-template <bool COUNT>
-__global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restrict__ chi, SurfParams g,
+//
+// Exactness at near-ties: two triangles whose distances differ by less than
+// the float32 rounding may be ranked either way, and the closest point (and
+// with it the vertex gradient of Eqs. 35-36) differs between them.  Each lane
+// keeps its kCand smallest float32 distances (four: triangles sharing the
+// closest edge tie exactly, so candidates come in pairs) and prunes against
+// the best plus a rounding margin; when the second lies within that margin
+// the node is a near-tie: the ids of the candidates within the margin go to
+// tie_a, tie_b and tie_cd (-1 for none; tie_b = -1 marks a decided node) and
+// sdf_tie_kernel re-decides it in float-float.  Without TIES (no closest
+// triangle is kept) the search keeps the float32 minimum alone, which is
+// within the same rounding of the exact distance.
+template <bool COUNT, bool TIES>
+__global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __restrict__ chi, SurfParams g,
                                                           DevState* __restrict__ st,
                                                           const Tri* __restrict__ tris,
                                                           const int* __restrict__ leaf_off, int64_t cap,
                                                           const float4* __restrict__ pyr, PyrInfo pi,
                                                           float* __restrict__ phi, float* __restrict__ sdf_out,
-                                                          int* __restrict__ ctri) {
+                                                          int* __restrict__ ctri, int* __restrict__ tie_a,
+                                                          int* __restrict__ tie_b, TieSlots tie_cd) {
   __shared__ unsigned int s_node[kWarps][kStack];
   const int n = g.res;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -603,8 +627,20 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
   const int ic = min(i, n - 1), jc = min(j, n - 1), kc = min(k, n - 1);
   const float3 p = make_float3((float)(g.lo[0] + (ic + 0.5) * g.h), (float)(g.lo[1] + (jc + 0.5) * g.h),
                                (float)(g.lo[2] + (kc + 0.5) * g.h));
-  float best = INFINITY;
-  int bt = -1;
+  constexpr int NC = TIES ? kCand : 1;
+  float coord = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    coord = fmaxf(coord, (float)fmax(fabs(g.lo[a]), fabs(g.lo[a] + n * g.h)));
+  const float mabs = kTieAbs * coord;
+  float cd[NC];
+  int ct[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    cd[q] = INFINITY;
+    ct[q] = -1;
+  }
+  float cut = INFINITY;
   unsigned int* stk = s_node[w];
   int sp = 0;
   const int top = pi.nlev - 1;
@@ -621,7 +657,7 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
     const int idx = (int)(e & ((1u << 27) - 1));
     const int64_t gi = pi.off[lev] + idx;
     const float lb = puck_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
-    if (!__any_sync(0xffffffffu, lb < best)) continue;
+    if (!__any_sync(0xffffffffu, lb < cut)) continue;
     if (COUNT) ++c_nodes;
     if (lev == 0) {
       const int dl = pi.dim[0];
@@ -636,9 +672,26 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
       for (int64_t t = s0; t < s1; ++t) {
         const Tri tr = tris[t];
         const float d2 = tri_closest(p, f3(tr.a), f3(tr.b), f3(tr.c), nullptr, nullptr, nullptr);
-        if (d2 < best) {
-          best = d2;
-          bt = (int)t;
+        if (d2 < cut && d2 < cd[NC - 1]) {
+          cd[NC - 1] = d2;
+          ct[NC - 1] = (int)t;
+#pragma unroll
+          for (int q = NC - 1; q > 0; --q) {
+            if (cd[q] < cd[q - 1]) {
+              const float tf = cd[q];
+              cd[q] = cd[q - 1];
+              cd[q - 1] = tf;
+              const int ti = ct[q];
+              ct[q] = ct[q - 1];
+              ct[q - 1] = ti;
+            }
+          }
+          if (TIES) {
+            const float r = sqrtf(cd[0]) * (1.f + kTieRel) + mabs;
+            cut = r * r;
+          } else {
+            cut = cd[0];
+          }
         }
       }
       continue;
@@ -659,7 +712,7 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
       const float4 A = pyr[2 * cg];
       if (A.w < 0.f) continue;
       const float d = puck_dist2(p, A, pyr[2 * cg + 1]);
-      if (!__any_sync(0xffffffffu, d < best)) continue;
+      if (!__any_sync(0xffffffffu, d < cut)) continue;
       const float dm = __shfl_sync(0xffffffffu, d, 0);   // ordering key: the first lane's bound
       int q2 = nc;
       while (q2 > 0 && key[q2 - 1] < dm) {
@@ -677,19 +730,75 @@ __global__ void __launch_bounds__(kWarps * 32) sdf_kernel(const float* __restric
     sp = min(sp + nc, kStack);
     __syncwarp();
   }
-  if (COUNT && lane == 0) {
-    atomicAdd(&st->sdf_cnt[0], c_nodes);
-    atomicAdd(&st->sdf_cnt[1], c_leaves);
-    atomicAdd(&st->sdf_cnt[2], c_tests);
+  const bool tie = TIES && valid && ct[NC > 1 ? 1 : 0] >= 0 && cd[NC > 1 ? 1 : 0] <= cut;
+  if (COUNT) {
+    const unsigned long long nt = (unsigned long long)__popc(__ballot_sync(0xffffffffu, tie));
+    if (lane == 0) {
+      atomicAdd(&st->sdf_cnt[0], c_nodes);
+      atomicAdd(&st->sdf_cnt[1], c_leaves);
+      atomicAdd(&st->sdf_cnt[2], c_tests);
+      atomicAdd(&st->sdf_cnt[3], nt);
+    }
   }
   if (!valid) return;
+  const float val = sqrtf(cd[0]);
+  const int bt = ct[0];
   const int64_t o = lin3(i, j, k, n);
   const double c = st->c;
   const float sgn = ((double)chi[o] >= c) ? 1.f : -1.f;
-  const float val = sgn * sqrtf(best);
-  phi[o] = val;
-  if (sdf_out) sdf_out[o] = val;
+  phi[o] = sgn * val;
+  if (sdf_out) sdf_out[o] = sgn * val;
   if (ctri) ctri[o] = bt;
+  if (TIES) {
+    if (tie) {
+      tie_a[o] = bt;
+      tie_cd.p[st->fwd.xidx ^ 1][o] = make_int2(cd[NC > 2 ? 2 : 0] <= cut ? ct[NC > 2 ? 2 : 0] : -1,
+                                                cd[NC > 3 ? 3 : 0] <= cut ? ct[NC > 3 ? 3 : 0] : -1);
+    }
+    tie_b[o] = tie ? ct[NC > 1 ? 1 : 0] : -1;
+  }
+}
+
+// Float-float decision between the float32 near-tie candidates of a node:
+// distances from the node position rounded once from double, the smaller
+// wins; equal distances (a shared edge or vertex: the same closest point)
+// take the smaller triangle index.
+__global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, const DevState* __restrict__ st,
+                               const Tri* __restrict__ tris, const int* __restrict__ tie_a,
+                               const int* __restrict__ tie_b, TieSlots tie_cd, float* __restrict__ phi,
+                               float* __restrict__ sdf_out, int* __restrict__ ctri) {
+  const int n = g.res;
+  const int64_t N = (int64_t)n * n * n;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N; o += (int64_t)gridDim.x * blockDim.x) {
+    const int t1 = tie_b[o];
+    if (t1 < 0) continue;
+    const int t0 = tie_a[o];
+    const int2 t23 = tie_cd.p[st->fwd.xidx ^ 1][o];
+    const int i = (int)(o % n), j = (int)((o / n) % n), k = (int)(o / ((int64_t)n * n));
+    const Vec3<Ff> pf = {ff_from_double(g.lo[0] + (i + 0.5) * g.h), ff_from_double(g.lo[1] + (j + 0.5) * g.h),
+                         ff_from_double(g.lo[2] + (k + 0.5) * g.h)};
+    Ff bd(INFINITY);
+    int bi = -1;
+    const int cand[kCand] = {t0, t1, t23.x, t23.y};
+    // one copy of the float-float distance in the loop: unrolled, the four
+    // copies overflow the instruction cache
+#pragma unroll 1
+    for (int q = 0; q < kCand; ++q) {
+      if (cand[q] < 0) continue;
+      const Tri tr = tris[cand[q]];
+      const Ff d2 = tri_closest_t<Ff>(pf, {Ff(tr.a.x), Ff(tr.a.y), Ff(tr.a.z)}, {Ff(tr.b.x), Ff(tr.b.y), Ff(tr.b.z)},
+                                      {Ff(tr.c.x), Ff(tr.c.y), Ff(tr.c.z)}, nullptr, nullptr, nullptr);
+      if (bi < 0 || d2 < bd || (!(bd < d2) && cand[q] < bi)) {
+        bd = d2;
+        bi = cand[q];
+      }
+    }
+    const float sgn = ((double)chi[o] >= st->c) ? 1.f : -1.f;
+    const float val = sgn * sqrtf(__fadd_rn(bd.hi, bd.lo));
+    phi[o] = val;
+    if (sdf_out) sdf_out[o] = val;
+    ctri[o] = bi;
+  }
 }
 
 // n = grad phi / |grad phi|: central differences inside, second-order one-sided
@@ -800,14 +909,39 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   stage_end(h, kStMC, slot, s);
   slot = stage_begin(h, kStSDF, s);
   const int ntx = (res + 7) / 8, ntz = (res + 1) / 2;
-  if (h->opt.stage_timing == 2)
-    sdf_kernel<true><<<ntx * ntx * ntz, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
-                                                            h->mesh_cap, h->pyramid, pi, h->phi, sdf_out,
-                                                            h->opt.keep_for_backward ? h->ctri : nullptr);
-  else
-    sdf_kernel<false><<<ntx * ntx * ntz, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
-                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out,
-                                                             h->opt.keep_for_backward ? h->ctri : nullptr);
+  // the solver's residual / correction scratch is idle until the next solve:
+  // it holds the near-tie candidates between the two kernels
+  int* tie_a = reinterpret_cast<int*>(h->r32);
+  int* tie_b = reinterpret_cast<int*>(h->e32);
+  // ... and so does the float-float iterate buffer that is not the current one
+  // (its index is on the device): two more candidates per node
+  TieSlots tie_cd;
+  tie_cd.p[0] = reinterpret_cast<int2*>(h->chiff[0]);
+  tie_cd.p[1] = reinterpret_cast<int2*>(h->chiff[1]);
+  int* ctri = h->opt.keep_for_backward ? h->ctri : nullptr;
+  const int nblk = ntx * ntx * ntz;
+  if (ctri) {
+    if (h->opt.stage_timing == 2)
+      sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off, h->mesh_cap,
+                                                          h->pyramid, pi, h->phi, sdf_out, ctri, tie_a, tie_b, tie_cd);
+    else
+      sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off, h->mesh_cap,
+                                                           h->pyramid, pi, h->phi, sdf_out, ctri, tie_a, tie_b,
+                                                           tie_cd);
+    WGEO_LAUNCH_CHECK();
+    const int64_t N = (int64_t)res * res * res;
+    sdf_tie_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(h->chi32, g, h->dstate, h->tris, tie_a, tie_b,
+                                                                 tie_cd, h->phi, sdf_out, ctri);
+  } else {
+    if (h->opt.stage_timing == 2)
+      sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off, h->mesh_cap,
+                                                           h->pyramid, pi, h->phi, sdf_out, nullptr, nullptr, nullptr,
+                                                           tie_cd);
+    else
+      sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
+                                                            h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
+                                                            nullptr, nullptr, tie_cd);
+  }
   WGEO_LAUNCH_CHECK();
   stage_end(h, kStSDF, slot, s);
   if (nrm_out) {

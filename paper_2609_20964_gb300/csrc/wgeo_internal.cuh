@@ -41,7 +41,8 @@ struct DevState {
   double dc;          // backward: dL/dc
   SolveState fwd;
   SolveState bwd;
-  unsigned long long sdf_cnt[3];   // octree nodes entered, leaves entered, lane point-triangle tests
+  unsigned long long sdf_cnt[4];   // octree nodes entered, leaves entered, lane point-triangle tests,
+                                   // nodes re-decided in float64
 };
 
 struct Tri {          // one marching-cubes triangle: vertex xyz + global edge id in .w
@@ -119,54 +120,109 @@ __device__ __forceinline__ float3 f3(const float4 v) { return make_float3(v.x, v
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// Float-float scalar (about 44 significant bits on the FP32 pipe) for the
+// near-tie decisions of the distance search: sums by two-sum, products with
+// the FMA residual (fma(a, b, -rn(a b)) is the exact error of the rounded
+// product), quotients with two correction steps.  Comparisons are exact for
+// normalised values (|lo| <= ulp(hi) / 2), which every operator returns.
+struct Ff {
+  float hi, lo;
+  __device__ __forceinline__ Ff() {}
+  __device__ __forceinline__ Ff(float x) : hi(x), lo(0.f) {}
+  __device__ __forceinline__ Ff(float h, float l) : hi(h), lo(l) {}
+};
+__device__ __forceinline__ Ff ff_from_double(double x) {
+  const float h = (float)x;
+  return Ff(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ Ff operator+(Ff a, Ff b) {
+  const float2 r = ff_add(make_float2(a.hi, a.lo), make_float2(b.hi, b.lo));
+  return Ff(r.x, r.y);
+}
+__device__ __forceinline__ Ff operator-(Ff a) { return Ff(-a.hi, -a.lo); }
+__device__ __forceinline__ Ff operator-(Ff a, Ff b) { return a + (-b); }
+__device__ __forceinline__ Ff operator*(Ff a, Ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float2 r = fast_two_sum(p, e);
+  return Ff(r.x, r.y);
+}
+__device__ __forceinline__ Ff operator/(Ff a, Ff b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const Ff r1 = a - b * Ff(q1);
+  const float q2 = __fdiv_rn(r1.hi, b.hi);
+  const Ff r2 = r1 - b * Ff(q2);
+  const float q3 = __fdiv_rn(r2.hi, b.hi);
+  return (Ff(q1) + Ff(q2)) + Ff(q3);
+}
+__device__ __forceinline__ bool operator<(Ff a, Ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(Ff a, Ff b) { return b < a; }
+__device__ __forceinline__ bool operator<=(Ff a, Ff b) { return !(b < a); }
+__device__ __forceinline__ bool operator>=(Ff a, Ff b) { return !(a < b); }
+
+template <typename T>
+struct Vec3 {
+  T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ Vec3<T> vsub(Vec3<T> a, Vec3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T>
+__device__ __forceinline__ T vdot(Vec3<T> a, Vec3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
 // Squared distance from p to triangle (a, b, c) and the barycentric weights of
-// the closest point (Voronoi regions: three vertices, three edges, the face).
-__device__ __forceinline__ float tri_closest(const float3 p, const float3 a, const float3 b, const float3 c,
-                             float* wa, float* wb, float* wc) {
-  const float3 ab = sub3(b, a), ac = sub3(c, a), ap = sub3(p, a);
-  float u = 1.f, v = 0.f, w = 0.f;
-  const float d1 = dot3(ab, ap), d2 = dot3(ac, ap);
-  if (d1 <= 0.f && d2 <= 0.f) {
-    u = 1.f; v = 0.f; w = 0.f;
+// the closest point (Voronoi regions: three vertices, three edges, the face),
+// in the precision T (float on the search path, double where near-ties are
+// re-evaluated).
+template <typename T>
+__device__ __forceinline__ T tri_closest_t(const Vec3<T> p, const Vec3<T> a, const Vec3<T> b, const Vec3<T> c,
+                                           T* wa, T* wb, T* wc) {
+  const T zero = T(0), one = T(1);
+  const Vec3<T> ab = vsub(b, a), ac = vsub(c, a), ap = vsub(p, a);
+  T u = one, v = zero, w = zero;
+  const T d1 = vdot(ab, ap), d2 = vdot(ac, ap);
+  if (d1 <= zero && d2 <= zero) {
+    u = one; v = zero; w = zero;
   } else {
-    const float3 bp = sub3(p, b);
-    const float d3 = dot3(ab, bp), d4 = dot3(ac, bp);
-    if (d3 >= 0.f && d4 <= d3) {
-      u = 0.f; v = 1.f; w = 0.f;
+    const Vec3<T> bp = vsub(p, b);
+    const T d3 = vdot(ab, bp), d4 = vdot(ac, bp);
+    if (d3 >= zero && d4 <= d3) {
+      u = zero; v = one; w = zero;
     } else {
-      const float vc = d1 * d4 - d3 * d2;
-      if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
-        const float t = d1 / (d1 - d3);
-        u = 1.f - t; v = t; w = 0.f;
+      const T vc = d1 * d4 - d3 * d2;
+      if (vc <= zero && d1 >= zero && d3 <= zero) {
+        const T t = d1 / (d1 - d3);
+        u = one - t; v = t; w = zero;
       } else {
-        const float3 cp = sub3(p, c);
-        const float d5 = dot3(ab, cp), d6 = dot3(ac, cp);
-        if (d6 >= 0.f && d5 <= d6) {
-          u = 0.f; v = 0.f; w = 1.f;
+        const Vec3<T> cp = vsub(p, c);
+        const T d5 = vdot(ab, cp), d6 = vdot(ac, cp);
+        if (d6 >= zero && d5 <= d6) {
+          u = zero; v = zero; w = one;
         } else {
-          const float vb = d5 * d2 - d1 * d6;
-          if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
-            const float t = d2 / (d2 - d6);
-            u = 1.f - t; v = 0.f; w = t;
+          const T vb = d5 * d2 - d1 * d6;
+          if (vb <= zero && d2 >= zero && d6 <= zero) {
+            const T t = d2 / (d2 - d6);
+            u = one - t; v = zero; w = t;
           } else {
-            const float va = d3 * d6 - d5 * d4;
-            if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
-              const float t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
-              u = 0.f; v = 1.f - t; w = t;
+            const T va = d3 * d6 - d5 * d4;
+            if (va <= zero && (d4 - d3) >= zero && (d5 - d6) >= zero) {
+              const T t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+              u = zero; v = one - t; w = t;
             } else {
-              const float den = va + vb + vc;
-              if (den > 0.f) {
-                const float inv = 1.f / den;
+              const T den = va + vb + vc;
+              if (den > zero) {
+                const T inv = one / den;
                 v = vb * inv;
                 w = vc * inv;
-                u = 1.f - v - w;
+                u = one - v - w;
               } else {
                 // degenerate (collapsed) triangle: nearest of the three vertices
-                const float3 cb = sub3(p, b), cc = sub3(p, c);
-                const float q0 = dot3(ap, ap), q1 = dot3(cb, cb), q2 = dot3(cc, cc);
-                if (q0 <= q1 && q0 <= q2) { u = 1.f; v = 0.f; w = 0.f; }
-                else if (q1 <= q2) { u = 0.f; v = 1.f; w = 0.f; }
-                else { u = 0.f; v = 0.f; w = 1.f; }
+                const Vec3<T> cb = vsub(p, b), cc = vsub(p, c);
+                const T q0 = vdot(ap, ap), q1 = vdot(cb, cb), q2 = vdot(cc, cc);
+                if (q0 <= q1 && q0 <= q2) { u = one; v = zero; w = zero; }
+                else if (q1 <= q2) { u = zero; v = one; w = zero; }
+                else { u = zero; v = zero; w = one; }
               }
             }
           }
@@ -174,11 +230,15 @@ __device__ __forceinline__ float tri_closest(const float3 p, const float3 a, con
       }
     }
   }
-  const float3 y = make_float3(u * a.x + v * b.x + w * c.x, u * a.y + v * b.y + w * c.y,
-                               u * a.z + v * b.z + w * c.z);
-  const float3 d = sub3(p, y);
+  const Vec3<T> y = {u * a.x + v * b.x + w * c.x, u * a.y + v * b.y + w * c.y, u * a.z + v * b.z + w * c.z};
+  const Vec3<T> d = vsub(p, y);
   if (wa) { *wa = u; *wb = v; *wc = w; }
-  return dot3(d, d);
+  return vdot(d, d);
+}
+
+__device__ __forceinline__ float tri_closest(const float3 p, const float3 a, const float3 b, const float3 c,
+                                             float* wa, float* wb, float* wc) {
+  return tri_closest_t<float>({p.x, p.y, p.z}, {a.x, a.y, a.z}, {b.x, b.y, b.z}, {c.x, c.y, c.z}, wa, wb, wc);
 }
 
 }  // namespace wgeo

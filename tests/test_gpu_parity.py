@@ -151,6 +151,33 @@ def test_query_and_backward_parity(W, name):
     rec.close()
 
 
+@pytest.mark.parametrize("name", ["sphere24", "shbody44"])
+def test_closest_point_parity(W, name):
+    """S7 argmin: the closest surface point of every node, wherever the oracle
+    finds it unique (no other triangle within 2e-7 of the minimum distance with
+    a closest point more than 1e-6 away); triangle ids differ between the two
+    meshes' orders, so the points are compared."""
+    from oracle import sdf as S
+    p, n, res = CASES[name]
+    ref = _oracle(name)
+    rec = W(res, len(p))
+    rec.reconstruct(_t(p), _t(n), BBOX, res)
+    ids = rec.field("closest").cpu().numpy().reshape(-1).astype(np.int64)
+    vg, _ = rec.mesh()
+    vg = vg.astype(np.float64)
+    nodes = OP.node_xyz(np.arange(res ** 3), res, ref.lo, ref.h)
+    vo = ref.mesh["verts"]
+    to = ref.tri.reshape(-1)
+    assert ids.min() >= 0 and ids.max() < len(vg)
+    yg, _ = S.closest_point_triangle(nodes, vg[ids, 0], vg[ids, 1], vg[ids, 2])
+    yo, _ = S.closest_point_triangle(nodes, vo[to, 0], vo[to, 1], vo[to, 2])
+    amb = S.closest_point_ambiguous(nodes, vo, np.abs(ref.phi).reshape(-1), 2e-7, 1e-6)
+    assert amb.mean() < 0.1, amb.mean()
+    err = np.linalg.norm(yg - yo, axis=1)[~amb]
+    assert err.max() <= 1e-5, f"closest point off by {err.max():.3e}"
+    rec.close()
+
+
 def test_grid_seed_backward_parity(W):
     p, n, res = CASES["sphere24"]
     ref = _oracle("sphere24")

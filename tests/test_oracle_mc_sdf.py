@@ -140,6 +140,26 @@ def test_point_triangle_regions():
         assert d <= lattice + 1e-12 and lattice - d < 2e-3 * (1 + d)
 
 
+def test_closest_point_ambiguity_cases():
+    """Non-unique closest points (Eq. 33 minimisers giving different points)."""
+    # two coplanar triangles sharing the edge x = 0 (y in [0, 1]) in the plane z = 0
+    V = np.array([[[0, 0, 0], [0, 1, 0], [-1, 0.5, 0]],
+                  [[0, 0, 0], [1, 0.5, 0], [0, 1, 0]],
+                  # a parallel triangle at z = 2 above the first one
+                  [[0, 0, 2], [-1, 0.5, 2], [0, 1, 2]]], dtype=np.float64)
+    q = np.array([[0.0, 0.5, 0.7],      # over the shared edge: both give the same point
+                  [-0.4, 0.5, 1.0],     # midway between the parallel triangles: two points
+                  [-0.4, 0.5, 0.3],     # over the interior of the first, nearer to it
+                  [-0.4, 0.5, 1.0 - 1e-9]])   # a hair off the medial plane: within delta
+    d, _ = S.brute_force_distance(q, V)
+    assert np.allclose(d, [0.7, 1.0, 0.3, 1.0 - 1e-9])
+    amb = S.closest_point_ambiguous(q, V, d, delta=1e-7, sep=1e-6)
+    assert amb.tolist() == [False, True, False, True]
+    # with a delta below the gap the last one is unique again
+    amb = S.closest_point_ambiguous(q, V, d, delta=1e-10, sep=1e-6)
+    assert amb.tolist() == [False, True, False, False]
+
+
 def test_pruned_search_equals_brute_force_and_parity(unit_bbox):
     p, n = synth.sphere_cloud(800, seed=11)
     rec = PL.forward_to_mesh(p, n, unit_bbox, 16)
