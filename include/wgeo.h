@@ -212,6 +212,33 @@ int wgeo_sh_surface_backward(wgeo_handle* h, const float* theta, int32_t K, cons
                              float base, const float* d_points, const float* d_normals,
                              float* d_theta, void* stream);
 
+/* The same adjoint as wgeo_sh_surface_backward, computed by the same kernels
+ * in the same order (identical results), without a handle and without
+ * allocating any memory: the partial sums go to a fixed array of 256 x 81
+ * doubles (162 KB) compiled into the library, one per device.  This entry
+ * point has no counterpart in the paper; it serves callers that must not
+ * allocate device memory while they run (a serving loop under a fixed memory
+ * budget, or code whose allocator owns all device memory) and that hold no
+ * reconstruction handle, whose creation allocates its workspace.
+ *
+ * Limits: K = (lmax+1)^2 <= 81 (lmax <= 8); any n >= 0.  K above 81, or not a
+ * square, returns WGEO_ERR_INVALID_ARG with nothing enqueued.  Arrays as for
+ * wgeo_sh_surface_backward (DEVICE pointers on the current device, d_theta
+ * [K] overwritten), enqueued on `stream`.
+ *
+ * Set-up: the first call on a device (with that device current) looks up the
+ * array's device address and checks the device is sm_103 (else
+ * WGEO_ERR_NOT_BUILT_FOR_DEVICE); later calls reuse the address.  Make that
+ * first call before any stream capture.  No part of the array needs to start
+ * at zero: each call writes every slot it reads.  The array is shared by all
+ * calls on a device, so calls that may overlap in time (other streams or host
+ * threads without ordering between them) race; order them on one stream or
+ * with events.  Errors: WGEO_ERR_INVALID_ARG for bad arguments,
+ * WGEO_ERR_CUDA if a launch fails. */
+int wgeo_sh_surface_backward_noalloc(const float* theta, int32_t K, const float* dirs, int64_t n, float base,
+                                     const float* d_points, const float* d_normals, float* d_theta,
+                                     void* stream);
+
 /* Accumulated device time per stage (needs opt.stage_timing): synchronises the
  * handle's recorded events and ADDS, for every stage s < WGEO_NUM_STAGES, the
  * milliseconds and the number of timed calls since the last reset into ms[s]

@@ -68,6 +68,7 @@ SIGNATURES = {
     "wgeo_mc_table": (C.c_int, [_vp, _vp]),
     "wgeo_sh_surface": (C.c_int, [_vp, _i32, _vp, _i64, _f32, _vp, _vp, _vp, _vp]),
     "wgeo_sh_surface_backward": (C.c_int, [_vp, _vp, _i32, _vp, _i64, _f32, _vp, _vp, _vp, _vp]),
+    "wgeo_sh_surface_backward_noalloc": (C.c_int, [_vp, _i32, _vp, _i64, _f32, _vp, _vp, _vp, _vp]),
     "wgeo_stage_times": (C.c_int, [_vp, _vp, _vp, _i32]),
     "wgeo_error_string": (C.c_char_p, [C.c_int]),
     "wgeo_status_string": (C.c_char_p, [C.c_uint32]),

@@ -12,6 +12,8 @@
 // per-warp shared slots and a fixed-order final pass (deterministic).
 #include <math.h>
 
+#include <mutex>
+
 #include "wgeo_internal.cuh"
 
 namespace wgeo {
@@ -247,3 +249,80 @@ int sh_valid_K(int K) {
 }
 
 }  // namespace wgeo
+
+// ------------------------------------------------ allocation-free adjoint
+//
+// The same two kernels as launch_sh_backward, with the per-block partial sums
+// in a fixed device array of this file instead of a handle's workspace.  The
+// array holds kShBlocks x kK doubles (256 x 81 x 8 B = 162 KB): the grid is
+// capped at kShBlocks blocks and K at kK = 81 (lmax 8), so every accepted
+// call fits.  No slot needs to start at zero: the block kernel writes every
+// slot [b * K + k] (b < blocks, k < K) that the final kernel reads.  One array
+// per device, shared by all calls on that device: calls that overlap in time
+// (different streams, or host threads, without ordering) race on it.
+
+namespace wgeo {
+
+static __device__ __align__(256) double sh_noalloc_scratch[kShBlocks * kK];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The first call
+// per device resolves it (cudaGetSymbolAddress, which may also load the
+// module on that device) and checks the device is sm_103; later calls read
+// the cached pointer.
+int noalloc_scratch(double** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return WGEO_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return WGEO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major * 10 + minor != 103) return WGEO_ERR_NOT_BUILT_FOR_DEVICE;
+    void* p = nullptr;
+    const cudaError_t rc = cudaGetSymbolAddress(&p, sh_noalloc_scratch);
+    if (rc != cudaSuccess || !p) {
+      cudaGetLastError();
+      return WGEO_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return WGEO_OK;
+}
+
+}  // namespace
+}  // namespace wgeo
+
+extern "C" int wgeo_sh_surface_backward_noalloc(const float* theta, int32_t K, const float* dirs, int64_t n,
+                                                float base, const float* d_points, const float* d_normals,
+                                                float* d_theta, void* stream) {
+  using namespace wgeo;
+  if (K < 1 || K > kK) return WGEO_ERR_INVALID_ARG;   // the scratch holds at most kK coefficients
+  if (!sh_valid_K(K) || n < 0 || !theta || !d_theta || (n > 0 && (!dirs || !d_points || !d_normals)))
+    return WGEO_ERR_INVALID_ARG;
+  double* scratch = nullptr;
+  const int rc = noalloc_scratch(&scratch);
+  if (rc != WGEO_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    WGEO_CUDA_TRY(cudaMemsetAsync(d_theta, 0, sizeof(float) * K, s));
+    return WGEO_OK;
+  }
+  const int nb = grid_blocks(n, kShThreads, kShBlocks);   // nb * K <= kShBlocks * kK
+  sh_backward_kernel<<<nb, kShThreads, 0, s>>>(theta, K, make_consts(K), dirs, n, base, d_points, d_normals,
+                                               scratch);
+  WGEO_LAUNCH_CHECK();
+  sh_finalize_kernel<<<1, 128, 0, s>>>(scratch, nb, K, d_theta);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}

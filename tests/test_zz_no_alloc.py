@@ -1,0 +1,77 @@
+"""Allocation-free spherical-harmonic adjoint (wgeo_sh_surface_backward_noalloc)
+against the handle-based entry point (wgeo_sh_surface_backward), both called
+through the C ABI.
+
+Two calls in a row with different sizes (K = 81 with a grid at its block cap,
+then K = 49 with fewer blocks) must each equal the handle-based result: the
+same kernels reduce in the same fixed order, so the results are identical.
+K above the scratch limit of 81 is refused before anything is enqueued.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from synth.shapes import random_sh_theta, uniform_dirs
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(n, lmax, seed):
+    rng = np.random.default_rng(seed)
+    dirs = uniform_dirs(n, rng).astype(np.float32)
+    theta = random_sh_theta(lmax, rng).astype(np.float32)
+    dpts = rng.standard_normal((n, 3)).astype(np.float32)
+    dnrm = rng.standard_normal((n, 3)).astype(np.float32)
+    return theta, dirs, dpts, dnrm
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def test_noalloc_adjoint_equals_handle_entry_point():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2609_20964_gb300 import _lib as L
+
+    lib = L.load()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    cases = [_inputs(100_000, 8, 401), _inputs(5_000, 6, 402)]
+    dev_cases = [tuple(torch.from_numpy(a).to(dev) for a in c) for c in cases]
+
+    # reference: the handle-based entry point (any handle; its workspace is the scratch)
+    h = C.c_void_p()
+    L.check(lib.wgeo_create(C.byref(h), 16, 16, None), "wgeo_create")
+    want = []
+    for theta, dirs, dpts, dnrm in dev_cases:
+        out = torch.empty_like(theta)
+        L.check(lib.wgeo_sh_surface_backward(h, _ptr(theta), theta.numel(), _ptr(dirs), dirs.shape[0], 0.3,
+                                             _ptr(dpts), _ptr(dnrm), _ptr(out), None),
+                "wgeo_sh_surface_backward")
+        want.append(out)
+    torch.cuda.synchronize()
+
+    # two allocation-free calls in a row, on the default stream
+    got = [torch.full_like(c[0], float("nan")) for c in dev_cases]
+    for (theta, dirs, dpts, dnrm), out in zip(dev_cases, got):
+        L.check(lib.wgeo_sh_surface_backward_noalloc(_ptr(theta), theta.numel(), _ptr(dirs), dirs.shape[0], 0.3,
+                                                     _ptr(dpts), _ptr(dnrm), _ptr(out), None),
+                "wgeo_sh_surface_backward_noalloc")
+    torch.cuda.synchronize()
+    for g, w in zip(got, want):
+        assert torch.isfinite(g).all()
+        assert torch.equal(g, w), float((g - w).abs().max())
+
+    # K = 100 (lmax 9) exceeds the 81 coefficients the scratch holds: refused, output untouched
+    theta, dirs, dpts, dnrm = dev_cases[1]
+    big = torch.zeros(100, device=dev)
+    sentinel = torch.full((100,), 7.0, device=dev)
+    rc = lib.wgeo_sh_surface_backward_noalloc(_ptr(big), 100, _ptr(dirs), dirs.shape[0], 0.3, _ptr(dpts),
+                                              _ptr(dnrm), _ptr(sentinel), None)
+    torch.cuda.synchronize()
+    assert rc == L.WGEO_ERR_INVALID_ARG
+    assert (sentinel == 7.0).all()
+    L.check(lib.wgeo_destroy(h), "wgeo_destroy")
