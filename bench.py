@@ -140,7 +140,11 @@ def run_ours(args):
     Nn = torch.from_numpy(n).cuda()
     Q = torch.from_numpy(q).cuda()
     G = torch.from_numpy(g).cuda()
-    rec = Reconstructor(RES, NPTS)
+    from paper_2609_20964_gb300 import _lib as L
+    lib = L.load()
+    # stage_timing = 1: CUDA events around each stage on the launching stream,
+    # read back after the timed region (the dominant kernel's live duration)
+    rec = Reconstructor(RES, NPTS, stage_timing=1)
     stream = torch.cuda.current_stream()
     N = RES ** 3
 
@@ -165,18 +169,25 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     barrier()
+    rec.stage_times(reset=True)
+    launches0 = lib.wgeo_kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     step_ms = []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.nvtx.range_push("timed")   # the profiler's launch list covers this range
     e0.record(stream)
     ev[0].record(stream)
     for k in range(args.steps):
         step()
         ev[k + 1].record(stream)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
+    launches = lib.wgeo_kernel_launches() - launches0
     clocks.stop()
+    st_timed = rec.stage_times(reset=True)
+    timed_stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in st_timed.items()}
     total_ms = e0.elapsed_time(e1)
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     t = torch.tensor([total_ms], device="cuda")
@@ -208,6 +219,7 @@ def run_ours(args):
     rec.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf)
     torch.cuda.synchronize()
     fp32_vs_mixed = float((sdf32 - sdf_buf).abs().max().item())
+    sdf_mixed = sdf_buf.clone()
     rec32.close()
 
     # per-stage device times (CUDA events on the library's stream), separate pass
@@ -266,10 +278,14 @@ def run_ours(args):
     h2d = (p.nbytes + n.nbytes + q.nbytes + g.nbytes)
     d2h = 2 * NPTS * 3 * 4
 
-    # roofline of the dominant kernel
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample_nodes)
+    # roofline of the dominant kernel, on the stage times of the timed region
     hbm, peak_kind = load_peaks()
-    dom = max(stages, key=lambda k: stages[k])
-    roof = roofline(dom, stages, info, hbm, peak_kind)
+    dom = max(timed_stage_ms, key=lambda k: timed_stage_ms[k])
+    roof = roofline(dom, timed_stage_ms, info, hbm, peak_kind,
+                    cpu["alg_tests_per_node"] if cpu else None)
 
     out = {
         "metric": METRIC,
@@ -282,13 +298,15 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64",
+        "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "SH body (degree<=8) 200k points, 256^3 grid, 1M queries, "
                                "forward + query + adjoint", "res": RES, "points": NPTS,
-                   "queries": NQ, "precision": "mixed FP32 multigrid / FP64 refinement",
+                   "queries": NQ, "precision": "mixed: FP32 multigrid V-cycles inside float-float "
+                                                        "defect-correction refinement",
                    "l2": "working set > 1 GB per step (fields of 67 MB) exceeds the 129 MB L2; no flush",
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}",
+                   "override": (RES, NPTS, NQ) != (256, 200_000, 1_000_000)},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99))},
         "fwd_cells_per_s": N / (fwd_ms / 1e3),
         "fwd_ms": fwd_ms,
@@ -308,23 +326,29 @@ def run_ours(args):
         "stage_ms": stages,
         "e2e": {"value": N / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": None,
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches / args.steps,
+        "timed_stage_ms": timed_stage_ms,
         "roofline": roof,
         "clocks": clocks.summary(),
     }
-    out["gpu_launches"] = count_launches_estimate()
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_nodes)
+    if cpu is not None:
+        # SDF error of both precisions against the oracle's exact distance on its sampled nodes
+        lin, ophi = cpu.pop("_sample")
+        idx = torch.from_numpy(lin.astype(np.int64)).cuda()
+        extent = float(np.max(BBOX[3:] - BBOX[:3]))
+        err = {}
+        for nm, f in (("mixed", sdf_mixed), ("fp32_plain", sdf32)):
+            got = f.reshape(-1)[idx].double().cpu().numpy()
+            err[nm] = float(np.abs(got - ophi).max() / extent)
+        out["sdf_err_vs_oracle"] = {"max_abs_over_extent": err, "nodes": int(len(lin)),
+                                    "bound": 1e-4}
+        out["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(out))
     rec.close()
     if ws > 1:
         dist.destroy_process_group()
-
-
-def count_launches_estimate():
-    """Kernel launches of one step of this build (counted from the launch sequence)."""
-    return None
 
 
 # Algorithmic bytes per cell (minimal traffic of each stage, see the design notes)
@@ -334,25 +358,64 @@ ALG_BYTES = {
     "query": 0.0,
 }
 
+# FP32 ALU peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FLOPS_PER_TRI_TEST = 40.0      # FP32 operations of one point-triangle distance
+STAGE_KERNEL = {"sdf": ("sdf_kernel", "paper_2609_20964_gb300/csrc/surface.cu")}
 
-def roofline(dom, stages, info, hbm, peak_kind):
+
+def source_digest(rel_paths):
+    import hashlib
+    h = hashlib.sha256()
+    for rp in rel_paths:
+        with open(os.path.join(ROOT, rp), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(kernel: str, src: str):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, or None
+    when the summary is missing or the kernel's sources changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    srcs = [src, "paper_2609_20964_gb300/csrc/wgeo_internal.cuh"]
+    if d.get("source_digest") != source_digest(srcs):
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
+def roofline(dom, stages, info, hbm, peak_kind, alg_tests_per_node):
     N = RES ** 3
     ms = stages[dom]
+    if dom == "sdf":
+        # ALU-bound search; algorithmic work = triangles whose box lower bound is
+        # below the node's exact distance (measured by the oracle on sampled nodes)
+        kernel, src = STAGE_KERNEL[dom]
+        achieved = frac = alg = None
+        if alg_tests_per_node is not None and ms > 0:
+            alg = alg_tests_per_node * N * FLOPS_PER_TRI_TEST
+            achieved = alg / (ms / 1e3) / 1e12
+            frac = achieved / FP32_PEAK_TFLOPS
+        return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": frac, "traffic": kernel_traffic(kernel, src),
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "alg_flops_per_launch": alg, "alg_tests_per_node": alg_tests_per_node,
+                "flops_per_test": FLOPS_PER_TRI_TEST, "launch_ms": ms}
     if dom in ("solve", "bwd_solve"):
-        # per refinement step: FP64 residual (read chi64 8 + b 4, write r 4), correction
-        # update (read e 4 + chi64 8, write chi64 8) and per V-cycle on the fine grid
+        # per refinement step: residual (read chi 8 + b 4, write r 4), correction
+        # update (read e 4 + chi 8, write chi 8) and per V-cycle on the fine grid
         # 2+2 RB sweeps (read x, b + write x: 12 B each) + restriction read (8 B) +
         # prolongation (read 4 + write 4)
         steps = max(info["solver_steps"], 1)
         per_step = 16 + 20 + 2 * (4 * 12 + 8 + 8) * 8 / 7
         alg = N * per_step * steps
-        return {"bound": "hbm", "kernel": f"{dom} (multigrid + FP64 refinement)",
+        return {"bound": "hbm", "kernel": f"{dom} (multigrid + refinement)",
                 "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": alg / (ms / 1e3) / 1e9 / hbm, "traffic": None,
                 "peak_kind": peak_kind, "alg_bytes_per_launch": alg}
-    if dom == "sdf":
-        return {"bound": "alu", "kernel": "sdf (exact nearest-triangle search)", "achieved": None,
-                "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None, "ms": ms}
     alg = N * ALG_BYTES.get(dom, 4.0)
     return {"bound": "hbm", "kernel": dom, "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm,
             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / hbm, "traffic": None,
@@ -360,10 +423,23 @@ def roofline(dom, stages, info, hbm, peak_kind):
 
 
 # --------------------------------------------------------------------- oracle
-def oracle_step(p, n, q, g, node_sample: int, rng):
+def box_candidates(nodes, verts, d):
+    """Per node, the triangles whose bounding-box lower bound is below the node's
+    exact distance d: the work any exact box-pruned search must do."""
+    lo = verts.min(axis=1)
+    hi = verts.max(axis=1)
+    out = np.empty(len(nodes), dtype=np.int64)
+    for i, x in enumerate(nodes):
+        gap = np.maximum(np.maximum(lo - x, x - hi), 0.0)
+        out[i] = int(np.count_nonzero(np.einsum("ij,ij->i", gap, gap) < d[i] * d[i]))
+    return out
+
+
+def oracle_step(p, n, q, g, node_sample: int, rng, point_frac: float = 1.0, count_nodes: int = 0):
     """One step of the oracle on the bench workload, with the per-node distance
-    search and the query stages on a random sample; returns (estimated seconds
-    for the full step, detail dict)."""
+    search and the query stages on a random sample (and, if point_frac < 1, the
+    per-point splat and splat adjoint on that fraction of the points, scaled);
+    returns (estimated seconds for the full step, detail dict)."""
     from oracle import divergence as D
     from oracle import grid as OG
     from oracle import iso as OI
@@ -373,15 +449,21 @@ def oracle_step(p, n, q, g, node_sample: int, rng):
     from oracle import splat as OS
     N = RES ** 3
     t = {}
-    t0 = time.perf_counter()
     lo = OG.grid_lo(BBOX)
     h = OG.grid_spacing(BBOX, RES)
     pp = p.astype(np.float64)
     nn = n.astype(np.float64)
     bins, fin, _ = OG.bin_points(pp, BBOX, RES)
-    V = OS.splat(pp, nn, bins, fin, lo, h, RES)
+    m = len(pp) if point_frac >= 1.0 else max(1, int(len(pp) * point_frac))
+    t0 = time.perf_counter()
+    Vs = OS.splat(pp[:m], nn[:m], bins[:m], fin[:m], lo, h, RES)
+    t["splat_est"] = (time.perf_counter() - t0) * len(pp) / m
+    # the global stages' cost does not depend on the values of V; with a point
+    # sample, the sample's splat (the same body, fewer points) stands in for it
+    V = Vs
+    t0 = time.perf_counter()
     b = D.divergence(V)
-    t["splat_div"] = time.perf_counter() - t0
+    t["div"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     chi = OPo.solve(b)
     t["solve"] = time.perf_counter() - t0
@@ -394,39 +476,47 @@ def oracle_step(p, n, q, g, node_sample: int, rng):
     # distance + sign on sampled nodes, extrapolated to all N nodes
     lin = rng.choice(N, node_sample, replace=False)
     t0 = time.perf_counter()
-    OP.sdf_at(rec, lin)
+    phi_s, dist, _ = OP.sdf_at(rec, lin)
     t["sdf_sample"] = time.perf_counter() - t0
     t["sdf_est"] = t["sdf_sample"] * N / node_sample
     # stencil normals cost ~ one more distance per node in the oracle's own form: counted as 0
-    # query + adjoints: adjoint solve (full), splat adjoint (all points), iso adjoint (all points)
+    # query + adjoints: adjoint solve (full), splat adjoint, iso adjoint
     t0 = time.perf_counter()
     lam = OPo.solve(chi)          # same operator and cost as the adjoint solve of dL/dchi
     t["adj_solve"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     dV = D.divergence_adjoint(lam)
-    OS.splat_adjoint(pp, nn, bins, fin, lo, h, RES, dV)
-    t["splat_adjoint"] = time.perf_counter() - t0
+    OS.splat_adjoint(pp[:m], nn[:m], bins[:m], fin[:m], lo, h, RES, dV)
+    t["splat_adjoint_est"] = (time.perf_counter() - t0) * len(pp) / m
     # trilinear query at the 1M points (vectorised, measured on a tenth, scaled)
     qs = q[: len(q) // 10].astype(np.float64)
     t0 = time.perf_counter()
     OI.trilinear(qs, lo, h, RES)
     t["query_est"] = (time.perf_counter() - t0) * 10
-    total = (t["splat_div"] + t["solve"] + t["iso_mc"] + t["sdf_est"] + t["adj_solve"]
-             + t["splat_adjoint"] + t["query_est"])
-    return total, t
+    total = (t["splat_est"] + t["div"] + t["solve"] + t["iso_mc"] + t["sdf_est"] + t["adj_solve"]
+             + t["splat_adjoint_est"] + t["query_est"])
+    extra = {"triangles": int(mesh["verts"].shape[0]), "sample_lin": lin, "sample_phi": phi_s}
+    if count_nodes:
+        k = min(count_nodes, node_sample)
+        nodes = OP.node_xyz(lin[:k], RES, lo, h)
+        cnt = box_candidates(nodes, mesh["verts"], dist[:k])
+        extra["alg_tests_per_node"] = float(cnt.mean())
+        extra["alg_count_nodes"] = k
+    return total, t, extra
 
 
 def cpu_baseline(node_sample: int):
     p, n, q, g = workload()
     rng = np.random.default_rng(7)
-    total, t = oracle_step(p, n, q, g, node_sample, rng)
-    cores = os.cpu_count()
-    return {"value": RES ** 3 / total, "unit": "cells/s", "cores": cores, "kind": "oracle",
-            "sample": (f"FP64 numpy oracle on the same step: splat, divergence, DCT solve, iso-value, "
-                       f"marching cubes, adjoint solve and splat adjoint on the full 256^3 problem; "
-                       f"exact distance on {node_sample} random nodes scaled to all 16.8M; query "
-                       f"interpolation on 100k of the 1M points scaled; est. step {total:.1f} s"),
-            "stage_s": t}
+    total, t, extra = oracle_step(p, n, q, g, node_sample, rng, count_nodes=500)
+    return {"value": RES ** 3 / total, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle (one thread) on the same step: splat, divergence, DCT solve, "
+                       f"iso-value, marching cubes, adjoint solve and splat adjoint on the full 256^3 "
+                       f"problem; exact distance on {node_sample} random nodes scaled to all 16.8M; "
+                       f"query interpolation on 100k of the 1M points scaled; est. step {total:.1f} s"),
+            "stage_s": t, "alg_tests_per_node": extra["alg_tests_per_node"],
+            "alg_count_nodes": extra["alg_count_nodes"],
+            "_sample": (extra["sample_lin"], extra["sample_phi"])}
 
 
 def run_reference(args):
@@ -436,21 +526,25 @@ def run_reference(args):
     p, n, q, g = workload()
     rng = np.random.default_rng(11)
     times = []
+    nodes = min(args.cpu_sample_nodes, 300)
     for k in range(args.warmup + args.steps):
-        total, t = oracle_step(p, n, q, g, args.cpu_sample_nodes, rng)
+        total, t, _ = oracle_step(p, n, q, g, nodes, rng, point_frac=0.1)
         if k >= args.warmup:
             times.append(total)
     ms = 1e3 * float(np.mean(times))
     value = RES ** 3 / (ms / 1e3)
-    cores = os.cpu_count()
+    cores = 1
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "SH body (degree<=8) 200k points, 256^3 grid, 1M queries, "
                                   "forward + query + adjoint", "res": RES, "points": NPTS, "queries": NQ},
            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
-                            "sample": f"per step: full global stages, distance on "
-                                      f"{args.cpu_sample_nodes} nodes scaled to 256^3"},
+                            "sample": f"per step (FP64 numpy, one thread): divergence, DCT solves, "
+                                      f"iso-value and marching cubes on the full 256^3 grid; splat and "
+                                      f"splat adjoint on 10% of the points, exact distance on {nodes} "
+                                      f"nodes and query on 10% of the queries, each scaled to the full "
+                                      f"step"},
            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -464,7 +558,13 @@ def main():
     ap.add_argument("--stage-steps", type=int, default=5)
     ap.add_argument("--cpu-sample-nodes", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # smaller cases of the same workload, for profiler captures only (the
+    # benchmark figure is the default 256^3 / 200k / 1M configuration)
+    ap.add_argument("--res", type=int, default=256)
+    ap.add_argument("--points", type=int, default=200_000)
+    ap.add_argument("--queries", type=int, default=1_000_000)
     args = ap.parse_args()
+    globals().update(RES=args.res, NPTS=args.points, NQ=args.queries)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -89,14 +89,15 @@ typedef struct {
 #define WGEO_STAGE_SOLVE       1   /* forward Poisson solve */
 #define WGEO_STAGE_ISO         2   /* iso-value */
 #define WGEO_STAGE_MC          3   /* marching cubes + box pyramid */
-#define WGEO_STAGE_SDF         4   /* exact distance search and sign */
+#define WGEO_STAGE_SDF         4   /* exact distance search and sign (float32 search) */
 #define WGEO_STAGE_NORMALS     5
 #define WGEO_STAGE_QUERY       6
 #define WGEO_STAGE_BWD_SEED    7   /* grid seeds + query adjoint */
 #define WGEO_STAGE_BWD_SURFACE 8   /* distance, marching-cubes and iso-value adjoints */
 #define WGEO_STAGE_BWD_SOLVE   9   /* adjoint Poisson solve */
 #define WGEO_STAGE_BWD_SPLAT   10  /* divergence transpose + splat adjoint */
-#define WGEO_NUM_STAGES        11
+#define WGEO_STAGE_SDF_TIE     11  /* float-float decisions of near-tie closest triangles */
+#define WGEO_NUM_STAGES        12
 
 typedef struct {
   uint32_t status;           /* WGEO_STATUS_* bits of the last call */
@@ -114,7 +115,7 @@ typedef struct {
   int64_t  sdf_tri_tests;    /* ... point-triangle distance evaluations (per node, i.e. per lane) */
   double   backward_dc;      /* dL/dc of the last backward */
   int64_t  sdf_tie_nodes;    /* with stage_timing = 2: nodes whose nearest triangle was a float32
-                                near-tie, re-decided in float64 */
+                                near-tie, re-decided in float-float arithmetic */
   int64_t  reserved[1];
 } wgeo_info;
 
@@ -238,6 +239,12 @@ int wgeo_sh_surface_backward(wgeo_handle* h, const float* theta, int32_t K, cons
 int wgeo_sh_surface_backward_noalloc(const float* theta, int32_t K, const float* dirs, int64_t n, float base,
                                      const float* d_points, const float* d_normals, float* d_theta,
                                      void* stream);
+
+/* Number of kernels this library has launched in this process so far, on any
+ * device and stream: kernels inside replays of its recorded solver graphs
+ * count at each replay; recording a graph counts nothing.  Host-only,
+ * never fails; take differences around a region to count its launches. */
+int64_t wgeo_kernel_launches(void);
 
 /* Accumulated device time per stage (needs opt.stage_timing): synchronises the
  * handle's recorded events and ADDS, for every stage s < WGEO_NUM_STAGES, the

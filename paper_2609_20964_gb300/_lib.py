@@ -25,7 +25,7 @@ STATUS_NOT_CONVERGED = 1 << 3
 STATUS_MESH_CAPACITY = 1 << 4
 
 STAGES = ("splat", "solve", "iso", "mc", "sdf", "normals", "query", "bwd_seed",
-          "bwd_surface", "bwd_solve", "bwd_splat")
+          "bwd_surface", "bwd_solve", "bwd_splat", "sdf_tie")
 
 PREC_MIXED = 0
 PREC_FP32 = 1
@@ -70,6 +70,7 @@ SIGNATURES = {
     "wgeo_sh_surface_backward": (C.c_int, [_vp, _vp, _i32, _vp, _i64, _f32, _vp, _vp, _vp, _vp]),
     "wgeo_sh_surface_backward_noalloc": (C.c_int, [_vp, _i32, _vp, _i64, _f32, _vp, _vp, _vp, _vp]),
     "wgeo_stage_times": (C.c_int, [_vp, _vp, _vp, _i32]),
+    "wgeo_kernel_launches": (_i64, []),
     "wgeo_error_string": (C.c_char_p, [C.c_int]),
     "wgeo_status_string": (C.c_char_p, [C.c_uint32]),
 }

@@ -119,6 +119,9 @@ void accumulate_slot(StageTimer& t, int slot) {
 
 namespace wgeo {
 
+std::atomic<long long> g_kernel_launches{0};
+thread_local long long t_kernel_launches = 0;
+
 int stage_begin(wgeo_handle* h, int stage, cudaStream_t s) {
   if (!h->opt.stage_timing) return -1;
   if (!h->timers) {
@@ -146,6 +149,8 @@ void stage_end(wgeo_handle* h, int stage, int slot, cudaStream_t s) {
 }  // namespace wgeo
 
 extern "C" {
+
+int64_t wgeo_kernel_launches(void) { return (int64_t)g_kernel_launches.load(std::memory_order_relaxed); }
 
 int wgeo_stage_times(wgeo_handle* h, double* ms, int64_t* counts, int32_t reset) {
   if (!h || !ms || !counts) return WGEO_ERR_INVALID_ARG;

@@ -883,7 +883,12 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
     }
     if (!h->capture_stream) WGEO_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     WGEO_CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = t_kernel_launches;
     int rc = enqueue_solve(h, res, mode, h->capture_stream);
+    // recorded, not run: counted at each replay instead
+    const long long captured = t_kernel_launches - before;
+    t_kernel_launches -= captured;
+    g_kernel_launches.fetch_sub(captured, std::memory_order_relaxed);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->capture_stream, &graph);
     if (rc) {
@@ -899,8 +904,11 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
     }
     g.res = res;
     g.mode = gmode;
+    g.launches = captured;
   }
   WGEO_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+  g_kernel_launches.fetch_add(g.launches, std::memory_order_relaxed);
+  t_kernel_launches += g.launches;
   return WGEO_OK;
 }
 

@@ -929,9 +929,13 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
                                                            h->pyramid, pi, h->phi, sdf_out, ctri, tie_a, tie_b,
                                                            tie_cd);
     WGEO_LAUNCH_CHECK();
+    stage_end(h, kStSDF, slot, s);
+    slot = stage_begin(h, kStSDFTie, s);
     const int64_t N = (int64_t)res * res * res;
     sdf_tie_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(h->chi32, g, h->dstate, h->tris, tie_a, tie_b,
                                                                  tie_cd, h->phi, sdf_out, ctri);
+    WGEO_LAUNCH_CHECK();
+    stage_end(h, kStSDFTie, slot, s);
   } else {
     if (h->opt.stage_timing == 2)
       sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off, h->mesh_cap,
@@ -941,9 +945,9 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
       sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
                                                             nullptr, nullptr, tie_cd);
+    WGEO_LAUNCH_CHECK();
+    stage_end(h, kStSDF, slot, s);
   }
-  WGEO_LAUNCH_CHECK();
-  stage_end(h, kStSDF, slot, s);
   if (nrm_out) {
     slot = stage_begin(h, kStNormals, s);
     const int64_t N = (int64_t)res * res * res;

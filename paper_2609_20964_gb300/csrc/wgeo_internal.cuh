@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/wgeo.h"
@@ -42,7 +43,7 @@ struct DevState {
   SolveState fwd;
   SolveState bwd;
   unsigned long long sdf_cnt[4];   // octree nodes entered, leaves entered, lane point-triangle tests,
-                                   // nodes re-decided in float64
+                                   // nodes re-decided in float-float
 };
 
 struct Tri {          // one marching-cubes triangle: vertex xyz + global edge id in .w
@@ -70,7 +71,8 @@ enum Stage {
   kStBwdSurf = 8,  // distance / marching-cubes / iso-value adjoints
   kStBwdSolve = 9,
   kStBwdSplat = 10,
-  kStages = 11
+  kStSDFTie = 11,  // near-tie decisions of the distance search
+  kStages = 12
 };
 constexpr int kRing = 256;
 
@@ -87,6 +89,7 @@ struct StageTimer {
 struct SolverGraph {
   int res = 0;
   int mode = -1;      // 0 forward, 1 backward
+  long long launches = 0;   // kernel nodes recorded in the graph
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -173,8 +176,8 @@ __device__ __forceinline__ T vdot(Vec3<T> a, Vec3<T> b) { return a.x * b.x + a.y
 
 // Squared distance from p to triangle (a, b, c) and the barycentric weights of
 // the closest point (Voronoi regions: three vertices, three edges, the face),
-// in the precision T (float on the search path, double where near-ties are
-// re-evaluated).
+// in the precision T (float on the search path, float-float where near-ties
+// are re-decided).
 template <typename T>
 __device__ __forceinline__ T tri_closest_t(const Vec3<T> p, const Vec3<T> a, const Vec3<T> b, const Vec3<T> c,
                                            T* wa, T* wb, T* wc) {
@@ -328,8 +331,16 @@ namespace wgeo {
     if (_e != cudaSuccess) return WGEO_ERR_CUDA;              \
   } while (0)
 
+// Kernel launches enqueued by this library (process-wide, and per host thread
+// so that a stream capture can tell its own launches apart).  Every launch is
+// followed by exactly one WGEO_LAUNCH_CHECK, which counts it.
+extern std::atomic<long long> g_kernel_launches;
+extern thread_local long long t_kernel_launches;
+
 #define WGEO_LAUNCH_CHECK()                                   \
   do {                                                        \
+    ::wgeo::g_kernel_launches.fetch_add(1, std::memory_order_relaxed); \
+    ++::wgeo::t_kernel_launches;                              \
     cudaError_t _e = cudaGetLastError();                      \
     if (_e != cudaSuccess) return WGEO_ERR_CUDA;              \
   } while (0)
