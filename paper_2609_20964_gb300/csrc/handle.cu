@@ -22,7 +22,7 @@ struct Layout {
   size_t total = 0;
   size_t off_b32, off_chi32, off_chi64, off_r32, off_e32, off_phi, off_ctri, off_dphi64, off_dchi64,
       off_lam64, off_lam32, off_levels, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
-      off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_pyr, off_partials,
+      off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_tris_s, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
       off_scan, off_state;
   size_t n_partials, n_scan;
   int64_t cap;
@@ -75,7 +75,10 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   if (cap < 4096) cap = 4096;
   L.cap = cap;
   L.off_tris = take(c, sizeof(Tri) * (size_t)cap);
+  L.off_tris_s = take(c, sizeof(float4) * 4 * (size_t)cap);
   L.off_pyr = take(c, 32 * pyramid_nodes(nb));
+  L.off_pyr_sums = take(c, 32 * pyramid_aux_nodes(nb));
+  L.off_pyr_rth = take(c, 8 * pyramid_aux_nodes(nb));
   L.n_partials = std::max<size_t>(2 * ntiles, std::max<size_t>(4 * kPartials, 81 * 256));
   L.off_partials = take(c, 8 * L.n_partials);
   L.n_scan = scan_tmp_size((int)std::max(ntiles, nbricks));
@@ -247,7 +250,10 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->leaf_off = (int*)(a + L.off_leaf_off);
   h->mesh_cap = L.cap;
   h->tris = (Tri*)(a + L.off_tris);
+  h->tris_s = (float4*)(a + L.off_tris_s);
   h->pyramid = (float4*)(a + L.off_pyr);
+  h->pyr_sums = (float4*)(a + L.off_pyr_sums);
+  h->pyr_rth = (unsigned*)(a + L.off_pyr_rth);
   h->partials = (double*)(a + L.off_partials);
   h->scan_tmp = (int*)(a + L.off_scan);
   h->scan_tmp_elems = L.n_scan;

@@ -391,8 +391,24 @@ __device__ __forceinline__ int leaf_index(int lx, int ly, int lz, int nb) {
 
 constexpr float kPuckPad = 1e-5f;   // relative inflation: rounding of the bound stays conservative
 
+// Search record of a triangle for the distance search: vertex a and the edge
+// vectors ab, ac with their Gram entries, and the reciprocals the Voronoi
+// regions divide by (0 for a zero-length edge or a collapsed triangle).
+__device__ __forceinline__ void write_search_record(const Tri& tr, float4* __restrict__ rec) {
+  const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
+  const float3 ab = sub3(b, a), ac = sub3(c, a), bc = sub3(c, b);
+  const float e00 = dot3(ab, ab), e01 = dot3(ab, ac), e11 = dot3(ac, ac), ebc = dot3(bc, bc);
+  const float3 cr = cross3(ab, ac);
+  const float det = dot3(cr, cr);   // = e00 e11 - e01^2, without the cancellation
+  rec[0] = make_float4(a.x, a.y, a.z, e00);
+  rec[1] = make_float4(ab.x, ab.y, ab.z, e01);
+  rec[2] = make_float4(ac.x, ac.y, ac.z, e11);
+  rec[3] = make_float4(e00 > 0.f ? 1.f / e00 : 0.f, e11 > 0.f ? 1.f / e11 : 0.f, ebc > 0.f ? 1.f / ebc : 0.f,
+                       det > 0.f ? 1.f / det : 0.f);
+}
+
 __global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const int* __restrict__ leaf_off, int nb,
-                                 int64_t cap, float4* __restrict__ pyr) {
+                                 int64_t cap, float4* __restrict__ pyr, float4* __restrict__ tris_s) {
   const int nl = 2 * nb;
   const int64_t nleaf = (int64_t)nl * nl * nl;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
@@ -409,6 +425,7 @@ __global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const int* __rest
     float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
     for (int64_t q = s0; q < s1; ++q) {
       const Tri tr = tris[q];
+      write_search_record(tr, tris_s + 4 * q);
       const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
       cs.x += a.x + b.x + c.x;
       cs.y += a.y + b.y + c.y;
@@ -441,125 +458,9 @@ __global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const int* __rest
   }
 }
 
-// Parent puck from its (up to 8) children: axis = normalised sum of child axes
-// weighted by r^2, centre = weighted mean of child centres, then radius and
-// half-thickness that bound every child cylinder in the parent's frame.
-__global__ void puck_up_kernel(float4* __restrict__ pyr, int64_t off_child, int dchild, int64_t off_parent,
-                               int dparent) {
-  const int64_t np = (int64_t)dparent * dparent * dparent;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < np;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % dparent), y = (int)((t / dparent) % dparent), z = (int)(t / ((int64_t)dparent * dparent));
-    float4 A[8], B[8];
-    int nc = 0;
-    float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
-    float ws = 0.f;
-    for (int c = 0; c < 8; ++c) {
-      const int cx = 2 * x + (c & 1), cy = 2 * y + ((c >> 1) & 1), cz = 2 * z + (c >> 2);
-      if (cx >= dchild || cy >= dchild || cz >= dchild) continue;
-      const int64_t ci = off_child + ((int64_t)cz * dchild + cy) * dchild + cx;
-      const float4 a = pyr[2 * ci], b = pyr[2 * ci + 1];
-      if (a.w < 0.f) continue;
-      A[nc] = a;
-      B[nc] = b;
-      const float w = a.w * a.w + b.w * b.w + 1e-20f;
-      cs.x += w * a.x;
-      cs.y += w * a.y;
-      cs.z += w * a.z;
-      ns.x += w * b.x;
-      ns.y += w * b.y;
-      ns.z += w * b.z;
-      ws += w;
-      ++nc;
-    }
-    if (nc == 0) {
-      pyr[2 * (off_parent + t)] = make_float4(0.f, 0.f, 0.f, -1.f);
-      pyr[2 * (off_parent + t) + 1] = make_float4(0.f, 0.f, 1.f, 0.f);
-      continue;
-    }
-    const float3 cc = make_float3(cs.x / ws, cs.y / ws, cs.z / ws);
-    const float nn = sqrtf(dot3(ns, ns));
-    const float3 nv = nn > 1e-12f ? make_float3(ns.x / nn, ns.y / nn, ns.z / nn) : make_float3(0.f, 0.f, 1.f);
-    float r = 0.f, th = 0.f;
-    for (int q = 0; q < nc; ++q) {
-      const float3 d = sub3(make_float3(A[q].x, A[q].y, A[q].z), cc);
-      const float3 ni = make_float3(B[q].x, B[q].y, B[q].z);
-      const float cz = dot3(d, nv);
-      const float crho = sqrtf(fmaxf(dot3(d, d) - cz * cz, 0.f));
-      const float cosi = fminf(fabsf(dot3(nv, ni)), 1.f);
-      const float sini = sqrtf(fmaxf(1.f - cosi * cosi, 0.f));
-      th = fmaxf(th, fabsf(cz) + A[q].w * sini + B[q].w * cosi);
-      r = fmaxf(r, crho + A[q].w + B[q].w * sini);
-    }
-    const float pad = kPuckPad * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cc.z) + r + th) + 1e-7f;
-    pyr[2 * (off_parent + t)] = make_float4(cc.x, cc.y, cc.z, r * (1.f + kPuckPad) + pad);
-    pyr[2 * (off_parent + t) + 1] = make_float4(nv.x, nv.y, nv.z, th * (1.f + kPuckPad) + pad);
-  }
-}
-
 // Tight puck of an internal node at level l >= 1 (dim d_l; level 1 = bricks):
 // axis and centre from its own triangles, radius and half-thickness from
 // their vertices (two passes over the bricks it covers).
-__global__ void puck_tight_kernel(const Tri* __restrict__ tris, const int* __restrict__ brick_off, int nb,
-                                  int64_t cap, int level, int dim, float4* __restrict__ out) {
-  const int64_t np = (int64_t)dim * dim * dim;
-  const int span = 1 << (level - 1);        // bricks per axis under one node
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < np;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(t % dim), y = (int)((t / dim) % dim), z = (int)(t / ((int64_t)dim * dim));
-    float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
-    int64_t cnt = 0;
-    for (int bz = z * span; bz < min((z + 1) * span, nb); ++bz)
-      for (int by = y * span; by < min((y + 1) * span, nb); ++by)
-        for (int bx = x * span; bx < min((x + 1) * span, nb); ++bx) {
-          const int br = (bz * nb + by) * nb + bx;
-          const int64_t s1 = min((int64_t)brick_off[br + 1], cap);
-          for (int64_t q = brick_off[br]; q < s1; ++q) {
-            const Tri tr = tris[q];
-            const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
-            cs.x += a.x + b.x + c.x;
-            cs.y += a.y + b.y + c.y;
-            cs.z += a.z + b.z + c.z;
-            const float3 cr = cross3(sub3(b, a), sub3(c, a));
-            ns.x += cr.x;
-            ns.y += cr.y;
-            ns.z += cr.z;
-            ++cnt;
-          }
-        }
-    if (cnt == 0) {
-      out[2 * t] = make_float4(0.f, 0.f, 0.f, -1.f);
-      out[2 * t + 1] = make_float4(0.f, 0.f, 1.f, 0.f);
-      continue;
-    }
-    const float inv = 1.f / (3.f * (float)cnt);
-    const float3 cc = make_float3(cs.x * inv, cs.y * inv, cs.z * inv);
-    const float nn = sqrtf(dot3(ns, ns));
-    const float3 nv = nn > 0.f ? make_float3(ns.x / nn, ns.y / nn, ns.z / nn) : make_float3(0.f, 0.f, 1.f);
-    float r = 0.f, th = 0.f;
-    for (int bz = z * span; bz < min((z + 1) * span, nb); ++bz)
-      for (int by = y * span; by < min((y + 1) * span, nb); ++by)
-        for (int bx = x * span; bx < min((x + 1) * span, nb); ++bx) {
-          const int br = (bz * nb + by) * nb + bx;
-          const int64_t s1 = min((int64_t)brick_off[br + 1], cap);
-          for (int64_t q = brick_off[br]; q < s1; ++q) {
-            const Tri tr = tris[q];
-            const float4 vv[3] = {tr.a, tr.b, tr.c};
-#pragma unroll
-            for (int v = 0; v < 3; ++v) {
-              const float3 d = sub3(f3(vv[v]), cc);
-              const float zz = dot3(d, nv);
-              th = fmaxf(th, fabsf(zz));
-              r = fmaxf(r, sqrtf(fmaxf(dot3(d, d) - zz * zz, 0.f)));
-            }
-          }
-        }
-    const float pad = kPuckPad * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cc.z) + r + th) + 1e-7f;
-    out[2 * t] = make_float4(cc.x, cc.y, cc.z, r * (1.f + kPuckPad) + pad);
-    out[2 * t + 1] = make_float4(nv.x, nv.y, nv.z, th * (1.f + kPuckPad) + pad);
-  }
-}
-
 // Squared distance from p to the solid cylinder of a puck (INF when empty).
 __device__ __forceinline__ float puck_dist2(const float3 p, const float4 A, const float4 B) {
   if (A.w < 0.f) return INFINITY;
@@ -569,6 +470,138 @@ __device__ __forceinline__ float puck_dist2(const float3 p, const float4 A, cons
   const float dz = fmaxf(fabsf(z) - B.w, 0.f);
   const float dr = fmaxf(rho - A.w, 0.f);
   return dz * dz + dr * dr;
+}
+
+// Vertex-fitted pucks for every octree level above the leaves.  A node's
+// frame is its vertex centroid and mean area normal; both come from sums
+// that add up the tree (per brick first: a level-1 node is one brick).  The
+// radius and half-thickness are the largest radial and axial vertex offsets
+// in that frame, taken in one pass over the leaves for all levels at once
+// (warp-aggregated atomic maxima on the bits of non-negative floats).  Aux
+// slots cover the nodes of levels >= 1: aux index = pyramid index - off[1].
+__device__ __forceinline__ void node_frame(const float4 s0, const float4 s1, float3& c, float3& ax) {
+  const float inv = 1.f / (3.f * s0.w);
+  c = make_float3(s0.x * inv, s0.y * inv, s0.z * inv);
+  const float nn = sqrtf(s1.x * s1.x + s1.y * s1.y + s1.z * s1.z);
+  ax = nn > 0.f ? make_float3(s1.x / nn, s1.y / nn, s1.z / nn) : make_float3(0.f, 0.f, 1.f);
+}
+
+__global__ void puck_sums_brick_kernel(const Tri* __restrict__ tris, const int* __restrict__ brick_off, int nb,
+                                       int64_t cap, float4* __restrict__ sums, unsigned* __restrict__ rth) {
+  const int64_t nbr = (int64_t)nb * nb * nb;
+  for (int64_t br = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; br < nbr;
+       br += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q0 = brick_off[br];
+    const int64_t q1 = min((int64_t)brick_off[br + 1], cap);
+    float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
+    for (int64_t q = q0; q < q1; ++q) {
+      const Tri tr = tris[q];
+      const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
+      cs.x += a.x + b.x + c.x;
+      cs.y += a.y + b.y + c.y;
+      cs.z += a.z + b.z + c.z;
+      const float3 cr = cross3(sub3(b, a), sub3(c, a));
+      ns.x += cr.x;
+      ns.y += cr.y;
+      ns.z += cr.z;
+    }
+    sums[2 * br] = make_float4(cs.x, cs.y, cs.z, (float)(q1 > q0 ? q1 - q0 : 0));
+    sums[2 * br + 1] = make_float4(ns.x, ns.y, ns.z, 0.f);
+    rth[2 * br] = 0u;
+    rth[2 * br + 1] = 0u;
+  }
+}
+
+__global__ void puck_sums_up_kernel(float4* __restrict__ sums, unsigned* __restrict__ rth, int64_t a_child,
+                                    int dchild, int64_t a_parent, int dparent) {
+  const int64_t np = (int64_t)dparent * dparent * dparent;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < np;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(t % dparent), y = (int)((t / dparent) % dparent), z = (int)(t / ((int64_t)dparent * dparent));
+    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < 8; ++q) {
+      const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
+      if (cx >= dchild || cy >= dchild || cz >= dchild) continue;
+      const int64_t ci = a_child + ((int64_t)cz * dchild + cy) * dchild + cx;
+      const float4 c0 = sums[2 * ci], c1 = sums[2 * ci + 1];
+      s0 = make_float4(s0.x + c0.x, s0.y + c0.y, s0.z + c0.z, s0.w + c0.w);
+      s1 = make_float4(s1.x + c1.x, s1.y + c1.y, s1.z + c1.z, 0.f);
+    }
+    sums[2 * (a_parent + t)] = s0;
+    sums[2 * (a_parent + t) + 1] = s1;
+    rth[2 * (a_parent + t)] = 0u;
+    rth[2 * (a_parent + t) + 1] = 0u;
+  }
+}
+
+__global__ void puck_rth_kernel(const Tri* __restrict__ tris, const int* __restrict__ leaf_off, int nb, int64_t cap,
+                                PyrInfo pi, const float4* __restrict__ sums, unsigned* __restrict__ rth) {
+  const int dl = pi.dim[0];
+  const int64_t nleaf = (int64_t)dl * dl * dl;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip count: every lane reaches the warp-wide reductions
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nleaf; base += stride) {
+    const int64_t t = base + threadIdx.x;
+    const bool in = t < nleaf;
+    const int lx = in ? (int)(t % dl) : 0, ly = in ? (int)((t / dl) % dl) : 0,
+              lz = in ? (int)(t / ((int64_t)dl * dl)) : 0;
+    int64_t q0 = 0, q1 = 0;
+    if (in) {
+      const int li = leaf_index(lx, ly, lz, nb);
+      q0 = leaf_off[li];
+      q1 = min((int64_t)leaf_off[li + 1], cap);
+    }
+    if (!__any_sync(0xffffffffu, q1 > q0)) continue;
+#pragma unroll 1
+    for (int l = 1; l < pi.nlev; ++l) {
+      const int d = pi.dim[l];
+      const int64_t node = ((int64_t)(lz >> l) * d + (ly >> l)) * d + (lx >> l);
+      const int64_t a = pi.off[l] - pi.off[1] + node;
+      float r = 0.f, th = 0.f;
+      if (q1 > q0) {
+        float3 c, ax;
+        node_frame(sums[2 * a], sums[2 * a + 1], c, ax);
+        for (int64_t q = q0; q < q1; ++q) {
+          const Tri tr = tris[q];
+          const float4 vv[3] = {tr.a, tr.b, tr.c};
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            const float3 dv = sub3(f3(vv[v]), c);
+            const float zz = dot3(dv, ax);
+            th = fmaxf(th, fabsf(zz));
+            r = fmaxf(r, sqrtf(fmaxf(dot3(dv, dv) - zz * zz, 0.f)));
+          }
+        }
+      }
+      const long long key = (q1 > q0) ? (long long)a : -1ll;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const unsigned rm = __reduce_max_sync(peers, __float_as_uint(r));
+      const unsigned tm = __reduce_max_sync(peers, __float_as_uint(th));
+      if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
+        atomicMax(&rth[2 * a], rm);
+        atomicMax(&rth[2 * a + 1], tm);
+      }
+    }
+  }
+}
+
+__global__ void puck_finalize_kernel(float4* __restrict__ pyr, const float4* __restrict__ sums,
+                                     const unsigned* __restrict__ rth, int64_t naux, int64_t pyr_base) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < naux; a += (int64_t)gridDim.x * blockDim.x) {
+    const float4 s0 = sums[2 * a], s1 = sums[2 * a + 1];
+    const int64_t gi = pyr_base + a;
+    if (!(s0.w > 0.f)) {
+      pyr[2 * gi] = make_float4(0.f, 0.f, 0.f, -1.f);
+      pyr[2 * gi + 1] = make_float4(0.f, 0.f, 1.f, 0.f);
+      continue;
+    }
+    float3 c, ax;
+    node_frame(s0, s1, c, ax);
+    const float r = __uint_as_float(rth[2 * a]), th = __uint_as_float(rth[2 * a + 1]);
+    const float pad = kPuckPad * (fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + r + th) + 1e-7f;
+    pyr[2 * gi] = make_float4(c.x, c.y, c.z, r * (1.f + kPuckPad) + pad);
+    pyr[2 * gi + 1] = make_float4(ax.x, ax.y, ax.z, th * (1.f + kPuckPad) + pad);
+  }
 }
 
 }  // namespace
@@ -589,6 +622,64 @@ struct TieSlots {
   int2* p[2];   // the two float-float iterate buffers; the one not current is free
 };
 
+// Squared distance from p to a triangle given by its search record (see
+// write_search_record): the Voronoi region picks the closest point
+// y = a + v ab + w ac (Ericson's case analysis, with the six dot products
+// reduced to d1 = ab.ap and d2 = ac.ap through the stored Gram entries and
+// the divisions replaced by the stored reciprocals), and the residual
+// p - y = ap - v ab - w ac is formed relative to a, so its rounding scales
+// with the distance and the edge length rather than with the coordinates.
+__device__ __forceinline__ float tri_dist2_rec(const float3 p, const float4* __restrict__ rec) {
+  const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
+  const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+  const float e00 = r0.w, e01 = r1.w, e11 = r2.w;
+  const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;   // ab . ap
+  const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;   // ac . ap
+  const float d3 = d1 - e00, d4 = d2 - e01;                  // ab . bp, ac . bp
+  const float d5 = d1 - e01, d6 = d2 - e11;                  // ab . cp, ac . cp
+  float v, w;
+  if (d1 <= 0.f && d2 <= 0.f) {
+    v = 0.f; w = 0.f;                                          // vertex a
+  } else if (d3 >= 0.f && d4 <= d3) {
+    v = 1.f; w = 0.f;                                          // vertex b
+  } else {
+    const float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+      v = d1 * r3.x; w = 0.f;                                  // edge ab
+    } else if (d6 >= 0.f && d5 <= d6) {
+      v = 0.f; w = 1.f;                                        // vertex c
+    } else {
+      const float vb = d5 * d2 - d1 * d6;
+      if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+        v = 0.f; w = d2 * r3.y;                                // edge ac
+      } else {
+        const float va = d3 * d6 - d5 * d4;
+        if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+          w = (d4 - d3) * r3.z; v = 1.f - w;                   // edge bc
+        } else if (r3.w > 0.f) {
+          v = vb * r3.w; w = vc * r3.w;                        // face
+        } else {
+          // collapsed triangle: the nearest of its three vertices
+          const float qa = ap.x * ap.x + ap.y * ap.y + ap.z * ap.z;
+          const float qb = qa - 2.f * d1 + e00, qc = qa - 2.f * d2 + e11;
+          v = (qb < qa && qb <= qc) ? 1.f : 0.f;
+          w = (qc < qa && qc < qb) ? 1.f : 0.f;
+        }
+      }
+    }
+  }
+  const float rx = ap.x - v * r1.x - w * r2.x;
+  const float ry = ap.y - v * r1.y - w * r2.y;
+  const float rz = ap.z - v * r1.z - w * r2.z;
+  return rx * rx + ry * ry + rz * rz;
+}
+
+// Octree entries on the traversal stack: level in bits 27..31, node
+// coordinates (< 512 per axis) in bits 0..8 (x), 9..17 (y), 18..26 (z).
+__device__ __forceinline__ unsigned pack_node(int lev, int x, int y, int z) {
+  return ((unsigned)lev << 27) | ((unsigned)z << 18) | ((unsigned)y << 9) | (unsigned)x;
+}
+
 // Warp-cooperative exact distance search: a warp owns a 4 x 4 x 2 patch of
 // nodes and walks the octree once for all of them (a subtree is entered when
 // its bound beats the current cut of at least one lane); leaves are tested
@@ -608,13 +699,20 @@ struct TieSlots {
 template <bool COUNT, bool TIES>
 __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __restrict__ chi, SurfParams g,
                                                           DevState* __restrict__ st,
-                                                          const Tri* __restrict__ tris,
+                                                          const float4* __restrict__ tris_s,
                                                           const int* __restrict__ leaf_off, int64_t cap,
                                                           const float4* __restrict__ pyr, PyrInfo pi,
                                                           float* __restrict__ phi, float* __restrict__ sdf_out,
                                                           int* __restrict__ ctri, int* __restrict__ tie_a,
                                                           int* __restrict__ tie_b, TieSlots tie_cd) {
   __shared__ unsigned int s_node[kWarps][kStack];
+  __shared__ long long s_off[12];
+  __shared__ int s_dim[12];
+  if (threadIdx.x < 12) {
+    s_off[threadIdx.x] = pi.off[threadIdx.x];
+    s_dim[threadIdx.x] = pi.dim[threadIdx.x];
+  }
+  __syncthreads();
   const int n = g.res;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // CTA covers 8 x 8 x 2 nodes: warp w -> (4 (w & 1), 4 (w >> 1)) in x, y
@@ -644,8 +742,8 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
   unsigned int* stk = s_node[w];
   int sp = 0;
   const int top = pi.nlev - 1;
-  const int nb = (pi.dim[0] + 1) / 2;
-  if (lane == 0) stk[0] = (unsigned)top << 27;
+  const int nb = (s_dim[0] + 1) / 2;
+  if (lane == 0) stk[0] = pack_node(top, 0, 0, 0);
   sp = 1;
   unsigned long long c_nodes = 0, c_leaves = 0, c_tests = 0;
   __syncwarp();
@@ -654,15 +752,14 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
     const unsigned e = stk[sp];
     __syncwarp();
     const int lev = (int)(e >> 27);
-    const int idx = (int)(e & ((1u << 27) - 1));
-    const int64_t gi = pi.off[lev] + idx;
+    const int x = (int)(e & 511u), y = (int)((e >> 9) & 511u), z = (int)((e >> 18) & 511u);
+    const int dp = s_dim[lev];
+    const int64_t gi = s_off[lev] + ((int64_t)z * dp + y) * dp + x;
     const float lb = puck_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
     if (!__any_sync(0xffffffffu, lb < cut)) continue;
     if (COUNT) ++c_nodes;
     if (lev == 0) {
-      const int dl = pi.dim[0];
-      const int lx = idx % dl, ly = (idx / dl) % dl, lz = idx / (dl * dl);
-      const int li = leaf_index(lx, ly, lz, nb);
+      const int li = leaf_index(x, y, z, nb);
       const int64_t s0 = leaf_off[li];
       const int64_t s1 = min((int64_t)leaf_off[li + 1], cap);
       if (COUNT) {
@@ -670,8 +767,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
         c_tests += 32ull * (unsigned long long)(s1 > s0 ? s1 - s0 : 0);
       }
       for (int64_t t = s0; t < s1; ++t) {
-        const Tri tr = tris[t];
-        const float d2 = tri_closest(p, f3(tr.a), f3(tr.b), f3(tr.c), nullptr, nullptr, nullptr);
+        const float d2 = tri_dist2_rec(p, tris_s + 4 * t);
         if (d2 < cut && d2 < cd[NC - 1]) {
           cd[NC - 1] = d2;
           ct[NC - 1] = (int)t;
@@ -696,8 +792,8 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
       }
       continue;
     }
-    const int dp = pi.dim[lev], dc = pi.dim[lev - 1];
-    const int x = idx % dp, y = (idx / dp) % dp, z = idx / (dp * dp);
+    const int dc = s_dim[lev - 1];
+    const int64_t cbase = s_off[lev - 1];
     // children: visit if any lane may improve; order nearest-first by the warp's
     // smallest bound (pushed far-to-near)
     float key[8];
@@ -707,8 +803,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
     for (int q = 0; q < 8; ++q) {
       const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
       if (cx >= dc || cy >= dc || cz >= dc) continue;
-      const int ci = (cz * dc + cy) * dc + cx;
-      const int64_t cg = pi.off[lev - 1] + ci;
+      const int64_t cg = cbase + ((int64_t)cz * dc + cy) * dc + cx;
       const float4 A = pyr[2 * cg];
       if (A.w < 0.f) continue;
       const float d = puck_dist2(p, A, pyr[2 * cg + 1]);
@@ -721,7 +816,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
         --q2;
       }
       key[q2] = dm;
-      ent[q2] = ((unsigned)(lev - 1) << 27) | (unsigned)ci;
+      ent[q2] = pack_node(lev - 1, cx, cy, cz);
       ++nc;
     }
     if (lane == 0) {
@@ -856,6 +951,11 @@ size_t pyramid_nodes(int nb) {
   return (size_t)(pi.off[pi.nlev - 1] + 1);
 }
 
+size_t pyramid_aux_nodes(int nb) {
+  PyrInfo pi = pyramid_info(2 * nb);
+  return (size_t)(pi.off[pi.nlev - 1] + 1 - pi.off[1]);
+}
+
 int launch_isovalue(wgeo_handle* h, const float* points, int64_t n, int res, cudaStream_t s) {
   SurfParams g;
   for (int a = 0; a < 3; ++a) g.lo[a] = h->lo[a];
@@ -894,16 +994,26 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   const PyrInfo pi = pyramid_info(2 * g.nb);
   const int64_t nleaf = (int64_t)pi.dim[0] * pi.dim[0] * pi.dim[0];
   puck_leaf_kernel<<<grid_blocks(nleaf, 256, 152 * 16), 256, 0, s>>>(h->tris, h->leaf_off, g.nb,
-                                                                      h->mesh_cap, h->pyramid);
+                                                                      h->mesh_cap, h->pyramid, h->tris_s);
   WGEO_LAUNCH_CHECK();
-  for (int l = 1; l < pi.nlev; ++l) {
-    const int64_t np = (int64_t)pi.dim[l] * pi.dim[l] * pi.dim[l];
-    if (l <= 2)   // fitted to the subtree's vertices (at most 2^3 bricks per node)
-      puck_tight_kernel<<<grid_blocks(np, 64, 152 * 32), 64, 0, s>>>(h->tris, h->brick_off, g.nb, h->mesh_cap,
-                                                                     l, pi.dim[l], h->pyramid + 2 * pi.off[l]);
-    else          // merged conservatively from the children
-      puck_up_kernel<<<grid_blocks(np, 128, 152 * 16), 128, 0, s>>>(h->pyramid, pi.off[l - 1], pi.dim[l - 1],
-                                                                    pi.off[l], pi.dim[l]);
+  {
+    // levels >= 1: sums per brick, sums up the tree, vertex maxima, pucks
+    const int64_t nbr = (int64_t)g.nb * g.nb * g.nb;
+    puck_sums_brick_kernel<<<grid_blocks(nbr, 128, 152 * 16), 128, 0, s>>>(h->tris, h->brick_off, g.nb,
+                                                                           h->mesh_cap, h->pyr_sums, h->pyr_rth);
+    WGEO_LAUNCH_CHECK();
+    for (int l = 2; l < pi.nlev; ++l) {
+      const int64_t np = (int64_t)pi.dim[l] * pi.dim[l] * pi.dim[l];
+      puck_sums_up_kernel<<<grid_blocks(np, 128, 152 * 16), 128, 0, s>>>(
+          h->pyr_sums, h->pyr_rth, pi.off[l - 1] - pi.off[1], pi.dim[l - 1], pi.off[l] - pi.off[1], pi.dim[l]);
+      WGEO_LAUNCH_CHECK();
+    }
+    puck_rth_kernel<<<grid_blocks(nleaf, 256, 152 * 16), 256, 0, s>>>(h->tris, h->leaf_off, g.nb, h->mesh_cap, pi,
+                                                                      h->pyr_sums, h->pyr_rth);
+    WGEO_LAUNCH_CHECK();
+    const int64_t naux = pi.off[pi.nlev - 1] + 1 - pi.off[1];
+    puck_finalize_kernel<<<grid_blocks(naux, 256, 152 * 16), 256, 0, s>>>(h->pyramid, h->pyr_sums, h->pyr_rth,
+                                                                          naux, pi.off[1]);
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStMC, slot, s);
@@ -922,10 +1032,10 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   const int nblk = ntx * ntx * ntz;
   if (ctri) {
     if (h->opt.stage_timing == 2)
-      sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off, h->mesh_cap,
+      sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off, h->mesh_cap,
                                                           h->pyramid, pi, h->phi, sdf_out, ctri, tie_a, tie_b, tie_cd);
     else
-      sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off, h->mesh_cap,
+      sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off, h->mesh_cap,
                                                            h->pyramid, pi, h->phi, sdf_out, ctri, tie_a, tie_b,
                                                            tie_cd);
     WGEO_LAUNCH_CHECK();
@@ -938,11 +1048,11 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
     stage_end(h, kStSDFTie, slot, s);
   } else {
     if (h->opt.stage_timing == 2)
-      sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off, h->mesh_cap,
+      sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off, h->mesh_cap,
                                                            h->pyramid, pi, h->phi, sdf_out, nullptr, nullptr, nullptr,
                                                            tie_cd);
     else
-      sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris, h->leaf_off,
+      sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
                                                             nullptr, nullptr, tie_cd);
     WGEO_LAUNCH_CHECK();

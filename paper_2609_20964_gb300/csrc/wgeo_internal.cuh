@@ -285,7 +285,11 @@ struct wgeo_handle {
   int* brick_off = nullptr;      // nbricks + 1
   int* leaf_off = nullptr;       // 8 * nbricks + 1: triangle offset of each 2^3 sub-brick
   wgeo::Tri* tris = nullptr;
-  float4* pyramid = nullptr;     // 2 float4 per node (lo, hi)
+  float4* tris_s = nullptr;        // per triangle: search record (a, |ab|^2), (ab, ab.ac), (ac, |ac|^2),
+                                   // (1/|ab|^2, 1/|ac|^2, 1/|bc|^2, 1/|ab x ac|^2)
+  float4* pyramid = nullptr;     // 2 float4 per node (puck: centre + radius, axis + half-thickness)
+  float4* pyr_sums = nullptr;    // levels >= 1: vertex sum + count, area-normal sum (puck construction)
+  unsigned* pyr_rth = nullptr;   // levels >= 1: radius, half-thickness as float bits (atomic maxima)
   double* dP = nullptr;          // backward: dL/d(vertex) per triangle corner, 9 doubles
 
   // reductions / scans
@@ -369,6 +373,7 @@ int launch_isovalue(wgeo_handle* h, const float* points, int64_t n, int res, cud
 int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_out, cudaStream_t s);
 int upload_mc_table();
 size_t pyramid_nodes(int nb);
+size_t pyramid_aux_nodes(int nb);   // nodes of the levels above the leaves
 void host_mc_table(int* counts, int* tris);
 // query.cu
 int launch_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s);
