@@ -81,7 +81,7 @@ typedef struct {
   int32_t use_graphs;        /* record the solver's fixed launch sequence once as a CUDA graph (default 1) */
   int32_t stage_timing;      /* bracket each stage with CUDA events on the call's stream (default 0) */
   int32_t reserved[5];
-  double  tol_rel_adjoint;   /* adjoint solve: stop when ||g - A lambda|| <= tol * ||g|| (default 1e-9) */
+  double  tol_rel_adjoint;   /* adjoint solve: stop when ||g - A lambda|| <= tol * ||g|| (default 1e-7) */
 } wgeo_options;
 
 /* Stage ids reported by wgeo_stage_times. */
@@ -240,10 +240,12 @@ int wgeo_sh_surface_backward_noalloc(const float* theta, int32_t K, const float*
                                      const float* d_points, const float* d_normals, float* d_theta,
                                      void* stream);
 
-/* Number of kernels this library has launched in this process so far, on any
- * device and stream: kernels inside replays of its recorded solver graphs
- * count at each replay; recording a graph counts nothing.  Host-only,
- * never fails; take differences around a region to count its launches. */
+/* Number of kernels this library has launched in this process so far: those
+ * enqueued from the host on any device and stream, plus those run by the
+ * recorded solver graphs' device-side loops on the current device (one body
+ * per iteration that ran; recording a graph counts nothing).  Reading the
+ * device-side part synchronises the current device.  Never fails; take
+ * differences around a region to count its launches. */
 int64_t wgeo_kernel_launches(void);
 
 /* Accumulated device time per stage (needs opt.stage_timing): synchronises the

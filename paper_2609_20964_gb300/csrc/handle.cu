@@ -54,7 +54,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.off_lam64 = take(c, keep ? 16 * N : 0);
   L.off_lam32 = take(c, keep ? 4 * N : 0);
   const size_t half = (size_t)(R / 2 + 1);
-  const size_t lev = 3 * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);
+  const size_t lev = 2 * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);   // x, b per coarse level
   L.off_levels = take(c, 4 * lev);
   const size_t Pp = (size_t)(P > 0 ? P : 1);
   L.off_pcell = take(c, 4 * Pp);
@@ -153,7 +153,9 @@ void stage_end(wgeo_handle* h, int stage, int slot, cudaStream_t s) {
 
 extern "C" {
 
-int64_t wgeo_kernel_launches(void) { return (int64_t)g_kernel_launches.load(std::memory_order_relaxed); }
+int64_t wgeo_kernel_launches(void) {
+  return (int64_t)g_kernel_launches.load(std::memory_order_relaxed) + (int64_t)loop_launches();
+}
 
 int wgeo_stage_times(wgeo_handle* h, double* ms, int64_t* counts, int32_t reset) {
   if (!h || !ms || !counts) return WGEO_ERR_INVALID_ARG;
@@ -184,7 +186,7 @@ int wgeo_default_options(wgeo_options* opt) {
   opt->keep_for_backward = 1;
   opt->mesh_capacity = 0;
   opt->use_graphs = 1;
-  opt->tol_rel_adjoint = 1e-9;
+  opt->tol_rel_adjoint = 1e-7;
   return WGEO_OK;
 }
 

@@ -22,20 +22,18 @@
 // Multigrid: cell-centred, halving while even and larger than 8; red-black
 // Gauss-Seidel, 2 pre- and 2 post-sweeps; residual restricted with weight 1/2
 // on the 8 children (average x H^2/h^2 for the unit-free operator); trilinear
-// prolongation (3/4, 1/4 per axis, mirrored at the walls).  Levels with
-// n >= 128 use two fused z-marching kernels per V-cycle: a CTA owns a 64 x 16
-// column tile and a 16-plane z chunk, keeps a ring of planes in shared memory
-// (next plane prefetched with cp.async) and pipelines the four half-sweeps
-// (half-sweep s works s planes behind the newest), which reproduces global
-// red-black Gauss-Seidel exactly while x is read from HBM once; the
-// pre-smoothing kernel also forms the residual and restricts it, the
-// post-smoothing kernel adds the prolonged coarse correction while loading.
-// Mid-size levels use one launch per half-sweep; grids of at most 16^3 run a
-// whole V-cycle hierarchy in one CTA's shared memory.
+// prolongation (3/4, 1/4 per axis, mirrored at the walls).  Levels above 16^3
+// run one plain kernel per half-sweep, restriction and prolongation, each
+// near its memory floor; grids of at most 16^3 run a whole V-cycle hierarchy
+// in one CTA's shared memory.
 //
-// Every kernel of the fixed launch sequence reads the solve's `done` flag and
-// returns at once when it is set, so the sequence (recorded once as a CUDA
-// graph) stops doing work as soon as the tolerance is met.
+// A solve is recorded once as a CUDA graph: the first residual and
+// convergence test, then a conditional WHILE node whose body (one correction,
+// residual and test) repeats until the test clears the condition, at the
+// latest after the last allowed step; nothing is launched after convergence.
+// Without graphs (or under the caller's own capture) the same kernels run as
+// a fixed sequence of the allowed steps, each returning at once once the
+// solve's `done` flag is set.
 #include "wgeo_internal.cuh"
 
 namespace wgeo {
@@ -44,8 +42,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kNu = 2;              // red-black sweeps before and after the coarse correction
-constexpr int kTX = 64, kTY = 16;
-constexpr int kSmThreads = 512;
 constexpr int kSmallN = 16;         // levels up to 16^3 are solved in one CTA
 
 __device__ __forceinline__ int64_t lin(int i, int j, int k, int n) {
@@ -72,7 +68,7 @@ __device__ __forceinline__ float rhs_hi(const double* b, int64_t t, float& lo) {
 // on this GPU the FP64 pipe made an FP64 stencil pass about 12x slower than its
 // memory traffic, while the error-free sums below run on the FP32 pipe.
 //   x_new = x + e (e may be null: no correction this step; cold: x := 0),
-//   x32 = hi(x_new), r32 = b - L x_new (each neighbour difference formed
+//   x32 = hi(x_new), r32 = b - L x_new (each neighbour difference split
 //   exactly), per-thread sums of r and r^2 in FP32, per-block sums in FP64.
 template <typename TB>
 __global__ void update_residual_kernel(PairFF xp, const float* __restrict__ e, const TB* __restrict__ b,
@@ -98,12 +94,24 @@ __global__ void update_residual_kernel(PairFF xp, const float* __restrict__ e, c
         return e ? ff_add_f(v, e[q]) : v;
       };
       xc = val(t);
-      if (i > 0) acc = ff_add(acc, ff_sub(val(t - 1), xc));
-      if (i < n - 1) acc = ff_add(acc, ff_sub(val(t + 1), xc));
-      if (j > 0) acc = ff_add(acc, ff_sub(val(t - n), xc));
-      if (j < n - 1) acc = ff_add(acc, ff_sub(val(t + n), xc));
-      if (k > 0) acc = ff_add(acc, ff_sub(val(t - (int64_t)n * n), xc));
-      if (k < n - 1) acc = ff_add(acc, ff_sub(val(t + (int64_t)n * n), xc));
+      // L x = sum of (x_q - x_p): each hi difference split exactly by two-sum,
+      // the hi parts summed by a two-sum chain (rounding errors carried in
+      // `err`), the lo differences (each below ulp(hi)) summed in float
+      float sh = 0.f, err = 0.f, lo = 0.f;
+      auto add = [&](float2 v) {
+        const float2 d = two_sum(v.x, -xc.x);
+        const float2 c = two_sum(sh, d.x);
+        sh = c.x;
+        err = __fadd_rn(err, __fadd_rn(c.y, d.y));
+        lo = __fadd_rn(lo, __fsub_rn(v.y, xc.y));
+      };
+      if (i > 0) add(val(t - 1));
+      if (i < n - 1) add(val(t + 1));
+      if (j > 0) add(val(t - n));
+      if (j < n - 1) add(val(t + n));
+      if (k > 0) add(val(t - (int64_t)n * n));
+      if (k < n - 1) add(val(t + (int64_t)n * n));
+      acc = two_sum(sh, __fadd_rn(err, lo));
     }
     float blo;
     const float bhi = rhs_hi(b, t, blo);
@@ -168,9 +176,16 @@ __global__ void residual32_kernel(const float* __restrict__ x, const float* __re
 // Fixed-order reduction of the residual partials and the convergence test.
 // fp32 != 0: sums in float (the plain FP32 comparator's dots).  flip != 0:
 // this step wrote the corrected x64 into the other buffer.
+// Kernels launched by the recorded solver loops' bodies (device-side loop: the
+// body's launch count is added once per iteration that runs).
+__device__ unsigned long long g_loop_launches;
+
+// step >= 0: the step number and whether it is the last allowed come from the
+// host (fixed launch sequence); step < 0: a recorded loop body, which counts
+// from the device state.  cond != 0: set the loop's condition to "not done".
 __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks, int64_t N,
-                                SolveState* ss, DevState* st, double tol, int step, int last, int fp32,
-                                int flip) {
+                                SolveState* ss, DevState* st, double tol, int step, int fp32, int flip,
+                                cudaGraphConditionalHandle hc, int cond) {
   if (ss->done) return;
   __shared__ double red[32];
   double s1 = 0.0, s2 = 0.0;
@@ -193,6 +208,11 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks
     s2 = block_sum<1024>(s2, red);
   }
   if (threadIdx.x == 0) {
+    if (step < 0) {
+      step = ss->iter + 1;
+      atomicAdd(&g_loop_launches, (unsigned long long)ss->body_launches);
+    }
+    const bool last = step >= ss->max_steps;
     if (flip) ss->xidx ^= 1;
     ss->cold = 0;
     const double mean = s1 / (double)N;
@@ -208,35 +228,28 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks
       atomicOr(&st->status, WGEO_STATUS_NOT_CONVERGED);
       ss->done = 1;
     }
+    if (cond) cudaGraphSetConditional(hc, ss->done ? 0u : 1u);
   }
 }
-
-__global__ void solve_begin_kernel(SolveState* ss, int cold) {
+__global__ void solve_begin_kernel(SolveState* ss, int cold, int max_steps, int body_launches) {
   ss->done = 0;
   ss->iter = 0;
   ss->rel = 0.0;
   ss->rmean = 0.0;
   ss->cold = cold;
+  ss->max_steps = max_steps;
+  ss->body_launches = body_launches;
 }
 
-// ---------------------------------------------------------------- fused smoothers
-// Levels with n >= kFusedMin.  A CTA owns a kTX x kTY column tile and a
-// kZC-plane z chunk and walks z, keeping a ring of x planes (with halo) in
-// shared memory; the next plane is prefetched with cp.async while the current
-// one is processed.  Half-sweep s of the pipeline works s planes behind the
-// newest plane, so every update sees exactly the neighbour values a global
-// red-black Gauss-Seidel sweep would.  b is read through the L1/L2 caches.
-constexpr int kFusedMin = 128;
-
-template <bool PRE>
-struct SmGeom {
-  static constexpr int H = PRE ? 2 * kNu + 1 : 2 * kNu;   // halo of the loaded tile
-  static constexpr int WX = kTX + 2 * H, WY = kTY + 2 * H, P = WX * WY;
-  static constexpr int RX = PRE ? 2 * kNu + 4 : 2 * kNu + 3; // planes alive + 1 prefetch slot
-  static constexpr int CW = WX / 2 + 3, CH = WY / 2 + 3;       // coarse staging window (POST)
-  static constexpr size_t smem =
-      sizeof(float) * ((size_t)RX * P + (PRE ? (kTX / 2) * (kTY / 2) : CW * CH));
-};
+// ---------------------------------------------------------------- levels above 16^3
+// Plain kernels, one launch per step, each close to its memory floor.  A
+// red-black half-sweep reads only cells of the other colour, so its updates
+// are independent: a thread owns one x pair of cells (one of each colour)
+// and updates the one of the sweep's colour in place.  x is read once from
+// HBM per half-sweep (neighbour reuse through L1/L2), b and the written half
+// once: about 8 bytes per cell.  Grids are 3D (32 pairs x 8 rows per block,
+// one z plane per blockIdx.z), so no thread divides to find its cell.
+constexpr int kSX = 32, kSY = 8;
 
 __device__ __forceinline__ float prolong_at(const float* __restrict__ xc, int nc, int gx, int gy, int gz) {
   const int I = gx >> 1, J = gy >> 1, K = gz >> 1;
@@ -250,286 +263,96 @@ __device__ __forceinline__ float prolong_at(const float* __restrict__ xc, int nc
          a * c * c * xc[lin(I, J2, K2, nc)] + c * c * c * xc[lin(I2, J2, K2, nc)];
 }
 
-__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// PRE: x_out = 2 red-black sweeps (red first) of x_in (or of 0 when ZERO), and
-//      bc = 1/2 * sum of the children residuals b - L x_out.
-// POST: x_out = 2 sweeps (black first) of x_in + P xc.
-template <bool PRE, bool ZERO>
-__global__ void __launch_bounds__(kSmThreads, 2) smooth_kernel(const float* __restrict__ xin,
-                                                               float* __restrict__ xout,
-                                                               const float* __restrict__ b,
-                                                               const double* __restrict__ shift, int n, int zc,
-                                                               const float* __restrict__ xc,
-                                                               float* __restrict__ bc,
-                                                               const int* __restrict__ gate) {
+// One half-sweep of colour `color` ((i + j + k) & 1 == color) on
+// L x = b - shift.  ZERO: x is taken as 0 (the first half-sweep of a cycle
+// from a zero start), and the pair's other cell is written 0.
+template <bool ZERO>
+__global__ void __launch_bounds__(kSX * kSY) rb_half_kernel(float* __restrict__ x, const float* __restrict__ b,
+                                                            const double* __restrict__ shift, int n, int color,
+                                                            const int* __restrict__ gate) {
   if (*gate) return;
-  using G = SmGeom<PRE>;
-  constexpr int NPAIR = G::P / 2;                               // cell pairs per plane (WX even)
-  constexpr int SLOTS = (NPAIR + kSmThreads - 1) / kSmThreads;  // pairs per thread
-  extern __shared__ float sm[];
-  float* xs = sm;                       // RX planes
-  float* cacc = sm + G::RX * G::P;      // coarse accumulator (PRE) / coarse staging (POST)
-  const int X0 = blockIdx.x * kTX, Y0 = blockIdx.y * kTY, z0 = blockIdx.z * zc;
-  const int z1 = min(z0 + zc, n);
-  const int ax = max(X0 - G::H, 0), bx = min(X0 + kTX + G::H, n);
-  const int ay = max(Y0 - G::H, 0), by = min(Y0 + kTY + G::H, n);
-  const int zlo = max(z0 - G::H, 0), zhi = min(z1 + G::H, n);
+  const int ih = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y, k = blockIdx.z;
+  if (2 * ih >= n || j >= n) return;
   const float sh = shift ? (float)*shift : 0.f;
-  const int nc = n >> 1;
+  const int odd = (j + k + color) & 1;
+  const int i = 2 * ih + odd;
   const int64_t nn = (int64_t)n * n;
-  const int c0 = PRE ? 0 : 1;           // colour of the first half-sweep
-  const int zend = zhi + 2 * kNu + (PRE ? 1 : 0);
-
-  // Per-thread cell table, built once.  Within one z step every half-sweep s
-  // works on plane zin - s with colour c0 ^ (s-1), so the cell of a pair that
-  // has the right colour depends only on (row, zin): phase = rowph ^ (zin & 1).
-  int cloc[SLOTS][2], boff[SLOTS][2], info[SLOTS][2];   // info: depth | neighbour mask << 8
-  int rowph[SLOTS];
-#pragma unroll
-  for (int k = 0; k < SLOTS; ++k) {
-    const int pr = threadIdx.x + k * kSmThreads;
-    const int ly = pr / (G::WX / 2), j = pr % (G::WX / 2);
-    const int gy = Y0 - G::H + ly;
-    rowph[k] = (c0 - 1 + gy + X0 + G::H) & 1;
-#pragma unroll
-    for (int ph = 0; ph < 2; ++ph) {
-      const int lx = 2 * j + ph, gx = X0 - G::H + lx;
-      cloc[k][ph] = ly * G::WX + lx;
-      boff[k][ph] = gy * n + gx;
-      int depth = -1;
-      if (pr < NPAIR && gx >= ax && gx < bx && gy >= ay && gy < by) {
-        depth = 2 * kNu;
-        if (ax > 0) depth = min(depth, gx - ax);
-        if (bx < n) depth = min(depth, bx - 1 - gx);
-        if (ay > 0) depth = min(depth, gy - ay);
-        if (by < n) depth = min(depth, by - 1 - gy);
-      }
-      const int mask = (gx > 0 ? 1 : 0) | (gx < n - 1 ? 2 : 0) | (gy > 0 ? 4 : 0) | (gy < n - 1 ? 8 : 0);
-      info[k][ph] = depth | (mask << 8);
-    }
+  const int64_t p = k * nn + (int64_t)j * n + i;
+  const int cnt = 6 - (i == 0) - (i == n - 1) - (j == 0) - (j == n - 1) - (k == 0) - (k == n - 1);
+  float acc = 0.f;
+  if (!ZERO) {
+    if (i > 0) acc += x[p - 1];
+    if (i < n - 1) acc += x[p + 1];
+    if (j > 0) acc += x[p - n];
+    if (j < n - 1) acc += x[p + n];
+    if (k > 0) acc += x[p - nn];
+    if (k < n - 1) acc += x[p + nn];
   }
-
-  auto issue = [&](int z) {             // start loading plane z into its ring slot
-    float* xp = xs + (z % G::RX) * G::P;
-    const float* src = xin + (int64_t)z * nn;
-    for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
-      const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
-      const bool in = gx >= ax && gx < bx && gy >= ay && gy < by;
-      if (in && !ZERO)
-        cp_async4(xp + c, src + gy * n + gx);
-      else
-        xp[c] = 0.f;
-    }
-  };
-
-  issue(zlo);
-  cp_async_commit();
-  for (int zin = zlo; zin < zend; ++zin) {
-    if (zin + 1 < zhi) issue(zin + 1);
-    cp_async_commit();
-    cp_async_wait1();                   // plane zin has landed (this thread's copies)
-    if (!PRE && zin < zhi) {
-      // prolongation, separably: the coarse window interpolated in z into shared
-      // memory (2 reads per coarse cell), then bilinear in x, y from there
-      float* cz = cacc;
-      const int K = zin >> 1;
-      const int K2 = min(max((zin & 1) ? K + 1 : K - 1, 0), nc - 1);
-      const int cI0 = ((X0 - G::H) >> 1) - 1, cJ0 = ((Y0 - G::H) >> 1) - 1;
-      const float* xk = xc + (int64_t)K * nc * nc;
-      const float* xk2 = xc + (int64_t)K2 * nc * nc;
-      for (int c = threadIdx.x; c < G::CW * G::CH; c += blockDim.x) {
-        const int ci = min(max(cI0 + c % G::CW, 0), nc - 1);
-        const int cj = min(max(cJ0 + c / G::CW, 0), nc - 1);
-        cz[c] = 0.75f * xk[cj * nc + ci] + 0.25f * xk2[cj * nc + ci];
-      }
-      __syncthreads();
-      float* xp = xs + (zin % G::RX) * G::P;
-      for (int c = threadIdx.x; c < G::P; c += blockDim.x) {
-        const int gx = X0 - G::H + c % G::WX, gy = Y0 - G::H + c / G::WX;
-        if (gx >= ax && gx < bx && gy >= ay && gy < by) {
-          const int I = gx >> 1, J = gy >> 1;
-          const int I2 = min(max((gx & 1) ? I + 1 : I - 1, 0), nc - 1);
-          const int J2 = min(max((gy & 1) ? J + 1 : J - 1, 0), nc - 1);
-          const int r1 = (J - cJ0) * G::CW, r2 = (J2 - cJ0) * G::CW;
-          xp[c] += 0.5625f * cz[r1 + I - cI0] + 0.1875f * cz[r1 + I2 - cI0] +
-                   0.1875f * cz[r2 + I - cI0] + 0.0625f * cz[r2 + I2 - cI0];
-        }
-      }
-    }
-    __syncthreads();
-    const int zph = zin & 1;
-#pragma unroll
-    for (int s = 1; s <= 2 * kNu; ++s) {
-      const int p = zin - s;
-      const int plo = zlo + (zlo > 0 ? s : 0), phi = zhi - (zhi < n ? s : 0);
-      if (p >= plo && p < phi) {
-        float* xp = xs + (p % G::RX) * G::P;
-        const float* xm = xs + ((p + G::RX - 1) % G::RX) * G::P;
-        const float* xq = xs + ((p + 1) % G::RX) * G::P;
-        const bool hm = p > 0, hq = p < n - 1;
-        const float* bp = b + (int64_t)p * nn;
-        const int zcnt = (hm ? 1 : 0) + (hq ? 1 : 0);
-#pragma unroll
-        for (int k = 0; k < SLOTS; ++k) {
-          const int ph = rowph[k] ^ zph;
-          const int inf = ph ? info[k][1] : info[k][0];     // selects keep the tables in registers
-          if ((inf & 0xff) < s || (inf & 0x80)) continue;   // outside this stage's region / domain
-          const int c = ph ? cloc[k][1] : cloc[k][0];
-          const int bo = ph ? boff[k][1] : boff[k][0];
-          const int m = inf >> 8;
-          float acc = 0.f;
-          int cnt = zcnt;
-          if (m & 1) { acc += xp[c - 1]; ++cnt; }
-          if (m & 2) { acc += xp[c + 1]; ++cnt; }
-          if (m & 4) { acc += xp[c - G::WX]; ++cnt; }
-          if (m & 8) { acc += xp[c + G::WX]; ++cnt; }
-          if (hm) acc += xm[c];
-          if (hq) acc += xq[c];
-          xp[c] = __fdividef(acc - (__ldg(bp + bo) - sh), (float)cnt);
-        }
-      }
-      __syncthreads();
-    }
-    if (PRE) {
-      const int q = zin - 2 * kNu - 1;
-      if (q >= z0 && q < z1) {
-        const float* xp = xs + (q % G::RX) * G::P;
-        const float* xm = xs + ((q + G::RX - 1) % G::RX) * G::P;
-        const float* xq = xs + ((q + 1) % G::RX) * G::P;
-        const bool hm = q > 0, hq = q < n - 1;
-        float* out = xout + (int64_t)q * nn;
-        const float* bq = b + (int64_t)q * nn;
-        for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
-          const int gx = X0 + c % kTX, gy = Y0 + c / kTX;
-          if (gx < n && gy < n) out[gy * n + gx] = xp[(gy - Y0 + G::H) * G::WX + (gx - X0 + G::H)];
-        }
-        // one thread per coarse cell of this plane: residual of its 4 children, fixed order
-        for (int c = threadIdx.x; c < (kTX / 2) * (kTY / 2); c += blockDim.x) {
-          const int cx = c % (kTX / 2), cy = c / (kTX / 2);
-          float r = 0.f;
-#pragma unroll
-          for (int ch = 0; ch < 4; ++ch) {
-            const int gx = X0 + 2 * cx + (ch & 1), gy = Y0 + 2 * cy + (ch >> 1);
-            if (gx >= n || gy >= n) continue;
-            const int lc = (gy - Y0 + G::H) * G::WX + (gx - X0 + G::H);
-            const float xv = xp[lc];
-            float lx = 0.f;
-            if (gx > 0) lx += xp[lc - 1] - xv;
-            if (gx < n - 1) lx += xp[lc + 1] - xv;
-            if (gy > 0) lx += xp[lc - G::WX] - xv;
-            if (gy < n - 1) lx += xp[lc + G::WX] - xv;
-            if (hm) lx += xm[lc] - xv;
-            if (hq) lx += xq[lc] - xv;
-            r += (__ldg(bq + gy * n + gx) - sh) - lx;
-          }
-          if ((q & 1) == 0) {
-            cacc[c] = r;
-          } else {
-            const int gcx = (X0 >> 1) + cx, gcy = (Y0 >> 1) + cy;
-            if (gcx < nc && gcy < nc) bc[lin(gcx, gcy, q >> 1, nc)] = 0.5f * (cacc[c] + r);
-          }
-        }
-      }
-      __syncthreads();
-    } else {
-      const int p = zin - 2 * kNu;
-      if (p >= z0 && p < z1) {
-        const float* xp = xs + (p % G::RX) * G::P;
-        float* out = xout + (int64_t)p * nn;
-        for (int c = threadIdx.x; c < kTX * kTY; c += blockDim.x) {
-          const int gx = X0 + c % kTX, gy = Y0 + c / kTX;
-          if (gx < n && gy < n) out[gy * n + gx] = xp[(gy - Y0 + G::H) * G::WX + (gx - X0 + G::H)];
-        }
-      }
-      __syncthreads();
-    }
-  }
+  x[p] = __fdividef(acc - (__ldg(b + p) - sh), (float)cnt);
+  if (ZERO) x[p + (odd ? -1 : 1)] = 0.f;
 }
 
-
-// ---------------------------------------------------------------- mid-size levels
-// 16 < n < kFusedMin: one launch per half-sweep (launch-latency regime, the
-// level is L2-resident).  In place on x.
-__global__ void zero_kernel(float* __restrict__ x, int64_t N, const int* __restrict__ gate) {
-  if (*gate) return;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x)
-    x[t] = 0.f;
-}
-
-__global__ void rbgs_kernel(float* __restrict__ x, const float* __restrict__ b,
-                            const double* __restrict__ shift, int n, int color,
-                            const int* __restrict__ gate) {
-  if (*gate) return;
-  const int half = n >> 1;
-  const int64_t M = (int64_t)half * n * n;
-  const float sh = shift ? (float)*shift : 0.f;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int ih = (int)(t % half);
-    const int64_t row = t / half;
-    const int j = (int)(row % n), k = (int)(row / n);
-    const int i = 2 * ih + ((j + k + color) & 1);
-    const int64_t p = lin(i, j, k, n);
-    float s = 0.f;
-    int cnt = 0;
-    if (i > 0) { s += x[p - 1]; ++cnt; }
-    if (i < n - 1) { s += x[p + 1]; ++cnt; }
-    if (j > 0) { s += x[p - n]; ++cnt; }
-    if (j < n - 1) { s += x[p + n]; ++cnt; }
-    if (k > 0) { s += x[p - (int64_t)n * n]; ++cnt; }
-    if (k < n - 1) { s += x[p + (int64_t)n * n]; ++cnt; }
-    x[p] = (s - (b[p] - sh)) / (float)cnt;
-  }
-}
-
-__global__ void resid_restrict_kernel(const float* __restrict__ x, const float* __restrict__ b,
-                                      const double* __restrict__ shift, int n,
-                                      float* __restrict__ bc, const int* __restrict__ gate) {
+// bc = 1/2 * sum over the 8 children of the residual b - shift - L x.
+__global__ void __launch_bounds__(kSX * kSY) restrict_kernel(const float* __restrict__ x,
+                                                             const float* __restrict__ b,
+                                                             const double* __restrict__ shift, int n,
+                                                             float* __restrict__ bc,
+                                                             const int* __restrict__ gate) {
   if (*gate) return;
   const int nc = n >> 1;
-  const int64_t Mc = (int64_t)nc * nc * nc;
+  const int I = blockIdx.x * kSX + threadIdx.x, J = blockIdx.y * kSY + threadIdx.y, K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
   const float sh = shift ? (float)*shift : 0.f;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Mc;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int I = (int)(t % nc), J = (int)((t / nc) % nc), K = (int)(t / ((int64_t)nc * nc));
-    float acc = 0.f;
+  const int64_t nn = (int64_t)n * n;
+  float acc = 0.f;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
-      const int64_t p = lin(i, j, k, n);
-      const float xc = x[p];
-      float lx = 0.f;
-      if (i > 0) lx += x[p - 1] - xc;
-      if (i < n - 1) lx += x[p + 1] - xc;
-      if (j > 0) lx += x[p - n] - xc;
-      if (j < n - 1) lx += x[p + n] - xc;
-      if (k > 0) lx += x[p - (int64_t)n * n] - xc;
-      if (k < n - 1) lx += x[p + (int64_t)n * n] - xc;
-      acc += (b[p] - sh) - lx;
-    }
-    bc[t] = 0.5f * acc;
+  for (int c = 0; c < 8; ++c) {
+    const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
+    const int64_t p = k * nn + (int64_t)j * n + i;
+    const float xv = x[p];
+    float lx = 0.f;
+    if (i > 0) lx += x[p - 1] - xv;
+    if (i < n - 1) lx += x[p + 1] - xv;
+    if (j > 0) lx += x[p - n] - xv;
+    if (j < n - 1) lx += x[p + n] - xv;
+    if (k > 0) lx += x[p - nn] - xv;
+    if (k < n - 1) lx += x[p + nn] - xv;
+    acc += (__ldg(b + p) - sh) - lx;
   }
+  bc[((int64_t)K * nc + J) * nc + I] = 0.5f * acc;
 }
 
-__global__ void prolong_kernel(const float* __restrict__ xc, float* __restrict__ x, int n,
-                               const int* __restrict__ gate) {
+// x += P xc for one x pair (2I, 2I+1) of row j, plane k: trilinear weights
+// 3/4, 1/4 per axis toward the nearer coarse neighbour (mirrored at the
+// walls), from the 12 coarse values the pair needs.
+__global__ void __launch_bounds__(kSX * kSY) prolong_pair_kernel(const float* __restrict__ xc,
+                                                                 float* __restrict__ x, int n,
+                                                                 const int* __restrict__ gate) {
   if (*gate) return;
   const int nc = n >> 1;
-  const int64_t N = (int64_t)n * n * n;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % n), j = (int)((t / n) % n), k = (int)(t / ((int64_t)n * n));
-    x[t] += prolong_at(xc, nc, i, j, k);
+  const int I = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y, k = blockIdx.z;
+  if (I >= nc || j >= n) return;
+  const int J = j >> 1, K = k >> 1;
+  const int J2 = min(max((j & 1) ? J + 1 : J - 1, 0), nc - 1);
+  const int K2 = min(max((k & 1) ? K + 1 : K - 1, 0), nc - 1);
+  const int Im = max(I - 1, 0), Ip = min(I + 1, nc - 1);
+  const int64_t ncc = (int64_t)nc * nc;
+  const int64_t r[4] = {K * ncc + (int64_t)J * nc, K * ncc + (int64_t)J2 * nc, K2 * ncc + (int64_t)J * nc,
+                        K2 * ncc + (int64_t)J2 * nc};
+  const float w[4] = {0.5625f, 0.1875f, 0.1875f, 0.0625f};
+  float ve = 0.f, vo = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float a0 = __ldg(xc + r[q] + I), am = __ldg(xc + r[q] + Im), ap = __ldg(xc + r[q] + Ip);
+    ve += w[q] * (0.75f * a0 + 0.25f * am);
+    vo += w[q] * (0.75f * a0 + 0.25f * ap);
   }
+  float2* xp = reinterpret_cast<float2*>(x + (int64_t)k * n * n + (int64_t)j * n + 2 * I);
+  float2 v = *xp;
+  v.x += ve;
+  v.y += vo;
+  *xp = v;
 }
-
 
 // ---------------------------------------------------------------- small grids
 // A whole V-cycle hierarchy for n <= 16 in one CTA's shared memory: solves
@@ -688,13 +511,12 @@ __global__ void rhs_stats_finalize_kernel(const double* __restrict__ partials, i
   }
 }
 
-// One V-cycle on level l.  x0 / x0b: level-0 iterate and its ping-pong
-// partner; b0, shift0: level-0 right-hand side.  zero0: level-0 x is zero.
-int vcycle(wgeo_handle* h, int l, float* x0, float* x0b, const float* b0, const double* shift0, bool zero0,
+// One V-cycle on level l, in place.  x0: level-0 iterate; b0, shift0:
+// level-0 right-hand side.  zero0: level-0 x starts at zero.
+int vcycle(wgeo_handle* h, int l, float* x0, const float* b0, const double* shift0, bool zero0,
            const int* gate, cudaStream_t s) {
   const int n = h->levels[l].n;
   float* x = (l == 0) ? x0 : h->levels[l].x;
-  float* xb = (l == 0) ? x0b : h->levels[l].x2;
   const float* b = (l == 0) ? b0 : h->levels[l].b;
   const double* shift = (l == 0) ? shift0 : nullptr;
   if (n <= kSmallN || l == h->nlevels - 1) {
@@ -704,85 +526,54 @@ int vcycle(wgeo_handle* h, int l, float* x0, float* x0b, const float* b0, const 
   }
   const bool zero = (l == 0) ? zero0 : true;
   const int nc = n >> 1;
-  const int64_t N = (int64_t)n * n * n, Nc = (int64_t)nc * nc * nc;
-  if (n < kFusedMin) {
-    // mid-size level: in place, one launch per half-sweep
-    const int gb = grid_blocks(N / 2, kThreads, 152 * 32);
-    if (zero) {
-      zero_kernel<<<grid_blocks(N, kThreads, 152 * 32), kThreads, 0, s>>>(x, N, gate);
+  const dim3 blk(kSX, kSY);
+  const dim3 gf(div_up(nc, kSX), div_up(n, kSY), n);      // fine pairs
+  const dim3 gc(div_up(nc, kSX), div_up(nc, kSY), nc);    // coarse cells
+  // pre-smoothing: kNu red-black sweeps, red first (the first from zero when zero)
+  for (int sw = 0; sw < kNu; ++sw)
+    for (int c = 0; c < 2; ++c) {
+      if (zero && sw == 0 && c == 0)
+        rb_half_kernel<true><<<gf, blk, 0, s>>>(x, b, shift, n, c, gate);
+      else
+        rb_half_kernel<false><<<gf, blk, 0, s>>>(x, b, shift, n, c, gate);
       WGEO_LAUNCH_CHECK();
     }
-    for (int sw = 0; sw < kNu; ++sw)
-      for (int c = 0; c < 2; ++c) {
-        rbgs_kernel<<<gb, kThreads, 0, s>>>(x, b, shift, n, c, gate);
-        WGEO_LAUNCH_CHECK();
-      }
-    resid_restrict_kernel<<<grid_blocks(Nc, kThreads, 152 * 32), kThreads, 0, s>>>(x, b, shift, n,
-                                                                                  h->levels[l + 1].b, gate);
-    WGEO_LAUNCH_CHECK();
-    int rc = vcycle(h, l + 1, x0, x0b, b0, shift0, zero0, gate, s);
-    if (rc) return rc;
-    prolong_kernel<<<grid_blocks(N, kThreads, 152 * 32), kThreads, 0, s>>>(h->levels[l + 1].x, x, n, gate);
-    WGEO_LAUNCH_CHECK();
-    for (int sw = 0; sw < kNu; ++sw)
-      for (int c = 1; c >= 0; --c) {
-        rbgs_kernel<<<gb, kThreads, 0, s>>>(x, b, shift, n, c, gate);
-        WGEO_LAUNCH_CHECK();
-      }
-    return WGEO_OK;
-  }
-  // z chunk: a CTA's pipeline costs ~ (zc + 3 * 2 kNu) plane steps and runs in
-  // ceil(CTAs / resident CTAs) waves; take the chunk with the lowest product
-  int zc = 16;
-  {
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    const int slots = 2 * sms;
-    long best = -1;
-    for (int cand = 16; cand <= 64; cand *= 2) {
-      const long ctas = (long)div_up(n, kTX) * div_up(n, kTY) * div_up(n, cand);
-      const long cost = ((ctas + slots - 1) / slots) * (cand + 6 * kNu);
-      if (best < 0 || cost < best) {
-        best = cost;
-        zc = cand;
-      }
-    }
-  }
-  const dim3 grid(div_up(n, kTX), div_up(n, kTY), div_up(n, zc));
-  if (zero)
-    smooth_kernel<true, true><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, zc, nullptr,
-                                                                           h->levels[l + 1].b, gate);
-  else
-    smooth_kernel<true, false><<<grid, kSmThreads, SmGeom<true>::smem, s>>>(x, xb, b, shift, n, zc, nullptr,
-                                                                            h->levels[l + 1].b, gate);
+  restrict_kernel<<<gc, blk, 0, s>>>(x, b, shift, n, h->levels[l + 1].b, gate);
   WGEO_LAUNCH_CHECK();
-  int rc = vcycle(h, l + 1, x0, x0b, b0, shift0, zero0, gate, s);
+  int rc = vcycle(h, l + 1, x0, b0, shift0, zero0, gate, s);
   if (rc) return rc;
-  smooth_kernel<false, false><<<grid, kSmThreads, SmGeom<false>::smem, s>>>(xb, x, b, shift, n, zc,
-                                                                            h->levels[l + 1].x, nullptr, gate);
+  prolong_pair_kernel<<<gf, blk, 0, s>>>(h->levels[l + 1].x, x, n, gate);
   WGEO_LAUNCH_CHECK();
+  // post-smoothing: kNu sweeps, black first
+  for (int sw = 0; sw < kNu; ++sw)
+    for (int c = 1; c >= 0; --c) {
+      rb_half_kernel<false><<<gf, blk, 0, s>>>(x, b, shift, n, c, gate);
+      WGEO_LAUNCH_CHECK();
+    }
   return WGEO_OK;
 }
 
-// The fixed launch sequence of one solve (mode 0: forward, 1: adjoint).
-int enqueue_solve(wgeo_handle* h, int res, int mode, cudaStream_t s) {
+// One solve (mode 0: forward, 1: adjoint) is a head -- the first residual
+// and convergence test -- followed by loop iterations, each a correction and
+// a new residual and test.  part 0 enqueues the head, part 1 one iteration.
+// step: the host's step number (fixed sequence) or -1 (recorded loop body,
+// counted on the device); hc / cond: the recorded loop's condition.
+int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGraphConditionalHandle hc, int cond,
+                 cudaStream_t s) {
   const int64_t N = (int64_t)res * res * res;
   SolveState* ss = mode == 0 ? &h->dstate->fwd : &h->dstate->bwd;
   const int* gate = &ss->done;
   const bool fp32 = (mode == 0 && h->opt.precision == WGEO_PREC_FP32);
   const int rb = grid_blocks(N, kThreads, kPartials);
   if (fp32) {
-    const double tol = h->opt.tol_rel;
-    const int maxv = h->opt.max_vcycles;
-    for (int it = 0; it <= maxv; ++it) {
-      residual32_kernel<<<rb, kThreads, 0, s>>>(h->chi32, h->b32, &ss->bmean, res, h->partials, gate);
-      WGEO_LAUNCH_CHECK();
-      finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, tol, it, it == maxv, 1, 0);
-      WGEO_LAUNCH_CHECK();
-      if (it == maxv) break;
-      int rc = vcycle(h, 0, h->chi32, h->r32, h->b32, &ss->bmean, false, gate, s);
+    if (part == 1) {
+      int rc = vcycle(h, 0, h->chi32, h->b32, &ss->bmean, false, gate, s);
       if (rc) return rc;
     }
+    residual32_kernel<<<rb, kThreads, 0, s>>>(h->chi32, h->b32, &ss->bmean, res, h->partials, gate);
+    WGEO_LAUNCH_CHECK();
+    finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, h->opt.tol_rel, step, 1, 0, hc, cond);
+    WGEO_LAUNCH_CHECK();
     return WGEO_OK;
   }
   const double tol = mode == 0 ? h->opt.tol_rel : h->opt.tol_rel_adjoint;
@@ -790,29 +581,108 @@ int enqueue_solve(wgeo_handle* h, int res, int mode, cudaStream_t s) {
   xp.buf[0] = mode == 0 ? h->chiff[0] : h->lamff[0];
   xp.buf[1] = mode == 0 ? h->chiff[1] : h->lamff[1];
   float* x32 = mode == 0 ? h->chi32 : h->lam32;
-  const int maxr = h->opt.max_refine;
-  const int nv = h->opt.vcycles_per_refine;
-  for (int it = 0; it <= maxr; ++it) {
-    const float* e = it == 0 ? nullptr : h->e32;
-    if (mode == 0)
-      update_residual_kernel<float><<<rb, kThreads, 0, s>>>(xp, e, h->b32, res, h->r32, x32, h->partials, ss);
-    else
-      update_residual_kernel<double><<<rb, kThreads, 0, s>>>(xp, e, h->dchi64, res, h->r32, x32, h->partials, ss);
-    WGEO_LAUNCH_CHECK();
-    finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, tol, it, it == maxr, 0, e ? 1 : 0);
-    WGEO_LAUNCH_CHECK();
-    if (it == maxr) break;
-    // correction: V-cycles on L e = r - mean(r); the FP32 copy x32 serves as the
-    // ping-pong partner (it is rewritten by the next refinement pass)
-    for (int v = 0; v < nv; ++v) {
-      int rc = vcycle(h, 0, h->e32, x32, h->r32, &ss->rmean, v == 0, gate, s);
+  if (part == 1) {
+    // correction: V-cycles on L e = r - mean(r)
+    for (int v = 0; v < h->opt.vcycles_per_refine; ++v) {
+      int rc = vcycle(h, 0, h->e32, h->r32, &ss->rmean, v == 0, gate, s);
       if (rc) return rc;
     }
   }
+  const float* e = part == 0 ? nullptr : h->e32;
+  if (mode == 0)
+    update_residual_kernel<float><<<rb, kThreads, 0, s>>>(xp, e, h->b32, res, h->r32, x32, h->partials, ss);
+  else
+    update_residual_kernel<double><<<rb, kThreads, 0, s>>>(xp, e, h->dchi64, res, h->r32, x32, h->partials, ss);
+  WGEO_LAUNCH_CHECK();
+  finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, tol, step, 0, e ? 1 : 0, hc, cond);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+int max_steps(const wgeo_handle* h, int mode) {
+  return (mode == 0 && h->opt.precision == WGEO_PREC_FP32) ? h->opt.max_vcycles : h->opt.max_refine;
+}
+
+// The fixed launch sequence: the head and max_steps gated iterations.
+int enqueue_solve(wgeo_handle* h, int res, int mode, cudaStream_t s) {
+  int rc = enqueue_part(h, res, mode, 0, 0, 0, 0, s);
+  for (int it = 1; it <= max_steps(h, mode) && rc == WGEO_OK; ++it)
+    rc = enqueue_part(h, res, mode, 1, it, 0, 0, s);
+  return rc;
+}
+
+// Records the solve as a graph: the head, then a conditional WHILE node whose
+// body (one iteration) runs until the convergence test clears the condition,
+// so no launch happens after convergence.  Counts: the head's launches are
+// returned in *head, one body's in *body.
+int record_solve(wgeo_handle* h, int res, int mode, cudaGraph_t* out, long long* head, long long* body) {
+  cudaStream_t cs = h->capture_stream;
+  cudaGraph_t g = nullptr;
+  WGEO_CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle hc;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&hc, g, 0, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return WGEO_ERR_CUDA;
+  }
+  long long t0 = t_kernel_launches;
+  e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? enqueue_part(h, res, mode, 0, 0, hc, 1, cs) : WGEO_ERR_CUDA;
+  std::vector<cudaGraphNode_t> deps;
+  if (e == cudaSuccess) {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &d, nullptr, &nd) == cudaSuccess)
+      deps.assign(d, d + nd);
+    cudaGraph_t gg = g;
+    if (cudaStreamEndCapture(cs, &gg) != cudaSuccess && rc == WGEO_OK) rc = WGEO_ERR_CUDA;
+  }
+  *head = t_kernel_launches - t0;
+  cudaGraph_t bodyg = nullptr;
+  if (rc == WGEO_OK) {
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hc;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps.data(), nullptr, deps.size(), &p) != cudaSuccess)
+      rc = WGEO_ERR_CUDA;
+    else
+      bodyg = p.conditional.phGraph_out[0];
+  }
+  t0 = t_kernel_launches;
+  if (rc == WGEO_OK) {
+    e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      rc = WGEO_ERR_CUDA;
+    } else {
+      rc = enqueue_part(h, res, mode, 1, -1, hc, 1, cs);
+      cudaGraph_t bb = bodyg;
+      if (cudaStreamEndCapture(cs, &bb) != cudaSuccess && rc == WGEO_OK) rc = WGEO_ERR_CUDA;
+    }
+  }
+  *body = t_kernel_launches - t0;
+  if (rc != WGEO_OK) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  *out = g;
   return WGEO_OK;
 }
 
 }  // namespace
+
+long long loop_launches() {
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_loop_launches, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (long long)v;
+}
 
 int coarsest_size(int res) {
   int n = res;
@@ -821,22 +691,11 @@ int coarsest_size(int res) {
 }
 
 int build_levels(wgeo_handle* h, int res) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(smooth_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)SmGeom<true>::smem);
-    cudaFuncSetAttribute(smooth_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)SmGeom<true>::smem);
-    cudaFuncSetAttribute(smooth_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)SmGeom<false>::smem);
-    attr_done = true;
-  }
   int n = res;
   int l = 0;
   float* pool = h->level_pool;
   h->levels[0].n = n;
   h->levels[0].x = nullptr;
-  h->levels[0].x2 = nullptr;
   h->levels[0].b = nullptr;
   while ((n % 2) == 0 && n > 8) {
     n /= 2;
@@ -846,9 +705,8 @@ int build_levels(wgeo_handle* h, int res) {
     const int64_t Ma = (M + 63) / 64 * 64;
     h->levels[l].n = n;
     h->levels[l].x = pool;
-    h->levels[l].x2 = pool + Ma;
-    h->levels[l].b = pool + 2 * Ma;
-    pool += 3 * Ma;
+    h->levels[l].b = pool + Ma;
+    pool += 2 * Ma;
   }
   if (n > 16) return WGEO_ERR_INVALID_ARG;
   h->nlevels = l + 1;
@@ -869,11 +727,14 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
     rhs_stats_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss);
     WGEO_LAUNCH_CHECK();
   }
-  solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0);
-  WGEO_LAUNCH_CHECK();
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   WGEO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
-  if (!h->opt.use_graphs || cap != cudaStreamCaptureStatusNone) return enqueue_solve(h, res, mode, s);
+  const int steps = max_steps(h, mode);
+  if (!h->opt.use_graphs || cap != cudaStreamCaptureStatusNone) {
+    solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0, steps, 0);
+    WGEO_LAUNCH_CHECK();
+    return enqueue_solve(h, res, mode, s);
+  }
   SolverGraph& g = h->graphs[mode];
   const int gmode = mode * 2 + (h->opt.precision == WGEO_PREC_FP32 ? 1 : 0);
   if (g.exec == nullptr || g.res != res || g.mode != gmode) {
@@ -882,21 +743,15 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
       g.exec = nullptr;
     }
     if (!h->capture_stream) WGEO_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
-    WGEO_CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-    const long long before = t_kernel_launches;
-    int rc = enqueue_solve(h, res, mode, h->capture_stream);
-    // recorded, not run: counted at each replay instead
-    const long long captured = t_kernel_launches - before;
-    t_kernel_launches -= captured;
-    g_kernel_launches.fetch_sub(captured, std::memory_order_relaxed);
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(h->capture_stream, &graph);
-    if (rc) {
-      if (graph) cudaGraphDestroy(graph);
-      return rc;
-    }
-    if (e != cudaSuccess) return WGEO_ERR_CUDA;
-    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    long long head = 0, body = 0;
+    int rc = record_solve(h, res, mode, &graph, &head, &body);
+    // recorded, not run: the head is counted at each replay, the body on the
+    // device once per iteration
+    t_kernel_launches -= head + body;
+    g_kernel_launches.fetch_sub(head + body, std::memory_order_relaxed);
+    if (rc) return rc;
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
       g.exec = nullptr;
@@ -904,8 +759,11 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
     }
     g.res = res;
     g.mode = gmode;
-    g.launches = captured;
+    g.launches = head;
+    g.body_launches = body;
   }
+  solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0, steps, (int)g.body_launches);
+  WGEO_LAUNCH_CHECK();
   WGEO_CUDA_TRY(cudaGraphLaunch(g.exec, s));
   g_kernel_launches.fetch_add(g.launches, std::memory_order_relaxed);
   t_kernel_launches += g.launches;

@@ -27,6 +27,8 @@ struct SolveState {
   int iter;          // refinement steps / V-cycles performed
   int xidx;          // which of the two FP64 buffers holds the current iterate
   int cold;          // 1: start from x = 0 (the first refinement pass writes zeros)
+  int max_steps;     // the last step allowed (refinement steps, or V-cycles in plain FP32)
+  int body_launches; // kernels of one iteration of the recorded loop body (launch accounting)
   double bnorm;      // || b - mean(b) ||
   double bmean;
   double rmean;      // mean of the last residual (projected out of the correction RHS)
@@ -53,7 +55,6 @@ struct Tri {          // one marching-cubes triangle: vertex xyz + global edge i
 struct Level {
   int n;
   float* x;
-  float* x2;   // ping-pong partner of x for the fused smoothers
   float* b;
 };
 
@@ -89,7 +90,8 @@ struct StageTimer {
 struct SolverGraph {
   int res = 0;
   int mode = -1;      // 0 forward, 1 backward
-  long long launches = 0;   // kernel nodes recorded in the graph
+  long long launches = 0;       // kernels of the graph's head (run once per replay)
+  long long body_launches = 0;  // kernels of one iteration of its device-side loop
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -359,6 +361,7 @@ inline int grid_blocks(int64_t n, int threads, int cap = 152 * 16) {
 
 // coarsest-level rule: halve while even and larger than 8
 int coarsest_size(int res);
+long long loop_launches();   // kernels run by recorded solver loops on the current device (syncs)
 int build_levels(wgeo_handle* h, int res);
 
 // ---------------------------------------------------------------- launchers
