@@ -35,6 +35,7 @@ NPTS = 200_000
 NQ = 1_000_000
 BBOX = np.array([0, 0, 0, 1, 1, 1], dtype=np.float32)
 L2_BYTES = 129 * 2 ** 20
+HANDLE_OPTS = {}          # extra handle options (profiler runs only)
 METRIC = "SDF+normal cells/s at 256^3 (fwd, fwd+adjoint) vs FP32 plain; p50/p99 latency"
 
 
@@ -144,7 +145,7 @@ def run_ours(args):
     lib = L.load()
     # stage_timing = 1: CUDA events around each stage on the launching stream,
     # read back after the timed region (the dominant kernel's live duration)
-    rec = Reconstructor(RES, NPTS, stage_timing=1)
+    rec = Reconstructor(RES, NPTS, stage_timing=1, **HANDLE_OPTS)
     stream = torch.cuda.current_stream()
     N = RES ** 3
 
@@ -212,7 +213,7 @@ def run_ours(args):
         return a.elapsed_time(b) / k
 
     fwd_ms = time_it(lambda: rec.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf), 5)
-    rec32 = Reconstructor(RES, NPTS, precision=PREC_FP32, keep_for_backward=0, max_vcycles=60)
+    rec32 = Reconstructor(RES, NPTS, precision=PREC_FP32, keep_for_backward=0, max_vcycles=60, **HANDLE_OPTS)
     fwd32_ms = time_it(lambda: rec32.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf), 5)
     info32 = rec32.info()
     sdf32 = sdf_buf.clone()
@@ -223,7 +224,7 @@ def run_ours(args):
     rec32.close()
 
     # per-stage device times (CUDA events on the library's stream), separate pass
-    rec_t = Reconstructor(RES, NPTS, stage_timing=2)
+    rec_t = Reconstructor(RES, NPTS, stage_timing=2, **HANDLE_OPTS)
     for _ in range(2):
         rec_t.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf_buf, nrm_out=nrm_buf)
         rec_t.query(Q, with_normals=False)
@@ -306,7 +307,7 @@ def run_ours(args):
                                                         "defect-correction refinement",
                    "l2": "working set > 1 GB per step (fields of 67 MB) exceeds the 129 MB L2; no flush",
                    "parallelism": f"replicas x{ws}",
-                   "override": (RES, NPTS, NQ) != (256, 200_000, 1_000_000)},
+                   "override": (RES, NPTS, NQ) != (256, 200_000, 1_000_000) or bool(HANDLE_OPTS)},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99))},
         "fwd_cells_per_s": N / (fwd_ms / 1e3),
         "fwd_ms": fwd_ms,
@@ -563,8 +564,13 @@ def main():
     ap.add_argument("--res", type=int, default=256)
     ap.add_argument("--points", type=int, default=200_000)
     ap.add_argument("--queries", type=int, default=1_000_000)
+    # solver kernels inside graphs with device-side loops cannot be profiled
+    # one by one: run the solves as plain launch sequences (profiler only)
+    ap.add_argument("--no-graphs", action="store_true")
     args = ap.parse_args()
     globals().update(RES=args.res, NPTS=args.points, NQ=args.queries)
+    if args.no_graphs:
+        HANDLE_OPTS["use_graphs"] = 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

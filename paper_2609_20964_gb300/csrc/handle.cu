@@ -75,7 +75,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   if (cap < 4096) cap = 4096;
   L.cap = cap;
   L.off_tris = take(c, sizeof(Tri) * (size_t)cap);
-  L.off_tris_s = take(c, sizeof(float4) * 4 * (size_t)cap);
+  L.off_tris_s = take(c, sizeof(float4) * kTriRec * (size_t)cap);
   L.off_pyr = take(c, 32 * pyramid_nodes(nb));
   L.off_pyr_sums = take(c, 32 * pyramid_aux_nodes(nb));
   L.off_pyr_rth = take(c, 8 * pyramid_aux_nodes(nb));

@@ -425,7 +425,7 @@ __global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const int* __rest
     float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
     for (int64_t q = s0; q < s1; ++q) {
       const Tri tr = tris[q];
-      write_search_record(tr, tris_s + 4 * q);
+      write_search_record(tr, tris_s + kTriRec * q);
       const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
       cs.x += a.x + b.x + c.x;
       cs.y += a.y + b.y + c.y;
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
         c_tests += 32ull * (unsigned long long)(s1 > s0 ? s1 - s0 : 0);
       }
       for (int64_t t = s0; t < s1; ++t) {
-        const float d2 = tri_dist2_rec(p, tris_s + 4 * t);
+        const float d2 = tri_dist2_rec(p, tris_s + kTriRec * t);
         if (d2 < cut && d2 < cd[NC - 1]) {
           cd[NC - 1] = d2;
           ct[NC - 1] = (int)t;

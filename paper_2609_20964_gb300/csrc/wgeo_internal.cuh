@@ -16,6 +16,7 @@ namespace wgeo {
 constexpr int kSplatTile = 8;        // output tile edge of the fused splat + divergence
 constexpr int kBrick = 4;            // marching-cubes cubes per brick edge (SDF leaf)
 constexpr int kMaxTriPerCube = 5;
+constexpr int kTriRec = 4;           // float4 per triangle search record
 constexpr int kPartials = 2048;      // per-block partial slots of the deterministic reductions
 constexpr int kMaxLevels = 12;
 constexpr double kFixScale = 68719476736.0;      // 2^36: fixed-point scale of the splat sums
@@ -287,8 +288,8 @@ struct wgeo_handle {
   int* brick_off = nullptr;      // nbricks + 1
   int* leaf_off = nullptr;       // 8 * nbricks + 1: triangle offset of each 2^3 sub-brick
   wgeo::Tri* tris = nullptr;
-  float4* tris_s = nullptr;        // per triangle: search record (a, |ab|^2), (ab, ab.ac), (ac, |ac|^2),
-                                   // (1/|ab|^2, 1/|ac|^2, 1/|bc|^2, 1/|ab x ac|^2)
+  float4* tris_s = nullptr;      // per triangle: search record (a, |ab|^2), (ab, ab.ac), (ac, |ac|^2),
+                                 // (1/|ab|^2, 1/|ac|^2, 1/|bc|^2, 1/|ab x ac|^2)
   float4* pyramid = nullptr;     // 2 float4 per node (puck: centre + radius, axis + half-thickness)
   float4* pyr_sums = nullptr;    // levels >= 1: vertex sum + count, area-normal sum (puck construction)
   unsigned* pyr_rth = nullptr;   // levels >= 1: radius, half-thickness as float bits (atomic maxima)
