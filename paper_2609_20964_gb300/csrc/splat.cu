@@ -84,16 +84,46 @@ __global__ void scatter_points_kernel(const float* __restrict__ nrm, int64_t n,
 
 constexpr int kR = kSplatTile + 2;  // V region edge: tile plus one halo cell per side
 
+// The fixed-point value rint(q) of a float q with |q| <= 2^36 as int64, from
+// two int32 conversions: qh = trunc(q / 2^16) and ql = q - qh 2^16 are exact
+// (|ql| < 2^16; for |q| >= 2^16, q and qh 2^16 are within a factor 2), and
+// rint(q) = qh 2^16 + rint(ql) because qh 2^16 is an even integer.  Equal to
+// __float2ll_rn(q), without the 64-bit conversion.
+__device__ __forceinline__ long long fix_round(float q) {
+  const float qh = truncf(q * 0x1p-16f);
+  const float ql = fmaf(-qh, 0x1p16f, q);
+  return (long long)__float2int_rz(qh) * 65536ll + (long long)__float2int_rn(ql);
+}
+
 // One CTA per 8^3 output tile, one thread per output cell.
 __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict__ srec,
                                                         const int* __restrict__ tile_off, int res,
                                                         int ntile, float* __restrict__ b,
                                                         double* __restrict__ partials) {
   __shared__ long long V[kR * kR * kR * 3];
-  __shared__ double red[32];
+  __shared__ double red[32];   // per-warp sums (16 warps x 2)
   const int tile = blockIdx.x;
   const int tx = tile % ntile, ty = (tile / ntile) % ntile, tz = tile / (ntile * ntile);
   const int T0[3] = {tx * kSplatTile, ty * kSplatTile, tz * kSplatTile};
+  // no point in the 27 neighbouring tiles: V = 0 and b = 0 on this tile
+  bool any = false;
+  for (int nt = 0; nt < 27 && !any; ++nt) {
+    const int ux = tx + nt % 3 - 1, uy = ty + (nt / 3) % 3 - 1, uz = tz + nt / 9 - 1;
+    if (ux < 0 || uy < 0 || uz < 0 || ux >= ntile || uy >= ntile || uz >= ntile) continue;
+    const int t = (uz * ntile + uy) * ntile + ux;
+    any = tile_off[t + 1] > tile_off[t];
+  }
+  if (!any) {
+    const int lx = threadIdx.x % kSplatTile, ly = (threadIdx.x / kSplatTile) % kSplatTile,
+              lz = threadIdx.x / (kSplatTile * kSplatTile);
+    const int px = T0[0] + lx, py = T0[1] + ly, pz = T0[2] + lz;
+    if (px < res && py < res && pz < res) b[((int64_t)pz * res + py) * res + px] = 0.f;
+    if (threadIdx.x == 0) {
+      partials[2 * (int64_t)tile] = 0.0;
+      partials[2 * (int64_t)tile + 1] = 0.0;
+    }
+    return;
+  }
   for (int k = threadIdx.x; k < kR * kR * kR * 3; k += blockDim.x) V[k] = 0;
   __syncthreads();
 
@@ -154,7 +184,7 @@ __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict
             long long* v = &V[((lz * kR + ly) * kR + lx) * 3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              const long long q = __float2ll_rn(alpha * nn[a] * (float)kFixScale);
+              const long long q = fix_round(alpha * nn[a] * (float)kFixScale);
               if (q) atomicAdd((unsigned long long*)&v[a], (unsigned long long)q);
             }
           }
@@ -165,7 +195,7 @@ __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict
   const int lx = threadIdx.x % kSplatTile, ly = (threadIdx.x / kSplatTile) % kSplatTile,
             lz = threadIdx.x / (kSplatTile * kSplatTile);
   const int p[3] = {T0[0] + lx, T0[1] + ly, T0[2] + lz};
-  double bv = 0.0;
+  float bv = 0.f;
   if (p[0] < res && p[1] < res && p[2] < res) {
     const int l = ((lz + 1) * kR + (ly + 1)) * kR + (lx + 1);
     const int strides[3] = {1, kR, kR * kR};
@@ -175,13 +205,29 @@ __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict
       if (p[a] + 1 < res) acc += V[l * 3 + a] + V[(l + strides[a]) * 3 + a];
       if (p[a] - 1 >= 0) acc -= V[(l - strides[a]) * 3 + a] + V[l * 3 + a];
     }
-    const float bf = (float)((double)acc * kFixInv2);
+    // acc * 2^-37 rounded once to float (the int64 -> float conversion rounds,
+    // the power-of-two scale is exact)
+    const float bf = __ll2float_rn(acc) * (float)kFixInv2;
     b[((int64_t)p[2] * res + p[1]) * res + p[0]] = bf;
-    bv = (double)bf;
+    bv = bf;
   }
-  const double s1 = block_sum<512>(bv, red);
-  const double s2 = block_sum<512>(bv * bv, red);
+  // sums of b and b^2: float within a warp, FP64 across the warps (fixed order)
+  float w1 = bv, w2 = bv * bv;
+  for (int o = 16; o > 0; o >>= 1) {
+    w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+    w2 += __shfl_xor_sync(0xffffffffu, w2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[2 * (threadIdx.x >> 5)] = (double)w1;
+    red[2 * (threadIdx.x >> 5) + 1] = (double)w2;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int q = 0; q < 16; ++q) {
+      s1 += red[2 * q];
+      s2 += red[2 * q + 1];
+    }
     partials[2 * (int64_t)tile] = s1;
     partials[2 * (int64_t)tile + 1] = s2;
   }

@@ -857,21 +857,39 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
 // Float-float decision between the float32 near-tie candidates of a node:
 // distances from the node position rounded once from double, the smaller
 // wins; equal distances (a shared edge or vertex: the same closest point)
-// take the smaller triangle index.
+// take the smaller triangle index.  The node coordinates come from per-axis
+// float-float tables built once per block, and chi >= c (c double) is tested
+// as chi >= the smallest float not below c, so no node needs FP64.
+constexpr int kMaxTieRes = 800;
+
 __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, const DevState* __restrict__ st,
                                const Tri* __restrict__ tris, const int* __restrict__ tie_a,
                                const int* __restrict__ tie_b, TieSlots tie_cd, float* __restrict__ phi,
                                float* __restrict__ sdf_out, int* __restrict__ ctri) {
+  __shared__ float2 s_ax[3][kMaxTieRes];
   const int n = g.res;
-  const int64_t N = (int64_t)n * n * n;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N; o += (int64_t)gridDim.x * blockDim.x) {
+  for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
+    const int a = t / n, i = t % n;
+    const double v = g.lo[a] + (i + 0.5) * g.h;
+    const float hi = (float)v;
+    s_ax[a][i] = make_float2(hi, (float)(v - (double)hi));
+  }
+  __syncthreads();
+  const double cd = st->c;
+  float cf = (float)cd;
+  if ((double)cf < cd) cf = nextafterf(cf, INFINITY);
+  const unsigned un = (unsigned)n;
+  const unsigned N = un * un * un;
+  const int xi = st->fwd.xidx ^ 1;
+  for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < N; o += gridDim.x * blockDim.x) {
     const int t1 = tie_b[o];
     if (t1 < 0) continue;
     const int t0 = tie_a[o];
-    const int2 t23 = tie_cd.p[st->fwd.xidx ^ 1][o];
-    const int i = (int)(o % n), j = (int)((o / n) % n), k = (int)(o / ((int64_t)n * n));
-    const Vec3<Ff> pf = {ff_from_double(g.lo[0] + (i + 0.5) * g.h), ff_from_double(g.lo[1] + (j + 0.5) * g.h),
-                         ff_from_double(g.lo[2] + (k + 0.5) * g.h)};
+    const int2 t23 = tie_cd.p[xi][o];
+    const unsigned row = o / un;
+    const int i = (int)(o - row * un), j = (int)(row % un), k = (int)(row / un);
+    const float2 px = s_ax[0][i], py = s_ax[1][j], pz = s_ax[2][k];
+    const Vec3<Ff> pf = {Ff(px.x, px.y), Ff(py.x, py.y), Ff(pz.x, pz.y)};
     Ff bd(INFINITY);
     int bi = -1;
     const int cand[kCand] = {t0, t1, t23.x, t23.y};
@@ -888,7 +906,7 @@ __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, cons
         bi = cand[q];
       }
     }
-    const float sgn = ((double)chi[o] >= st->c) ? 1.f : -1.f;
+    const float sgn = (chi[o] >= cf) ? 1.f : -1.f;
     const float val = sgn * sqrtf(__fadd_rn(bd.hi, bd.lo));
     phi[o] = val;
     if (sdf_out) sdf_out[o] = val;
