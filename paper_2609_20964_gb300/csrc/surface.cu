@@ -617,6 +617,7 @@ constexpr int kStack = 96;         // per-warp traversal stack
 constexpr float kTieRel = 4e-7f;
 constexpr float kTieAbs = 1.5e-7f;
 constexpr int kCand = 4;           // smallest float32 distances kept per node
+constexpr int kSdfCoarse = 2;      // stride of the coarsest (unseeded) search pass
 
 struct TieSlots {
   int2* p[2];   // the two float-float iterate buffers; the one not current is free
@@ -696,6 +697,14 @@ __device__ __forceinline__ unsigned pack_node(int lev, int x, int y, int z) {
 // sdf_tie_kernel re-decides it in float-float.  Without TIES (no closest
 // triangle is kept) the search keeps the float32 minimum alone, which is
 // within the same rounding of the exact distance.
+//
+// Coarse to fine passes over nested lattices: pass `stride` S handles the
+// nodes whose coordinates are all multiples of S but not all multiples of 2S
+// (the coarsest pass, S = kSdfCoarse, takes all its lattice's nodes and
+// starts from nothing).  A finer pass starts from the closest triangles of
+// the up to 8 nodes of the 2S lattice around its node (seed_ids, written by
+// every pass for its nodes): real triangle distances, so the cut is an upper
+// bound from the start and the search mostly has to certify.
 template <bool COUNT, bool TIES>
 __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __restrict__ chi, SurfParams g,
                                                           DevState* __restrict__ st,
@@ -704,7 +713,8 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
                                                           const float4* __restrict__ pyr, PyrInfo pi,
                                                           float* __restrict__ phi, float* __restrict__ sdf_out,
                                                           int* __restrict__ ctri, int* __restrict__ tie_a,
-                                                          int* __restrict__ tie_b, TieSlots tie_cd) {
+                                                          int* __restrict__ tie_b, TieSlots tie_cd,
+                                                          int* __restrict__ seed_ids, int stride) {
   __shared__ unsigned int s_node[kWarps][kStack];
   __shared__ long long s_off[12];
   __shared__ int s_dim[12];
@@ -715,13 +725,17 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
   __syncthreads();
   const int n = g.res;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // CTA covers 8 x 8 x 2 nodes: warp w -> (4 (w & 1), 4 (w >> 1)) in x, y
-  const int ntx = (n + 7) / 8, nty = (n + 7) / 8;
+  // CTA covers 8 x 8 x 2 nodes of this pass's lattice: warp w -> (4 (w & 1),
+  // 4 (w >> 1)) in x, y
+  const int S = stride;
+  const bool seeded = S < kSdfCoarse;
+  const int nl = (n + S - 1) / S;
+  const int ntx = (nl + 7) / 8, nty = (nl + 7) / 8;
   const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
-  const int i = bx * 8 + 4 * (w & 1) + (lane & 3);
-  const int j = by * 8 + 4 * (w >> 1) + ((lane >> 2) & 3);
-  const int k = bz * 2 + (lane >> 4);
-  const bool valid = (i < n) && (j < n) && (k < n);
+  const int i = S * (bx * 8 + 4 * (w & 1) + (lane & 3));
+  const int j = S * (by * 8 + 4 * (w >> 1) + ((lane >> 2) & 3));
+  const int k = S * (bz * 2 + (lane >> 4));
+  const bool valid = (i < n) && (j < n) && (k < n) && (!seeded || ((i | j | k) & S));
   const int ic = min(i, n - 1), jc = min(j, n - 1), kc = min(k, n - 1);
   const float3 p = make_float3((float)(g.lo[0] + (ic + 0.5) * g.h), (float)(g.lo[1] + (jc + 0.5) * g.h),
                                (float)(g.lo[2] + (kc + 0.5) * g.h));
@@ -738,7 +752,45 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
     cd[q] = INFINITY;
     ct[q] = -1;
   }
-  float cut = INFINITY;
+  float cut = valid ? INFINITY : -INFINITY;   // a lane without a node never asks for a subtree
+  // candidate list insertion (sorted, duplicates of a listed triangle ignored)
+  auto offer = [&](float d2, int t) {
+    if (!(d2 < cut && d2 < cd[NC - 1])) return;
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if (ct[q] == t) return;
+    cd[NC - 1] = d2;
+    ct[NC - 1] = t;
+#pragma unroll
+    for (int q = NC - 1; q > 0; --q) {
+      if (cd[q] < cd[q - 1]) {
+        const float tf = cd[q];
+        cd[q] = cd[q - 1];
+        cd[q - 1] = tf;
+        const int ti = ct[q];
+        ct[q] = ct[q - 1];
+        ct[q - 1] = ti;
+      }
+    }
+    if (TIES) {
+      const float r = sqrtf(cd[0]) * (1.f + kTieRel) + mabs;
+      cut = r * r;
+    } else {
+      cut = cd[0];
+    }
+  };
+  if (seeded && valid) {
+    // seeds: the closest triangles of the 2S-lattice nodes around this node
+    const int S2 = 2 * S;
+    const int i0 = i & ~(S2 - 1), j0 = j & ~(S2 - 1), k0 = k & ~(S2 - 1);
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const int ii = i0 + S2 * (q & 1), jj = j0 + S2 * ((q >> 1) & 1), kk = k0 + S2 * (q >> 2);
+      if (ii >= n || jj >= n || kk >= n) continue;
+      const int t = seed_ids[lin3(ii, jj, kk, n)];
+      if (t >= 0) offer(tri_dist2_rec(p, tris_s + kTriRec * (int64_t)t), t);
+    }
+  }
   unsigned int* stk = s_node[w];
   int sp = 0;
   const int top = pi.nlev - 1;
@@ -767,28 +819,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
         c_tests += 32ull * (unsigned long long)(s1 > s0 ? s1 - s0 : 0);
       }
       for (int64_t t = s0; t < s1; ++t) {
-        const float d2 = tri_dist2_rec(p, tris_s + kTriRec * t);
-        if (d2 < cut && d2 < cd[NC - 1]) {
-          cd[NC - 1] = d2;
-          ct[NC - 1] = (int)t;
-#pragma unroll
-          for (int q = NC - 1; q > 0; --q) {
-            if (cd[q] < cd[q - 1]) {
-              const float tf = cd[q];
-              cd[q] = cd[q - 1];
-              cd[q - 1] = tf;
-              const int ti = ct[q];
-              ct[q] = ct[q - 1];
-              ct[q - 1] = ti;
-            }
-          }
-          if (TIES) {
-            const float r = sqrtf(cd[0]) * (1.f + kTieRel) + mabs;
-            cut = r * r;
-          } else {
-            cut = cd[0];
-          }
-        }
+        offer(tri_dist2_rec(p, tris_s + kTriRec * t), (int)t);
       }
       continue;
     }
@@ -844,6 +875,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
   phi[o] = sgn * val;
   if (sdf_out) sdf_out[o] = sgn * val;
   if (ctri) ctri[o] = bt;
+  if (S > 1) seed_ids[o] = bt;
   if (TIES) {
     if (tie) {
       tie_a[o] = bt;
@@ -1036,7 +1068,6 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   }
   stage_end(h, kStMC, slot, s);
   slot = stage_begin(h, kStSDF, s);
-  const int ntx = (res + 7) / 8, ntz = (res + 1) / 2;
   // the solver's residual / correction scratch is idle until the next solve:
   // it holds the near-tie candidates between the two kernels
   int* tie_a = reinterpret_cast<int*>(h->r32);
@@ -1047,34 +1078,40 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   tie_cd.p[0] = reinterpret_cast<int2*>(h->chiff[0]);
   tie_cd.p[1] = reinterpret_cast<int2*>(h->chiff[1]);
   int* ctri = h->opt.keep_for_backward ? h->ctri : nullptr;
-  const int nblk = ntx * ntx * ntz;
-  if (ctri) {
-    if (h->opt.stage_timing == 2)
-      sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off, h->mesh_cap,
-                                                          h->pyramid, pi, h->phi, sdf_out, ctri, tie_a, tie_b, tie_cd);
-    else
-      sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off, h->mesh_cap,
-                                                           h->pyramid, pi, h->phi, sdf_out, ctri, tie_a, tie_b,
-                                                           tie_cd);
+  // closest triangles of the coarser passes, read by the finer ones as seeds
+  int* seed_ids = ctri ? ctri : tie_a;
+  for (int stride = kSdfCoarse; stride >= 1; stride /= 2) {
+    const int nl = (res + stride - 1) / stride;
+    const int nblk = ((nl + 7) / 8) * ((nl + 7) / 8) * ((nl + 1) / 2);
+    if (ctri) {
+      if (h->opt.stage_timing == 2)
+        sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
+                                                            h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, ctri,
+                                                            tie_a, tie_b, tie_cd, seed_ids, stride);
+      else
+        sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
+                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, ctri,
+                                                             tie_a, tie_b, tie_cd, seed_ids, stride);
+    } else {
+      if (h->opt.stage_timing == 2)
+        sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
+                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
+                                                             nullptr, nullptr, tie_cd, seed_ids, stride);
+      else
+        sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
+                                                              h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
+                                                              nullptr, nullptr, tie_cd, seed_ids, stride);
+    }
     WGEO_LAUNCH_CHECK();
-    stage_end(h, kStSDF, slot, s);
+  }
+  stage_end(h, kStSDF, slot, s);
+  if (ctri) {
     slot = stage_begin(h, kStSDFTie, s);
     const int64_t N = (int64_t)res * res * res;
     sdf_tie_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(h->chi32, g, h->dstate, h->tris, tie_a, tie_b,
                                                                  tie_cd, h->phi, sdf_out, ctri);
     WGEO_LAUNCH_CHECK();
     stage_end(h, kStSDFTie, slot, s);
-  } else {
-    if (h->opt.stage_timing == 2)
-      sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off, h->mesh_cap,
-                                                           h->pyramid, pi, h->phi, sdf_out, nullptr, nullptr, nullptr,
-                                                           tie_cd);
-    else
-      sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
-                                                            h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
-                                                            nullptr, nullptr, tie_cd);
-    WGEO_LAUNCH_CHECK();
-    stage_end(h, kStSDF, slot, s);
   }
   if (nrm_out) {
     slot = stage_begin(h, kStNormals, s);
