@@ -135,11 +135,9 @@ def test_query_and_backward_parity(W, name):
     ang = _angle_deg(nq.cpu().numpy()[good], rn[good])
     good = np.all(OI.gather(_smooth_nodes(ref), corners), axis=1)
     assert ang.max() <= ANGLE_TOL_DEG
-    # backward through the query loss (phi and normals at q) to points, normals and q;
-    # normal seeds only where the normal is defined (off the medial axis, where
-    # dn/dphi ~ 1/|grad phi| and the closest triangle is a near-tie)
-    # seeds only where phi is differentiable (unique closest point): on the medial
-    # axis the closest triangle is a near-tie that FP32 and FP64 may break differently
+    # backward through the query loss (phi and normals at q) to points, normals and
+    # q, seeded only at queries whose stencils stay off the medial axis: there phi
+    # is not differentiable (two distinct closest points) and dn/dphi ~ 1/|grad phi|
     gn[~good] = 0.0
     gs[~good] = 0.0
     dp, dn, dq = rec.backward(q=Q, d_sdf_q=_t(gs), d_nrm_q=_t(gn), want_dq=True)
@@ -210,6 +208,38 @@ def test_deterministic_and_handle_reuse(W):
     s2, n2b = rec.reconstruct(_t(p), _t(n), BBOX, res)
     assert torch.equal(s1, s2) and torch.equal(n1, n2b)
     rec.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_graph_loop_equals_fixed_sequence(W, precision):
+    """The solve recorded as a graph with a device-side loop and the same
+    kernels enqueued as a fixed gated sequence give identical results,
+    forward and backward."""
+    from paper_2609_20964_gb300 import PREC_FP32, PREC_MIXED
+    p, n, res = CASES["shbody44"]
+    prec = PREC_FP32 if precision == "fp32" else PREC_MIXED
+    q = _t(synth.uniform_queries(500, seed=7))
+    g = _t(np.random.default_rng(8).standard_normal(500).astype(np.float32))
+    out = []
+    for use_graphs in (1, 0):
+        rec = W(res, len(p), precision=prec, use_graphs=use_graphs, max_vcycles=60)
+        sdf, nrm = rec.reconstruct(_t(p), _t(n), BBOX, res)
+        sdf, nrm = sdf.clone(), nrm.clone()
+        info = rec.info()
+        dp = dn = None
+        if precision == "mixed":
+            dp, dn, _ = rec.backward(q=q, d_sdf_q=g)
+            dp, dn = dp.clone(), dn.clone()
+            info = rec.info()
+        out.append((sdf, nrm, dp, dn, info["solver_steps"], info["backward_steps"], info["residual_rel"]))
+        rec.close()
+    a, b = out
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    if precision == "mixed":
+        # the backward scatters with FP64 atomics: equal up to their rounding order
+        for x, y in ((a[2], b[2]), (a[3], b[3])):
+            assert float((x - y).norm() / y.norm()) <= 1e-6
+    assert a[4:] == b[4:]
 
 
 def test_fp32_plain_mode_and_mixed_agree(W):
