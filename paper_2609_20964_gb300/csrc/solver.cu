@@ -133,12 +133,12 @@ __global__ void update_residual_kernel(PairFF xp, const float* __restrict__ e, c
 }
 
 __global__ void residual32_kernel(const float* __restrict__ x, const float* __restrict__ b,
-                                  const double* __restrict__ shift, int n,
+                                  const float* __restrict__ shift, int n,
                                   double* __restrict__ partials, const int* __restrict__ gate) {
   if (*gate) return;
   __shared__ float red[32];
   const int64_t N = (int64_t)n * n * n;
-  const float sh = (float)*shift;
+  const float sh = *shift;
   float s1 = 0.f, s2 = 0.f;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -218,6 +218,7 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks
     const double mean = s1 / (double)N;
     const double rn = sqrt(fmax(s2 - s1 * mean, 0.0));
     ss->rmean = mean;
+    ss->rmean32 = (float)mean;
     const double bn = ss->bnorm;
     const double rel = (bn > 0.0) ? rn / bn : 0.0;
     ss->rel = rel;
@@ -236,6 +237,7 @@ __global__ void solve_begin_kernel(SolveState* ss, int cold, int max_steps, int 
   ss->iter = 0;
   ss->rel = 0.0;
   ss->rmean = 0.0;
+  ss->rmean32 = 0.f;
   ss->cold = cold;
   ss->max_steps = max_steps;
   ss->body_launches = body_launches;
@@ -268,12 +270,12 @@ __device__ __forceinline__ float prolong_at(const float* __restrict__ xc, int nc
 // from a zero start), and the pair's other cell is written 0.
 template <bool ZERO>
 __global__ void __launch_bounds__(kSX * kSY) rb_half_kernel(float* __restrict__ x, const float* __restrict__ b,
-                                                            const double* __restrict__ shift, int n, int color,
+                                                            const float* __restrict__ shift, int n, int color,
                                                             const int* __restrict__ gate) {
   if (*gate) return;
   const int ih = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y, k = blockIdx.z;
   if (2 * ih >= n || j >= n) return;
-  const float sh = shift ? (float)*shift : 0.f;
+  const float sh = shift ? *shift : 0.f;
   const int odd = (j + k + color) & 1;
   const int i = 2 * ih + odd;
   const int64_t nn = (int64_t)n * n;
@@ -295,14 +297,14 @@ __global__ void __launch_bounds__(kSX * kSY) rb_half_kernel(float* __restrict__ 
 // bc = 1/2 * sum over the 8 children of the residual b - shift - L x.
 __global__ void __launch_bounds__(kSX * kSY) restrict_kernel(const float* __restrict__ x,
                                                              const float* __restrict__ b,
-                                                             const double* __restrict__ shift, int n,
+                                                             const float* __restrict__ shift, int n,
                                                              float* __restrict__ bc,
                                                              const int* __restrict__ gate) {
   if (*gate) return;
   const int nc = n >> 1;
   const int I = blockIdx.x * kSX + threadIdx.x, J = blockIdx.y * kSY + threadIdx.y, K = blockIdx.z;
   if (I >= nc || J >= nc) return;
-  const float sh = shift ? (float)*shift : 0.f;
+  const float sh = shift ? *shift : 0.f;
   const int64_t nn = (int64_t)n * n;
   float acc = 0.f;
 #pragma unroll
@@ -383,7 +385,7 @@ __device__ void small_rbgs(float* x, const float* b, int n, int color) {
 }
 
 __global__ void __launch_bounds__(1024) small_vcycle_kernel(float* __restrict__ xg, const float* __restrict__ bg,
-                                                            const double* __restrict__ shift, int n0,
+                                                            const float* __restrict__ shift, int n0,
                                                             const int* __restrict__ gate) {
   if (*gate) return;
   __shared__ float xs[kSmallCap];
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(1024) small_vcycle_kernel(float* __restrict__ 
     }
   }
   const int N0 = n0 * n0 * n0;
-  const float sh = shift ? (float)*shift : 0.f;
+  const float sh = shift ? *shift : 0.f;
   double s = 0.0;
   for (int t = threadIdx.x; t < N0; t += blockDim.x) {
     const float v = bg[t] - sh;
@@ -512,18 +514,19 @@ __global__ void rhs_stats_finalize_kernel(const double* __restrict__ partials, i
   if (threadIdx.x == 0) {
     const double mean = s1 / (double)N;
     ss->bmean = mean;
+    ss->bmean32 = (float)mean;
     ss->bnorm = sqrt(fmax(s2 - s1 * mean, 0.0));
   }
 }
 
 // One V-cycle on level l, in place.  x0: level-0 iterate; b0, shift0:
 // level-0 right-hand side.  zero0: level-0 x starts at zero.
-int vcycle(wgeo_handle* h, int l, float* x0, const float* b0, const double* shift0, bool zero0,
+int vcycle(wgeo_handle* h, int l, float* x0, const float* b0, const float* shift0, bool zero0,
            const int* gate, cudaStream_t s) {
   const int n = h->levels[l].n;
   float* x = (l == 0) ? x0 : h->levels[l].x;
   const float* b = (l == 0) ? b0 : h->levels[l].b;
-  const double* shift = (l == 0) ? shift0 : nullptr;
+  const float* shift = (l == 0) ? shift0 : nullptr;
   if (n <= kSmallN || l == h->nlevels - 1) {
     small_vcycle_kernel<<<1, 1024, 0, s>>>(x, b, shift, n, gate);
     WGEO_LAUNCH_CHECK();
@@ -572,10 +575,10 @@ int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGrap
   const int rb = grid_blocks(N, kThreads, kPartials);
   if (fp32) {
     if (part == 1) {
-      int rc = vcycle(h, 0, h->chi32, h->b32, &ss->bmean, false, gate, s);
+      int rc = vcycle(h, 0, h->chi32, h->b32, &ss->bmean32, false, gate, s);
       if (rc) return rc;
     }
-    residual32_kernel<<<rb, kThreads, 0, s>>>(h->chi32, h->b32, &ss->bmean, res, h->partials, gate);
+    residual32_kernel<<<rb, kThreads, 0, s>>>(h->chi32, h->b32, &ss->bmean32, res, h->partials, gate);
     WGEO_LAUNCH_CHECK();
     finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, h->opt.tol_rel, step, 1, 0, hc, cond);
     WGEO_LAUNCH_CHECK();
@@ -589,7 +592,7 @@ int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGrap
   if (part == 1) {
     // correction: V-cycles on L e = r - mean(r)
     for (int v = 0; v < h->opt.vcycles_per_refine; ++v) {
-      int rc = vcycle(h, 0, h->e32, h->r32, &ss->rmean, v == 0, gate, s);
+      int rc = vcycle(h, 0, h->e32, h->r32, &ss->rmean32, v == 0, gate, s);
       if (rc) return rc;
     }
   }

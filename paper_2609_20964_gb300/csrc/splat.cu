@@ -247,6 +247,7 @@ __global__ void b_stats_kernel(const double* __restrict__ partials, int ntiles, 
   if (threadIdx.x == 0) {
     const double mean = s1 / (double)N;
     st->fwd.bmean = mean;
+    st->fwd.bmean32 = (float)mean;
     st->fwd.bnorm = sqrt(fmax(s2 - s1 * mean, 0.0));
   }
 }

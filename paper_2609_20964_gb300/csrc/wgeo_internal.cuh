@@ -33,6 +33,8 @@ struct SolveState {
   double bnorm;      // || b - mean(b) ||
   double bmean;
   double rmean;      // mean of the last residual (projected out of the correction RHS)
+  float bmean32;     // the two means rounded to float once, for the FP32 kernels
+  float rmean32;
   double rel;        // last || r || / || b ||
 };
 
