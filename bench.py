@@ -323,7 +323,7 @@ def run_ours(args):
                        "leaf_visits": info_t["sdf_leaf_visits"],
                        "tri_tests": info_t["sdf_tri_tests"],
                        "tri_tests_per_node": info_t["sdf_tri_tests"] / N,
-                       "float64_tie_nodes": info_t["sdf_tie_nodes"]},
+                       "near_tie_nodes": info_t["sdf_tie_nodes"]},
         "stage_ms": stages,
         "e2e": {"value": N / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -630,15 +630,13 @@ struct TieSlots {
 // the divisions replaced by the stored reciprocals), and the residual
 // p - y = ap - v ab - w ac is formed relative to a, so its rounding scales
 // with the distance and the edge length rather than with the coordinates.
-__device__ __forceinline__ float tri_dist2_rec(const float3 p, const float4* __restrict__ rec) {
-  const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
-  const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+// Closest-point weights (v, w) of y = a + v ab + w ac from d1 = ab.ap,
+// d2 = ac.ap and the record's Gram entries and reciprocals.
+__device__ __forceinline__ void rec_weights(const float3 ap, float d1, float d2, const float4 r0, const float4 r1,
+                                            const float4 r2, const float4 r3, float& v, float& w) {
   const float e00 = r0.w, e01 = r1.w, e11 = r2.w;
-  const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;   // ab . ap
-  const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;   // ac . ap
   const float d3 = d1 - e00, d4 = d2 - e01;                  // ab . bp, ac . bp
   const float d5 = d1 - e01, d6 = d2 - e11;                  // ab . cp, ac . cp
-  float v, w;
   if (d1 <= 0.f && d2 <= 0.f) {
     v = 0.f; w = 0.f;                                          // vertex a
   } else if (d3 >= 0.f && d4 <= d3) {
@@ -669,9 +667,44 @@ __device__ __forceinline__ float tri_dist2_rec(const float3 p, const float4* __r
       }
     }
   }
+}
+
+__device__ __forceinline__ float tri_dist2_rec(const float3 p, const float4* __restrict__ rec) {
+  const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
+  const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+  const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;   // ab . ap
+  const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;   // ac . ap
+  float v, w;
+  rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
   const float rx = ap.x - v * r1.x - w * r2.x;
   const float ry = ap.y - v * r1.y - w * r2.y;
   const float rz = ap.z - v * r1.z - w * r2.z;
+  return rx * rx + ry * ry + rz * rz;
+}
+
+// The same distance in float-float for the near-tie decisions.  Only ap and
+// the residual need the extra precision: a region chosen wrongly near a
+// region boundary, and rounding of the weights (v, w), change |p - y| only to
+// second order (the residual is normal to the directions they move y in), so
+// the region and the weights come from the float32 path; ap is formed in
+// float-float from the float-float node position, v ab + w ac from exact
+// products, and |p - y|^2 in float-float.
+__device__ __forceinline__ Ff two_prod_ff(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return Ff(p, __fmaf_rn(a, b, -p));
+}
+
+__device__ __forceinline__ Ff tri_dist2_rec_ff(const Vec3<Ff> p, const float4* __restrict__ rec) {
+  const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
+  const Ff apx = p.x - Ff(r0.x), apy = p.y - Ff(r0.y), apz = p.z - Ff(r0.z);
+  const float3 ap = make_float3(apx.hi, apy.hi, apz.hi);
+  const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
+  const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
+  float v, w;
+  rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
+  const Ff rx = apx - (two_prod_ff(v, r1.x) + two_prod_ff(w, r2.x));
+  const Ff ry = apy - (two_prod_ff(v, r1.y) + two_prod_ff(w, r2.y));
+  const Ff rz = apz - (two_prod_ff(v, r1.z) + two_prod_ff(w, r2.z));
   return rx * rx + ry * ry + rz * rz;
 }
 
@@ -887,15 +920,15 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
 }
 
 // Float-float decision between the float32 near-tie candidates of a node:
-// distances from the node position rounded once from double, the smaller
-// wins; equal distances (a shared edge or vertex: the same closest point)
-// take the smaller triangle index.  The node coordinates come from per-axis
+// distances (tri_dist2_rec_ff) from the node position rounded once from
+// double, the smaller wins; equal distances (a shared edge or vertex: the
+// same closest point) take the smaller triangle index.  The node coordinates come from per-axis
 // float-float tables built once per block, and chi >= c (c double) is tested
 // as chi >= the smallest float not below c, so no node needs FP64.
 constexpr int kMaxTieRes = 800;
 
 __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, const DevState* __restrict__ st,
-                               const Tri* __restrict__ tris, const int* __restrict__ tie_a,
+                               const float4* __restrict__ tris_s, const int* __restrict__ tie_a,
                                const int* __restrict__ tie_b, TieSlots tie_cd, float* __restrict__ phi,
                                float* __restrict__ sdf_out, int* __restrict__ ctri) {
   __shared__ float2 s_ax[3][kMaxTieRes];
@@ -930,9 +963,7 @@ __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, cons
 #pragma unroll 1
     for (int q = 0; q < kCand; ++q) {
       if (cand[q] < 0) continue;
-      const Tri tr = tris[cand[q]];
-      const Ff d2 = tri_closest_t<Ff>(pf, {Ff(tr.a.x), Ff(tr.a.y), Ff(tr.a.z)}, {Ff(tr.b.x), Ff(tr.b.y), Ff(tr.b.z)},
-                                      {Ff(tr.c.x), Ff(tr.c.y), Ff(tr.c.z)}, nullptr, nullptr, nullptr);
+      const Ff d2 = tri_dist2_rec_ff(pf, tris_s + kTriRec * (int64_t)cand[q]);
       if (bi < 0 || d2 < bd || (!(bd < d2) && cand[q] < bi)) {
         bd = d2;
         bi = cand[q];
@@ -1108,7 +1139,7 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   if (ctri) {
     slot = stage_begin(h, kStSDFTie, s);
     const int64_t N = (int64_t)res * res * res;
-    sdf_tie_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(h->chi32, g, h->dstate, h->tris, tie_a, tie_b,
+    sdf_tie_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, tie_a, tie_b,
                                                                  tie_cd, h->phi, sdf_out, ctri);
     WGEO_LAUNCH_CHECK();
     stage_end(h, kStSDFTie, slot, s);
