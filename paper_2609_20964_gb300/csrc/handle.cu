@@ -79,7 +79,11 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.off_pyr = take(c, 32 * pyramid_nodes(nb));
   L.off_pyr_sums = take(c, 32 * pyramid_aux_nodes(nb));
   L.off_pyr_rth = take(c, 8 * pyramid_aux_nodes(nb));
-  L.n_partials = std::max<size_t>(2 * ntiles, std::max<size_t>(4 * kPartials, 81 * 256));
+  // per-block partial pairs: splat tiles, the refinement pass (one block per
+  // 64 x 8 cells of a plane), fixed-size reductions, SH adjoint
+  const size_t resid_blocks = (size_t)div_up(R, 64) * div_up(R, 8) * R;
+  L.n_partials = std::max<size_t>(std::max<size_t>(2 * ntiles, 2 * resid_blocks),
+                                  std::max<size_t>(4 * kPartials, 81 * 256));
   L.off_partials = take(c, 8 * L.n_partials);
   L.n_scan = scan_tmp_size((int)std::max(ntiles, nbricks));
   L.off_scan = take(c, 4 * L.n_scan);

@@ -41,6 +41,7 @@ namespace wgeo {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kSX = 32, kSY = 8;    // 3D-grid blocks: 32 x pairs by 8 rows of one plane
 constexpr int kNu = 2;              // red-black sweeps before and after the coarse correction
 constexpr int kSmallN = 16;         // levels up to 16^3 are solved in one CTA
 
@@ -71,64 +72,125 @@ __device__ __forceinline__ float rhs_hi(const double* b, int64_t t, float& lo) {
 //   x32 = hi(x_new), r32 = b - L x_new (each neighbour difference split
 //   exactly), per-thread sums of r and r^2 in FP32, per-block sums in FP64.
 template <typename TB>
-__global__ void update_residual_kernel(PairFF xp, const float* __restrict__ e, const TB* __restrict__ b,
-                                       int n, float* __restrict__ r32, float* __restrict__ x32,
-                                       double* __restrict__ partials, SolveState* ss) {
+__global__ void __launch_bounds__(kSX * kSY) update_residual_kernel(PairFF xp, const float* __restrict__ e,
+                                                                    const TB* __restrict__ b, int n,
+                                                                    float* __restrict__ r32, float* __restrict__ x32,
+                                                                    double* __restrict__ partials, SolveState* ss) {
   if (ss->done) return;
-  __shared__ double red[32];
+  __shared__ double red[2 * (kSX * kSY / 32)];
   const int cur = ss->xidx;
   const bool cold = ss->cold != 0;
   const float2* __restrict__ xin = xp.buf[cur];
   float2* __restrict__ xout = xp.buf[e ? cur ^ 1 : cur];
-  const int64_t N = (int64_t)n * n * n;
+  // one x pair (i0 = 2 I, i0 + 1) of row j, plane k per thread; vector
+  // accesses need an even n (pairs then start on even cells); an odd n (only
+  // grids up to 15^3) takes scalar accesses and a last pair of one cell
+  const int I = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y, k = blockIdx.z;
+  const int i0 = 2 * I;
+  const bool vec = (n & 1) == 0;
   float s1 = 0.f, s2 = 0.f;
-  (void)N;
-  for (int row = blockIdx.x; row < n * n; row += gridDim.x) {     // rows (j, k), x along threads
-   const int j = row % n, k = row / n;
-   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int64_t t = (int64_t)row * n + i;
-    float2 xc = make_float2(0.f, 0.f), acc = make_float2(0.f, 0.f);
+  if (i0 < n && j < n) {
+    const bool has1 = i0 + 1 < n;
+    const int64_t nn = (int64_t)n * n;
+    const int64_t t0 = (int64_t)k * nn + (int64_t)j * n + i0;
+    auto pair = [&](int64_t q, float2& a, float2& c) {   // x_new at cells q, q + 1
+      if (vec) {
+        const float4 v = *reinterpret_cast<const float4*>(xin + q);
+        a = make_float2(v.x, v.y);
+        c = make_float2(v.z, v.w);
+        if (e) {
+          const float2 ev = *reinterpret_cast<const float2*>(e + q);
+          a = ff_add_f(a, ev.x);
+          c = ff_add_f(c, ev.y);
+        }
+      } else {
+        a = xin[q];
+        if (e) a = ff_add_f(a, e[q]);
+        c = make_float2(0.f, 0.f);
+        if (has1) {
+          c = xin[q + 1];
+          if (e) c = ff_add_f(c, e[q + 1]);
+        }
+      }
+    };
+    auto single = [&](int64_t q) {
+      const float2 v = xin[q];
+      return e ? ff_add_f(v, e[q]) : v;
+    };
+    float2 xc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     if (!cold) {
-      auto val = [&](int64_t q) {
-        const float2 v = xin[q];
-        return e ? ff_add_f(v, e[q]) : v;
-      };
-      xc = val(t);
+      pair(t0, xc[0], xc[1]);
       // L x = sum of (x_q - x_p): each hi difference split exactly by two-sum,
       // the hi parts summed by a two-sum chain (rounding errors carried in
       // `err`), the lo differences (each below ulp(hi)) summed in float
-      float sh = 0.f, err = 0.f, lo = 0.f;
-      auto add = [&](float2 v) {
-        const float2 d = two_sum(v.x, -xc.x);
-        const float2 c = two_sum(sh, d.x);
-        sh = c.x;
-        err = __fadd_rn(err, __fadd_rn(c.y, d.y));
-        lo = __fadd_rn(lo, __fsub_rn(v.y, xc.y));
+      float sh[2] = {0.f, 0.f}, err[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
+      auto add = [&](int c, float2 v) {
+        const float2 d = two_sum(v.x, -xc[c].x);
+        const float2 q = two_sum(sh[c], d.x);
+        sh[c] = q.x;
+        err[c] = __fadd_rn(err[c], __fadd_rn(q.y, d.y));
+        lo[c] = __fadd_rn(lo[c], __fsub_rn(v.y, xc[c].y));
       };
-      if (i > 0) add(val(t - 1));
-      if (i < n - 1) add(val(t + 1));
-      if (j > 0) add(val(t - n));
-      if (j < n - 1) add(val(t + n));
-      if (k > 0) add(val(t - (int64_t)n * n));
-      if (k < n - 1) add(val(t + (int64_t)n * n));
-      acc = two_sum(sh, __fadd_rn(err, lo));
+      if (has1) {
+        add(0, xc[1]);                     // the pair's own cells are x neighbours
+        add(1, xc[0]);
+      }
+      if (i0 > 0) add(0, single(t0 - 1));
+      if (i0 + 2 < n) add(1, single(t0 + 2));
+      float2 a, c;
+      if (j > 0) { pair(t0 - n, a, c); add(0, a); add(1, c); }
+      if (j < n - 1) { pair(t0 + n, a, c); add(0, a); add(1, c); }
+      if (k > 0) { pair(t0 - nn, a, c); add(0, a); add(1, c); }
+      if (k < n - 1) { pair(t0 + nn, a, c); add(0, a); add(1, c); }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) acc[q] = two_sum(sh[q], __fadd_rn(err[q], lo[q]));
     }
-    float blo;
-    const float bhi = rhs_hi(b, t, blo);
-    const float2 r = ff_sub(make_float2(bhi, blo), acc);
-    if (e || cold) xout[t] = xc;
-    x32[t] = xc.x;
-    const float rf = r.x + r.y;
-    r32[t] = rf;
-    s1 += rf;
-    s2 += rf * rf;
-   }
+    float rf[2] = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q == 1 && !has1) break;
+      float blo;
+      const float bhi = rhs_hi(b, t0 + q, blo);
+      const float2 r = ff_sub(make_float2(bhi, blo), acc[q]);
+      rf[q] = r.x + r.y;
+      s1 += rf[q];
+      s2 += rf[q] * rf[q];
+    }
+    if (vec) {
+      if (e || cold) *reinterpret_cast<float4*>(xout + t0) = make_float4(xc[0].x, xc[0].y, xc[1].x, xc[1].y);
+      *reinterpret_cast<float2*>(x32 + t0) = make_float2(xc[0].x, xc[1].x);
+      *reinterpret_cast<float2*>(r32 + t0) = make_float2(rf[0], rf[1]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (q == 1 && !has1) break;
+        if (e || cold) xout[t0 + q] = xc[q];
+        x32[t0 + q] = xc[q].x;
+        r32[t0 + q] = rf[q];
+      }
+    }
   }
-  double d1 = block_sum<kThreads>((double)s1, red);
-  double d2 = block_sum<kThreads>((double)s2, red);
-  if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = d1;
-    partials[2 * blockIdx.x + 1] = d2;
+  // per-block sums of r and r^2: float within a warp, FP64 across the warps
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  const int lane = (threadIdx.y * kSX + threadIdx.x) & 31, wid = (threadIdx.y * kSX + threadIdx.x) >> 5;
+  if (lane == 0) {
+    red[2 * wid] = (double)s1;
+    red[2 * wid + 1] = (double)s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double d1 = 0.0, d2 = 0.0;
+    for (int q = 0; q < kSX * kSY / 32; ++q) {
+      d1 += red[2 * q];
+      d2 += red[2 * q + 1];
+    }
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    partials[2 * blk] = d1;
+    partials[2 * blk + 1] = d2;
   }
 }
 
@@ -251,7 +313,6 @@ __global__ void solve_begin_kernel(SolveState* ss, int cold, int max_steps, int 
 // HBM per half-sweep (neighbour reuse through L1/L2), b and the written half
 // once: about 8 bytes per cell.  Grids are 3D (32 pairs x 8 rows per block,
 // one z plane per blockIdx.z), so no thread divides to find its cell.
-constexpr int kSX = 32, kSY = 8;
 
 __device__ __forceinline__ float prolong_at(const float* __restrict__ xc, int nc, int gx, int gy, int gz) {
   const int I = gx >> 1, J = gy >> 1, K = gz >> 1;
@@ -358,11 +419,13 @@ __global__ void __launch_bounds__(kSX * kSY) prolong_pair_kernel(const float* __
 
 // ---------------------------------------------------------------- small grids
 // A whole V-cycle hierarchy for n <= 16 in one CTA's shared memory: solves
-// L x = b - shift - mean approximately (one V-cycle from zero, 2n + 8
-// red-black sweeps on its coarsest level), writes x.  As the coarse-grid
-// correction of the outer cycle it needs no more: on the 256^3 benchmark the
-// refinement takes the same number of steps as with two cycles and 2n^2 + 16
-// sweeps.
+// L x = b - shift - mean approximately, writes x.  With a hierarchy above a
+// coarsest level of at most 4^3: one V-cycle from zero, 2n + 8 red-black
+// sweeps on the coarsest level; as the coarse-grid correction of the outer
+// cycle it needs no more (on the 256^3 benchmark the refinement takes the
+// same number of steps as with two cycles and 2n^2 + 16 sweeps).  Otherwise
+// (a single level, e.g. an odd grid, or a larger coarsest level): two
+// V-cycles, 2n^2 + 16 sweeps on the coarsest level.
 constexpr int kSmallCap = 4096 + 512 + 64 + 27 + 8;
 constexpr int kSmallCycles = 1;     // V-cycles of the coarse-grid solve
 
@@ -418,7 +481,8 @@ __global__ void __launch_bounds__(1024) small_vcycle_kernel(float* __restrict__ 
   __syncthreads();
   for (int t = threadIdx.x; t < N0; t += blockDim.x) bsm[t] -= meanb;
   __syncthreads();
-  for (int cyc = 0; cyc < kSmallCycles; ++cyc) {
+  const int cycles = L > 1 ? kSmallCycles : 2;
+  for (int cyc = 0; cyc < cycles; ++cyc) {
     // down
     for (int l = 0; l < L - 1; ++l) {
       const int n = ns[l];
@@ -457,7 +521,9 @@ __global__ void __launch_bounds__(1024) small_vcycle_kernel(float* __restrict__ 
       const int n = ns[L - 1];
       float* x = xs + off[L - 1];
       const float* b = bsm + off[L - 1];
-      const int sweeps = 2 * n + 8;
+      // a coarsest level of at most 4^3 below a hierarchy needs only a rough
+      // solve; a larger one (no hierarchy, e.g. an odd grid) is the whole solve
+      const int sweeps = (n <= 4 && L > 1) ? 2 * n + 8 : 2 * n * n + 16;
       for (int sw = 0; sw < sweeps; ++sw) {
         small_rbgs(x, b, n, 0);
         small_rbgs(x, b, n, 1);
@@ -597,12 +663,15 @@ int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGrap
     }
   }
   const float* e = part == 0 ? nullptr : h->e32;
+  const dim3 rg(div_up(div_up(res, 2), kSX), div_up(res, kSY), res);
+  const int nrb = (int)(rg.x * rg.y * rg.z);
   if (mode == 0)
-    update_residual_kernel<float><<<rb, kThreads, 0, s>>>(xp, e, h->b32, res, h->r32, x32, h->partials, ss);
+    update_residual_kernel<float><<<rg, dim3(kSX, kSY), 0, s>>>(xp, e, h->b32, res, h->r32, x32, h->partials, ss);
   else
-    update_residual_kernel<double><<<rb, kThreads, 0, s>>>(xp, e, h->dchi64, res, h->r32, x32, h->partials, ss);
+    update_residual_kernel<double><<<rg, dim3(kSX, kSY), 0, s>>>(xp, e, h->dchi64, res, h->r32, x32, h->partials,
+                                                                 ss);
   WGEO_LAUNCH_CHECK();
-  finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss, h->dstate, tol, step, 0, e ? 1 : 0, hc, cond);
+  finalize_kernel<<<1, 1024, 0, s>>>(h->partials, nrb, N, ss, h->dstate, tol, step, 0, e ? 1 : 0, hc, cond);
   WGEO_LAUNCH_CHECK();
   return WGEO_OK;
 }

@@ -176,6 +176,27 @@ def test_closest_point_parity(W, name):
     rec.close()
 
 
+def test_odd_resolution(W):
+    """An odd grid (15^3: no multigrid level above the one-CTA solve, pairs of
+    cells ending in a single cell) against the oracle, forward and backward."""
+    p, n = synth.sphere_cloud(1200, seed=23)
+    res = 15
+    ref = oracle.reconstruct(p, n, BBOX, res)
+    rec = W(res, len(p))
+    sdf, _ = rec.reconstruct(_t(p), _t(n), BBOX, res)
+    assert rec.info()["status"] == 0
+    assert np.abs(sdf.cpu().numpy().astype(np.float64) - ref.phi).max() <= SDF_TOL
+    rng = np.random.default_rng(4)
+    wg = rng.standard_normal((res, res, res)).astype(np.float32)
+    wg[~_smooth_nodes(ref)] = 0.0
+    dp, dn, _ = rec.backward(d_sdf_grid=_t(wg))
+    odp, odn, _ = OP.backward(ref, d_sdf_grid=wg.astype(np.float64))
+    for got, want in ((dp, odp), (dn, odn)):
+        got = got.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= GRAD_TOL
+    rec.close()
+
+
 def test_grid_seed_backward_parity(W):
     p, n, res = CASES["sphere24"]
     ref = _oracle("sphere24")
