@@ -176,6 +176,21 @@ def test_closest_point_parity(W, name):
     rec.close()
 
 
+@pytest.mark.parametrize("res", [9, 12, 18, 28, 36, 40, 56])
+def test_hierarchy_shapes_converge(W, res):
+    """Grids whose multigrid hierarchies end differently (coarsest sizes 9, 6,
+    9, 7, 9, 5, 7; zero to three levels above the one-CTA solve): the solve
+    converges and the SDF matches the oracle."""
+    p, n = synth.sphere_cloud(2000, seed=24)
+    ref = oracle.reconstruct(p, n, BBOX, res)
+    rec = W(res, len(p))
+    sdf, _ = rec.reconstruct(_t(p), _t(n), BBOX, res)
+    info = rec.info()
+    assert info["status"] == 0, info
+    assert np.abs(sdf.cpu().numpy().astype(np.float64) - ref.phi).max() <= SDF_TOL
+    rec.close()
+
+
 def test_odd_resolution(W):
     """An odd grid (15^3: no multigrid level above the one-CTA solve, pairs of
     cells ending in a single cell) against the oracle, forward and backward."""
