@@ -244,57 +244,84 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
 
 // Distance + marching-cubes adjoint, one thread per node with a nonzero dphi.
 // FP32 arithmetic per node; FP64 only in the scatter (atomics) and the dc sum.
+// Per node with dL/dphi != 0: phi = s |p - y| with y the closest point of the
+// node's triangle (Eqs. 33-34), y = sum_v beta_v P_v, and each vertex P_v on
+// the cube edge (chi1, chi2) at eta = (c - chi1) / (chi2 - chi1) (Eq. 28):
+// dL/dP_v = -s dphi beta_v u (u the unit vector from y to p), scattered to
+// dL/dchi1, dL/dchi2 and dL/dc.  The closest point comes from the triangle's
+// search record, as in the forward search; node coordinates from per-axis
+// tables (the forward's float positions), the sign test against the
+// smallest float not below c, c - chi1 from c as a float-float pair, and the
+// dL/dc sum in float-float, so no node needs the FP64 pipe.
+constexpr int kMaxAdjRes = 800;
+
 __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int* __restrict__ ctri,
                                       const float* __restrict__ chi, const DevState* __restrict__ st,
-                                      const Tri* __restrict__ tris, QParams g,
+                                      const Tri* __restrict__ tris, const float4* __restrict__ tris_s, QParams g,
                                       double* __restrict__ dchi, double* __restrict__ partials) {
   __shared__ double red[32];
+  __shared__ float s_ax[3][kMaxAdjRes];
   const int n = g.res;
-  const int64_t N = (int64_t)n * n * n;
-  const double c = st->c;
+  for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
+    const int a = t / n, i = t % n;
+    s_ax[a][i] = (float)(g.lo[a] + (i + 0.5) * g.h);
+  }
+  __syncthreads();
+  const double cd = st->c;
+  float cf = (float)cd;
+  if ((double)cf < cd) cf = nextafterf(cf, INFINITY);
+  const float c_hi = (float)cd, c_lo = (float)(cd - (double)c_hi);
   const float hf = (float)g.h;
-  double dcacc = 0.0;    // dL/dc: terms of both signs that nearly cancel -> FP64
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N;
-       o += (int64_t)gridDim.x * blockDim.x) {
+  const unsigned un = (unsigned)n;
+  const unsigned N = un * un * un;
+  float2 dcacc = make_float2(0.f, 0.f);   // dL/dc: terms of both signs that nearly cancel
+  for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < N; o += gridDim.x * blockDim.x) {
     const double gphi64 = dphi[o];
     if (gphi64 == 0.0) continue;
     const int t = ctri[o];
     if (t < 0) continue;
     const float gphi = (float)gphi64;
-    const int i = (int)(o % n), j = (int)((o / n) % n), k = (int)(o / ((int64_t)n * n));
-    const float3 p = make_float3((float)(g.lo[0] + (i + 0.5) * g.h), (float)(g.lo[1] + (j + 0.5) * g.h),
-                                 (float)(g.lo[2] + (k + 0.5) * g.h));
+    const unsigned row = o / un;
+    const int i = (int)(o - row * un), j = (int)(row % un), k = (int)(row / un);
+    const float3 p = make_float3(s_ax[0][i], s_ax[1][j], s_ax[2][k]);
+    const float4* rec = tris_s + kTriRec * (int64_t)t;
+    const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
+    const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+    const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
+    const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
+    float v, w;
+    rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
+    const float rx = ap.x - v * r1.x - w * r2.x;
+    const float ry = ap.y - v * r1.y - w * r2.y;
+    const float rz = ap.z - v * r1.z - w * r2.z;
+    const float dd = rx * rx + ry * ry + rz * rz;
+    if (!(dd > 0.f)) continue;
+    const float invd = rsqrtf(dd);
+    const float sgn = (chi[o] >= cf) ? 1.f : -1.f;
+    const float u[3] = {rx * invd, ry * invd, rz * invd};
+    const float bw[3] = {fmaxf(1.f - v - w, 0.f), v, w};
     const Tri tr = tris[t];
-    float bw[3];
-    const float d2 = tri_closest(p, f3(tr.a), f3(tr.b), f3(tr.c), &bw[0], &bw[1], &bw[2]);
-    if (!(d2 > 0.f)) continue;
-    const float3 y = make_float3(bw[0] * tr.a.x + bw[1] * tr.b.x + bw[2] * tr.c.x,
-                                 bw[0] * tr.a.y + bw[1] * tr.b.y + bw[2] * tr.c.y,
-                                 bw[0] * tr.a.z + bw[1] * tr.b.z + bw[2] * tr.c.z);
-    const float invd = rsqrtf(d2);
-    const float sgn = ((double)chi[o] >= c) ? 1.f : -1.f;
-    const float u[3] = {(p.x - y.x) * invd, (p.y - y.y) * invd, (p.z - y.z) * invd};
-    const float4 vv[3] = {tr.a, tr.b, tr.c};
+    const float gv[3] = {tr.a.w, tr.b.w, tr.c.w};
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      if (bw[v] == 0.f) continue;
-      const int gid = __float_as_int(vv[v].w);
-      const int ax = gid % 3;
-      const int64_t pl = gid / 3;
-      const int64_t stv = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+    for (int q = 0; q < 3; ++q) {
+      if (bw[q] == 0.f) continue;
+      const unsigned gid = (unsigned)__float_as_int(gv[q]);
+      const int ax = (int)(gid % 3u);
+      const unsigned pl = gid / 3u;
+      const unsigned stv = (ax == 0) ? 1u : (ax == 1 ? un : un * un);
       const float c1 = chi[pl], c2 = chi[pl + stv];
-      const float den = c2 - c1;                       // neighbouring values: exact
-      const float cm = (float)(c - (double)c1);        // c - chi1 without losing c's low bits
+      const float den = c2 - c1;                                   // neighbouring values: exact
+      const float cm = __fadd_rn(__fsub_rn(c_hi, c1), c_lo);       // c - chi1, keeping c's low bits
       const float eta = cm / den;
       // dL/dP_v[ax] = -s dphi beta_v u[ax];  dP/deta = h e_ax
-      const float deta = -sgn * gphi * bw[v] * u[ax] * hf;
-      const float w = deta / den;
-      atomicAdd(&dchi[pl], (double)(w * (eta - 1.f)));
-      atomicAdd(&dchi[pl + stv], (double)(-w * eta));
-      dcacc += (double)w;
+      const float deta = -sgn * gphi * bw[q] * u[ax] * hf;
+      const float wq = deta / den;
+      atomicAdd(&dchi[pl], (double)(wq * (eta - 1.f)));
+      atomicAdd(&dchi[pl + stv], (double)(-wq * eta));
+      dcacc = ff_add_f(dcacc, wq);
     }
   }
-  const double s = block_sum<256>(dcacc, red);
+  const double s = block_sum<256>((double)dcacc.x + (double)dcacc.y, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -503,7 +530,7 @@ int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_
   stage_end(h, kStBwdSeed, slot, s);
   slot = stage_begin(h, kStBwdSurf, s);
   const int nb = grid_blocks(N, 256, kPartials);
-  sdf_mc_adjoint_kernel<<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, g,
+  sdf_mc_adjoint_kernel<<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, h->tris_s, g,
                                            h->dchi64, h->partials);
   WGEO_LAUNCH_CHECK();
   dc_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, nb, h->dstate);

@@ -630,44 +630,6 @@ struct TieSlots {
 // the divisions replaced by the stored reciprocals), and the residual
 // p - y = ap - v ab - w ac is formed relative to a, so its rounding scales
 // with the distance and the edge length rather than with the coordinates.
-// Closest-point weights (v, w) of y = a + v ab + w ac from d1 = ab.ap,
-// d2 = ac.ap and the record's Gram entries and reciprocals.
-__device__ __forceinline__ void rec_weights(const float3 ap, float d1, float d2, const float4 r0, const float4 r1,
-                                            const float4 r2, const float4 r3, float& v, float& w) {
-  const float e00 = r0.w, e01 = r1.w, e11 = r2.w;
-  const float d3 = d1 - e00, d4 = d2 - e01;                  // ab . bp, ac . bp
-  const float d5 = d1 - e01, d6 = d2 - e11;                  // ab . cp, ac . cp
-  if (d1 <= 0.f && d2 <= 0.f) {
-    v = 0.f; w = 0.f;                                          // vertex a
-  } else if (d3 >= 0.f && d4 <= d3) {
-    v = 1.f; w = 0.f;                                          // vertex b
-  } else {
-    const float vc = d1 * d4 - d3 * d2;
-    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
-      v = d1 * r3.x; w = 0.f;                                  // edge ab
-    } else if (d6 >= 0.f && d5 <= d6) {
-      v = 0.f; w = 1.f;                                        // vertex c
-    } else {
-      const float vb = d5 * d2 - d1 * d6;
-      if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
-        v = 0.f; w = d2 * r3.y;                                // edge ac
-      } else {
-        const float va = d3 * d6 - d5 * d4;
-        if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
-          w = (d4 - d3) * r3.z; v = 1.f - w;                   // edge bc
-        } else if (r3.w > 0.f) {
-          v = vb * r3.w; w = vc * r3.w;                        // face
-        } else {
-          // collapsed triangle: the nearest of its three vertices
-          const float qa = ap.x * ap.x + ap.y * ap.y + ap.z * ap.z;
-          const float qb = qa - 2.f * d1 + e00, qc = qa - 2.f * d2 + e11;
-          v = (qb < qa && qb <= qc) ? 1.f : 0.f;
-          w = (qc < qa && qc < qb) ? 1.f : 0.f;
-        }
-      }
-    }
-  }
-}
 
 __device__ __forceinline__ float tri_dist2_rec(const float3 p, const float4* __restrict__ rec) {
   const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];

@@ -244,6 +244,49 @@ __device__ __forceinline__ T tri_closest_t(const Vec3<T> p, const Vec3<T> a, con
   return vdot(d, d);
 }
 
+// Closest-point weights (v, w) of y = a + v ab + w ac on a triangle given by
+// its search record (r0 = (a, |ab|^2), r1 = (ab, ab.ac), r2 = (ac, |ac|^2),
+// r3 = (1/|ab|^2, 1/|ac|^2, 1/|bc|^2, 1/|ab x ac|^2)), from ap = p - a,
+// d1 = ab.ap and d2 = ac.ap: Ericson's Voronoi-region case analysis with the
+// six dot products reduced to two through the Gram entries and the
+// divisions replaced by the reciprocals.
+__device__ __forceinline__ void rec_weights(const float3 ap, float d1, float d2, const float4 r0, const float4 r1,
+                                            const float4 r2, const float4 r3, float& v, float& w) {
+  const float e00 = r0.w, e01 = r1.w, e11 = r2.w;
+  const float d3 = d1 - e00, d4 = d2 - e01;                  // ab . bp, ac . bp
+  const float d5 = d1 - e01, d6 = d2 - e11;                  // ab . cp, ac . cp
+  if (d1 <= 0.f && d2 <= 0.f) {
+    v = 0.f; w = 0.f;                                          // vertex a
+  } else if (d3 >= 0.f && d4 <= d3) {
+    v = 1.f; w = 0.f;                                          // vertex b
+  } else {
+    const float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+      v = d1 * r3.x; w = 0.f;                                  // edge ab
+    } else if (d6 >= 0.f && d5 <= d6) {
+      v = 0.f; w = 1.f;                                        // vertex c
+    } else {
+      const float vb = d5 * d2 - d1 * d6;
+      if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+        v = 0.f; w = d2 * r3.y;                                // edge ac
+      } else {
+        const float va = d3 * d6 - d5 * d4;
+        if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+          w = (d4 - d3) * r3.z; v = 1.f - w;                   // edge bc
+        } else if (r3.w > 0.f) {
+          v = vb * r3.w; w = vc * r3.w;                        // face
+        } else {
+          // collapsed triangle: the nearest of its three vertices
+          const float qa = ap.x * ap.x + ap.y * ap.y + ap.z * ap.z;
+          const float qb = qa - 2.f * d1 + e00, qc = qa - 2.f * d2 + e11;
+          v = (qb < qa && qb <= qc) ? 1.f : 0.f;
+          w = (qc < qa && qc < qb) ? 1.f : 0.f;
+        }
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ float tri_closest(const float3 p, const float3 a, const float3 b, const float3 c,
                                              float* wa, float* wb, float* wc) {
   return tri_closest_t<float>({p.x, p.y, p.z}, {a.x, a.y, a.z}, {b.x, b.y, b.z}, {c.x, c.y, c.z}, wa, wb, wc);
