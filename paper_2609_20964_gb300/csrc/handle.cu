@@ -104,6 +104,7 @@ __global__ void reset_status_kernel(DevState* st) {
   st->status = 0;
   st->ntris = 0;
   st->c = 0.0;
+  st->c_up = 0.f;
   st->npts = 0;
   st->sdf_cnt[0] = 0;
   st->sdf_cnt[1] = 0;

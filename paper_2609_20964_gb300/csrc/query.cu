@@ -268,8 +268,7 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
   }
   __syncthreads();
   const double cd = st->c;
-  float cf = (float)cd;
-  if ((double)cf < cd) cf = nextafterf(cf, INFINITY);
+  const float cf = st->c_up;
   const float c_hi = (float)cd, c_lo = (float)(cd - (double)c_hi);
   const float hf = (float)g.h;
   const unsigned un = (unsigned)n;

@@ -243,17 +243,21 @@ __global__ void isovalue_finalize_kernel(const double* __restrict__ partials, in
   cnt = block_sum<1024>(cnt, red);
   if (threadIdx.x == 0) {
     st->c = cnt > 0.0 ? s / cnt : 0.0;
+    float cu = (float)st->c;
+    if ((double)cu < st->c) cu = nextafterf(cu, INFINITY);
+    st->c_up = cu;
     st->npts = (long long)cnt;
   }
 }
 
-__device__ __forceinline__ int cube_code(const float* __restrict__ chi, int i, int j, int k, int n,
-                                         double c) {
+// Case code of a cube: bit q set when corner q is inside (chi < c, tested as
+// chi < c_up, the smallest float >= c).
+__device__ __forceinline__ int cube_code(const float* __restrict__ chi, int i, int j, int k, int n, float c_up) {
   int code = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const float v = chi[lin3(i + (q & 1), j + ((q >> 1) & 1), k + (q >> 2), n)];
-    code |= ((double)v < c) ? (1 << q) : 0;
+    code |= (v < c_up) ? (1 << q) : 0;
   }
   return code;
 }
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(64) mc_count_kernel(const float* __restrict__ 
   const int i = bx * kBrick + lx, j = by * kBrick + ly, k = bz * kBrick + lz;
   const int m = g.res - 1;
   int cnt = 0;
-  if (i < m && j < m && k < m) cnt = c_mc_count[cube_code(chi, i, j, k, g.res, st->c)];
+  if (i < m && j < m && k < m) cnt = c_mc_count[cube_code(chi, i, j, k, g.res, st->c_up)];
   cnt = warp_sumi(cnt);
   __shared__ int s[2];
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ c
   const double c = st->c;
   int code = 0, cnt = 0;
   if (i < m && j < m && k < m) {
-    code = cube_code(chi, i, j, k, n, c);
+    code = cube_code(chi, i, j, k, n, st->c_up);
     cnt = c_mc_count[code];
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -865,8 +869,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
   const float val = sqrtf(cd[0]);
   const int bt = ct[0];
   const int64_t o = lin3(i, j, k, n);
-  const double c = st->c;
-  const float sgn = ((double)chi[o] >= c) ? 1.f : -1.f;
+  const float sgn = (chi[o] >= st->c_up) ? 1.f : -1.f;
   phi[o] = sgn * val;
   if (sdf_out) sdf_out[o] = sgn * val;
   if (ctri) ctri[o] = bt;
@@ -902,9 +905,7 @@ __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, cons
     s_ax[a][i] = make_float2(hi, (float)(v - (double)hi));
   }
   __syncthreads();
-  const double cd = st->c;
-  float cf = (float)cd;
-  if ((double)cf < cd) cf = nextafterf(cf, INFINITY);
+  const float cf = st->c_up;
   const unsigned un = (unsigned)n;
   const unsigned N = un * un * un;
   const int xi = st->fwd.xidx ^ 1;

@@ -44,6 +44,7 @@ struct DevState {
   long long npts;     // finite points used by the forward
   long long ntris;    // triangles found (uncapped)
   double c;           // iso-value
+  float c_up;         // the smallest float >= c: for float chi, chi < c <=> chi < c_up
   double dc;          // backward: dL/dc
   SolveState fwd;
   SolveState bwd;
