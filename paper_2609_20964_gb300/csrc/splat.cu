@@ -83,6 +83,7 @@ __global__ void scatter_points_kernel(const float* __restrict__ nrm, int64_t n,
 }
 
 constexpr int kR = kSplatTile + 2;  // V region edge: tile plus one halo cell per side
+constexpr int kList = 4096;          // shared list of the points reaching a tile
 
 // The fixed-point value rint(q) of a float q with |q| <= 2^36 as int64, from
 // two int32 conversions: qh = trunc(q / 2^16) and ql = q - qh 2^16 are exact
@@ -102,6 +103,8 @@ __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict
                                                         double* __restrict__ partials) {
   __shared__ long long V[kR * kR * kR * 3];
   __shared__ double red[32];   // per-warp sums (16 warps x 2)
+  __shared__ int s_list[kList];
+  __shared__ int s_cnt;
   const int tile = blockIdx.x;
   const int tx = tile % ntile, ty = (tile / ntile) % ntile, tz = tile / (ntile * ntile);
   const int T0[3] = {tx * kSplatTile, ty * kSplatTile, tz * kSplatTile};
@@ -125,70 +128,95 @@ __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict
     return;
   }
   for (int k = threadIdx.x; k < kR * kR * kR * 3; k += blockDim.x) V[k] = 0;
+  if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
 
+  // splat one listed point into the V region (sums in 64-bit fixed point)
+  auto splat_point = [&](int k) {
+    const float4 r0 = srec[2 * (int64_t)k];
+    const int c = __float_as_int(r0.w);
+    const int bc[3] = {cell_x(c), cell_y(c), cell_z(c)};
+    const float4 r1 = srec[2 * (int64_t)k + 1];
+    const float fr[3] = {r0.x, r0.y, r0.z};
+    const float nn[3] = {r1.x, r1.y, r1.z};
+    // per-axis factors for offsets -1, 0, +1: (x - c_o)/h = frac - 1/2 - delta
+    float fac[3][3];
+    bool ing[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float t = fabsf(fr[a] - 0.5f - (float)(d - 1));
+        fac[a][d] = 0.5f * fmaxf(0.f, 1.f - 0.5f * t);
+        const int o = bc[a] + d - 1;
+        ing[a][d] = (o >= 0) && (o < res);
+      }
+    }
+    float S = 0.f;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
+          const bool centre = (dx == 1 && dy == 1 && dz == 1);
+          S += centre ? 0.5f : fac[0][dx] * fac[1][dy] * fac[2][dz];
+        }
+    const float inv = 1.f / S;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
+          const int lx = bc[0] + dx - 1 - (T0[0] - 1);
+          const int ly = bc[1] + dy - 1 - (T0[1] - 1);
+          const int lz = bc[2] + dz - 1 - (T0[2] - 1);
+          if (lx < 0 || ly < 0 || lz < 0 || lx >= kR || ly >= kR || lz >= kR) continue;
+          const bool centre = (dx == 1 && dy == 1 && dz == 1);
+          const float alpha = (centre ? 0.5f : fac[0][dx] * fac[1][dy] * fac[2][dz]) * inv;
+          long long* v = &V[((lz * kR + ly) * kR + lx) * 3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const long long q = fix_round(alpha * nn[a] * (float)kFixScale);
+            if (q) atomicAdd((unsigned long long*)&v[a], (unsigned long long)q);
+          }
+        }
+  };
+  // the points of the 27 neighbouring tiles whose stencil reaches this tile's
+  // V region go to a shared list first (flushed when it could overflow), so
+  // the splatting is spread evenly over the block
   for (int nt = 0; nt < 27; ++nt) {
     const int ux = tx + nt % 3 - 1, uy = ty + (nt / 3) % 3 - 1, uz = tz + nt / 9 - 1;
     if (ux < 0 || uy < 0 || uz < 0 || ux >= ntile || uy >= ntile || uz >= ntile) continue;
     const int t = (uz * ntile + uy) * ntile + ux;
     const int s0 = tile_off[t], s1 = tile_off[t + 1];
-    for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-      const float4 r0 = srec[2 * (int64_t)k];
-      const int c = __float_as_int(r0.w);
-      const int bc[3] = {cell_x(c), cell_y(c), cell_z(c)};
-      bool rel = true;
+    for (int base = s0; base < s1; base += blockDim.x) {
+      const int k = base + threadIdx.x;
+      if (k < s1) {
+        const int c = __float_as_int(srec[2 * (int64_t)k].w);
+        const int bc[3] = {cell_x(c), cell_y(c), cell_z(c)};
+        bool rel = true;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) rel &= (bc[a] >= T0[a] - 2) && (bc[a] <= T0[a] + kSplatTile + 1);
-      if (!rel) continue;
-      const float4 r1 = srec[2 * (int64_t)k + 1];
-      const float fr[3] = {r0.x, r0.y, r0.z};
-      const float nn[3] = {r1.x, r1.y, r1.z};
-      // per-axis factors for offsets -1, 0, +1: (x - c_o)/h = frac - 1/2 - delta
-      float fac[3][3];
-      bool ing[3][3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const float t = fabsf(fr[a] - 0.5f - (float)(d - 1));
-          fac[a][d] = 0.5f * fmaxf(0.f, 1.f - 0.5f * t);
-          const int o = bc[a] + d - 1;
-          ing[a][d] = (o >= 0) && (o < res);
-        }
+        for (int a = 0; a < 3; ++a) rel &= (bc[a] >= T0[a] - 2) && (bc[a] <= T0[a] + kSplatTile + 1);
+        if (rel) s_list[atomicAdd(&s_cnt, 1)] = k;
       }
-      float S = 0.f;
-#pragma unroll
-      for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-          for (int dx = 0; dx < 3; ++dx) {
-            if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
-            const bool centre = (dx == 1 && dy == 1 && dz == 1);
-            S += centre ? 0.5f : fac[0][dx] * fac[1][dy] * fac[2][dz];
-          }
-      const float inv = 1.f / S;
-#pragma unroll
-      for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-          for (int dx = 0; dx < 3; ++dx) {
-            if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
-            const int lx = bc[0] + dx - 1 - (T0[0] - 1);
-            const int ly = bc[1] + dy - 1 - (T0[1] - 1);
-            const int lz = bc[2] + dz - 1 - (T0[2] - 1);
-            if (lx < 0 || ly < 0 || lz < 0 || lx >= kR || ly >= kR || lz >= kR) continue;
-            const bool centre = (dx == 1 && dy == 1 && dz == 1);
-            const float alpha = (centre ? 0.5f : fac[0][dx] * fac[1][dy] * fac[2][dz]) * inv;
-            long long* v = &V[((lz * kR + ly) * kR + lx) * 3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const long long q = fix_round(alpha * nn[a] * (float)kFixScale);
-              if (q) atomicAdd((unsigned long long*)&v[a], (unsigned long long)q);
-            }
-          }
+      __syncthreads();
+      const int cnt = s_cnt;
+      __syncthreads();   // every thread has read the count before the next appends
+      if (cnt > kList - (int)blockDim.x) {
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) splat_point(s_list[q]);
+        __syncthreads();
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+      }
     }
+  }
+  {
+    const int cnt = s_cnt;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) splat_point(s_list[q]);
   }
   __syncthreads();
 
