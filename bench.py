@@ -333,6 +333,8 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clocks.summary(),
     }
+    if rank == 0 and ws == 1 and args.serving_requests > 0:
+        out["serving"] = serving_bench(args.serving_requests, value)
     if cpu is not None:
         # SDF error of both precisions against the oracle's exact distance on its sampled nodes
         lin, ophi = cpu.pop("_sample")
@@ -421,6 +423,79 @@ def roofline(dom, stages, info, hbm, peak_kind, alg_tests_per_node):
     return {"bound": "hbm", "kernel": dom, "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm,
             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / hbm, "traffic": None,
             "peak_kind": peak_kind}
+
+
+# --------------------------------------------------------------------- serving
+def _rotation(rng):
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def serving_bench(n_req: int, step_cells_per_s: float, load: float = 0.7):
+    """The serving request mix through the request loop: grid sizes {64, 128,
+    256} w.p. {0.5, 0.35, 0.15}, point counts log-uniform in [1e4, 5e5], half
+    of the requests with gradients, exponential inter-arrival gaps at `load`
+    times the capacity estimated from the benchmark step.  Point clouds: one
+    seeded degree-8 SH body of 5e5 points; request i takes its first n_i points
+    rotated about the body centre by a rotation seeded with its id.  Latency =
+    completion - scheduled arrival (queueing included)."""
+    import torch
+    import synth
+    from paper_2609_20964_gb300.serving import Request, Server
+    mix = synth.serving_requests(n_req)
+    bp, bn, _ = synth.sh_body_cloud(500_000, lmax=8, seed=50_000)
+    c = np.array([0.5, 0.5, 0.5])
+    nq = 50_000
+    reqs = []
+    for r in mix:
+        rng = np.random.default_rng(r["seed"])
+        R = _rotation(rng)
+        n = min(r["n"], len(bp))
+        pts = ((bp[:n].astype(np.float64) - c) @ R.T + c).astype(np.float32)
+        nrm = (bn[:n].astype(np.float64) @ R.T).astype(np.float32)
+        q = rng.random((nq, 3)).astype(np.float32)
+        g = (rng.standard_normal(nq) / nq).astype(np.float32) if r["grad"] else None
+        reqs.append((r, torch.from_numpy(pts).pin_memory(), torch.from_numpy(nrm).pin_memory(),
+                     torch.from_numpy(q).pin_memory(), None if g is None else torch.from_numpy(g).pin_memory()))
+    mean_cells = float(np.mean([r["res"] ** 3 for r in mix]))
+    rate = load * step_cells_per_s / mean_cells          # requests per second
+    srv = Server(budget_bytes=32 << 30, n_streams=4, max_points=500_000)
+    # warm-up: one request per grid size (workspaces allocated, solver graphs recorded)
+    warm = []
+    for res in (64, 128, 256):
+        r, P, N, Q, G = next(x for x in reqs if x[0]["res"] == res)
+        warm.append(srv.submit(Request(points=P, normals=N, res=res, queries=Q, d_sdf_q=G)))
+    for f in warm:
+        f.result()
+    srv.latencies.clear()
+    depth = []
+    futs = []
+    t0 = time.perf_counter()
+    t_arr = t0
+    for r, P, N, Q, G in reqs:
+        t_arr += r["gap"] / rate
+        while time.perf_counter() < t_arr:
+            time.sleep(0.0002)
+        depth.append(len(srv.pending) + len(srv.inflight))
+        futs.append(srv.submit(Request(points=P, normals=N, res=r["res"], queries=Q, d_sdf_q=G,
+                                       arrival=t_arr, rid=r["id"])))
+    results = [f.result() for f in futs]
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([x.latency_s for x in results]) * 1e3
+    cells = sum(r["res"] ** 3 for r in mix)
+    points = sum(min(r["n"], len(bp)) for r in mix)
+    return {"requests": n_req, "offered_rate_per_s": rate, "offered_load": load,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "cells_per_s": cells / wall, "points_per_s": points / wall,
+            "wall_s": wall, "queue_depth_max": int(max(depth)), "queue_depth_mean": float(np.mean(depth)),
+            "streams": 4, "with_gradients": int(sum(r["grad"] for r in mix)),
+            "clouds": "one seeded degree-8 SH body of 5e5 points, per-request subset and seeded rotation",
+            "queries_per_request": nq}
 
 
 # --------------------------------------------------------------------- oracle
@@ -559,6 +634,7 @@ def main():
     ap.add_argument("--stage-steps", type=int, default=5)
     ap.add_argument("--cpu-sample-nodes", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=300)
     # smaller cases of the same workload, for profiler captures only (the
     # benchmark figure is the default 256^3 / 200k / 1M configuration)
     ap.add_argument("--res", type=int, default=256)
