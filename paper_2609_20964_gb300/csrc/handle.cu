@@ -15,7 +15,6 @@ using namespace wgeo;
 
 namespace {
 
-constexpr int kMaxRes = 800;       // packed cell coordinates and int32 edge ids stay in range
 constexpr size_t kAlign = 256;
 
 struct Layout {

@@ -253,14 +253,13 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
 // tables (the forward's float positions), the sign test against the
 // smallest float not below c, c - chi1 from c as a float-float pair, and the
 // dL/dc sum in float-float, so no node needs the FP64 pipe.
-constexpr int kMaxAdjRes = 800;
 
 __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int* __restrict__ ctri,
                                       const float* __restrict__ chi, const DevState* __restrict__ st,
                                       const Tri* __restrict__ tris, const float4* __restrict__ tris_s, QParams g,
                                       double* __restrict__ dchi, double* __restrict__ partials) {
   __shared__ double red[32];
-  __shared__ float s_ax[3][kMaxAdjRes];
+  __shared__ float s_ax[3][kMaxRes];
   const int n = g.res;
   for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
     const int a = t / n, i = t % n;

@@ -890,13 +890,12 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
 // same closest point) take the smaller triangle index.  The node coordinates come from per-axis
 // float-float tables built once per block, and chi >= c (c double) is tested
 // as chi >= the smallest float not below c, so no node needs FP64.
-constexpr int kMaxTieRes = 800;
 
 __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, const DevState* __restrict__ st,
                                const float4* __restrict__ tris_s, const int* __restrict__ tie_a,
                                const int* __restrict__ tie_b, TieSlots tie_cd, float* __restrict__ phi,
                                float* __restrict__ sdf_out, int* __restrict__ ctri) {
-  __shared__ float2 s_ax[3][kMaxTieRes];
+  __shared__ float2 s_ax[3][kMaxRes];
   const int n = g.res;
   for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
     const int a = t / n, i = t % n;

@@ -17,6 +17,8 @@ constexpr int kSplatTile = 8;        // output tile edge of the fused splat + di
 constexpr int kBrick = 4;            // marching-cubes cubes per brick edge (SDF leaf)
 constexpr int kMaxTriPerCube = 5;
 constexpr int kTriRec = 4;           // float4 per triangle search record
+constexpr int kMaxRes = 800;         // grid bound: packed coordinates, int32 edge ids and
+                                     // 32-bit node indices stay in range
 constexpr int kPartials = 2048;      // per-block partial slots of the deterministic reductions
 constexpr int kMaxLevels = 12;
 constexpr double kFixScale = 68719476736.0;      // 2^36: fixed-point scale of the splat sums
@@ -132,18 +134,14 @@ __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a
 // Float-float scalar (about 44 significant bits on the FP32 pipe) for the
 // near-tie decisions of the distance search: sums by two-sum, products with
 // the FMA residual (fma(a, b, -rn(a b)) is the exact error of the rounded
-// product), quotients with two correction steps.  Comparisons are exact for
-// normalised values (|lo| <= ulp(hi) / 2), which every operator returns.
+// product).  Comparisons are exact for normalised values (|lo| <= ulp(hi) /
+// 2), which every operator returns.
 struct Ff {
   float hi, lo;
   __device__ __forceinline__ Ff() {}
   __device__ __forceinline__ Ff(float x) : hi(x), lo(0.f) {}
   __device__ __forceinline__ Ff(float h, float l) : hi(h), lo(l) {}
 };
-__device__ __forceinline__ Ff ff_from_double(double x) {
-  const float h = (float)x;
-  return Ff(h, (float)(x - (double)h));
-}
 __device__ __forceinline__ Ff operator+(Ff a, Ff b) {
   const float2 r = ff_add(make_float2(a.hi, a.lo), make_float2(b.hi, b.lo));
   return Ff(r.x, r.y);
@@ -158,92 +156,10 @@ __device__ __forceinline__ Ff operator*(Ff a, Ff b) {
   const float2 r = fast_two_sum(p, e);
   return Ff(r.x, r.y);
 }
-__device__ __forceinline__ Ff operator/(Ff a, Ff b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
-  const Ff r1 = a - b * Ff(q1);
-  const float q2 = __fdiv_rn(r1.hi, b.hi);
-  const Ff r2 = r1 - b * Ff(q2);
-  const float q3 = __fdiv_rn(r2.hi, b.hi);
-  return (Ff(q1) + Ff(q2)) + Ff(q3);
-}
 __device__ __forceinline__ bool operator<(Ff a, Ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool operator>(Ff a, Ff b) { return b < a; }
 __device__ __forceinline__ bool operator<=(Ff a, Ff b) { return !(b < a); }
 __device__ __forceinline__ bool operator>=(Ff a, Ff b) { return !(a < b); }
-
-template <typename T>
-struct Vec3 {
-  T x, y, z;
-};
-template <typename T>
-__device__ __forceinline__ Vec3<T> vsub(Vec3<T> a, Vec3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-template <typename T>
-__device__ __forceinline__ T vdot(Vec3<T> a, Vec3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-
-// Squared distance from p to triangle (a, b, c) and the barycentric weights of
-// the closest point (Voronoi regions: three vertices, three edges, the face),
-// in the precision T (float on the search path, float-float where near-ties
-// are re-decided).
-template <typename T>
-__device__ __forceinline__ T tri_closest_t(const Vec3<T> p, const Vec3<T> a, const Vec3<T> b, const Vec3<T> c,
-                                           T* wa, T* wb, T* wc) {
-  const T zero = T(0), one = T(1);
-  const Vec3<T> ab = vsub(b, a), ac = vsub(c, a), ap = vsub(p, a);
-  T u = one, v = zero, w = zero;
-  const T d1 = vdot(ab, ap), d2 = vdot(ac, ap);
-  if (d1 <= zero && d2 <= zero) {
-    u = one; v = zero; w = zero;
-  } else {
-    const Vec3<T> bp = vsub(p, b);
-    const T d3 = vdot(ab, bp), d4 = vdot(ac, bp);
-    if (d3 >= zero && d4 <= d3) {
-      u = zero; v = one; w = zero;
-    } else {
-      const T vc = d1 * d4 - d3 * d2;
-      if (vc <= zero && d1 >= zero && d3 <= zero) {
-        const T t = d1 / (d1 - d3);
-        u = one - t; v = t; w = zero;
-      } else {
-        const Vec3<T> cp = vsub(p, c);
-        const T d5 = vdot(ab, cp), d6 = vdot(ac, cp);
-        if (d6 >= zero && d5 <= d6) {
-          u = zero; v = zero; w = one;
-        } else {
-          const T vb = d5 * d2 - d1 * d6;
-          if (vb <= zero && d2 >= zero && d6 <= zero) {
-            const T t = d2 / (d2 - d6);
-            u = one - t; v = zero; w = t;
-          } else {
-            const T va = d3 * d6 - d5 * d4;
-            if (va <= zero && (d4 - d3) >= zero && (d5 - d6) >= zero) {
-              const T t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
-              u = zero; v = one - t; w = t;
-            } else {
-              const T den = va + vb + vc;
-              if (den > zero) {
-                const T inv = one / den;
-                v = vb * inv;
-                w = vc * inv;
-                u = one - v - w;
-              } else {
-                // degenerate (collapsed) triangle: nearest of the three vertices
-                const Vec3<T> cb = vsub(p, b), cc = vsub(p, c);
-                const T q0 = vdot(ap, ap), q1 = vdot(cb, cb), q2 = vdot(cc, cc);
-                if (q0 <= q1 && q0 <= q2) { u = one; v = zero; w = zero; }
-                else if (q1 <= q2) { u = zero; v = one; w = zero; }
-                else { u = zero; v = zero; w = one; }
-              }
-            }
-          }
-        }
-      }
-    }
-  }
-  const Vec3<T> y = {u * a.x + v * b.x + w * c.x, u * a.y + v * b.y + w * c.y, u * a.z + v * b.z + w * c.z};
-  const Vec3<T> d = vsub(p, y);
-  if (wa) { *wa = u; *wb = v; *wc = w; }
-  return vdot(d, d);
-}
 
 // Closest-point weights (v, w) of y = a + v ab + w ac on a triangle given by
 // its search record (r0 = (a, |ab|^2), r1 = (ab, ab.ac), r2 = (ac, |ac|^2),
@@ -288,10 +204,11 @@ __device__ __forceinline__ void rec_weights(const float3 ap, float d1, float d2,
   }
 }
 
-__device__ __forceinline__ float tri_closest(const float3 p, const float3 a, const float3 b, const float3 c,
-                                             float* wa, float* wb, float* wc) {
-  return tri_closest_t<float>({p.x, p.y, p.z}, {a.x, a.y, a.z}, {b.x, b.y, b.z}, {c.x, c.y, c.z}, wa, wb, wc);
-}
+template <typename T>
+struct Vec3 {
+  T x, y, z;
+};
+
 
 }  // namespace wgeo
 
