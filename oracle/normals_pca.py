@@ -13,6 +13,13 @@ For every point x_i:
 A neighbourhood of fewer than 3 points, or a covariance with no positive
 eigenvalue, has no normal: the zero vector is returned.  The sign of n_i is
 not part of the definition; callers compare directions up to sign.
+
+Membership |x_j - x_i| <= R decides an integer (who is a neighbour), so it is
+taken in the paper's precision, float32 (its kernels run in Warp's float32):
+the differences, their squares and the two sums each rounded to float32, in
+the order ((dx^2 + dy^2) + dz^2), against R^2 rounded to float32.  Everything
+after the membership (weights, centroid, covariance, eigenvectors) is FP64.
+`exact_ball=True` takes the FP64 test instead (the mathematical ball).
 """
 from __future__ import annotations
 
@@ -38,31 +45,60 @@ def dpca_point(x, neighbours, eps):
     return V[:, 0], lam, len(X)
 
 
-def dpca_normals(points, radius: float, eps: float):
+def in_ball_f32(P32, i, cand, radius: float):
+    """The members of `cand` (indices) within `radius` of point i, decided in
+    float32 as described in the module docstring."""
+    cand = np.asarray(cand, dtype=np.int64)
+    d = P32[cand] - P32[i]
+    d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    r = np.float32(radius)
+    return cand[d2 <= r * r]
+
+
+def _finite(P):
+    return np.isfinite(P).all(axis=1)
+
+
+def dpca_normals(points, radius: float, eps: float, exact_ball: bool = False):
     """(normals [n,3], eigenvalues [n,3] ascending, neighbour counts [n]) for all
-    points; neighbourhoods from a k-d tree ball query."""
+    points; neighbourhoods from a k-d tree ball query.  Points with a non-finite
+    coordinate take part in no neighbourhood and get the zero normal."""
     P = np.asarray(points, dtype=np.float64)
     n = len(P)
     normals = np.zeros((n, 3))
     lam = np.zeros((n, 3))
     cnt = np.zeros(n, dtype=np.int64)
-    if n == 0:
+    ok = _finite(P) if n else np.zeros(0, dtype=bool)
+    if not ok.any():
         return normals, lam, cnt
-    tree = cKDTree(P)
-    nbrs = tree.query_ball_point(P, radius)
-    for i in range(n):
-        normals[i], lam[i], cnt[i] = dpca_point(P[i], P[nbrs[i]], eps)
+    idx = np.nonzero(ok)[0]
+    Q = P[idx]
+    Q32 = Q.astype(np.float32)
+    tree = cKDTree(Q)
+    # float32 membership can admit a point a few float32 ulps beyond R: query a
+    # slightly larger ball and let the float32 test decide
+    nbrs = tree.query_ball_point(Q, radius if exact_ball else radius * (1 + 1e-5))
+    for k, i in enumerate(idx):
+        nb = np.asarray(nbrs[k], dtype=np.int64) if exact_ball else in_ball_f32(Q32, k, nbrs[k], radius)
+        normals[i], lam[i], cnt[i] = dpca_point(P[i], Q[nb], eps)
     return normals, lam, cnt
 
 
-def dpca_normals_brute(points, radius: float, eps: float):
+def dpca_normals_brute(points, radius: float, eps: float, exact_ball: bool = False):
     """The same by testing every pair (small clouds)."""
     P = np.asarray(points, dtype=np.float64)
     n = len(P)
     normals = np.zeros((n, 3))
     lam = np.zeros((n, 3))
     cnt = np.zeros(n, dtype=np.int64)
-    for i in range(n):
-        d = np.linalg.norm(P - P[i], axis=1)
-        normals[i], lam[i], cnt[i] = dpca_point(P[i], P[d <= radius], eps)
+    ok = _finite(P) if n else np.zeros(0, dtype=bool)
+    idx = np.nonzero(ok)[0]
+    Q = P[idx]
+    Q32 = Q.astype(np.float32)
+    for k, i in enumerate(idx):
+        if exact_ball:
+            nb = np.nonzero(np.linalg.norm(Q - Q[k], axis=1) <= radius)[0]
+        else:
+            nb = in_ball_f32(Q32, k, np.arange(len(Q)), radius)
+        normals[i], lam[i], cnt[i] = dpca_point(P[i], Q[nb], eps)
     return normals, lam, cnt

@@ -101,3 +101,25 @@ def test_covariance_by_the_moment_identity():
     # the uncentred moment would point elsewhere: the pin can tell them apart
     lam3, V3 = np.linalg.eigh(np.einsum("j,ja,jb->ab", w, y, y) / w.sum())
     assert abs(abs(n @ V3[:, 0]) - 1) > 1e-3
+
+
+def test_float32_membership_matches_the_ball_away_from_its_boundary():
+    # the float32 test and the FP64 ball differ only for pairs whose distance
+    # is within a few float32 ulps of R; planted pairs at R(1 -+ 1e-5) are
+    # decided the same by both, a pair at exactly R is inside for both
+    rng = np.random.default_rng(4)
+    P = rng.uniform(-1, 1, (400, 3)).astype(np.float32).astype(np.float64)
+    R = 0.25
+    a = D.dpca_normals(P, R, 1e-4)
+    b = D.dpca_normals(P, R, 1e-4, exact_ball=True)
+    d = np.linalg.norm(P[:, None, :] - P[None, :, :], axis=2)
+    near = (np.abs(d - R) < 1e-6 * R).any(axis=1)
+    assert np.array_equal(a[2][~near], b[2][~near])
+    P2 = np.array([[0, 0, 0], [R * (1 - 1e-5), 0, 0], [0, R * (1 + 1e-5), 0], [0, 0, 0.25]])
+    c = D.dpca_normals_brute(P2, R, 1e-4)
+    assert c[2].tolist() == [3, 2, 1, 2]
+    # a non-finite point joins no neighbourhood and has no normal
+    P3 = np.r_[P[:50], [[np.nan, 0, 0]]]
+    e = D.dpca_normals(P3, R, 1e-4)
+    f = D.dpca_normals(P[:50], R, 1e-4)
+    assert np.array_equal(e[2][:50], f[2]) and e[2][50] == 0 and not e[0][50].any()
