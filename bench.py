@@ -335,6 +335,8 @@ def run_ours(args):
     }
     if rank == 0 and ws == 1 and args.serving_requests > 0:
         out["serving"] = serving_bench(args.serving_requests, value)
+    if rank == 0 and args.pca_reps > 0:
+        out["normal_estimation"] = normal_estimation_bench(rec, P, args.pca_reps, cpu is not None)
     if cpu is not None:
         # SDF error of both precisions against the oracle's exact distance on its sampled nodes
         lin, ophi = cpu.pop("_sample")
@@ -423,6 +425,61 @@ def roofline(dom, stages, info, hbm, peak_kind, alg_tests_per_node):
     return {"bound": "hbm", "kernel": dom, "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm,
             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / hbm, "traffic": None,
             "peak_kind": peak_kind}
+
+
+# --------------------------------------------------------- normal estimation
+PCA_RADIUS = 0.1               # the paper's default neighbourhood radius (unit box)
+FLOPS_PER_PAIR = 33.0          # FP32 operations per (point, neighbour) pair: distance,
+                               # weight, first and second weighted moments
+
+
+def normal_estimation_bench(rec, P, reps: int, with_oracle: bool):
+    """D-PCA normals of the workload's cloud at R = 0.1 (inputs resident, CUDA
+    events around each call on the launching stream)."""
+    import torch
+    eps = 1e-3 * PCA_RADIUS
+    nrm = torch.empty_like(P)
+    nrm_cnt, cnt = rec.estimate_normals(P, BBOX, PCA_RADIUS, eps, with_counts=True)
+    torch.cuda.synchronize()
+    pairs = int(cnt.long().sum())
+    for _ in range(3):
+        rec.estimate_normals(P, BBOX, PCA_RADIUS, eps, normals_out=nrm)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    l0 = rec.lib.wgeo_kernel_launches()
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        rec.estimate_normals(P, BBOX, PCA_RADIUS, eps, normals_out=nrm)
+        b.record(stream)
+    torch.cuda.synchronize()
+    launches = rec.lib.wgeo_kernel_launches() - l0
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    n = int(P.shape[0])
+    achieved = pairs * FLOPS_PER_PAIR / (ms / 1e3) / 1e12
+    out = {"points_per_s": n / (ms / 1e3), "ms": ms, "points": n, "radius": PCA_RADIUS, "eps": eps,
+           "mean_neighbours": pairs / n, "reps": reps, "gpu_launches_per_call": launches / reps,
+           "same_as_first_call": bool(torch.equal(nrm, nrm_cnt)),
+           "roofline": {"bound": "alu", "kernel": "dpca_normal_kernel (whole call timed)",
+                        "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                        "alg_flops_per_launch": pairs * FLOPS_PER_PAIR, "flops_per_pair": FLOPS_PER_PAIR,
+                        "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}}
+    if with_oracle:
+        # the oracle on a bounded sample of points (each over the whole cloud)
+        from oracle import normals_pca as D
+        p64 = P.double().cpu().numpy()
+        p32 = P.cpu().numpy()
+        idx = np.random.default_rng(9).choice(n, 64, replace=False)
+        allj = np.arange(n)
+        t0 = time.perf_counter()
+        for i in idx:
+            nb = D.in_ball_f32(p32, i, allj, PCA_RADIUS)
+            D.dpca_point(p64[i], p64[nb], eps)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(idx) / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{len(idx)} points, each against the whole {n}-point cloud"}
+    return out
 
 
 # --------------------------------------------------------------------- serving
@@ -635,6 +692,7 @@ def main():
     ap.add_argument("--cpu-sample-nodes", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--pca-reps", type=int, default=10)
     # smaller cases of the same workload, for profiler captures only (the
     # benchmark figure is the default 256^3 / 200k / 1M configuration)
     ap.add_argument("--res", type=int, default=256)

@@ -97,7 +97,8 @@ typedef struct {
 #define WGEO_STAGE_BWD_SOLVE   9   /* adjoint Poisson solve */
 #define WGEO_STAGE_BWD_SPLAT   10  /* divergence transpose + splat adjoint */
 #define WGEO_STAGE_SDF_TIE     11  /* float-float decisions of near-tie closest triangles */
-#define WGEO_NUM_STAGES        12
+#define WGEO_STAGE_POINT_PCA   12  /* D-PCA point-normal estimation (wgeo_estimate_normals) */
+#define WGEO_NUM_STAGES        13
 
 typedef struct {
   uint32_t status;           /* WGEO_STATUS_* bits of the last call */
@@ -164,6 +165,30 @@ int wgeo_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* n
 int wgeo_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid,
                   const float* q, const float* d_sdf_q, const float* d_nrm_q, int64_t m,
                   float* d_points, float* d_normals, float* d_q, void* stream);
+
+/* Normal estimation by distance-weighted PCA (Sec. 2.1, the neighbourhood,
+ * weight, weighted-centroid and weighted-covariance equations and the
+ * eigen-decomposition that follows them): for every point x_i of points
+ * [n][3], N_i = { x_j : |x_j - x_i| <= radius } (x_i itself included),
+ * w_ij = 1 / (|x_j - x_i| + eps), C_i the w-weighted covariance about the
+ * w-weighted centroid, and normals[i] = the unit eigenvector of C_i with the
+ * smallest eigenvalue.  The sign is arbitrary (unoriented).  A neighbourhood of
+ * fewer than 3 points, a covariance with no positive eigenvalue, or a point
+ * with a non-finite coordinate gives the zero vector; non-finite points belong
+ * to no neighbourhood.  Membership is decided in float32 with each operation
+ * rounded: ((dx*dx + dy*dy) + dz*dz) <= radius*radius, dx = x_j.x - x_i.x.
+ * counts [n] (int32, may be NULL) receives |N_i| (0 for non-finite points).
+ * bbox is a HOST array {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z} of finite floats
+ * with hi >= lo: it only places the search cells, so points outside it are
+ * still handled exactly (they share the boundary cells).  radius > 0 finite,
+ * eps finite with eps >= 1e-6 * radius (the float weights R / (d + eps) then
+ * stay below 1e6); 0 <= n <= max_points.  Results are deterministic (sums in a
+ * fixed order).  Uses the handle's normal-estimation workspace only: the
+ * state kept by the last wgeo_reconstruct for wgeo_query / wgeo_backward is
+ * untouched.  Enqueued on `stream`; errors WGEO_ERR_INVALID_ARG (nothing
+ * enqueued) or WGEO_ERR_CUDA. */
+int wgeo_estimate_normals(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float radius,
+                          float eps, float* normals, int32_t* counts, void* stream);
 
 /* Synchronises the stream of the handle's last call and copies the device
  * status into *out. */

@@ -104,6 +104,23 @@ class Reconstructor:
         L.check(rc, "wgeo_backward")
         return d_points, d_normals, d_q
 
+    def estimate_normals(self, points: torch.Tensor, bbox, radius: float, eps: float | None = None,
+                         with_counts: bool = False, normals_out=None, stream=None):
+        """Unoriented D-PCA normals of `points` (Sec. 2.1); eps defaults to
+        1e-3 * radius.  Returns (normals [n,3], counts [n] int32 or None)."""
+        n = int(points.shape[0])
+        if eps is None:
+            eps = 1e-3 * radius
+        if normals_out is None:
+            normals_out = torch.empty((n, 3), device=self.device, dtype=torch.float32)
+        counts = torch.empty((n,), device=self.device, dtype=torch.int32) if with_counts else None
+        rc = self.lib.wgeo_estimate_normals(self.h, _dev(points, "points", 3), n, _bbox(bbox), float(radius),
+                                            float(eps), _dev(normals_out, "normals_out", 3),
+                                            C.c_void_p(counts.data_ptr()) if counts is not None else None,
+                                            C.c_void_p(_stream(stream)))
+        L.check(rc, "wgeo_estimate_normals")
+        return normals_out, counts
+
     def info(self) -> dict:
         inf = L.Info()
         L.check(self.lib.wgeo_get_info(self.h, C.byref(inf)), "wgeo_get_info")

@@ -22,8 +22,10 @@ struct Layout {
   size_t off_b32, off_chi32, off_chi64, off_r32, off_e32, off_phi, off_ctri, off_dphi64, off_dchi64,
       off_lam64, off_lam32, off_levels, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
       off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_tris_s, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
-      off_scan, off_state;
-  size_t n_partials, n_scan;
+      off_scan, off_state, off_dp_cell, off_dp_count, off_dp_off, off_dp_cursor, off_dp_scan, off_dp_tmp,
+      off_dp_sorted, off_dp_key, off_dp_gbox;
+  size_t n_partials, n_scan, n_dp_scan;
+  int64_t dp_cap;
   int64_t cap;
 };
 
@@ -87,6 +89,19 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.n_scan = scan_tmp_size((int)std::max(ntiles, nbricks));
   L.off_scan = take(c, 4 * L.n_scan);
   L.off_state = take(c, sizeof(DevState));
+  // normal estimation: per point a cell, a key and two float4 copies, per
+  // kDpcaBox points a box, per cell a count, an offset and a cursor
+  L.dp_cap = dpca_cell_cap(P);
+  L.off_dp_cell = take(c, 4 * Pp);
+  L.off_dp_tmp = take(c, 16 * Pp);
+  L.off_dp_sorted = take(c, 16 * Pp);
+  L.off_dp_count = take(c, 4 * ((size_t)L.dp_cap + 1));
+  L.off_dp_off = take(c, 4 * ((size_t)L.dp_cap + 2));
+  L.off_dp_cursor = take(c, 4 * ((size_t)L.dp_cap + 1));
+  L.off_dp_key = take(c, 4 * Pp);
+  L.off_dp_gbox = take(c, 32 * ((Pp + kDpcaBox - 1) / kDpcaBox));
+  L.n_dp_scan = scan_tmp_size((int)L.dp_cap);
+  L.off_dp_scan = take(c, 4 * L.n_dp_scan);
   L.total = (c + kAlign - 1) / kAlign * kAlign;
   return L;
 }
@@ -264,6 +279,16 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->scan_tmp = (int*)(a + L.off_scan);
   h->scan_tmp_elems = L.n_scan;
   h->dstate = (DevState*)(a + L.off_state);
+  h->dp_cell_cap = L.dp_cap;
+  h->dp_cell = (int*)(a + L.off_dp_cell);
+  h->dp_tmp = (float4*)(a + L.off_dp_tmp);
+  h->dp_sorted = (float4*)(a + L.off_dp_sorted);
+  h->dp_count = (int*)(a + L.off_dp_count);
+  h->dp_off = (int*)(a + L.off_dp_off);
+  h->dp_cursor = (int*)(a + L.off_dp_cursor);
+  h->dp_key = (int*)(a + L.off_dp_key);
+  h->dp_gbox = (float4*)(a + L.off_dp_gbox);
+  h->dp_scan = (int*)(a + L.off_dp_scan);
   if (upload_mc_table() != WGEO_OK || cudaMemset(h->dstate, 0, sizeof(DevState)) != cudaSuccess ||
       cudaMemset(h->chiff[0], 0, 16 * N) != cudaSuccess) {
     cudaFree(h->arena);
@@ -364,6 +389,22 @@ int wgeo_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_gr
   if (cudaSetDevice(h->device) != cudaSuccess) return WGEO_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = launch_backward(h, d_sdf_grid, d_nrm_grid, q, d_sdf_q, d_nrm_q, m, d_points, d_normals, d_q, s);
+  h->last_stream = s;
+  return rc;
+}
+
+int wgeo_estimate_normals(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float radius,
+                          float eps, float* normals, int32_t* counts, void* stream) {
+  if (!h || !bbox || n < 0 || n > h->max_points) return WGEO_ERR_INVALID_ARG;
+  if (n > 0 && (!points || !normals)) return WGEO_ERR_INVALID_ARG;
+  if (!(isfinite(radius) && radius > 0.f && isfinite(eps) && eps >= 1e-6f * radius)) return WGEO_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(bbox[a]) || !isfinite(bbox[a + 3]) || !(bbox[a + 3] >= bbox[a])) return WGEO_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return WGEO_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int slot = stage_begin(h, kStPointPca, s);
+  int rc = launch_dpca(h, points, n, bbox, radius, eps, normals, counts, s);
+  stage_end(h, kStPointPca, slot, s);
   h->last_stream = s;
   return rc;
 }

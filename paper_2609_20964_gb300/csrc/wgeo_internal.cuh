@@ -21,6 +21,11 @@ constexpr int kMaxRes = 800;         // grid bound: packed coordinates, int32 ed
                                      // 32-bit node indices stay in range
 constexpr int kPartials = 2048;      // per-block partial slots of the deterministic reductions
 constexpr int kMaxLevels = 12;
+constexpr int kDpcaAxisCells = 1024;  // normal estimation: cells per axis at most
+constexpr int kDpcaSub = 2;           // normal estimation: cell edge R / kDpcaSub (when the caps allow)
+constexpr int kDpcaLanes = 4;         // normal estimation: lanes per point
+constexpr int kDpcaPts = 32 / kDpcaLanes;   // points per warp chunk
+constexpr int kDpcaBox = 16;          // sorted entries per bounding box
 constexpr double kFixScale = 68719476736.0;      // 2^36: fixed-point scale of the splat sums
 constexpr double kFixInv2 = 1.0 / 137438953472.0; // 1 / 2^37 (the face form sums 2 F)
 
@@ -79,7 +84,8 @@ enum Stage {
   kStBwdSolve = 9,
   kStBwdSplat = 10,
   kStSDFTie = 11,  // near-tie decisions of the distance search
-  kStages = 12
+  kStPointPca = 12,  // D-PCA normal estimation
+  kStages = 13
 };
 constexpr int kRing = 256;
 
@@ -258,6 +264,19 @@ struct wgeo_handle {
   unsigned* pyr_rth = nullptr;   // levels >= 1: radius, half-thickness as float bits (atomic maxima)
   double* dP = nullptr;          // backward: dL/d(vertex) per triangle corner, 9 doubles
 
+  // normal estimation (its own buffers: a call between a forward and its
+  // backward leaves the forward's state intact)
+  int64_t dp_cell_cap = 0;       // cells the workspace holds
+  int* dp_cell = nullptr;        // cell per point (original order); -1 = non-finite
+  int* dp_count = nullptr;       // dp_cell_cap + 1
+  int* dp_off = nullptr;         // dp_cell_cap + 2 (exclusive scan, total last)
+  int* dp_cursor = nullptr;      // dp_cell_cap + 1 (after the call's cells: the chunk counter)
+  int* dp_key = nullptr;         // sub-cell key per grouped entry
+  float4* dp_gbox = nullptr;     // 2 float4 per kDpcaBox sorted entries: bounding box
+  int* dp_scan = nullptr;
+  float4* dp_tmp = nullptr;      // points grouped by cell, unordered within a cell
+  float4* dp_sorted = nullptr;   // the same, point-index order within each cell
+
   // reductions / scans
   double* partials = nullptr;    // kPartials * 4 doubles
   int* scan_tmp = nullptr;
@@ -348,6 +367,11 @@ int launch_export_adjoint(wgeo_handle* h, int which, float* out, cudaStream_t s)
 int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
                     const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,
                     float* d_normals, float* d_q, cudaStream_t s);
+// dpca.cu
+int64_t dpca_cell_cap(int64_t max_points);
+int dpca_grid(const float* bbox, float radius, int64_t n, int64_t cap_ws, int dims[3], double* cs_out);
+int launch_dpca(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float radius, float eps,
+                float* normals, int* counts, cudaStream_t s);
 // scan.cu
 int exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s);
 size_t scan_tmp_size(int n);
