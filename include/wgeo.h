@@ -98,7 +98,8 @@ typedef struct {
 #define WGEO_STAGE_BWD_SPLAT   10  /* divergence transpose + splat adjoint */
 #define WGEO_STAGE_SDF_TIE     11  /* float-float decisions of near-tie closest triangles */
 #define WGEO_STAGE_POINT_PCA   12  /* D-PCA point-normal estimation (wgeo_estimate_normals) */
-#define WGEO_NUM_STAGES        13
+#define WGEO_STAGE_ORIENT      13  /* parity normal orientation (wgeo_orient_normals) */
+#define WGEO_NUM_STAGES        14
 
 typedef struct {
   uint32_t status;           /* WGEO_STATUS_* bits of the last call */
@@ -189,6 +190,35 @@ int wgeo_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_gr
  * enqueued) or WGEO_ERR_CUDA. */
 int wgeo_estimate_normals(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float radius,
                           float eps, float* normals, int32_t* counts, void* stream);
+
+/* Parity-based normal orientation (Sec. 2.2): flips, in place, the normals
+ * [n][3] of points [n][3] to point out of the closed surface the cloud samples.
+ *   r_d = gamma * r_{d,0}, r_{d,0} = 1/2 max_i min_{j != i} |x_i - x_j|
+ *     (Eqs. baseline_detection_radius and expanded_detection_radius);
+ *   probes y_m = x_i + m r_d u_i, m = 0, 1, ..., with u_i = n_i / |n_i|, up to
+ *     the first probe outside the points' bounding box widened by r_d;
+ *   d_m = 1 iff some point lies within r_d of y_m;
+ *   N = (number of m >= 1 with d_m = 0, d_{m-1} = 1) - 1 (Eq. N_i_define),
+ *     N_one = number of leading ones of d;
+ *   iteration 0: flip if N is odd (Eq. basic_parity_flip); iteration 1: flip
+ *     if N != 0 or N_one > n_tol along the current normal; iteration 2: flip
+ *     if N along the current normal exceeds N along its opposite.
+ * Every decision is taken in float32 with each operation rounded and no
+ * contraction: d2 = ((dx*dx + dy*dy) + dz*dz) <= r_d*r_d, y = x + (m r_d) u,
+ * r_{d,0} = 0.5 sqrt(max d2), r_d = gamma r_{d,0}.  A flip negates the
+ * normal as given.  Zero or non-finite normals, non-finite points (which are
+ * not part of the cloud) and r_d = 0 (fewer than two distinct points) leave
+ * normals unchanged.  Rays stop at 2^24 probes.
+ * stats [n][5] int32 (may be NULL): N along +n, N_one along +n, N along -n,
+ * N_one along -n, flags (1, 2, 4: flipped by iteration 0, 1, 2; 8: final
+ * normal is the negated input); zeros where nothing was decided.  rd_out
+ * (DEVICE float, may be NULL) receives r_d.  bbox is a HOST array as for
+ * wgeo_estimate_normals (it places the search cells only).  gamma >= 1 finite
+ * (the paper's default 2.5), n_tol >= 0 (default 2), 0 <= n <= max_points.
+ * Uses the normal-estimation workspace only.  Enqueued on `stream`; errors
+ * WGEO_ERR_INVALID_ARG (nothing enqueued) or WGEO_ERR_CUDA. */
+int wgeo_orient_normals(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float gamma,
+                        int32_t n_tol, float* normals, int32_t* stats, float* rd_out, void* stream);
 
 /* Synchronises the stream of the handle's last call and copies the device
  * status into *out. */

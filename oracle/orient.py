@@ -5,7 +5,7 @@ infrastructure only: the CUDA path never imports it.
 Steps, in the paper's order and notation:
   r_{d,0} = 1/2 max_i min_{j != i} |x_i - x_j|          (Eq. baseline_detection_radius)
   r_d     = gamma_r r_{d,0}                             (Eq. expanded_detection_radius)
-  y_{i,m} = x_i + m ds n_i,  m = 0, 1, ..., M           (probe points)
+  y_{i,m} = x_i + m ds u_i,  m = 0, 1, ..., M           (probe points, u_i = n_i / |n_i|)
   d_{i,m} = 1 if some x_j lies within r_d of y_{i,m}    (detection array)
   N_all   = #{m >= 1 : d_{i,m} = 0 and d_{i,m-1} = 1}   (1 -> 0 transitions)
   N_i     = N_all - 1                                   (Eq. N_i_define)
@@ -22,14 +22,18 @@ Readings where the paper is silent:
   * every iteration looks at every point, along its current normal.  Only
     signs change, so the patterns along +n_i and -n_i (as given) settle all
     three iterations;
+  * the ray direction is the normal scaled to unit length in float32,
+    u = n / sqrt((n_x^2 + n_y^2) + n_z^2), each operation rounded (D-PCA
+    normals are unit already; the scaling bounds the probe count);
   * the integer decisions (nearest-neighbour distances, detections, the box
     exit) are taken in float32, the precision of the paper's kernels:
     d2 = ((dx*dx + dy*dy) + dz*dz) with every operation rounded, probes
-    y = x + (m ds) n rounded per operation, r_{d,0} = 0.5 sqrt(max d2) and
+    y = x + (m ds) u rounded per operation, r_{d,0} = 0.5 sqrt(max d2) and
     r_d = gamma_r r_{d,0} rounded to float32;
-  * a zero normal, a non-finite point, or r_d = 0 (fewer than two distinct
-    points) leaves the normal as it is, with zero statistics.  Non-finite
-    points are not part of the cloud.
+  * a zero or non-finite normal, a non-finite point, or r_d = 0 (fewer than
+    two distinct points) leaves the normal as it is, with zero statistics.
+    Non-finite points are not part of the cloud.  A flip negates the normal
+    as given.
 """
 from __future__ import annotations
 
@@ -97,6 +101,15 @@ class _Detector:
         return out
 
 
+def unit_direction(n):
+    """n / |n| in float32, or None for a zero or non-finite normal."""
+    n32 = np.asarray(n, dtype=np.float32)
+    ss = (n32[0] * n32[0] + n32[1] * n32[1]) + n32[2] * n32[2]
+    if not (ss > 0 and np.isfinite(ss)):
+        return None
+    return n32 / np.sqrt(ss)
+
+
 def detection_array(x, n, rd, det: _Detector, lo, hi):
     """d_{i,0..M} along y_m = x + m ds n, ds = r_d, ending at the first probe
     outside [lo - r_d, hi + r_d] (float32 throughout)."""
@@ -133,11 +146,12 @@ def crossings(d):
     return n_all - 1, n_one
 
 
-def orient(points, normals, gamma: float = 2.5, n_tol: int = 2):
+def orient(points, normals, gamma: float = 2.5, n_tol: int = 2, only=None):
     """Oriented normals and per-point statistics int64 [n, 5]:
     (N along +n, N_one along +n, N along -n, N_one along -n, flags) with flag
     bits 1, 2, 4 = flipped by iteration 0, 1, 2 and 8 = final normal is -n.
-    Also returns r_d."""
+    Also returns r_d.  `only` (indices) restricts the rays to those points;
+    r_d and the detections still use the whole cloud."""
     P = np.asarray(points, dtype=np.float64)
     Nrm = np.asarray(normals, dtype=np.float32).copy()
     n = len(P)
@@ -151,12 +165,14 @@ def orient(points, normals, gamma: float = 2.5, n_tol: int = 2):
     lo = C.astype(np.float32).min(axis=0)
     hi = C.astype(np.float32).max(axis=0)
     P32 = P.astype(np.float32)
-    for i in np.nonzero(ok)[0]:
+    todo = np.nonzero(ok)[0] if only is None else [i for i in np.asarray(only) if ok[i]]
+    for i in todo:
         nv = Nrm[i]
-        if not nv.any():
+        u = unit_direction(nv)
+        if u is None:
             continue
-        Np, op = crossings(detection_array(P32[i], nv, rd, det, lo, hi))
-        Nm, om = crossings(detection_array(P32[i], -nv, rd, det, lo, hi))
+        Np, op = crossings(detection_array(P32[i], u, rd, det, lo, hi))
+        Nm, om = crossings(detection_array(P32[i], -u, rd, det, lo, hi))
         s, flags = 1, 0
         # iteration 0: standard parity along the estimated normal
         if Np % 2 == 1:

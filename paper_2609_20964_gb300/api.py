@@ -121,6 +121,23 @@ class Reconstructor:
         L.check(rc, "wgeo_estimate_normals")
         return normals_out, counts
 
+    def orient_normals(self, points: torch.Tensor, normals: torch.Tensor, bbox, gamma: float = 2.5,
+                       n_tol: int = 2, with_stats: bool = False, stream=None):
+        """Flips `normals` in place to point out of the sampled surface by
+        parity ray casting (Sec. 2.2).  Returns (normals, stats [n,5] int32 or
+        None, r_d as a one-element device tensor)."""
+        n = int(points.shape[0])
+        if normals.shape[0] != n:
+            raise ValueError("points and normals differ in length")
+        stats = torch.empty((n, 5), device=self.device, dtype=torch.int32) if with_stats else None
+        rd = torch.empty((1,), device=self.device, dtype=torch.float32)
+        rc = self.lib.wgeo_orient_normals(self.h, _dev(points, "points", 3), n, _bbox(bbox), float(gamma),
+                                          int(n_tol), _dev(normals, "normals", 3),
+                                          C.c_void_p(stats.data_ptr()) if stats is not None else None,
+                                          _dev(rd, "rd"), C.c_void_p(_stream(stream)))
+        L.check(rc, "wgeo_orient_normals")
+        return normals, stats, rd
+
     def info(self) -> dict:
         inf = L.Info()
         L.check(self.lib.wgeo_get_info(self.h, C.byref(inf)), "wgeo_get_info")

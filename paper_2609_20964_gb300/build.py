@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwgeo.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["handle.cu", "splat.cu", "solver.cu", "surface.cu", "query.cu", "scan.cu", "shgen.cu", "dpca.cu"]
+SOURCES = ["handle.cu", "splat.cu", "solver.cu", "surface.cu", "query.cu", "scan.cu", "shgen.cu", "dpca.cu", "orient.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

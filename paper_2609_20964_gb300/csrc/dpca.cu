@@ -34,42 +34,22 @@ namespace wgeo {
 
 namespace {
 
-struct DpcaGrid {
-  float lo[3];
-  float inv_cs;   // 1 / cell edge
-  int dim[3];
-};
-
-__device__ __forceinline__ void dpca_cell3(const DpcaGrid& g, float x, float y, float z, int c[3]) {
-  const float p[3] = {x, y, z};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    // clamp in float before converting: far points land in the edge cells
-    const float u = fminf(fmaxf(floorf((p[a] - g.lo[a]) * g.inv_cs), 0.f), (float)(g.dim[a] - 1));
-    c[a] = (int)u;
-  }
-}
-
-__device__ __forceinline__ int dpca_cell(const DpcaGrid& g, float x, float y, float z) {
-  int c[3];
-  dpca_cell3(g, x, y, z, c);
-  return (c[2] * g.dim[1] + c[1]) * g.dim[0] + c[0];
-}
-
 // Cell of every point and the per-cell counts; points with a non-finite
-// coordinate join no cell and get the zero normal here.
-__global__ void dpca_bin_kernel(const float* __restrict__ pts, int n, DpcaGrid g, int* __restrict__ cell_of,
+// coordinate join no cell (and get the zero normal here when normals is set).
+__global__ void dpca_bin_kernel(const float* __restrict__ pts, int n, PointGrid g, int* __restrict__ cell_of,
                                 int* __restrict__ count, float* __restrict__ normals) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float x = pts[3 * (int64_t)i], y = pts[3 * (int64_t)i + 1], z = pts[3 * (int64_t)i + 2];
     if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
       cell_of[i] = -1;
-      normals[3 * (int64_t)i] = 0.f;
-      normals[3 * (int64_t)i + 1] = 0.f;
-      normals[3 * (int64_t)i + 2] = 0.f;
+      if (normals) {
+        normals[3 * (int64_t)i] = 0.f;
+        normals[3 * (int64_t)i + 1] = 0.f;
+        normals[3 * (int64_t)i + 2] = 0.f;
+      }
       continue;
     }
-    const int cell = dpca_cell(g, x, y, z);
+    const int cell = grid_cell(g, x, y, z);
     cell_of[i] = cell;
     atomicAdd(&count[cell], 1);
   }
@@ -77,10 +57,10 @@ __global__ void dpca_bin_kernel(const float* __restrict__ pts, int n, DpcaGrid g
 
 // Position of a point inside its cell as a 9-bit Morton key of an 8 x 8 x 8
 // split of the cell (coordinates outside the cell clamp to its faces).
-__device__ __forceinline__ int dpca_subkey(const DpcaGrid& g, float x, float y, float z) {
+__device__ __forceinline__ int dpca_subkey(const PointGrid& g, float x, float y, float z) {
   const float p[3] = {x, y, z};
   int c[3];
-  dpca_cell3(g, x, y, z, c);
+  grid_cell3(g, x, y, z, c);
   int key = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -93,7 +73,7 @@ __device__ __forceinline__ int dpca_subkey(const DpcaGrid& g, float x, float y, 
 
 // Unordered scatter into the cells' ranges: (x, y, z, point index bits) and
 // the entry's sub-cell key.
-__global__ void dpca_scatter_kernel(const float* __restrict__ pts, int n, DpcaGrid g,
+__global__ void dpca_scatter_kernel(const float* __restrict__ pts, int n, PointGrid g,
                                     const int* __restrict__ cell_of, const int* __restrict__ off,
                                     int* __restrict__ cursor, float4* __restrict__ tmp, int* __restrict__ tkey) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -264,7 +244,7 @@ __device__ __forceinline__ float approx_rcp(float x) {
 
 __global__ void __launch_bounds__(128, 4) dpca_normal_kernel(const float4* __restrict__ sorted,
                                                           const int* __restrict__ off,
-                                                          const int* __restrict__ total, DpcaGrid g,
+                                                          const int* __restrict__ total, PointGrid g,
                                                           const float4* __restrict__ gbox, int* __restrict__ next,
                                                           float radius, float eps_r, float rc,
                                                           float* __restrict__ normals, int* __restrict__ counts) {
@@ -396,53 +376,66 @@ __global__ void dpca_zero_counts_kernel(const int* __restrict__ cell_of, int n, 
 
 }  // namespace
 
-int64_t dpca_cell_cap(int64_t max_points) {
+int64_t point_grid_cap(int64_t max_points) {
   return std::min<int64_t>(std::max<int64_t>(2 * max_points, 4096), (int64_t)1 << 26);
 }
 
-int dpca_grid(const float* bbox, float radius, int64_t n, int64_t cap_ws, int dims[3], double* cs_out) {
+int point_grid_dims(const float* bbox, double cs_min, int64_t n, int64_t cap_ws, PointGrid* g) {
   const int64_t cap = std::min<int64_t>(cap_ws, std::max<int64_t>(2 * n, 4096));
   double ext[3], emax = 0.0;
   for (int a = 0; a < 3; ++a) {
     ext[a] = std::max(0.0, (double)bbox[3 + a] - (double)bbox[a]);
     emax = std::max(emax, ext[a]);
   }
-  // cells of edge R / kDpcaSub: a warp's union of balls is trimmed to whole cells
-  double cs = std::max((double)radius / kDpcaSub, emax / kDpcaAxisCells);
+  double cs = std::max(cs_min, emax / kDpcaAxisCells);
+  if (!(cs > 0.0)) cs = 1.0;   // a box of one point
   for (;;) {
     int64_t tot = 1;
     for (int a = 0; a < 3; ++a) {
-      dims[a] = (int)std::min<double>(std::max(1.0, ceil(ext[a] / cs)), (double)kDpcaAxisCells);
-      tot *= dims[a];
+      g->dim[a] = (int)std::min<double>(std::max(1.0, ceil(ext[a] / cs)), (double)kDpcaAxisCells);
+      tot *= g->dim[a];
     }
     if (tot <= cap) break;
     cs *= 1.25;
   }
-  *cs_out = cs;
-  return dims[0] * dims[1] * dims[2];
+  for (int a = 0; a < 3; ++a) g->lo[a] = bbox[a];
+  g->cs = cs;
+  g->inv_cs = (float)(1.0 / cs);
+  g->ncell = g->dim[0] * g->dim[1] * g->dim[2];
+  return g->ncell;
+}
+
+int build_point_grid(wgeo_handle* h, const float* points, int n, const float* bbox, double cs_min, bool ordered,
+                     float* zero_normals, PointGrid* g, cudaStream_t s) {
+  point_grid_dims(bbox, cs_min, n, h->dp_cell_cap, g);
+  const int ncell = g->ncell;
+  WGEO_CUDA_TRY(cudaMemsetAsync(h->dp_count, 0, sizeof(int) * (size_t)ncell, s));
+  WGEO_CUDA_TRY(cudaMemsetAsync(h->dp_cursor, 0, sizeof(int) * ((size_t)ncell + 1), s));
+  dpca_bin_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(points, n, *g, h->dp_cell, h->dp_count, zero_normals);
+  WGEO_LAUNCH_CHECK();
+  int rc = exclusive_scan(h->dp_count, h->dp_off, ncell, h->dp_scan, s);
+  if (rc) return rc;
+  dpca_scatter_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(points, n, *g, h->dp_cell, h->dp_off, h->dp_cursor,
+                                                          ordered ? h->dp_tmp : h->dp_sorted, h->dp_key);
+  WGEO_LAUNCH_CHECK();
+  if (ordered) {
+    dpca_rank_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(h->dp_tmp, h->dp_key, h->dp_cell, h->dp_off,
+                                                         h->dp_off + ncell, h->dp_sorted);
+    WGEO_LAUNCH_CHECK();
+  }
+  return WGEO_OK;
 }
 
 int launch_dpca(wgeo_handle* h, const float* points, int64_t n64, const float* bbox, float radius, float eps,
                 float* normals, int* counts, cudaStream_t s) {
   if (n64 == 0) return WGEO_OK;
   const int n = (int)n64;
-  DpcaGrid g;
-  double cs = radius;
-  const int ncell = dpca_grid(bbox, radius, n64, h->dp_cell_cap, g.dim, &cs);
-  for (int a = 0; a < 3; ++a) g.lo[a] = bbox[a];
-  g.inv_cs = (float)(1.0 / cs);
-  WGEO_CUDA_TRY(cudaMemsetAsync(h->dp_count, 0, sizeof(int) * (size_t)ncell, s));
-  WGEO_CUDA_TRY(cudaMemsetAsync(h->dp_cursor, 0, sizeof(int) * ((size_t)ncell + 1), s));
-  dpca_bin_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(points, n, g, h->dp_cell, h->dp_count, normals);
-  WGEO_LAUNCH_CHECK();
-  int rc = exclusive_scan(h->dp_count, h->dp_off, ncell, h->dp_scan, s);
+  PointGrid g;
+  // cells of edge R / kDpcaSub: a warp's union of balls is trimmed to whole cells
+  int rc = build_point_grid(h, points, n, bbox, (double)radius / kDpcaSub, true, normals, &g, s);
   if (rc) return rc;
-  dpca_scatter_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(points, n, g, h->dp_cell, h->dp_off, h->dp_cursor,
-                                                          h->dp_tmp, h->dp_key);
-  WGEO_LAUNCH_CHECK();
-  dpca_rank_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(h->dp_tmp, h->dp_key, h->dp_cell, h->dp_off,
-                                                       h->dp_off + ncell, h->dp_sorted);
-  WGEO_LAUNCH_CHECK();
+  const int ncell = g.ncell;
+  const double cs = g.cs;
   dpca_group_box_kernel<<<grid_blocks(div_up(n, 2 * kDpcaBox) * 32, 256), 256, 0, s>>>(
       h->dp_sorted, h->dp_off + ncell, h->dp_gbox);
   WGEO_LAUNCH_CHECK();

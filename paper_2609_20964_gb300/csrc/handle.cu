@@ -23,7 +23,7 @@ struct Layout {
       off_lam64, off_lam32, off_levels, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
       off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_tris_s, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
       off_scan, off_state, off_dp_cell, off_dp_count, off_dp_off, off_dp_cursor, off_dp_scan, off_dp_tmp,
-      off_dp_sorted, off_dp_key, off_dp_gbox;
+      off_dp_sorted, off_dp_key, off_dp_gbox, off_or_scal;
   size_t n_partials, n_scan, n_dp_scan;
   int64_t dp_cap;
   int64_t cap;
@@ -91,7 +91,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.off_state = take(c, sizeof(DevState));
   // normal estimation: per point a cell, a key and two float4 copies, per
   // kDpcaBox points a box, per cell a count, an offset and a cursor
-  L.dp_cap = dpca_cell_cap(P);
+  L.dp_cap = point_grid_cap(P);
   L.off_dp_cell = take(c, 4 * Pp);
   L.off_dp_tmp = take(c, 16 * Pp);
   L.off_dp_sorted = take(c, 16 * Pp);
@@ -100,6 +100,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.off_dp_cursor = take(c, 4 * ((size_t)L.dp_cap + 1));
   L.off_dp_key = take(c, 4 * Pp);
   L.off_dp_gbox = take(c, 32 * ((Pp + kDpcaBox - 1) / kDpcaBox));
+  L.off_or_scal = take(c, 16 * sizeof(unsigned));
   L.n_dp_scan = scan_tmp_size((int)L.dp_cap);
   L.off_dp_scan = take(c, 4 * L.n_dp_scan);
   L.total = (c + kAlign - 1) / kAlign * kAlign;
@@ -288,6 +289,7 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->dp_cursor = (int*)(a + L.off_dp_cursor);
   h->dp_key = (int*)(a + L.off_dp_key);
   h->dp_gbox = (float4*)(a + L.off_dp_gbox);
+  h->or_scal = (unsigned*)(a + L.off_or_scal);
   h->dp_scan = (int*)(a + L.off_dp_scan);
   if (upload_mc_table() != WGEO_OK || cudaMemset(h->dstate, 0, sizeof(DevState)) != cudaSuccess ||
       cudaMemset(h->chiff[0], 0, 16 * N) != cudaSuccess) {
@@ -405,6 +407,22 @@ int wgeo_estimate_normals(wgeo_handle* h, const float* points, int64_t n, const 
   const int slot = stage_begin(h, kStPointPca, s);
   int rc = launch_dpca(h, points, n, bbox, radius, eps, normals, counts, s);
   stage_end(h, kStPointPca, slot, s);
+  h->last_stream = s;
+  return rc;
+}
+
+int wgeo_orient_normals(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float gamma,
+                        int32_t n_tol, float* normals, int32_t* stats, float* rd_out, void* stream) {
+  if (!h || !bbox || n < 0 || n > h->max_points) return WGEO_ERR_INVALID_ARG;
+  if (n > 0 && (!points || !normals)) return WGEO_ERR_INVALID_ARG;
+  if (!(isfinite(gamma) && gamma >= 1.f) || n_tol < 0) return WGEO_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(bbox[a]) || !isfinite(bbox[a + 3]) || !(bbox[a + 3] >= bbox[a])) return WGEO_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return WGEO_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int slot = stage_begin(h, kStOrient, s);
+  int rc = launch_orient(h, points, n, bbox, gamma, n_tol, normals, stats, rd_out, s);
+  stage_end(h, kStOrient, slot, s);
   h->last_stream = s;
   return rc;
 }

@@ -85,7 +85,8 @@ enum Stage {
   kStBwdSplat = 10,
   kStSDFTie = 11,  // near-tie decisions of the distance search
   kStPointPca = 12,  // D-PCA normal estimation
-  kStages = 13
+  kStOrient = 13,    // parity orientation
+  kStages = 14
 };
 constexpr int kRing = 256;
 
@@ -273,6 +274,7 @@ struct wgeo_handle {
   int* dp_cursor = nullptr;      // dp_cell_cap + 1 (after the call's cells: the chunk counter)
   int* dp_key = nullptr;         // sub-cell key per grouped entry
   float4* dp_gbox = nullptr;     // 2 float4 per kDpcaBox sorted entries: bounding box
+  unsigned* or_scal = nullptr;   // orientation: cloud box (ordered bits), max nearest distance^2
   int* dp_scan = nullptr;
   float4* dp_tmp = nullptr;      // points grouped by cell, unordered within a cell
   float4* dp_sorted = nullptr;   // the same, point-index order within each cell
@@ -367,11 +369,26 @@ int launch_export_adjoint(wgeo_handle* h, int which, float* out, cudaStream_t s)
 int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
                     const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,
                     float* d_normals, float* d_q, cudaStream_t s);
-// dpca.cu
-int64_t dpca_cell_cap(int64_t max_points);
-int dpca_grid(const float* bbox, float radius, int64_t n, int64_t cap_ws, int dims[3], double* cs_out);
+// dpca.cu: point grids (cubic cells over a box; points outside it fall in the
+// edge cells), built into the handle's normal-estimation workspace.  ordered:
+// entries by (cell, sub-cell key, index) in dp_sorted; else by cell only,
+// in arrival order, also in dp_sorted.
+struct PointGrid {
+  float lo[3];
+  float inv_cs;   // 1 / cell edge
+  int dim[3];
+  int ncell;
+  double cs;      // cell edge
+};
+int64_t point_grid_cap(int64_t max_points);
+int point_grid_dims(const float* bbox, double cs_min, int64_t n, int64_t cap_ws, PointGrid* g);
+int build_point_grid(wgeo_handle* h, const float* points, int n, const float* bbox, double cs_min, bool ordered,
+                     float* zero_normals, PointGrid* g, cudaStream_t s);
 int launch_dpca(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float radius, float eps,
                 float* normals, int* counts, cudaStream_t s);
+// orient.cu
+int launch_orient(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float gamma, int n_tol,
+                  float* normals, int* stats, float* rd_out, cudaStream_t s);
 // scan.cu
 int exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s);
 size_t scan_tmp_size(int n);
@@ -412,6 +429,22 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   }
   __syncthreads();
   return t;
+}
+
+// Cell of a point in a PointGrid, clamped into the grid (float clamp before
+// the conversion, so far points land in the edge cells).
+__device__ __forceinline__ void grid_cell3(const PointGrid& g, float x, float y, float z, int c[3]) {
+  const float p[3] = {x, y, z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float u = fminf(fmaxf(floorf((p[a] - g.lo[a]) * g.inv_cs), 0.f), (float)(g.dim[a] - 1));
+    c[a] = (int)u;
+  }
+}
+__device__ __forceinline__ int grid_cell(const PointGrid& g, float x, float y, float z) {
+  int c[3];
+  grid_cell3(g, x, y, z, c);
+  return (c[2] * g.dim[1] + c[1]) * g.dim[0] + c[0];
 }
 
 __device__ __forceinline__ int pack_cell(int x, int y, int z) { return x | (y << 10) | (z << 20); }
