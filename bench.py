@@ -337,6 +337,7 @@ def run_ours(args):
         out["serving"] = serving_bench(args.serving_requests, value)
     if rank == 0 and args.pca_reps > 0:
         out["normal_estimation"] = normal_estimation_bench(rec, P, args.pca_reps, cpu is not None)
+        out["normal_orientation"] = orientation_bench(rec, P, n, args.pca_reps)
     if cpu is not None:
         # SDF error of both precisions against the oracle's exact distance on its sampled nodes
         lin, ophi = cpu.pop("_sample")
@@ -480,6 +481,50 @@ def normal_estimation_bench(rec, P, reps: int, with_oracle: bool):
         out["cpu_baseline"] = {"value": len(idx) / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
                                "sample": f"{len(idx)} points, each against the whole {n}-point cloud"}
     return out
+
+
+def orientation_bench(rec, P, n_exact, reps: int):
+    """Parity orientation (gamma 2.5, N_tol 2) of the workload's cloud from its
+    analytic normals with seeded random signs, and of the D-PCA normals
+    (R = 0.1); CUDA events around each call; the share of results that point
+    the analytic way."""
+    import torch
+    Nx = torch.from_numpy(n_exact).cuda()
+    sgn = torch.from_numpy(np.random.default_rng(11).choice([-1.0, 1.0], len(n_exact)).astype(np.float32)).cuda()
+    N0 = Nx * sgn[:, None]
+    N = N0.clone()
+    for _ in range(3):
+        N.copy_(N0)
+        rec.orient_normals(P, N, BBOX)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        N.copy_(N0)
+        a.record(stream)
+        rec.orient_normals(P, N, BBOX)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    _, st, rd = rec.orient_normals(P, N0.clone(), BBOX, with_stats=True)
+    N.copy_(N0)
+    rec.orient_normals(P, N, BBOX)
+    outward = float(((N * Nx).sum(1) > 0).float().mean())
+    # the paper's preprocessing from raw points: D-PCA, then orientation
+    Npca, _ = rec.estimate_normals(P, BBOX, PCA_RADIUS)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    rec.estimate_normals(P, BBOX, PCA_RADIUS, normals_out=Npca)
+    rec.orient_normals(P, Npca, BBOX)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ok = Npca.abs().sum(1) > 0
+    pca_out = float(((Npca * Nx).sum(1)[ok] > 0).float().mean())
+    st = st.cpu().numpy()
+    return {"points_per_s": len(n_exact) / (ms / 1e3), "ms": ms, "gamma": 2.5, "n_tol": 2,
+            "r_d": float(rd.item()), "outward_share_from_random_signs": outward,
+            "mean_crossings": {"plus": float(st[:, 0].mean()), "minus": float(st[:, 2].mean())},
+            "raw_points_to_oriented_normals_ms": t0.elapsed_time(t1),
+            "outward_share_from_dpca": pca_out}
 
 
 # --------------------------------------------------------------------- serving
