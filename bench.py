@@ -336,6 +336,7 @@ def run_ours(args):
     if rank == 0 and ws == 1 and args.serving_requests > 0:
         out["serving"] = serving_bench(args.serving_requests, value)
     if rank == 0 and args.pca_reps > 0:
+        out["exact_query"] = exact_query_bench(rec, P, Nn, Q, args.pca_reps)
         out["normal_estimation"] = normal_estimation_bench(rec, P, args.pca_reps, cpu is not None)
         out["normal_orientation"] = orientation_bench(rec, P, n, args.pca_reps)
     if cpu is not None:
@@ -426,6 +427,31 @@ def roofline(dom, stages, info, hbm, peak_kind, alg_tests_per_node):
     return {"bound": "hbm", "kernel": dom, "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm,
             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / hbm, "traffic": None,
             "peak_kind": peak_kind}
+
+
+# ---------------------------------------------------------------- exact queries
+def exact_query_bench(rec, P, Nn, Q, reps: int):
+    """Exact off-grid signed distance and gradient at the workload's queries
+    on its reconstruction (CUDA events around each call), beside the
+    interpolated query of the same points."""
+    import torch
+    rec.reconstruct(P, Nn, BBOX, RES, with_sdf=False, with_normals=False)
+    for _ in range(3):
+        rec.query_exact(Q)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        rec.query_exact(Q)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    se, _ = rec.query_exact(Q, with_grad=False)
+    si, _ = rec.query(Q, with_normals=False)
+    torch.cuda.synchronize()
+    m = int(Q.shape[0])
+    return {"queries_per_s": m / (ms / 1e3), "ms": ms, "queries": m,
+            "max_abs_exact_minus_interpolated": float((se - si).abs().max())}
 
 
 # --------------------------------------------------------- normal estimation

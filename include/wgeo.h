@@ -99,7 +99,8 @@ typedef struct {
 #define WGEO_STAGE_SDF_TIE     11  /* float-float decisions of near-tie closest triangles */
 #define WGEO_STAGE_POINT_PCA   12  /* D-PCA point-normal estimation (wgeo_estimate_normals) */
 #define WGEO_STAGE_ORIENT      13  /* parity normal orientation (wgeo_orient_normals) */
-#define WGEO_NUM_STAGES        14
+#define WGEO_STAGE_QUERY_EXACT 14  /* exact off-grid signed distance (wgeo_query_exact) */
+#define WGEO_NUM_STAGES        15
 
 typedef struct {
   uint32_t status;           /* WGEO_STATUS_* bits of the last call */
@@ -154,6 +155,22 @@ int wgeo_reconstruct(wgeo_handle* h, const float* points, const float* normals, 
  * positions clamped into the node hull [lo+h/2, lo+(res-1/2)h].  sdf_q [m];
  * nrm_q [m][3] or NULL.  Needs a prior wgeo_reconstruct on this handle. */
 int wgeo_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, void* stream);
+
+/* Exact query (Sec. 2.4, Eqs. 29-34 evaluated off the grid): at each point
+ * q [m][3], sdf_q [m] = s(q) d(q) with d(q) the exact distance to the last
+ * forward's marching-cubes surface (nearest triangle, float32 search) and
+ * s(q) = -1 inside, +1 outside by the parity of the crossings of a segment
+ * from q to a corner of the cube holding q (q clamped into the node hull for
+ * the sign only; on a closed surface this is the parity of any ray from q).
+ * grad_q [m][3] (may be NULL) receives s(q) (q - y) / d(q), y the closest
+ * surface point: d(sdf_q)/dq where the closest point is unique and d > 0;
+ * zero where d = 0.  Non-finite q give NaN and a zero gradient; an empty
+ * surface gives +/-infinity.  Queries may lie anywhere (no clamping of the
+ * distance).  The queries are sorted internally in chunks of
+ * max(max_points, min(2^20, max(65536, max_res^3 / 4))), in the
+ * normal-estimation workspace.  Needs a prior
+ * wgeo_reconstruct on this handle (else WGEO_ERR_NO_FORWARD). */
+int wgeo_query_exact(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* grad_q, void* stream);
 
 /* Backward (Sec. 2.5, Eqs. 35-39): given dL/dphi on the grid (d_sdf_grid
  * [res^3] or NULL), dL/dn on the grid (d_nrm_grid [3][res^3] or NULL) and/or

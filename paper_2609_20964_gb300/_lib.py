@@ -25,7 +25,7 @@ STATUS_NOT_CONVERGED = 1 << 3
 STATUS_MESH_CAPACITY = 1 << 4
 
 STAGES = ("splat", "solve", "iso", "mc", "sdf", "normals", "query", "bwd_seed",
-          "bwd_surface", "bwd_solve", "bwd_splat", "sdf_tie", "point_pca", "orient")
+          "bwd_surface", "bwd_solve", "bwd_splat", "sdf_tie", "point_pca", "orient", "query_exact")
 
 PREC_MIXED = 0
 PREC_FP32 = 1
@@ -60,6 +60,7 @@ SIGNATURES = {
     "wgeo_destroy": (C.c_int, [_vp]),
     "wgeo_reconstruct": (C.c_int, [_vp, _vp, _vp, _i64, C.POINTER(_f32), _i32, _vp, _vp, _vp]),
     "wgeo_query": (C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "wgeo_query_exact": (C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "wgeo_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "wgeo_estimate_normals": (C.c_int, [_vp, _vp, _i64, C.POINTER(_f32), _f32, _f32, _vp, _vp, _vp]),
     "wgeo_orient_normals": (C.c_int, [_vp, _vp, _i64, C.POINTER(_f32), _f32, _i32, _vp, _vp, _vp, _vp]),

@@ -91,6 +91,17 @@ class Reconstructor:
         L.check(rc, "wgeo_query")
         return sdf_q, nrm_q
 
+    def query_exact(self, q: torch.Tensor, with_grad: bool = True, stream=None):
+        """Exact signed distance to the reconstructed surface at q [m, 3] and
+        its gradient (Sec. 2.4 off the grid).  Returns (sdf [m], grad [m, 3] or None)."""
+        m = int(q.shape[0])
+        sdf_q = torch.empty((m,), device=self.device, dtype=torch.float32)
+        grad = torch.empty((m, 3), device=self.device, dtype=torch.float32) if with_grad else None
+        rc = self.lib.wgeo_query_exact(self.h, _dev(q, "q", 3), m, _dev(sdf_q, "sdf_q"), _dev(grad, "grad"),
+                                       C.c_void_p(_stream(stream)))
+        L.check(rc, "wgeo_query_exact")
+        return sdf_q, grad
+
     def backward(self, d_sdf_grid=None, d_nrm_grid=None, q=None, d_sdf_q=None, d_nrm_q=None,
                  want_dq: bool = False, stream=None):
         m = int(q.shape[0]) if q is not None else 0

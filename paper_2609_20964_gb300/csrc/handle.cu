@@ -25,7 +25,7 @@ struct Layout {
       off_scan, off_state, off_dp_cell, off_dp_count, off_dp_off, off_dp_cursor, off_dp_scan, off_dp_tmp,
       off_dp_sorted, off_dp_key, off_dp_gbox, off_or_scal;
   size_t n_partials, n_scan, n_dp_scan;
-  int64_t dp_cap;
+  int64_t dp_cap, dp_points;
   int64_t cap;
 };
 
@@ -91,15 +91,20 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.off_state = take(c, sizeof(DevState));
   // normal estimation: per point a cell, a key and two float4 copies, per
   // kDpcaBox points a box, per cell a count, an offset and a cursor
-  L.dp_cap = point_grid_cap(P);
-  L.off_dp_cell = take(c, 4 * Pp);
-  L.off_dp_tmp = take(c, 16 * Pp);
-  L.off_dp_sorted = take(c, 16 * Pp);
+  // the same buffers sort exact queries, in chunks of Pd: up to 2^20 (one
+  // chunk for a million queries on large grids, where a chunk of a few
+  // hundred thousand leaves the search with too few warps per wave)
+  const size_t Pd = std::max<size_t>(Pp, std::min<size_t>((size_t)1 << 20, std::max<size_t>(65536, N / 4)));
+  L.dp_points = (int64_t)Pd;
+  L.dp_cap = point_grid_cap((int64_t)Pd);
+  L.off_dp_cell = take(c, 4 * Pd);
+  L.off_dp_tmp = take(c, 16 * Pd);
+  L.off_dp_sorted = take(c, 16 * Pd);
   L.off_dp_count = take(c, 4 * ((size_t)L.dp_cap + 1));
   L.off_dp_off = take(c, 4 * ((size_t)L.dp_cap + 2));
   L.off_dp_cursor = take(c, 4 * ((size_t)L.dp_cap + 1));
-  L.off_dp_key = take(c, 4 * Pp);
-  L.off_dp_gbox = take(c, 32 * ((Pp + kDpcaBox - 1) / kDpcaBox));
+  L.off_dp_key = take(c, 4 * Pd);
+  L.off_dp_gbox = take(c, 32 * ((Pd + kDpcaBox - 1) / kDpcaBox));
   L.off_or_scal = take(c, 16 * sizeof(unsigned));
   L.n_dp_scan = scan_tmp_size((int)L.dp_cap);
   L.off_dp_scan = take(c, 4 * L.n_dp_scan);
@@ -281,6 +286,7 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->scan_tmp_elems = L.n_scan;
   h->dstate = (DevState*)(a + L.off_state);
   h->dp_cell_cap = L.dp_cap;
+  h->dp_points = L.dp_points;
   h->dp_cell = (int*)(a + L.off_dp_cell);
   h->dp_tmp = (float4*)(a + L.off_dp_tmp);
   h->dp_sorted = (float4*)(a + L.off_dp_sorted);
@@ -377,6 +383,19 @@ int wgeo_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* n
   const int slot = stage_begin(h, kStQuery, s);
   int rc = launch_query(h, q, m, sdf_q, nrm_q, s);
   stage_end(h, kStQuery, slot, s);
+  h->last_stream = s;
+  return rc;
+}
+
+int wgeo_query_exact(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* grad_q, void* stream) {
+  if (!h || m < 0) return WGEO_ERR_INVALID_ARG;
+  if (m > 0 && (!q || !sdf_q)) return WGEO_ERR_INVALID_ARG;
+  if (!h->have_forward) return WGEO_ERR_NO_FORWARD;
+  if (cudaSetDevice(h->device) != cudaSuccess) return WGEO_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int slot = stage_begin(h, kStQueryExact, s);
+  int rc = launch_query_exact(h, q, m, sdf_q, grad_q, s);
+  stage_end(h, kStQueryExact, slot, s);
   h->last_stream = s;
   return rc;
 }

@@ -970,6 +970,334 @@ __global__ void normals_kernel(const float* __restrict__ phi, int n, double h,
   }
 }
 
+// ---- exact signed distance at arbitrary query points (Sec. 2.4, Eqs. 29-34,
+// evaluated off the grid).  Two kernels: the distance search over queries
+// sorted by cell (a warp of 32 neighbouring queries walks the octree as the
+// node search does), then the sign, one thread per query.
+
+// Distance search.  The cut starts from an upper bound: the nearest node's
+// |phi| plus the node's distance to q (triangle inequality), widened for the
+// float rounding of both; with the nodes' closest triangles kept (SEEDS),
+// those of the 8 nodes around q are offered first.  Writes the unsigned distance and the unit
+// direction (q - y) / |q - y| to the closest surface point y (zero when q is
+// on the surface, infinite distance when the mesh is empty).
+template <bool SEEDS>
+__global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* __restrict__ phi, SurfParams g,
+                                                                const float4* __restrict__ tris_s,
+                                                                const int* __restrict__ leaf_off, int64_t cap,
+                                                                const float4* __restrict__ pyr, PyrInfo pi,
+                                                                const float4* __restrict__ sorted,
+                                                                const int* __restrict__ total,
+                                                                const int* __restrict__ ctri,
+                                                                float* __restrict__ dist_out,
+                                                                float* __restrict__ dir_out) {
+  __shared__ unsigned int s_node[kWarps][kStack];
+  __shared__ long long s_off[12];
+  __shared__ int s_dim[12];
+  if (threadIdx.x < 12) {
+    s_off[threadIdx.x] = pi.off[threadIdx.x];
+    s_dim[threadIdx.x] = pi.dim[threadIdx.x];
+  }
+  __syncthreads();
+  const int m = *total;
+  const int n = g.res;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float coord = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    coord = fmaxf(coord, (float)fmax(fabs(g.lo[a]), fabs(g.lo[a] + n * g.h)));
+  const int top = pi.nlev - 1;
+  const int nb = (s_dim[0] + 1) / 2;
+  unsigned int* stk = s_node[w];
+  const int nwarps = gridDim.x * kWarps;
+  for (int base = (blockIdx.x * kWarps + w) * 32; base < m; base += nwarps * 32) {
+    const int k = base + lane;
+    const bool valid = k < m;
+    const float4 e = sorted[valid ? k : base];
+    const float3 p = make_float3(e.x, e.y, e.z);
+    // nearest node and the bound |phi(node)| + |q - node|
+    int ni[3];
+    const float pq[3] = {e.x, e.y, e.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double f = ((double)pq[a] - g.lo[a]) / g.h - 0.5;
+      ni[a] = (int)fmin(fmax(rint(f), 0.0), (double)(n - 1));
+    }
+    const int64_t o = lin3(ni[0], ni[1], ni[2], n);
+    const float3 nd = make_float3((float)(g.lo[0] + (ni[0] + 0.5) * g.h), (float)(g.lo[1] + (ni[1] + 0.5) * g.h),
+                                  (float)(g.lo[2] + (ni[2] + 0.5) * g.h));
+    const float dn = sqrtf((p.x - nd.x) * (p.x - nd.x) + (p.y - nd.y) * (p.y - nd.y) + (p.z - nd.z) * (p.z - nd.z));
+    const float bnd = (fabsf(phi[o]) + dn) * (1.f + 1e-5f) + 1e-6f * coord;
+    float cut = valid ? bnd * bnd : -INFINITY;
+    float cd = INFINITY;
+    int ct = -1;
+    auto offer = [&](float d2, int t) {
+      if (d2 < cut && d2 < cd) {
+        cd = d2;
+        ct = t;
+        cut = d2;
+      }
+    };
+    if (SEEDS && valid) {
+      // the closest triangles of the 8 nodes around q
+      int c0[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double f = ((double)pq[a] - g.lo[a]) / g.h - 0.5;
+        c0[a] = (int)fmin(fmax(floor(f), 0.0), (double)(n - 2));
+      }
+#pragma unroll 1
+      for (int qn = 0; qn < 8; ++qn) {
+        const int t = ctri[lin3(c0[0] + (qn & 1), c0[1] + ((qn >> 1) & 1), c0[2] + (qn >> 2), n)];
+        if (t >= 0) offer(tri_dist2_rec(p, tris_s + kTriRec * (int64_t)t), t);
+      }
+    }
+    int sp = 1;
+    if (lane == 0) stk[0] = pack_node(top, 0, 0, 0);
+    __syncwarp();
+    while (sp > 0) {
+      --sp;
+      const unsigned en = stk[sp];
+      __syncwarp();
+      const int lev = (int)(en >> 27);
+      const int x = (int)(en & 511u), y = (int)((en >> 9) & 511u), z = (int)((en >> 18) & 511u);
+      const int dp = s_dim[lev];
+      const int64_t gi = s_off[lev] + ((int64_t)z * dp + y) * dp + x;
+      const float lb = puck_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
+      if (!__any_sync(0xffffffffu, lb < cut)) continue;
+      if (lev == 0) {
+        const int li = leaf_index(x, y, z, nb);
+        const int64_t s0 = leaf_off[li];
+        const int64_t s1 = min((int64_t)leaf_off[li + 1], cap);
+        for (int64_t t = s0; t < s1; ++t) offer(tri_dist2_rec(p, tris_s + kTriRec * t), (int)t);
+        continue;
+      }
+      const int dc = s_dim[lev - 1];
+      const int64_t cbase = s_off[lev - 1];
+      float key[8];
+      unsigned ent[8];
+      int nc = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
+        if (cx >= dc || cy >= dc || cz >= dc) continue;
+        const int64_t cg = cbase + ((int64_t)cz * dc + cy) * dc + cx;
+        const float4 A = pyr[2 * cg];
+        if (A.w < 0.f) continue;
+        const float d = puck_dist2(p, A, pyr[2 * cg + 1]);
+        if (!__any_sync(0xffffffffu, d < cut)) continue;
+        const float dm = __shfl_sync(0xffffffffu, d, 0);
+        int q2 = nc;
+        while (q2 > 0 && key[q2 - 1] < dm) {
+          key[q2] = key[q2 - 1];
+          ent[q2] = ent[q2 - 1];
+          --q2;
+        }
+        key[q2] = dm;
+        ent[q2] = pack_node(lev - 1, cx, cy, cz);
+        ++nc;
+      }
+      if (lane == 0)
+        for (int q = 0; q < nc && sp + q < kStack; ++q) stk[sp + q] = ent[q];
+      sp = min(sp + nc, kStack);
+      __syncwarp();
+    }
+    if (!valid) continue;
+    const int idx = __float_as_int(e.w);
+    float3 dir = make_float3(0.f, 0.f, 0.f);
+    if (ct >= 0 && cd > 0.f) {
+      // residual q - y of the closest point y, as in the distance itself
+      const float4* rec = tris_s + kTriRec * (int64_t)ct;
+      const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
+      const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+      const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
+      const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
+      float v, wt;
+      rec_weights(ap, d1, d2, r0, r1, r2, r3, v, wt);
+      const float3 r = make_float3(ap.x - v * r1.x - wt * r2.x, ap.y - v * r1.y - wt * r2.y,
+                                   ap.z - v * r1.z - wt * r2.z);
+      const float len = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+      if (len > 0.f) dir = make_float3(r.x / len, r.y / len, r.z / len);
+    }
+    dist_out[idx] = ct >= 0 ? sqrtf(cd) : INFINITY;
+    if (dir_out) {
+      dir_out[3 * (int64_t)idx] = dir.x;
+      dir_out[3 * (int64_t)idx + 1] = dir.y;
+      dir_out[3 * (int64_t)idx + 2] = dir.z;
+    }
+  }
+}
+
+__device__ __forceinline__ float orient3(float3 a, float3 b, float3 c, float3 d) {
+  // (a - d) . ((b - d) x (c - d))
+  const float3 ad = make_float3(a.x - d.x, a.y - d.y, a.z - d.z);
+  const float3 bd = make_float3(b.x - d.x, b.y - d.y, b.z - d.z);
+  const float3 cd = make_float3(c.x - d.x, c.y - d.y, c.z - d.z);
+  return ad.x * (bd.y * cd.z - bd.z * cd.y) + ad.y * (bd.z * cd.x - bd.x * cd.z) + ad.z * (bd.x * cd.y - bd.y * cd.x);
+}
+
+// Squared distance from p to triangle (a, b, c): the closest point by Voronoi
+// regions (Ericson, Real-Time Collision Detection, 5.1.5), in float.
+__device__ float pt_tri_dist2(float3 p, float3 a, float3 b, float3 c) {
+  const float3 ab = sub3(b, a), ac = sub3(c, a), ap = sub3(p, a);
+  const float d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+  float3 y;
+  if (d1 <= 0.f && d2 <= 0.f) {
+    y = a;
+  } else {
+    const float3 bp = sub3(p, b);
+    const float d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+    const float3 cp = sub3(p, c);
+    const float d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+    const float vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+    if (d3 >= 0.f && d4 <= d3) {
+      y = b;
+    } else if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+      const float t = d1 / (d1 - d3);
+      y = make_float3(a.x + t * ab.x, a.y + t * ab.y, a.z + t * ab.z);
+    } else if (d6 >= 0.f && d5 <= d6) {
+      y = c;
+    } else if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+      const float t = d2 / (d2 - d6);
+      y = make_float3(a.x + t * ac.x, a.y + t * ac.y, a.z + t * ac.z);
+    } else if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+      const float t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+      y = make_float3(b.x + t * (c.x - b.x), b.y + t * (c.y - b.y), b.z + t * (c.z - b.z));
+    } else {
+      const float den = va + vb + vc;
+      const float v = den != 0.f ? vb / den : 0.f, ww = den != 0.f ? vc / den : 0.f;
+      y = make_float3(a.x + v * ab.x + ww * ac.x, a.y + v * ab.y + ww * ac.y, a.z + v * ab.z + ww * ac.z);
+    }
+  }
+  const float3 r = sub3(p, y);
+  return dot3(r, r);
+}
+
+// Sign of every query by a parity test local to the cube that holds it (the
+// query clamped into the node hull, where no triangle lies between it and its
+// clamp): the segment from q to a corner v of the cube stays in the cube, so
+// only that cube's marching-cubes triangles, regenerated from chi exactly as
+// mc_emit_kernel writes them, can cross it; v's class is known (chi < c
+// inside), and an odd number of crossings gives q the other class.  v is the
+// corner farthest from the cube's triangles, so no triangle passes within
+// rounding of it, among the corners off every cube face that q lies on (so
+// the open segment avoids the faces, where triangles of the neighbouring cubes
+// meet this cube's); q exactly at a corner takes that node's class.  A crossing needs q and v strictly on opposite sides of the
+// triangle's plane and the line qv inside the triangle: the three orientations
+// of the line against the triangle's edges agree in sign.  Each edge's
+// orientation is evaluated once, in the order of its endpoints' global edge
+// ids, and negated for the triangle that runs it the other way, so a line
+// through an edge shared by two triangles counts for exactly one of them.  A
+// float orientation can be wrong only when q lies within rounding of a
+// triangle, where |phi| is of rounding size.  Non-finite queries get NaN and a
+// zero gradient.
+__global__ void query_sign_kernel(const float* __restrict__ q, int64_t m, const float* __restrict__ chi,
+                                  SurfParams g, const DevState* __restrict__ st, float* __restrict__ sdf_q,
+                                  float* __restrict__ nrm_q) {
+  const int n = g.res;
+  const double c = st->c;
+  const float c_up = st->c_up;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    const float x0 = q[3 * t], x1 = q[3 * t + 1], x2 = q[3 * t + 2];
+    if (!(isfinite(x0) && isfinite(x1) && isfinite(x2))) {
+      sdf_q[t] = __int_as_float(0x7fc00000);
+      if (nrm_q) nrm_q[3 * t] = nrm_q[3 * t + 1] = nrm_q[3 * t + 2] = 0.f;
+      continue;
+    }
+    const float xs[3] = {x0, x1, x2};
+    float qc[3];
+    int cc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double lo = g.lo[a] + 0.5 * g.h, hi = g.lo[a] + (n - 0.5) * g.h;
+      const double v = fmin(fmax((double)xs[a], lo), hi);
+      qc[a] = (float)v;
+      cc[a] = min((int)floor((v - g.lo[a]) / g.h - 0.5), n - 2);
+      cc[a] = max(cc[a], 0);
+    }
+    const int code = cube_code(chi, cc[0], cc[1], cc[2], n, c_up);
+    // faces of the cube that q lies on: the segment's corner must be on the
+    // opposite face, so that the open segment runs inside the cube (where only
+    // this cube's triangles are); at a corner q takes that node's class
+    int need_hi = 0, need_lo = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float flo = (float)(g.lo[a] + (cc[a] + 0.5) * g.h), fhi = (float)(g.lo[a] + (cc[a] + 1.5) * g.h);
+      if (qc[a] == flo) need_hi |= 1 << a;
+      if (qc[a] == fhi) need_lo |= 1 << a;
+    }
+    bool inside;
+    if ((need_hi | need_lo) == 7) {
+      const int corner = (need_lo & 1) | (((need_lo >> 1) & 1) << 1) | (((need_lo >> 2) & 1) << 2);
+      inside = ((code >> corner) & 1) != 0;
+    } else if (code == 0 || code == 255) {
+      inside = code == 255;
+    } else {
+      // the cube's triangles
+      float3 vt[kMaxTriPerCube][3];
+      int gid[kMaxTriPerCube][3];
+      const int ntri = c_mc_count[code];
+      for (int tr = 0; tr < ntri; ++tr)
+        for (int v = 0; v < 3; ++v) {
+          const int ed = c_mc_tris[code][tr][v];
+          int ox, oy, oz, ax;
+          edge_lower_offset(ed, ox, oy, oz, ax);
+          const int pi = cc[0] + ox, pj = cc[1] + oy, pk = cc[2] + oz;
+          const int64_t pl = lin3(pi, pj, pk, n);
+          const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+          const double c1 = (double)chi[pl], c2 = (double)chi[pl + stride];
+          const double eta = (c - c1) / (c2 - c1);
+          double pos[3] = {g.lo[0] + (pi + 0.5) * g.h, g.lo[1] + (pj + 0.5) * g.h, g.lo[2] + (pk + 0.5) * g.h};
+          pos[ax] += eta * g.h;
+          vt[tr][v] = make_float3((float)pos[0], (float)pos[1], (float)pos[2]);
+          gid[tr][v] = (int)(3 * pl + ax);
+        }
+      // the corner farthest from the triangles
+      int best_c = 0;
+      float best_d = -1.f;
+      float3 vpos = make_float3(0.f, 0.f, 0.f);
+      for (int qn = 0; qn < 8; ++qn) {
+        if ((qn & need_hi) != need_hi || (qn & need_lo) != 0) continue;
+        const float3 cp = make_float3((float)(g.lo[0] + (cc[0] + (qn & 1) + 0.5) * g.h),
+                                      (float)(g.lo[1] + (cc[1] + ((qn >> 1) & 1) + 0.5) * g.h),
+                                      (float)(g.lo[2] + (cc[2] + (qn >> 2) + 0.5) * g.h));
+        float dmin = INFINITY;
+        for (int tr = 0; tr < ntri; ++tr) dmin = fminf(dmin, pt_tri_dist2(cp, vt[tr][0], vt[tr][1], vt[tr][2]));
+        if (dmin > best_d) {
+          best_d = dmin;
+          best_c = qn;
+          vpos = cp;
+        }
+      }
+      const float3 qp = make_float3(qc[0], qc[1], qc[2]);
+      int cross = 0;
+      for (int tr = 0; tr < ntri; ++tr) {
+        const float sq = orient3(vt[tr][0], vt[tr][1], vt[tr][2], qp);
+        const float sv = orient3(vt[tr][0], vt[tr][1], vt[tr][2], vpos);
+        if (!((sq > 0.f && sv < 0.f) || (sq < 0.f && sv > 0.f))) continue;
+        int sg[3];
+        for (int ei = 0; ei < 3; ++ei) {
+          const int a = ei, b = (ei + 1) % 3;
+          const bool fwd = gid[tr][a] < gid[tr][b];
+          const float3 A = fwd ? vt[tr][a] : vt[tr][b], B = fwd ? vt[tr][b] : vt[tr][a];
+          const int sgn = orient3(qp, vpos, A, B) >= 0.f ? 1 : -1;
+          sg[ei] = fwd ? sgn : -sgn;
+        }
+        cross += (sg[0] == sg[1] && sg[1] == sg[2]) ? 1 : 0;
+      }
+      inside = (((code >> best_c) & 1) != 0) != ((cross & 1) != 0);
+    }
+    if (inside) {
+      sdf_q[t] = -sdf_q[t];
+      if (nrm_q) {
+        nrm_q[3 * t] = -nrm_q[3 * t];
+        nrm_q[3 * t + 1] = -nrm_q[3 * t + 1];
+        nrm_q[3 * t + 2] = -nrm_q[3 * t + 2];
+      }
+    }
+  }
+}
+
 PyrInfo pyramid_info(int nl) {
   PyrInfo pi;
   int d = nl;
@@ -1113,6 +1441,42 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
     WGEO_LAUNCH_CHECK();
     stage_end(h, kStNormals, slot, s);
   }
+  return WGEO_OK;
+}
+
+int launch_query_exact(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s) {
+  if (m == 0) return WGEO_OK;
+  SurfParams g;
+  for (int a = 0; a < 3; ++a) g.lo[a] = h->lo[a];
+  g.h = h->h;
+  g.res = h->res;
+  g.nb = div_up(h->res - 1, kBrick);
+  const PyrInfo pi = pyramid_info(2 * g.nb);
+  const int* ctri = h->opt.keep_for_backward ? h->ctri : nullptr;
+  // queries sorted by (cell of 8 h, sub-cell key), so that a warp's 32
+  // queries lie close together, in chunks the point-grid workspace holds
+  const float box[6] = {(float)g.lo[0], (float)g.lo[1], (float)g.lo[2], (float)(g.lo[0] + g.res * g.h),
+                        (float)(g.lo[1] + g.res * g.h), (float)(g.lo[2] + g.res * g.h)};
+  const int64_t chunk = h->dp_points;
+  for (int64_t c0 = 0; c0 < m; c0 += chunk) {
+    const int nq = (int)std::min<int64_t>(chunk, m - c0);
+    PointGrid pg;
+    int rc = build_point_grid(h, q + 3 * c0, nq, box, 8.0 * g.h, true, nullptr, &pg, s);
+    if (rc) return rc;
+    const int* total = h->dp_off + pg.ncell;
+    const int nblk = grid_blocks((int64_t)nq, kWarps * 32, 152 * 8);
+    if (ctri)
+      sdf_query_kernel<true><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris_s, h->leaf_off, h->mesh_cap, h->pyramid,
+                                                          pi, h->dp_sorted, total, ctri, sdf_q + c0,
+                                                          nrm_q ? nrm_q + 3 * c0 : nullptr);
+    else
+      sdf_query_kernel<false><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris_s, h->leaf_off, h->mesh_cap,
+                                                           h->pyramid, pi, h->dp_sorted, total, nullptr, sdf_q + c0,
+                                                           nrm_q ? nrm_q + 3 * c0 : nullptr);
+    WGEO_LAUNCH_CHECK();
+  }
+  query_sign_kernel<<<grid_blocks(m, 128, 152 * 16), 128, 0, s>>>(q, m, h->chi32, g, h->dstate, sdf_q, nrm_q);
+  WGEO_LAUNCH_CHECK();
   return WGEO_OK;
 }
 

@@ -86,7 +86,8 @@ enum Stage {
   kStSDFTie = 11,  // near-tie decisions of the distance search
   kStPointPca = 12,  // D-PCA normal estimation
   kStOrient = 13,    // parity orientation
-  kStages = 14
+  kStQueryExact = 14,  // exact off-grid signed distance
+  kStages = 15
 };
 constexpr int kRing = 256;
 
@@ -268,6 +269,7 @@ struct wgeo_handle {
   // normal estimation (its own buffers: a call between a forward and its
   // backward leaves the forward's state intact)
   int64_t dp_cell_cap = 0;       // cells the workspace holds
+  int64_t dp_points = 0;         // points it holds (exact queries are sorted in chunks of this size)
   int* dp_cell = nullptr;        // cell per point (original order); -1 = non-finite
   int* dp_count = nullptr;       // dp_cell_cap + 1
   int* dp_off = nullptr;         // dp_cell_cap + 2 (exclusive scan, total last)
@@ -365,6 +367,8 @@ size_t pyramid_aux_nodes(int nb);   // nodes of the levels above the leaves
 void host_mc_table(int* counts, int* tris);
 // query.cu
 int launch_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s);
+// surface.cu: exact signed distance and its gradient at arbitrary points
+int launch_query_exact(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s);
 int launch_export_adjoint(wgeo_handle* h, int which, float* out, cudaStream_t s);
 int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
                     const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,

@@ -1,0 +1,133 @@
+"""Exact off-grid signed distance (Sec. 2.4, Eqs. 29-34 at arbitrary points)
+on the GPU vs the oracle, through the C ABI.
+
+Bars: phi within 1e-4 of the box extent (as on the grid); the sign equal
+wherever |phi| exceeds that; the gradient within 0.1 degree where the
+oracle's closest point is unique and |phi| > 1e-3 (there phi is smooth).
+The oracle works on its own reconstruction (its own mesh), so its distances
+and the GPU's differ by the mesh's own parity error."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pipeline as OP
+from oracle import query_exact as QE
+from oracle import sdf as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+BBOX = np.array([0, 0, 0, 1, 1, 1], dtype=np.float32)
+SDF_TOL = 1e-4
+ANGLE_TOL_DEG = 0.1
+
+
+@pytest.fixture(scope="module")
+def W():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2609_20964_gb300 import Reconstructor
+    torch.cuda.set_device(0)
+    return Reconstructor
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _queries(p, n, seed, m=1500):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-0.1, 1.1, (m, 3))                          # anywhere, also outside the box
+    i = rng.choice(len(p), m, replace=False)
+    b = p[i] + n[i] * rng.uniform(-0.05, 0.05, (m, 1))           # near the surface, both sides
+    return np.r_[a, b].astype(np.float32)
+
+
+def _angle_deg(a, b):
+    c = np.sum(a * b, axis=1) / (np.linalg.norm(a, axis=1) * np.linalg.norm(b, axis=1))
+    return np.degrees(np.arccos(np.clip(c, -1, 1)))
+
+
+def _check(sq, gq, q, ref, min_unique=0.9):
+    verts = ref.mesh["verts"]
+    ophi, ograd, _ = QE.query_exact(q.astype(np.float64), verts)
+    assert np.abs(sq - ophi).max() <= SDF_TOL
+    clear = np.abs(ophi) > SDF_TOL
+    assert np.array_equal(np.sign(sq[clear]), np.sign(ophi[clear]))
+    amb = S.closest_point_ambiguous(q.astype(np.float64), verts, np.abs(ophi), 1e-6, 1e-4)
+    ok = (~amb) & (np.abs(ophi) > 1e-3)
+    assert ok.mean() > min_unique
+    assert _angle_deg(gq[ok], ograd[ok]).max() <= ANGLE_TOL_DEG
+    assert np.abs(np.linalg.norm(gq[ok], axis=1) - 1).max() < 1e-5
+
+
+@pytest.mark.parametrize("keep", [1, 0])
+def test_exact_queries_match_the_oracle(W, keep):
+    p, n, _ = synth.sh_body_cloud(6000, seed=22, noise=0.002)
+    res = 44
+    rec = W(res, len(p), keep_for_backward=keep)
+    rec.reconstruct(_t(p), _t(n), BBOX, res)
+    q = _queries(p, n, 3)
+    sq, gq = rec.query_exact(_t(q))
+    torch.cuda.synchronize()
+    ref = OP.forward_to_mesh(p, n, BBOX, res)
+    _check(sq.cpu().numpy(), gq.cpu().numpy(), q, ref)
+    rec.close()
+
+
+def test_grid_nodes_reproduce_the_grid(W):
+    # at the nodes the exact query is the grid's phi (the sign from the local
+    # parity equals the indicator class)
+    p, n = synth.sphere_cloud(1500, seed=21)
+    res = 24
+    rec = W(res, len(p))
+    sdf, _ = rec.reconstruct(_t(p), _t(n), BBOX, res, with_normals=False)
+    h = 1.0 / res
+    k, j, i = np.meshgrid(np.arange(res), np.arange(res), np.arange(res), indexing="ij")
+    nodes = np.c_[(i.ravel() + 0.5) * h, (j.ravel() + 0.5) * h, (k.ravel() + 0.5) * h].astype(np.float32)
+    sq, _ = rec.query_exact(_t(nodes), with_grad=False)
+    torch.cuda.synchronize()
+    g = sdf.cpu().numpy().reshape(-1)
+    e = sq.cpu().numpy()
+    assert np.array_equal(np.sign(e), np.sign(g))
+    assert np.abs(e - g).max() <= 1e-6
+    rec.close()
+
+
+def test_edge_cases(W):
+    from paper_2609_20964_gb300 import WgeoError
+    p, n = synth.sphere_cloud(1500, seed=23)
+    rec = W(24, len(p))
+    with pytest.raises(WgeoError) as ei:
+        rec.query_exact(_t(np.zeros((4, 3))))
+    assert ei.value.code == 4                                   # no forward yet
+    rec.reconstruct(_t(p), _t(n), BBOX, 24)
+    q = np.array([[np.nan, 0.5, 0.5], [0.5, 0.5, 0.5], [5.0, 5.0, 5.0], [0.5, np.inf, 0.5]], np.float32)
+    sq, gq = rec.query_exact(_t(q))
+    sq, gq = sq.cpu().numpy(), gq.cpu().numpy()
+    assert np.isnan(sq[0]) and np.isnan(sq[3]) and not gq[[0, 3]].any()
+    assert sq[1] < 0 and sq[2] > 0                              # centre inside, far point outside
+    assert abs(sq[2] - (np.sqrt(3) * 4.5 - 0.3)) < 0.01
+    e, g = rec.query_exact(torch.zeros((0, 3), device="cuda"))
+    assert e.shape == (0,)
+    rec.close()
+
+
+def test_full_size_sampled(W):
+    # the benchmark workload: 1M uniform queries on the 256^3 star body,
+    # sampled against the oracle's exact query on its own mesh
+    p, n, _ = synth.sh_body_cloud(200_000, lmax=8)
+    res = 256
+    rec = W(res, len(p))
+    rec.reconstruct(_t(p), _t(n), BBOX, res, with_normals=False)
+    q = synth.uniform_queries(1_000_000, seed=2001)
+    sq, gq = rec.query_exact(_t(q))
+    torch.cuda.synchronize()
+    assert rec.info()["status"] == 0
+    ref = OP.forward_to_mesh(p, n, BBOX, res)
+    idx = np.random.default_rng(19).choice(len(q), 150, replace=False)
+    # far uniform queries over a fine mesh (306k triangles) meet more
+    # near-ties between triangles with distinct closest points
+    _check(sq.cpu().numpy()[idx], gq.cpu().numpy()[idx], q[idx], ref, min_unique=0.75)
+    rec.close()
