@@ -175,8 +175,14 @@ def query(rec: Reconstruction, q):
 
 
 def backward(rec: Reconstruction, d_sdf_grid=None, d_nrm_grid=None, q=None,
-             d_sdf_q=None, d_nrm_q=None, return_parts: bool = False):
-    """(d_points [n,3], d_normals [n,3], d_q [m,3] or None)."""
+             d_sdf_q=None, d_nrm_q=None, return_parts: bool = False, q_exact=None, d_sdf_exact=None):
+    """(d_points [n,3], d_normals [n,3], d_q [m,3] or None).
+
+    q_exact / d_sdf_exact: seeds dL/dphi(q) of the exact off-grid distance
+    (Eqs. 30 and 33 at arbitrary q, `query_exact`).  They enter like the
+    node seeds, through the closest point of each query's closest triangle:
+    d phi / d y = -s u, u = (q - y) / |q - y|.  With them, the returned d_q is
+    that of the exact queries (s u times the seed)."""
     res, h, lo = rec.res, rec.h, rec.lo
     dphi = np.zeros((res, res, res))
     dn = np.zeros((3, res, res, res))
@@ -215,6 +221,18 @@ def backward(rec: Reconstruction, d_sdf_grid=None, d_nrm_grid=None, q=None,
     verts = rec.mesh["verts"]
     T = verts.shape[0]
     dP = np.zeros((T, 3, 3))
+    if q_exact is not None and d_sdf_exact is not None and T > 0:
+        from . import query_exact as QE
+        qe = as_f64(q_exact)
+        ge = np.asarray(d_sdf_exact, dtype=np.float64)
+        phi_e, grad_e, tri_e = QE.query_exact(qe, verts)
+        act_e = (ge != 0) & (tri_e >= 0)
+        y, bary = S.closest_point_triangle(qe[act_e], verts[tri_e[act_e], 0], verts[tri_e[act_e], 1],
+                                           verts[tri_e[act_e], 2])
+        coef = -ge[act_e, None] * grad_e[act_e]                        # -s u dL/dphi
+        for v in range(3):
+            np.add.at(dP[:, v, :], tri_e[act_e], bary[:, v:v + 1] * coef)
+        dq = grad_e * ge[:, None]
     flat = dphi.reshape(-1)
     act = np.nonzero(flat)[0]
     if T > 0 and len(act):

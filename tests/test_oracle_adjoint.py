@@ -77,3 +77,34 @@ def test_backward_linear_in_seeds(small_case):
     ab = PL.backward(rec, w["g"], w["gn"])
     assert np.allclose(ab[0], a[0] + b[0], rtol=1e-10, atol=1e-12)
     assert np.allclose(ab[1], a[1] + b[1], rtol=1e-10, atol=1e-12)
+
+
+def test_exact_query_seeds_match_central_fd(small_case):
+    # the adjoint of the exact off-grid distance (Eq. 33 at arbitrary q):
+    # central differences of sum g phi_exact(q) through the whole forward
+    from oracle import query_exact as QE
+    res, p, n, bbox, q, w, rec = small_case
+    rng = np.random.default_rng(9)
+    qe = rng.uniform(0.15, 0.85, (60, 3))
+    ge = rng.standard_normal(60)
+    dp, dn, dq = PL.backward(rec, q_exact=qe, d_sdf_exact=ge)
+
+    def loss(pp, nn, qq):
+        r = PL.forward_to_mesh(pp, nn, bbox, res, frozen_bins=rec.bins)
+        return float(np.sum(ge * QE.query_exact(qq, r.mesh["verts"])[0]))
+
+    eps = 1e-6
+    for i, ax in [(3, 0), (17, 2), (100, 1), (250, 0)]:
+        for arr, g, is_p in ((p, dp, True), (n, dn, False)):
+            a1, a2 = arr.copy(), arr.copy()
+            a1[i, ax] += eps
+            a2[i, ax] -= eps
+            f1 = loss(a1, n, qe) if is_p else loss(p, a1, qe)
+            f2 = loss(a2, n, qe) if is_p else loss(p, a2, qe)
+            assert (f1 - f2) / (2 * eps) == pytest.approx(g[i, ax], rel=1e-5, abs=1e-6 * np.abs(g).max())
+    for i, ax in [(4, 0), (20, 1), (41, 2)]:
+        q1, q2 = qe.copy(), qe.copy()
+        q1[i, ax] += eps
+        q2[i, ax] -= eps
+        fd = (loss(p, n, q1) - loss(p, n, q2)) / (2 * eps)
+        assert fd == pytest.approx(dq[i, ax], rel=1e-5, abs=1e-6 * np.abs(dq).max())
