@@ -237,6 +237,20 @@ int wgeo_estimate_normals(wgeo_handle* h, const float* points, int64_t n, const 
 int wgeo_orient_normals(wgeo_handle* h, const float* points, int64_t n, const float* bbox, float gamma,
                         int32_t n_tol, float* normals, int32_t* stats, float* rd_out, void* stream);
 
+/* Backward of exact queries (Sec. 2.5 with the off-grid distance of
+ * wgeo_query_exact): as wgeo_backward, with d_sdf_q [m] the seeds dL/dphi(q)
+ * of exact queries at q [m][3] (no normal seeds: the exact gradient is not
+ * differentiated again).  Each query's closest point y on its closest
+ * triangle carries dL/dP_v = -dL/dphi beta_v (grad phi)(q) to the triangle's
+ * vertices (beta the barycentric weights of y), and from there the chain is
+ * that of the node seeds.  d_q [m][3] (may be NULL) receives
+ * dL/dphi (grad phi)(q).  Grid seeds (d_sdf_grid, d_nrm_grid, either may be
+ * NULL) are added as in wgeo_backward.  The queries are searched again
+ * (chunked as in wgeo_query_exact).  Requires keep_for_backward. */
+int wgeo_backward_exact(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
+                        const float* d_sdf_q, int64_t m, float* d_points, float* d_normals, float* d_q,
+                        void* stream);
+
 /* Synchronises the stream of the handle's last call and copies the device
  * status into *out. */
 int wgeo_get_info(wgeo_handle* h, wgeo_info* out);

@@ -25,8 +25,8 @@ def __getattr__(name):
     if name in ("Reconstructor", "sh_surface", "sh_surface_backward"):
         from . import api
         return getattr(api, name)
-    if name in ("sdf_query", "sdf_grid", "sh_points", "WgeoQueryFunction", "WgeoGridFunction",
-                "SHSurfaceFunction"):
+    if name in ("sdf_query", "sdf_query_exact", "sdf_grid", "sh_points", "WgeoQueryFunction",
+                "WgeoExactQueryFunction", "WgeoGridFunction", "SHSurfaceFunction"):
         from . import autograd
         return getattr(autograd, name)
     if name in ("Server", "Request"):

@@ -61,6 +61,7 @@ SIGNATURES = {
     "wgeo_reconstruct": (C.c_int, [_vp, _vp, _vp, _i64, C.POINTER(_f32), _i32, _vp, _vp, _vp]),
     "wgeo_query": (C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "wgeo_query_exact": (C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "wgeo_backward_exact": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "wgeo_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "wgeo_estimate_normals": (C.c_int, [_vp, _vp, _i64, C.POINTER(_f32), _f32, _f32, _vp, _vp, _vp]),
     "wgeo_orient_normals": (C.c_int, [_vp, _vp, _i64, C.POINTER(_f32), _f32, _i32, _vp, _vp, _vp, _vp]),

@@ -149,6 +149,21 @@ class Reconstructor:
         L.check(rc, "wgeo_orient_normals")
         return normals, stats, rd
 
+    def backward_exact(self, q, d_sdf_q, d_sdf_grid=None, d_nrm_grid=None, want_dq: bool = False,
+                       stream=None):
+        """Adjoint of exact queries (and optional grid seeds): (d_points,
+        d_normals, d_q or None)."""
+        m = int(q.shape[0])
+        d_points = torch.empty((self.n, 3), device=self.device, dtype=torch.float32)
+        d_normals = torch.empty((self.n, 3), device=self.device, dtype=torch.float32)
+        d_q = torch.empty((m, 3), device=self.device, dtype=torch.float32) if (want_dq and m) else None
+        rc = self.lib.wgeo_backward_exact(self.h, _dev(d_sdf_grid, "d_sdf_grid"), _dev(d_nrm_grid, "d_nrm_grid"),
+                                          _dev(q, "q", 3), _dev(d_sdf_q, "d_sdf_q"), m,
+                                          _dev(d_points, "d_points"), _dev(d_normals, "d_normals"),
+                                          _dev(d_q, "d_q"), C.c_void_p(_stream(stream)))
+        L.check(rc, "wgeo_backward_exact")
+        return d_points, d_normals, d_q
+
     def info(self) -> dict:
         inf = L.Info()
         L.check(self.lib.wgeo_get_info(self.h, C.byref(inf)), "wgeo_get_info")

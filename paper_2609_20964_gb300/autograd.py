@@ -31,6 +31,28 @@ class WgeoQueryFunction(torch.autograd.Function):
         return dp, dn, dq, None, None, None
 
 
+class WgeoExactQueryFunction(torch.autograd.Function):
+    """(points, normals, q) -> exact phi(q) (off-grid distance to the
+    reconstructed surface, Sec. 2.4) through a Reconstructor; the gradient of
+    phi(q) is saved for d/dq and the mesh adjoint reruns the query search."""
+
+    @staticmethod
+    def forward(ctx, points, normals, q, recon: Reconstructor, bbox, res: int):
+        recon.reconstruct(points.contiguous(), normals.contiguous(), bbox, res,
+                          with_sdf=False, with_normals=False)
+        sdf_q, _ = recon.query_exact(q.contiguous(), with_grad=False)
+        ctx.recon = recon
+        ctx.save_for_backward(q)
+        return sdf_q
+
+    @staticmethod
+    def backward(ctx, g_sdf_q):
+        (q,) = ctx.saved_tensors
+        dp, dn, dq = ctx.recon.backward_exact(q.contiguous(), g_sdf_q.contiguous(),
+                                              want_dq=ctx.needs_input_grad[2])
+        return dp, dn, dq, None, None, None
+
+
 class WgeoGridFunction(torch.autograd.Function):
     """(points, normals) -> (phi grid [res]^3, normal grid [3][res]^3)."""
 
@@ -70,6 +92,10 @@ class SHSurfaceFunction(torch.autograd.Function):
 
 def sdf_query(points, normals, q, recon: Reconstructor, bbox, res: int):
     return WgeoQueryFunction.apply(points, normals, q, recon, bbox, res)
+
+
+def sdf_query_exact(points, normals, q, recon: Reconstructor, bbox, res: int):
+    return WgeoExactQueryFunction.apply(points, normals, q, recon, bbox, res)
 
 
 def sdf_grid(points, normals, recon: Reconstructor, bbox, res: int):

@@ -446,6 +446,20 @@ int wgeo_orient_normals(wgeo_handle* h, const float* points, int64_t n, const fl
   return rc;
 }
 
+int wgeo_backward_exact(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
+                        const float* d_sdf_q, int64_t m, float* d_points, float* d_normals, float* d_q,
+                        void* stream) {
+  if (!h || m < 0) return WGEO_ERR_INVALID_ARG;
+  if (!h->have_forward || !h->opt.keep_for_backward) return WGEO_ERR_NO_FORWARD;
+  if (h->npts > 0 && (!d_points || !d_normals)) return WGEO_ERR_INVALID_ARG;
+  if (m > 0 && (d_sdf_q || d_q) && !q) return WGEO_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return WGEO_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = launch_backward_exact(h, d_sdf_grid, d_nrm_grid, q, d_sdf_q, m, d_points, d_normals, d_q, s);
+  h->last_stream = s;
+  return rc;
+}
+
 int wgeo_get_info(wgeo_handle* h, wgeo_info* out) {
   if (!h || !out) return WGEO_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return WGEO_ERR_CUDA;

@@ -16,6 +16,8 @@
 //   5. divergence transpose dV = D^T lambda and the splat adjoint per point:
 //      dn_i = sum_o alpha_oi dV_o, dx_i += sum_o (n_i . dV_o) d alpha_oi / dx_i.
 // Scatters use FP64 atomics into FP64 grids.
+#include <algorithm>
+
 #include "wgeo_internal.cuh"
 
 namespace wgeo {
@@ -331,6 +333,77 @@ __global__ void dc_finalize_kernel(const double* __restrict__ partials, int nblo
   if (threadIdx.x == 0) st->dc = s;
 }
 
+// Adds a chunk's block partials of dL/dc to the running sum (chunks in order).
+__global__ void dc_add_kernel(const double* __restrict__ partials, int nblocks, DevState* st) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += partials[i];
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) st->dc += s;
+}
+
+// Adjoint of exact off-grid queries: phi(q) = s |q - y|, y = sum_v beta_v P_v
+// on the query's closest triangle, so dL/dP_v = -dL/dphi beta_v s u with
+// s u = (grad phi)(q), the gradient the forward query wrote; then through
+// the marching-cubes vertex P_v = node + eta h e_ax to chi and c, as for the
+// node seeds.  d_q = dL/dphi (grad phi)(q).  Queries with a non-finite
+// distance or none (empty surface) contribute nothing.
+__global__ void exact_adjoint_kernel(const float* __restrict__ q, int nq, const float* __restrict__ g_sdf,
+                                     const float* __restrict__ tsdf, const float* __restrict__ tgrad,
+                                     const int* __restrict__ ttri, const float* __restrict__ chi,
+                                     const DevState* __restrict__ st, const Tri* __restrict__ tris,
+                                     const float4* __restrict__ tris_s, QParams g, double* __restrict__ dchi,
+                                     double* __restrict__ partials, float* __restrict__ d_q) {
+  __shared__ double red[32];
+  const double cd = st->c;
+  const float c_hi = (float)cd, c_lo = (float)(cd - (double)c_hi);
+  const float hf = (float)g.h;
+  const unsigned un = (unsigned)g.res;
+  float2 dcacc = make_float2(0.f, 0.f);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+    const float gi = g_sdf[i], d = tsdf[i];
+    const int t = ttri[i];
+    const float us[3] = {tgrad[3 * (int64_t)i], tgrad[3 * (int64_t)i + 1], tgrad[3 * (int64_t)i + 2]};
+    const bool ok = gi != 0.f && isfinite(d) && t >= 0;
+    if (d_q) {
+      d_q[3 * (int64_t)i] = ok ? gi * us[0] : 0.f;
+      d_q[3 * (int64_t)i + 1] = ok ? gi * us[1] : 0.f;
+      d_q[3 * (int64_t)i + 2] = ok ? gi * us[2] : 0.f;
+    }
+    if (!ok || d == 0.f) continue;
+    const float3 p = make_float3(q[3 * (int64_t)i], q[3 * (int64_t)i + 1], q[3 * (int64_t)i + 2]);
+    const float4* rec = tris_s + kTriRec * (int64_t)t;
+    const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
+    const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+    const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
+    const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
+    float v, w;
+    rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
+    const float bw[3] = {fmaxf(1.f - v - w, 0.f), v, w};
+    const Tri tr = tris[t];
+    const float gv[3] = {tr.a.w, tr.b.w, tr.c.w};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (bw[k] == 0.f) continue;
+      const unsigned gid = (unsigned)__float_as_int(gv[k]);
+      const int ax = (int)(gid % 3u);
+      const unsigned pl = gid / 3u;
+      const unsigned stv = (ax == 0) ? 1u : (ax == 1 ? un : un * un);
+      const float c1 = chi[pl], c2 = chi[pl + stv];
+      const float den = c2 - c1;
+      const float cm = __fadd_rn(__fsub_rn(c_hi, c1), c_lo);
+      const float eta = cm / den;
+      const float deta = -gi * bw[k] * us[ax] * hf;
+      const float wq = deta / den;
+      atomicAdd(&dchi[pl], (double)(wq * (eta - 1.f)));
+      atomicAdd(&dchi[pl + stv], (double)(-wq * eta));
+      dcacc = ff_add_f(dcacc, wq);
+    }
+  }
+  const double s = block_sum<256>((double)dcacc.x + (double)dcacc.y, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 // Iso-value adjoint: dchi += dc/N_p * w at the 8 corners; d_points = dc/N_p * sum dw chi.
 __global__ void iso_adjoint_kernel(const int* __restrict__ pcell, const float4* __restrict__ pfrac,
                                    int64_t np, const float* __restrict__ chi,
@@ -506,41 +579,45 @@ int launch_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float*
   return WGEO_OK;
 }
 
-int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
-                    const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,
-                    float* d_normals, float* d_q, cudaStream_t s) {
-  const int res = h->res;
-  const int64_t N = (int64_t)res * res * res;
-  const QParams g = qparams(h);
-  int slot = stage_begin(h, kStBwdSeed, s);
+namespace {
+
+// Seeds on the grid (phi and normal seeds): dphi64 cleared and filled.
+int backward_grid_seeds(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, cudaStream_t s) {
+  const int64_t N = (int64_t)h->res * h->res * h->res;
   WGEO_CUDA_TRY(cudaMemsetAsync(h->dphi64, 0, sizeof(double) * N, s));
   WGEO_CUDA_TRY(cudaMemsetAsync(h->dchi64, 0, sizeof(double) * N, s));
   if (d_sdf_grid || d_nrm_grid) {
-    grid_seed_kernel<<<grid_blocks(N, 256, 152 * 32), 256, 0, s>>>(d_sdf_grid, d_nrm_grid, h->phi, g,
+    grid_seed_kernel<<<grid_blocks(N, 256, 152 * 32), 256, 0, s>>>(d_sdf_grid, d_nrm_grid, h->phi, qparams(h),
                                                                    h->dphi64);
     WGEO_LAUNCH_CHECK();
   }
-  if (m > 0 && q && (d_sdf_q || d_nrm_q || d_q)) {
-    query_adjoint_kernel<<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, g, h->phi, d_sdf_q, d_nrm_q,
-                                                                       h->dphi64, d_q);
-    WGEO_LAUNCH_CHECK();
-  }
-  stage_end(h, kStBwdSeed, slot, s);
-  slot = stage_begin(h, kStBwdSurf, s);
+  return WGEO_OK;
+}
+
+// Node phi seeds through the closest triangles and marching cubes to dchi64
+// and dL/dc (dstate->dc).
+int backward_mesh_nodes(wgeo_handle* h, cudaStream_t s) {
+  const int64_t N = (int64_t)h->res * h->res * h->res;
   const int nb = grid_blocks(N, 256, kPartials);
-  sdf_mc_adjoint_kernel<<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, h->tris_s, g,
+  sdf_mc_adjoint_kernel<<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, h->tris_s, qparams(h),
                                            h->dchi64, h->partials);
   WGEO_LAUNCH_CHECK();
   dc_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, nb, h->dstate);
   WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+// From dchi64 and dL/dc: iso-value adjoint, adjoint solve, splat adjoint.
+int backward_tail(wgeo_handle* h, float* d_points, float* d_normals, cudaStream_t s) {
+  const QParams g = qparams(h);
   if (h->npts > 0) {
     iso_adjoint_kernel<<<grid_blocks(h->npts, 256, 152 * 32), 256, 0, s>>>(
         h->pcell, h->pfrac, h->npts, h->chi32, h->dstate, g, h->dchi64, d_points);
     WGEO_LAUNCH_CHECK();
   }
-  stage_end(h, kStBwdSurf, slot, s);
-  slot = stage_begin(h, kStBwdSolve, s);
-  int rc = launch_solve(h, res, 1, true, s);
+  stage_end(h, kStBwdSurf, h->bwd_slot, s);
+  int slot = stage_begin(h, kStBwdSolve, s);
+  int rc = launch_solve(h, h->res, 1, true, s);
   if (rc) return rc;
   stage_end(h, kStBwdSolve, slot, s);
   slot = stage_begin(h, kStBwdSplat, s);
@@ -552,6 +629,59 @@ int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_
   }
   stage_end(h, kStBwdSplat, slot, s);
   return WGEO_OK;
+}
+
+}  // namespace
+
+int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
+                    const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,
+                    float* d_normals, float* d_q, cudaStream_t s) {
+  int slot = stage_begin(h, kStBwdSeed, s);
+  int rc = backward_grid_seeds(h, d_sdf_grid, d_nrm_grid, s);
+  if (rc) return rc;
+  if (m > 0 && q && (d_sdf_q || d_nrm_q || d_q)) {
+    query_adjoint_kernel<<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, qparams(h), h->phi, d_sdf_q, d_nrm_q,
+                                                                       h->dphi64, d_q);
+    WGEO_LAUNCH_CHECK();
+  }
+  stage_end(h, kStBwdSeed, slot, s);
+  h->bwd_slot = stage_begin(h, kStBwdSurf, s);
+  rc = backward_mesh_nodes(h, s);
+  if (rc) return rc;
+  return backward_tail(h, d_points, d_normals, s);
+}
+
+int launch_backward_exact(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
+                          const float* d_sdf_q, int64_t m, float* d_points, float* d_normals, float* d_q,
+                          cudaStream_t s) {
+  int slot = stage_begin(h, kStBwdSeed, s);
+  int rc = backward_grid_seeds(h, d_sdf_grid, d_nrm_grid, s);
+  if (rc) return rc;
+  stage_end(h, kStBwdSeed, slot, s);
+  h->bwd_slot = stage_begin(h, kStBwdSurf, s);
+  rc = backward_mesh_nodes(h, s);
+  if (rc) return rc;
+  // exact queries, chunk by chunk: the forward query again (distance, the
+  // gradient and the closest triangle, held in the point-grid scratch that
+  // the query's sort no longer needs), then their adjoint
+  const int64_t P = h->dp_points;
+  float* tsdf = reinterpret_cast<float*>(h->dp_tmp);
+  float* tgrad = tsdf + P;
+  int* ttri = h->dp_key;
+  for (int64_t c0 = 0; c0 < m && d_sdf_q; c0 += P) {
+    const int nq = (int)std::min<int64_t>(P, m - c0);
+    rc = launch_query_exact_chunk(h, q + 3 * c0, nq, tsdf, tgrad, ttri, s);
+    if (rc) return rc;
+    const int nb = grid_blocks(nq, 256, kPartials);
+    exact_adjoint_kernel<<<nb, 256, 0, s>>>(q + 3 * c0, nq, d_sdf_q + c0, tsdf, tgrad, ttri, h->chi32, h->dstate,
+                                            h->tris, h->tris_s, qparams(h), h->dchi64, h->partials,
+                                            d_q ? d_q + 3 * c0 : nullptr);
+    WGEO_LAUNCH_CHECK();
+    dc_add_kernel<<<1, 1024, 0, s>>>(h->partials, nb, h->dstate);
+    WGEO_LAUNCH_CHECK();
+  }
+  if (!d_sdf_q && d_q && m > 0) WGEO_CUDA_TRY(cudaMemsetAsync(d_q, 0, sizeof(float) * 3 * (size_t)m, s));
+  return backward_tail(h, d_points, d_normals, s);
 }
 
 }  // namespace wgeo

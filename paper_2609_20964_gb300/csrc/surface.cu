@@ -990,7 +990,8 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
                                                                 const int* __restrict__ total,
                                                                 const int* __restrict__ ctri,
                                                                 float* __restrict__ dist_out,
-                                                                float* __restrict__ dir_out) {
+                                                                float* __restrict__ dir_out,
+                                                                int* __restrict__ tri_out) {
   __shared__ unsigned int s_node[kWarps][kStack];
   __shared__ long long s_off[12];
   __shared__ int s_dim[12];
@@ -1120,6 +1121,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
       if (len > 0.f) dir = make_float3(r.x / len, r.y / len, r.z / len);
     }
     dist_out[idx] = ct >= 0 ? sqrtf(cd) : INFINITY;
+    if (tri_out) tri_out[idx] = ct;
     if (dir_out) {
       dir_out[3 * (int64_t)idx] = dir.x;
       dir_out[3 * (int64_t)idx + 1] = dir.y;
@@ -1444,8 +1446,9 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   return WGEO_OK;
 }
 
-int launch_query_exact(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s) {
-  if (m == 0) return WGEO_OK;
+int launch_query_exact_chunk(wgeo_handle* h, const float* q, int nq, float* sdf_q, float* nrm_q, int* tri,
+                             cudaStream_t s) {
+  if (nq == 0) return WGEO_OK;
   SurfParams g;
   for (int a = 0; a < 3; ++a) g.lo[a] = h->lo[a];
   g.h = h->h;
@@ -1454,29 +1457,34 @@ int launch_query_exact(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, 
   const PyrInfo pi = pyramid_info(2 * g.nb);
   const int* ctri = h->opt.keep_for_backward ? h->ctri : nullptr;
   // queries sorted by (cell of 8 h, sub-cell key), so that a warp's 32
-  // queries lie close together, in chunks the point-grid workspace holds
+  // queries lie close together
   const float box[6] = {(float)g.lo[0], (float)g.lo[1], (float)g.lo[2], (float)(g.lo[0] + g.res * g.h),
                         (float)(g.lo[1] + g.res * g.h), (float)(g.lo[2] + g.res * g.h)};
-  const int64_t chunk = h->dp_points;
-  for (int64_t c0 = 0; c0 < m; c0 += chunk) {
-    const int nq = (int)std::min<int64_t>(chunk, m - c0);
-    PointGrid pg;
-    int rc = build_point_grid(h, q + 3 * c0, nq, box, 8.0 * g.h, true, nullptr, &pg, s);
-    if (rc) return rc;
-    const int* total = h->dp_off + pg.ncell;
-    const int nblk = grid_blocks((int64_t)nq, kWarps * 32, 152 * 8);
-    if (ctri)
-      sdf_query_kernel<true><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris_s, h->leaf_off, h->mesh_cap, h->pyramid,
-                                                          pi, h->dp_sorted, total, ctri, sdf_q + c0,
-                                                          nrm_q ? nrm_q + 3 * c0 : nullptr);
-    else
-      sdf_query_kernel<false><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris_s, h->leaf_off, h->mesh_cap,
-                                                           h->pyramid, pi, h->dp_sorted, total, nullptr, sdf_q + c0,
-                                                           nrm_q ? nrm_q + 3 * c0 : nullptr);
-    WGEO_LAUNCH_CHECK();
-  }
-  query_sign_kernel<<<grid_blocks(m, 128, 152 * 16), 128, 0, s>>>(q, m, h->chi32, g, h->dstate, sdf_q, nrm_q);
+  PointGrid pg;
+  int rc = build_point_grid(h, q, nq, box, 8.0 * g.h, true, nullptr, &pg, s);
+  if (rc) return rc;
+  const int* total = h->dp_off + pg.ncell;
+  const int nblk = grid_blocks((int64_t)nq, kWarps * 32, 152 * 8);
+  if (ctri)
+    sdf_query_kernel<true><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris_s, h->leaf_off, h->mesh_cap, h->pyramid,
+                                                        pi, h->dp_sorted, total, ctri, sdf_q, nrm_q, tri);
+  else
+    sdf_query_kernel<false><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris_s, h->leaf_off, h->mesh_cap,
+                                                         h->pyramid, pi, h->dp_sorted, total, nullptr, sdf_q, nrm_q,
+                                                         tri);
   WGEO_LAUNCH_CHECK();
+  query_sign_kernel<<<grid_blocks(nq, 128, 152 * 16), 128, 0, s>>>(q, nq, h->chi32, g, h->dstate, sdf_q, nrm_q);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+int launch_query_exact(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s) {
+  // in chunks the point-grid workspace can sort
+  for (int64_t c0 = 0; c0 < m; c0 += h->dp_points) {
+    const int nq = (int)std::min<int64_t>(h->dp_points, m - c0);
+    int rc = launch_query_exact_chunk(h, q + 3 * c0, nq, sdf_q + c0, nrm_q ? nrm_q + 3 * c0 : nullptr, nullptr, s);
+    if (rc) return rc;
+  }
   return WGEO_OK;
 }
 

@@ -307,6 +307,7 @@ struct wgeo_handle {
 
   // per-stage event timers (allocated on first use when opt.stage_timing is set)
   wgeo::StageTimer* timers = nullptr;
+  int bwd_slot = -1;             // timer slot of the backward's surface stage
 };
 
 namespace wgeo {
@@ -369,6 +370,13 @@ void host_mc_table(int* counts, int* tris);
 int launch_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s);
 // surface.cu: exact signed distance and its gradient at arbitrary points
 int launch_query_exact(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float* nrm_q, cudaStream_t s);
+// one chunk of at most dp_points queries; tri (may be NULL) receives the closest triangles
+int launch_query_exact_chunk(wgeo_handle* h, const float* q, int nq, float* sdf_q, float* nrm_q, int* tri,
+                             cudaStream_t s);
+// query.cu: the backward with seeds of exact queries
+int launch_backward_exact(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
+                          const float* d_sdf_q, int64_t m, float* d_points, float* d_normals, float* d_q,
+                          cudaStream_t s);
 int launch_export_adjoint(wgeo_handle* h, int which, float* out, cudaStream_t s);
 int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, const float* q,
                     const float* d_sdf_q, const float* d_nrm_q, int64_t m, float* d_points,
