@@ -19,6 +19,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import divergence as D
+from . import galerkin_q1 as Q1
 from . import grid as G
 from . import iso as I
 from . import mc as M
@@ -50,6 +51,7 @@ class Reconstruction:
     nrm: np.ndarray | None = None          # [3,z,y,x]
     gmag: np.ndarray | None = None
     extra: dict = field(default_factory=dict)
+    operator: str = "lumped"               # "lumped": 7-point forms; "q1": unlumped Galerkin
 
 
 def as_f64(a):
@@ -60,11 +62,13 @@ def as_f64(a):
     return a.astype(np.float32).astype(np.float64)
 
 
-def forward_to_mesh(points, normals, bbox, res, frozen_bins=None):
+def forward_to_mesh(points, normals, bbox, res, frozen_bins=None, operator: str = "lumped"):
     """Stages up to and including marching cubes.
 
     ``frozen_bins`` replaces the central cells (used by finite-difference
-    checks, so that both sides differentiate the same smooth branch)."""
+    checks, so that both sides differentiate the same smooth branch).
+    ``operator``: "lumped" (the 7-point operator and face divergence) or "q1"
+    (the unlumped trilinear Galerkin forms of `galerkin_q1`)."""
     lo = G.grid_lo(bbox)
     h = G.grid_spacing(bbox, res)
     p = as_f64(points)
@@ -73,14 +77,21 @@ def forward_to_mesh(points, normals, bbox, res, frozen_bins=None):
     if frozen_bins is not None:
         bins = np.asarray(frozen_bins, dtype=np.int64)
     V = SP.splat(p, nr, bins, finite, lo, h, res)
-    b = D.divergence(V)
-    chi = P.solve(b)
+    if operator == "q1":
+        b = Q1.divergence27(V)
+        chi = Q1.solve27(b)
+    elif operator == "lumped":
+        b = D.divergence(V)
+        chi = P.solve(b)
+    else:
+        raise ValueError(operator)
     c = I.isovalue(chi, p, finite, lo, h, res)
     mesh = M.marching_cubes(chi, c, lo, h)
     if mesh["gid"].shape[0] == 0:
         status |= G.STATUS_EMPTY_SURFACE
     return Reconstruction(res=res, h=h, lo=lo, points=p, normals_in=nr, bins=bins,
-                          finite=finite, status=status, V=V, b=b, chi=chi, c=c, mesh=mesh)
+                          finite=finite, status=status, V=V, b=b, chi=chi, c=c, mesh=mesh,
+                          operator=operator)
 
 
 def node_xyz(lin, res, lo, h):
@@ -100,8 +111,9 @@ def sdf_at(rec: Reconstruction, lin):
     return sgn * d, d, tri
 
 
-def reconstruct(points, normals, bbox, res, with_normals: bool = True, frozen_bins=None):
-    rec = forward_to_mesh(points, normals, bbox, res, frozen_bins)
+def reconstruct(points, normals, bbox, res, with_normals: bool = True, frozen_bins=None,
+                operator: str = "lumped"):
+    rec = forward_to_mesh(points, normals, bbox, res, frozen_bins, operator)
     N = res ** 3
     phi, d, tri = sdf_at(rec, np.arange(N))
     rec.phi = phi.reshape(res, res, res)
@@ -273,8 +285,12 @@ def backward(rec: Reconstruction, d_sdf_grid=None, d_nrm_grid=None, q=None,
         chic = I.gather(rec.chi, corners)
         dpts_iso[fin] = np.einsum("nc,ncx->nx", chic, dw) * (dc / npf)
     # adjoint solve (L symmetric): lambda = L^+ P dchi
-    lam = P.solve(dchi)
-    dV = D.divergence_adjoint(lam)
+    if rec.operator == "q1":
+        lam = Q1.solve27(dchi)
+        dV = Q1.divergence27_adjoint(lam)
+    else:
+        lam = P.solve(dchi)
+        dV = D.divergence_adjoint(lam)
     dpts, dnrm = SP.splat_adjoint(rec.points, rec.normals_in, rec.bins, rec.finite, lo, h, res, dV)
     dpts = dpts + dpts_iso
     if return_parts:
