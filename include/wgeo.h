@@ -80,7 +80,13 @@ typedef struct {
   int64_t mesh_capacity;     /* maximum triangles; 0 = default 16 * max_res^2 */
   int32_t use_graphs;        /* record the solver's fixed launch sequence once as a CUDA graph (default 1) */
   int32_t stage_timing;      /* bracket each stage with CUDA events on the call's stream (default 0) */
-  int32_t reserved[5];
+  int32_t galerkin;          /* 0 (default): the transverse-lumped 7-point operator and face divergence;
+                                1: the unlumped trilinear Galerkin forms (27-point operator
+                                A = S M M + M S M + M M S and right-hand side sum D M M V, with the
+                                1-D stiffness S = {-1,2,-1}, mass M = {1,4,1}/6 and central
+                                difference D, the walls mirrored; Sec. 2.3, Eqs. 20-22 and 26).
+                                Needs WGEO_PREC_MIXED. */
+  int32_t reserved[4];
   double  tol_rel_adjoint;   /* adjoint solve: stop when ||g - A lambda|| <= tol * ||g|| (default 1e-7) */
 } wgeo_options;
 

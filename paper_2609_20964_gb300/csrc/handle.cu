@@ -55,7 +55,8 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.off_lam64 = take(c, keep ? 16 * N : 0);
   L.off_lam32 = take(c, keep ? 4 * N : 0);
   const size_t half = (size_t)(R / 2 + 1);
-  const size_t lev = 2 * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);   // x, b per coarse level
+  // x, b per coarse level (and a Jacobi buffer t for the unlumped operator)
+  const size_t lev = (opt.galerkin ? 3 : 2) * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);
   L.off_levels = take(c, 4 * lev);
   const size_t Pp = (size_t)(P > 0 ? P : 1);
   L.off_pcell = take(c, 4 * Pp);
@@ -117,6 +118,7 @@ bool valid_opt(const wgeo_options& o) {
          o.max_refine >= 0 &&
          o.max_refine <= 200 && o.vcycles_per_refine >= 1 && o.vcycles_per_refine <= 20 &&
          (o.precision == WGEO_PREC_MIXED || o.precision == WGEO_PREC_FP32) && o.mesh_capacity >= 0 &&
+         (o.galerkin == 0 || (o.galerkin == 1 && o.precision == WGEO_PREC_MIXED)) &&
          o.mesh_capacity < (int64_t)1 << 31;
 }
 

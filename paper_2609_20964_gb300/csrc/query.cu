@@ -479,6 +479,40 @@ __device__ __forceinline__ void dV_at(const float2* __restrict__ lam, int x, int
   }
 }
 
+// The unlumped Galerkin right-hand side b = sum_xi M M D_xi V_xi has the
+// adjoint dV_xi = M M D_xi^T lambda (M symmetric, the walls mirrored): the
+// D^T lambda of the 9 transverse neighbours, weighted {1, 4, 1} / 6 per axis.
+__device__ __forceinline__ int q1_mass_w(int d, int c, int n) {
+  if (d < 0) return c > 0 ? 1 : 0;
+  if (d > 0) return c < n - 1 ? 1 : 0;
+  return 4 + (c == 0 ? 1 : 0) + (c == n - 1 ? 1 : 0);
+}
+
+__device__ __forceinline__ void dV_q1_at(const float2* __restrict__ lam, int x, int y, int z, int n, float dv[3]) {
+  const int idx[3] = {x, y, z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ab = a == 0 ? 1 : 0, ac = a == 2 ? 1 : 2;
+    float v = 0.f;
+    for (int db = -1; db <= 1; ++db) {
+      const int wb = q1_mass_w(db, idx[ab], n);
+      if (!wb) continue;
+      for (int dc = -1; dc <= 1; ++dc) {
+        const int wc = q1_mass_w(dc, idx[ac], n);
+        if (!wc) continue;
+        int q[3] = {x, y, z};
+        q[ab] += db;
+        q[ac] += dc;
+        float d[3];
+        dV_at(lam, q[0], q[1], q[2], n, d);
+        v += (float)(wb * wc) * d[a];
+      }
+    }
+    dv[a] = v * (1.f / 36.f);
+  }
+}
+
+template <bool Q1>
 __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4* __restrict__ pfrac,
                                      const float4* __restrict__ pnrm, int64_t np,
                                      const float2* __restrict__ lam0, const float2* __restrict__ lam1,
@@ -534,7 +568,10 @@ __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4
       const int dx = q % 3, dy = (q / 3) % 3, dz = q / 9;
       if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
       float dv[3];
-      dV_at(lam, b[0] + dx - 1, b[1] + dy - 1, b[2] + dz - 1, n, dv);
+      if (Q1)
+        dV_q1_at(lam, b[0] + dx - 1, b[1] + dy - 1, b[2] + dz - 1, n, dv);
+      else
+        dV_at(lam, b[0] + dx - 1, b[1] + dy - 1, b[2] + dz - 1, n, dv);
       float a, da[3];
       if (q == 13) {
         a = 0.5f;
@@ -622,9 +659,14 @@ int backward_tail(wgeo_handle* h, float* d_points, float* d_normals, cudaStream_
   stage_end(h, kStBwdSolve, slot, s);
   slot = stage_begin(h, kStBwdSplat, s);
   if (h->npts > 0) {
-    splat_adjoint_kernel<<<grid_blocks(h->npts, 128, 152 * 64), 128, 0, s>>>(
-        h->pcell, h->pfrac, h->pnrm, h->npts, h->lamff[0], h->lamff[1], &h->dstate->bwd.xidx, g,
-        d_points, d_normals);
+    if (h->opt.galerkin)
+      splat_adjoint_kernel<true><<<grid_blocks(h->npts, 128, 152 * 64), 128, 0, s>>>(
+          h->pcell, h->pfrac, h->pnrm, h->npts, h->lamff[0], h->lamff[1], &h->dstate->bwd.xidx, g,
+          d_points, d_normals);
+    else
+      splat_adjoint_kernel<false><<<grid_blocks(h->npts, 128, 152 * 64), 128, 0, s>>>(
+          h->pcell, h->pfrac, h->pnrm, h->npts, h->lamff[0], h->lamff[1], &h->dstate->bwd.xidx, g,
+          d_points, d_normals);
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStBwdSplat, slot, s);

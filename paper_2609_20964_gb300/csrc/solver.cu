@@ -194,6 +194,165 @@ __global__ void __launch_bounds__(kSX * kSY) update_residual_kernel(PairFF xp, c
   }
 }
 
+// ---------------------------------------------------------------- unlumped Galerkin operator
+// The same refinement pass for L' (weights 2 on the 12 edge neighbours, 1 on
+// the 8 corners, walls mirrored): the weighted neighbour differences are
+// exact (doubling is exact) and summed by the same two-sum chain.  One x pair
+// per thread, as update_residual_kernel, so the grid and the partials match.
+__device__ __forceinline__ int q1_fold(int v, int n) { return min(max(v, 0), n - 1); }
+
+template <typename TB>
+__global__ void __launch_bounds__(kSX * kSY) update_residual_q1_kernel(PairFF xp, const float* __restrict__ e,
+                                                                       const TB* __restrict__ b, int n,
+                                                                       float* __restrict__ r32,
+                                                                       float* __restrict__ x32,
+                                                                       double* __restrict__ partials,
+                                                                       SolveState* ss) {
+  if (ss->done) return;
+  __shared__ double red[2 * (kSX * kSY / 32)];
+  const int cur = ss->xidx;
+  const bool cold = ss->cold != 0;
+  const float2* __restrict__ xin = xp.buf[cur];
+  float2* __restrict__ xout = xp.buf[e ? cur ^ 1 : cur];
+  const int I = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y, k = blockIdx.z;
+  float s1 = 0.f, s2 = 0.f;
+  auto xnew = [&](int64_t q) {
+    const float2 v = xin[q];
+    return e ? ff_add_f(v, e[q]) : v;
+  };
+  for (int c = 0; c < 2; ++c) {
+    const int i = 2 * I + c;
+    if (i >= n || j >= n) break;
+    const int64_t t = lin(i, j, k, n);
+    float2 xc = make_float2(0.f, 0.f);
+    float2 acc = make_float2(0.f, 0.f);
+    if (!cold) {
+      xc = xnew(t);
+      float sh = 0.f, err = 0.f, lo = 0.f;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+            if (nz < 2) continue;                       // the centre and the faces: weight 0
+            const int qi = q1_fold(i + dx, n), qj = q1_fold(j + dy, n), qk = q1_fold(k + dz, n);
+            if (qi == i && qj == j && qk == k) continue;   // folded onto the cell itself
+            const float w = nz == 2 ? 2.f : 1.f;
+            const float2 v = xnew(lin(qi, qj, qk, n));
+            const float2 d = two_sum(v.x, -xc.x);
+            const float2 q = two_sum(sh, w * d.x);
+            sh = q.x;
+            err = __fadd_rn(err, __fadd_rn(q.y, w * d.y));
+            lo = __fadd_rn(lo, w * __fsub_rn(v.y, xc.y));
+          }
+      acc = two_sum(sh, __fadd_rn(err, lo));
+    }
+    float blo;
+    const float bhi = rhs_hi(b, t, blo);
+    const float2 r = ff_sub(make_float2(bhi, blo), acc);
+    const float rf = r.x + r.y;
+    s1 += rf;
+    s2 += rf * rf;
+    if (e || cold) xout[t] = xc;
+    x32[t] = xc.x;
+    r32[t] = rf;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  const int lane = (threadIdx.y * kSX + threadIdx.x) & 31, wid = (threadIdx.y * kSX + threadIdx.x) >> 5;
+  if (lane == 0) {
+    red[2 * wid] = (double)s1;
+    red[2 * wid + 1] = (double)s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double d1 = 0.0, d2 = 0.0;
+    for (int q = 0; q < kSX * kSY / 32; ++q) {
+      d1 += red[2 * q];
+      d2 += red[2 * q + 1];
+    }
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    partials[2 * blk] = d1;
+    partials[2 * blk + 1] = d2;
+  }
+}
+
+// (L' x)_p and the weight sum of the neighbours that do not fold onto p
+// (the diagonal of L' is minus that sum).
+__device__ __forceinline__ float q1_apply(const float* __restrict__ x, int i, int j, int k, int n, float xc,
+                                          float* wsum) {
+  float acc = 0.f, ws = 0.f;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+        if (nz < 2) continue;
+        const int qi = q1_fold(i + dx, n), qj = q1_fold(j + dy, n), qk = q1_fold(k + dz, n);
+        if (qi == i && qj == j && qk == k) continue;
+        const float w = nz == 2 ? 2.f : 1.f;
+        acc += w * (__ldg(x + lin(qi, qj, qk, n)) - xc);
+        ws += w;
+      }
+  *wsum = ws;
+  return acc;
+}
+
+constexpr float kQ1Omega = 8.f / 9.f;   // Jacobi damping: D^-1 A spans [3/4, 3/2] on the rough modes
+
+// One damped Jacobi sweep on L' x = b - shift: xo = x + omega (L' x - (b - shift)) / W
+// (W the folded weight sum; ZERO: x taken as 0).  One cell per thread.
+template <bool ZERO>
+__global__ void __launch_bounds__(kSX * kSY) jacobi_q1_kernel(const float* __restrict__ x, float* __restrict__ xo,
+                                                              const float* __restrict__ b,
+                                                              const float* __restrict__ shift, int n,
+                                                              const int* __restrict__ gate) {
+  if (*gate) return;
+  const int i = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y, k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int64_t t = lin(i, j, k, n);
+  const float rhs = b[t] - (shift ? *shift : 0.f);
+  if (ZERO) {
+    float ws = 0.f;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+          if (nz < 2) continue;
+          const int qi = q1_fold(i + dx, n), qj = q1_fold(j + dy, n), qk = q1_fold(k + dz, n);
+          if (qi == i && qj == j && qk == k) continue;
+          ws += nz == 2 ? 2.f : 1.f;
+        }
+    xo[t] = ws > 0.f ? -kQ1Omega * rhs / ws : 0.f;
+    return;
+  }
+  const float xc = x[t];
+  float ws;
+  const float lx = q1_apply(x, i, j, k, n, xc, &ws);
+  xo[t] = ws > 0.f ? xc + kQ1Omega * (lx - rhs) / ws : xc;
+}
+
+// bc = 1/2 * sum over the 8 children of the residual b - shift - L' x.
+__global__ void __launch_bounds__(kSX * kSY) restrict_q1_kernel(const float* __restrict__ x,
+                                                                const float* __restrict__ b,
+                                                                const float* __restrict__ shift, int n,
+                                                                float* __restrict__ bc, const int* __restrict__ gate) {
+  if (*gate) return;
+  const int nc = n >> 1;
+  const int I = blockIdx.x * kSX + threadIdx.x, J = blockIdx.y * kSY + threadIdx.y, K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
+  const float sh = shift ? *shift : 0.f;
+  float acc = 0.f;
+  for (int ch = 0; ch < 8; ++ch) {
+    const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+    const int64_t t = lin(i, j, k, n);
+    float ws;
+    const float lx = q1_apply(x, i, j, k, n, x[t], &ws);
+    acc += (b[t] - sh) - lx;
+  }
+  bc[lin(I, J, K, nc)] = 0.5f * acc;
+}
+
 __global__ void residual32_kernel(const float* __restrict__ x, const float* __restrict__ b,
                                   const float* __restrict__ shift, int n,
                                   double* __restrict__ partials, const int* __restrict__ gate) {
@@ -549,6 +708,132 @@ __global__ void __launch_bounds__(1024) small_vcycle_kernel(float* __restrict__ 
   for (int t = threadIdx.x; t < N0; t += blockDim.x) xg[t] = xs[t];
 }
 
+// The same hierarchy for L' with Gauss-Seidel in 8 colours ((i, j, k) mod 2:
+// no two cells of a colour are neighbours in the 27-point stencil), in place.
+__device__ void small_gs8(float* x, const float* b, int n, int color) {
+  const int N = n * n * n;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const int i = t % n, j = (t / n) % n, k = t / (n * n);
+    if (((i & 1) | ((j & 1) << 1) | ((k & 1) << 2)) != color) continue;
+    float acc = 0.f, ws = 0.f;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+          if (nz < 2) continue;
+          const int qi = q1_fold(i + dx, n), qj = q1_fold(j + dy, n), qk = q1_fold(k + dz, n);
+          if (qi == i && qj == j && qk == k) continue;
+          const float w = nz == 2 ? 2.f : 1.f;
+          acc += w * x[(qk * n + qj) * n + qi];
+          ws += w;
+        }
+    x[t] = ws > 0.f ? (acc - b[t]) / ws : 0.f;
+  }
+  __syncthreads();
+}
+
+__device__ float small_q1_residual(const float* x, const float* b, int n, int i, int j, int k) {
+  const int p = (k * n + j) * n + i;
+  const float xv = x[p];
+  float lx = 0.f;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+        if (nz < 2) continue;
+        const int qi = q1_fold(i + dx, n), qj = q1_fold(j + dy, n), qk = q1_fold(k + dz, n);
+        if (qi == i && qj == j && qk == k) continue;
+        lx += (nz == 2 ? 2.f : 1.f) * (x[(qk * n + qj) * n + qi] - xv);
+      }
+  return b[p] - lx;
+}
+
+__global__ void __launch_bounds__(1024) small_vcycle_q1_kernel(float* __restrict__ xg, const float* __restrict__ bg,
+                                                               const float* __restrict__ shift, int n0,
+                                                               const int* __restrict__ gate) {
+  if (*gate) return;
+  __shared__ float xs[kSmallCap];
+  __shared__ float bsm[kSmallCap];
+  __shared__ double red[32];
+  __shared__ float meanb;
+  int ns[8], off[8], L = 0;
+  {
+    int n = n0, o = 0;
+    while (true) {
+      ns[L] = n;
+      off[L] = o;
+      o += n * n * n;
+      ++L;
+      if ((n % 2) != 0 || n <= 4 || L == 8) break;
+      n /= 2;
+    }
+  }
+  const int N0 = n0 * n0 * n0;
+  const float sh = shift ? *shift : 0.f;
+  double s = 0.0;
+  for (int t = threadIdx.x; t < N0; t += blockDim.x) {
+    const float v = bg[t] - sh;
+    bsm[t] = v;
+    xs[t] = 0.f;
+    s += v;
+  }
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) meanb = (float)(s / N0);
+  __syncthreads();
+  for (int t = threadIdx.x; t < N0; t += blockDim.x) bsm[t] -= meanb;
+  __syncthreads();
+  const int cycles = L > 1 ? kSmallCycles : 2;
+  for (int cyc = 0; cyc < cycles; ++cyc) {
+    for (int l = 0; l < L - 1; ++l) {
+      const int n = ns[l];
+      float* x = xs + off[l];
+      const float* b = bsm + off[l];
+      for (int sw = 0; sw < kNu; ++sw)
+        for (int c = 0; c < 8; ++c) small_gs8(x, b, n, c);
+      const int nc = ns[l + 1];
+      float* xcn = xs + off[l + 1];
+      float* bcn = bsm + off[l + 1];
+      for (int t = threadIdx.x; t < nc * nc * nc; t += blockDim.x) {
+        const int I = t % nc, J = (t / nc) % nc, K = t / (nc * nc);
+        float acc = 0.f;
+        for (int ch = 0; ch < 8; ++ch)
+          acc += small_q1_residual(x, b, n, 2 * I + (ch & 1), 2 * J + ((ch >> 1) & 1), 2 * K + (ch >> 2));
+        bcn[t] = 0.5f * acc;
+        xcn[t] = 0.f;
+      }
+      __syncthreads();
+    }
+    {
+      const int n = ns[L - 1];
+      float* x = xs + off[L - 1];
+      const float* b = bsm + off[L - 1];
+      const int sweeps = (n <= 4 && L > 1) ? 2 * n + 8 : 2 * n * n + 16;
+      for (int sw = 0; sw < sweeps; ++sw)
+        for (int c = 0; c < 8; ++c) small_gs8(x, b, n, c);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+      const int n = ns[l], nc = ns[l + 1];
+      float* x = xs + off[l];
+      const float* b = bsm + off[l];
+      const float* xcn = xs + off[l + 1];
+      for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
+        const int i = t % n, j = (t / n) % n, k = t / (n * n);
+        x[t] += prolong_at(xcn, nc, i, j, k);
+      }
+      __syncthreads();
+      for (int sw = 0; sw < kNu; ++sw)
+        for (int c = 7; c >= 0; --c) small_gs8(x, b, n, c);
+    }
+  }
+  for (int t = threadIdx.x; t < N0; t += blockDim.x) xg[t] = xs[t];
+}
+
+// dchi *= s (the adjoint right-hand side of the scaled operator L' = 12 L).
+__global__ void scale64_kernel(double* __restrict__ v, int64_t N, double s) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x)
+    v[t] *= s;
+}
+
 __global__ void rhs_stats64_kernel(const double* __restrict__ b, int64_t N,
                                    double* __restrict__ partials) {
   __shared__ double red[32];
@@ -587,6 +872,9 @@ __global__ void rhs_stats_finalize_kernel(const double* __restrict__ partials, i
 
 // One V-cycle on level l, in place.  x0: level-0 iterate; b0, shift0:
 // level-0 right-hand side.  zero0: level-0 x starts at zero.
+int vcycle_q1(wgeo_handle* h, int l, float* x0, const float* b0, const float* shift0, bool zero0, float* t0,
+              const int* gate, cudaStream_t s);
+
 int vcycle(wgeo_handle* h, int l, float* x0, const float* b0, const float* shift0, bool zero0,
            const int* gate, cudaStream_t s) {
   const int n = h->levels[l].n;
@@ -627,6 +915,53 @@ int vcycle(wgeo_handle* h, int l, float* x0, const float* b0, const float* shift
   return WGEO_OK;
 }
 
+// One V-cycle for L' on level l, in place: damped Jacobi sweeps (ping-pong
+// through the level's t buffer; t0 on level 0), the same transfers, the
+// 8-colour small-grid kernel at 16^3 and below.
+int vcycle_q1(wgeo_handle* h, int l, float* x0, const float* b0, const float* shift0, bool zero0, float* t0,
+              const int* gate, cudaStream_t s) {
+  const int n = h->levels[l].n;
+  float* x = (l == 0) ? x0 : h->levels[l].x;
+  float* t = (l == 0) ? t0 : h->levels[l].t;
+  const float* b = (l == 0) ? b0 : h->levels[l].b;
+  const float* shift = (l == 0) ? shift0 : nullptr;
+  if (n <= kSmallN || l == h->nlevels - 1) {
+    small_vcycle_q1_kernel<<<1, 1024, 0, s>>>(x, b, shift, n, gate);
+    WGEO_LAUNCH_CHECK();
+    return WGEO_OK;
+  }
+  const bool zero = (l == 0) ? zero0 : true;
+  const int nc = n >> 1;
+  const dim3 blk(kSX, kSY);
+  const dim3 gcell(div_up(n, kSX), div_up(n, kSY), n);
+  const dim3 gf(div_up(nc, kSX), div_up(n, kSY), n);      // fine pairs (prolongation)
+  const dim3 gc(div_up(nc, kSX), div_up(nc, kSY), nc);
+  // kNu sweeps x -> t -> x (kNu even)
+  static_assert(kNu % 2 == 0, "Jacobi ping-pong ends in x");
+  for (int sw = 0; sw < kNu; ++sw) {
+    const float* src = (sw & 1) ? t : x;
+    float* dst = (sw & 1) ? x : t;
+    if (zero && sw == 0)
+      jacobi_q1_kernel<true><<<gcell, blk, 0, s>>>(src, dst, b, shift, n, gate);
+    else
+      jacobi_q1_kernel<false><<<gcell, blk, 0, s>>>(src, dst, b, shift, n, gate);
+    WGEO_LAUNCH_CHECK();
+  }
+  restrict_q1_kernel<<<gc, blk, 0, s>>>(x, b, shift, n, h->levels[l + 1].b, gate);
+  WGEO_LAUNCH_CHECK();
+  int rc = vcycle_q1(h, l + 1, x0, b0, shift0, zero0, t0, gate, s);
+  if (rc) return rc;
+  prolong_pair_kernel<<<gf, blk, 0, s>>>(h->levels[l + 1].x, x, n, gate);
+  WGEO_LAUNCH_CHECK();
+  for (int sw = 0; sw < kNu; ++sw) {
+    const float* src = (sw & 1) ? t : x;
+    float* dst = (sw & 1) ? x : t;
+    jacobi_q1_kernel<false><<<gcell, blk, 0, s>>>(src, dst, b, shift, n, gate);
+    WGEO_LAUNCH_CHECK();
+  }
+  return WGEO_OK;
+}
+
 // One solve (mode 0: forward, 1: adjoint) is a head -- the first residual
 // and convergence test -- followed by loop iterations, each a correction and
 // a new residual and test.  part 0 enqueues the head, part 1 one iteration.
@@ -658,18 +993,27 @@ int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGrap
   if (part == 1) {
     // correction: V-cycles on L e = r - mean(r)
     for (int v = 0; v < h->opt.vcycles_per_refine; ++v) {
-      int rc = vcycle(h, 0, h->e32, h->r32, &ss->rmean32, v == 0, gate, s);
+      int rc = h->opt.galerkin ? vcycle_q1(h, 0, h->e32, h->r32, &ss->rmean32, v == 0, x32, gate, s)
+                               : vcycle(h, 0, h->e32, h->r32, &ss->rmean32, v == 0, gate, s);
       if (rc) return rc;
     }
   }
   const float* e = part == 0 ? nullptr : h->e32;
   const dim3 rg(div_up(div_up(res, 2), kSX), div_up(res, kSY), res);
   const int nrb = (int)(rg.x * rg.y * rg.z);
-  if (mode == 0)
+  if (h->opt.galerkin) {
+    if (mode == 0)
+      update_residual_q1_kernel<float><<<rg, dim3(kSX, kSY), 0, s>>>(xp, e, h->b32, res, h->r32, x32, h->partials,
+                                                                     ss);
+    else
+      update_residual_q1_kernel<double><<<rg, dim3(kSX, kSY), 0, s>>>(xp, e, h->dchi64, res, h->r32, x32,
+                                                                      h->partials, ss);
+  } else if (mode == 0) {
     update_residual_kernel<float><<<rg, dim3(kSX, kSY), 0, s>>>(xp, e, h->b32, res, h->r32, x32, h->partials, ss);
-  else
+  } else {
     update_residual_kernel<double><<<rg, dim3(kSX, kSY), 0, s>>>(xp, e, h->dchi64, res, h->r32, x32, h->partials,
                                                                  ss);
+  }
   WGEO_LAUNCH_CHECK();
   finalize_kernel<<<1, 1024, 0, s>>>(h->partials, nrb, N, ss, h->dstate, tol, step, 0, e ? 1 : 0, hc, cond);
   WGEO_LAUNCH_CHECK();
@@ -774,6 +1118,7 @@ int build_levels(wgeo_handle* h, int res) {
   h->levels[0].n = n;
   h->levels[0].x = nullptr;
   h->levels[0].b = nullptr;
+  h->levels[0].t = nullptr;
   while ((n % 2) == 0 && n > 8) {
     n /= 2;
     ++l;
@@ -783,7 +1128,8 @@ int build_levels(wgeo_handle* h, int res) {
     h->levels[l].n = n;
     h->levels[l].x = pool;
     h->levels[l].b = pool + Ma;
-    pool += 2 * Ma;
+    h->levels[l].t = h->opt.galerkin ? pool + 2 * Ma : nullptr;
+    pool += (h->opt.galerkin ? 3 : 2) * Ma;
   }
   if (n > 16) return WGEO_ERR_INVALID_ARG;
   h->nlevels = l + 1;
@@ -799,6 +1145,11 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
   SolveState* ss = mode == 0 ? &h->dstate->fwd : &h->dstate->bwd;
   if (mode == 1) {
     const int rb = grid_blocks(N, kThreads, kPartials);
+    if (h->opt.galerkin) {
+      // the adjoint system L lambda = dchi, written for L' = 12 L
+      scale64_kernel<<<grid_blocks(N, kThreads, 152 * 16), kThreads, 0, s>>>(h->dchi64, N, (double)kQ1Scale);
+      WGEO_LAUNCH_CHECK();
+    }
     rhs_stats64_kernel<<<rb, kThreads, 0, s>>>(h->dchi64, N, h->partials);
     WGEO_LAUNCH_CHECK();
     rhs_stats_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss);

@@ -96,7 +96,19 @@ __device__ __forceinline__ long long fix_round(float q) {
   return (long long)__float2int_rz(qh) * 65536ll + (long long)__float2int_rn(ql);
 }
 
-// One CTA per 8^3 output tile, one thread per output cell.
+// Weights of the mass matrix M = {1, 4, 1} / 6 around a cell at coordinate c
+// (offset d = -1, 0, +1), the walls mirrored: an outside neighbour's weight
+// folds onto the cell itself.
+__device__ __forceinline__ int q1_mass_w(int d, int c, int n) {
+  if (d < 0) return c > 0 ? 1 : 0;
+  if (d > 0) return c < n - 1 ? 1 : 0;
+  return 4 + (c == 0 ? 1 : 0) + (c == n - 1 ? 1 : 0);
+}
+
+// One CTA per 8^3 output tile, one thread per output cell.  Q1: the unlumped
+// Galerkin right-hand side b' = 12 sum_xi M M (D_xi V_xi) (the scale of the
+// solver's integer-weight operator) instead of the face divergence.
+template <bool Q1>
 __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict__ srec,
                                                         const int* __restrict__ tile_off, int res,
                                                         int ntile, float* __restrict__ b,
@@ -228,14 +240,39 @@ __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict
     const int l = ((lz + 1) * kR + (ly + 1)) * kR + (lx + 1);
     const int strides[3] = {1, kR, kR * kR};
     long long acc = 0;
+    float bf;
+    if (!Q1) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (p[a] + 1 < res) acc += V[l * 3 + a] + V[(l + strides[a]) * 3 + a];
-      if (p[a] - 1 >= 0) acc -= V[(l - strides[a]) * 3 + a] + V[l * 3 + a];
+      for (int a = 0; a < 3; ++a) {
+        if (p[a] + 1 < res) acc += V[l * 3 + a] + V[(l + strides[a]) * 3 + a];
+        if (p[a] - 1 >= 0) acc -= V[(l - strides[a]) * 3 + a] + V[l * 3 + a];
+      }
+      // acc * 2^-37 rounded once to float (the int64 -> float conversion
+      // rounds, the power-of-two scale is exact)
+      bf = __ll2float_rn(acc) * (float)kFixInv2;
+    } else {
+      // 36 sum_xi M M (D_xi V_xi) in exact integer arithmetic: integer mass
+      // weights on the two transverse axes around each face difference
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int ab = a == 0 ? 1 : 0, ac = a == 2 ? 1 : 2;
+        for (int db = -1; db <= 1; ++db) {
+          const int wb = q1_mass_w(db, p[ab], res);
+          if (!wb) continue;
+          for (int dc = -1; dc <= 1; ++dc) {
+            const int wc = q1_mass_w(dc, p[ac], res);
+            if (!wc) continue;
+            const int lq = l + db * strides[ab] + dc * strides[ac];
+            long long d = 0;
+            if (p[a] + 1 < res) d += V[lq * 3 + a] + V[(lq + strides[a]) * 3 + a];
+            if (p[a] - 1 >= 0) d -= V[(lq - strides[a]) * 3 + a] + V[lq * 3 + a];
+            acc += (long long)(wb * wc) * d;
+          }
+        }
+      }
+      // 12 b27 = acc * 2^-37 / 3, rounded once to float
+      bf = (float)((double)acc * (kFixInv2 / 3.0));
     }
-    // acc * 2^-37 rounded once to float (the int64 -> float conversion rounds,
-    // the power-of-two scale is exact)
-    const float bf = __ll2float_rn(acc) * (float)kFixInv2;
     b[((int64_t)p[2] * res + p[1]) * res + p[0]] = bf;
     bv = bf;
   }
@@ -323,7 +360,10 @@ int launch_bin_sort_splat(wgeo_handle* h, const float* points, const float* norm
                                                               h->tile_cursor, h->srec);
     WGEO_LAUNCH_CHECK();
   }
-  splat_div_kernel<<<ntiles, 512, 0, s>>>(h->srec, h->tile_off, res, g.ntile, h->b32, h->partials);
+  if (h->opt.galerkin)
+    splat_div_kernel<true><<<ntiles, 512, 0, s>>>(h->srec, h->tile_off, res, g.ntile, h->b32, h->partials);
+  else
+    splat_div_kernel<false><<<ntiles, 512, 0, s>>>(h->srec, h->tile_off, res, g.ntile, h->b32, h->partials);
   WGEO_LAUNCH_CHECK();
   b_stats_kernel<<<1, 1024, 0, s>>>(h->partials, ntiles, (int64_t)res * res * res, h->dstate);
   WGEO_LAUNCH_CHECK();

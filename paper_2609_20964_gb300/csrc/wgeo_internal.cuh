@@ -67,7 +67,15 @@ struct Level {
   int n;
   float* x;
   float* b;
+  float* t;   // Jacobi ping-pong buffer (unlumped Galerkin operator only)
 };
+
+// Unlumped trilinear Galerkin operator, scaled by 12 so that its weights are
+// integers: (L' x)_p = sum over the 12 edge neighbours of 2 (x_q - x_p) plus
+// the 8 corner neighbours of (x_q - x_p) (the 6 face neighbours have weight
+// 0), the walls mirrored (an index outside the grid folds onto the cell
+// inside).  12 times the unit-free form -(S M M + M S M + M M S).
+constexpr int kQ1Scale = 12;
 
 // ---------------------------------------------------------------- stage timers
 // Stage ids of the per-stage CUDA-event timers (option stage_timing).
