@@ -336,6 +336,7 @@ def run_ours(args):
     if rank == 0 and ws == 1 and args.serving_requests > 0:
         out["serving"] = serving_bench(args.serving_requests, value)
     if rank == 0 and args.pca_reps > 0:
+        out["galerkin_q1"] = galerkin_q1_bench(Reconstructor, P, Nn, Q, G, sdf_mixed, args.pca_reps)
         out["exact_query"] = exact_query_bench(rec, P, Nn, Q, args.pca_reps)
         out["normal_estimation"] = normal_estimation_bench(rec, P, args.pca_reps, cpu is not None)
         out["normal_orientation"] = orientation_bench(rec, P, n, args.pca_reps)
@@ -427,6 +428,48 @@ def roofline(dom, stages, info, hbm, peak_kind, alg_tests_per_node):
     return {"bound": "hbm", "kernel": dom, "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm,
             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / hbm, "traffic": None,
             "peak_kind": peak_kind}
+
+
+# ------------------------------------------------------------ unlumped Galerkin
+def galerkin_q1_bench(Reconstructor, P, Nn, Q, G, sdf_lumped, reps: int):
+    """The same forward, and forward + query + adjoint, with the unlumped
+    27-point Galerkin operator (option galerkin = 1), CUDA events around each
+    step; the solver's steps and the largest SDF difference from the lumped
+    7-point result on the same cloud."""
+    import torch
+    rec = Reconstructor(RES, NPTS, galerkin=1, **HANDLE_OPTS)
+    sdf = torch.empty((RES, RES, RES), device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        rec.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf, with_normals=False)
+
+    def step():
+        rec.reconstruct(P, Nn, BBOX, RES, sdf_out=sdf, with_normals=False)
+        rec.query(Q, with_normals=False)
+        rec.backward(q=Q, d_sdf_q=G)
+
+    out = {}
+    for name, fn in (("fwd", fwd), ("fwd_query_adjoint", step)):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_ms"] = statistics.median(a.elapsed_time(b) for a, b in ev)
+    fwd()
+    info = rec.info()
+    N = RES ** 3
+    out.update({"fwd_cells_per_s": N / (out["fwd_ms"] / 1e3),
+                "step_cells_per_s": N / (out["fwd_query_adjoint_ms"] / 1e3),
+                "solver_steps": info["solver_steps"], "residual_rel": info["residual_rel"],
+                "status": info["status"],
+                "max_abs_sdf_diff_vs_lumped": float((sdf - sdf_lumped).abs().max())})
+    rec.close()
+    return out
 
 
 # ---------------------------------------------------------------- exact queries
