@@ -86,7 +86,11 @@ typedef struct {
                                 1-D stiffness S = {-1,2,-1}, mass M = {1,4,1}/6 and central
                                 difference D, the walls mirrored; Sec. 2.3, Eqs. 20-22 and 26).
                                 Needs WGEO_PREC_MIXED. */
-  int32_t reserved[4];
+  int32_t spectral;          /* MIXED mode: 1 (default) = each refinement step's correction is a
+                                direct spectral solve (the operator is diagonal in the cosine basis
+                                of the mirrored walls) when res is a power of two >= 16, else
+                                multigrid; 0 = always multigrid V-cycles */
+  int32_t reserved[3];
   double  tol_rel_adjoint;   /* adjoint solve: stop when ||g - A lambda|| <= tol * ||g|| (default 1e-7) */
 } wgeo_options;
 

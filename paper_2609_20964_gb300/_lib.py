@@ -41,7 +41,7 @@ class Options(C.Structure):
     _fields_ = [("tol_rel", C.c_double), ("max_vcycles", _i32), ("max_refine", _i32),
                 ("vcycles_per_refine", _i32), ("precision", _i32), ("warm_start", _i32),
                 ("keep_for_backward", _i32), ("mesh_capacity", _i64), ("use_graphs", _i32),
-                ("stage_timing", _i32), ("galerkin", _i32), ("reserved", _i32 * 4),
+                ("stage_timing", _i32), ("galerkin", _i32), ("spectral", _i32), ("reserved", _i32 * 3),
                 ("tol_rel_adjoint", C.c_double)]
 
 

@@ -20,7 +20,7 @@ constexpr size_t kAlign = 256;
 struct Layout {
   size_t total = 0;
   size_t off_b32, off_chi32, off_chi64, off_r32, off_e32, off_phi, off_ctri, off_dphi64, off_dchi64,
-      off_lam64, off_lam32, off_levels, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
+      off_lam64, off_lam32, off_levels, off_dct, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
       off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_tris_s, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
       off_scan, off_state, off_dp_cell, off_dp_count, off_dp_off, off_dp_cursor, off_dp_scan, off_dp_tmp,
       off_dp_sorted, off_dp_key, off_dp_gbox, off_or_scal;
@@ -58,6 +58,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   // x, b per coarse level (and a Jacobi buffer t for the unlumped operator)
   const size_t lev = (opt.galerkin ? 3 : 2) * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);
   L.off_levels = take(c, 4 * lev);
+  L.off_dct = take(c, 8 * 512 + 8 * 1024 + 4 * 1024);   // spectral tables for n <= 1024
   const size_t Pp = (size_t)(P > 0 ? P : 1);
   L.off_pcell = take(c, 4 * Pp);
   L.off_pfrac = take(c, 16 * Pp);
@@ -119,6 +120,7 @@ bool valid_opt(const wgeo_options& o) {
          o.max_refine <= 200 && o.vcycles_per_refine >= 1 && o.vcycles_per_refine <= 20 &&
          (o.precision == WGEO_PREC_MIXED || o.precision == WGEO_PREC_FP32) && o.mesh_capacity >= 0 &&
          (o.galerkin == 0 || (o.galerkin == 1 && o.precision == WGEO_PREC_MIXED)) &&
+         (o.spectral == 0 || o.spectral == 1) &&
          o.mesh_capacity < (int64_t)1 << 31;
 }
 
@@ -213,6 +215,7 @@ int wgeo_default_options(wgeo_options* opt) {
   opt->keep_for_backward = 1;
   opt->mesh_capacity = 0;
   opt->use_graphs = 1;
+  opt->spectral = 1;
   opt->tol_rel_adjoint = 1e-7;
   return WGEO_OK;
 }
@@ -267,6 +270,9 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->lamff[1] = keep ? h->lamff[0] + N : nullptr;
   h->lam32 = keep ? (float*)(a + L.off_lam32) : nullptr;
   h->level_pool = (float*)(a + L.off_levels);
+  h->dct_tw = (float2*)(a + L.off_dct);
+  h->dct_wm = h->dct_tw + 512;
+  h->dct_s = (float*)(h->dct_wm + 1024);
   h->pcell = (int*)(a + L.off_pcell);
   h->pfrac = (float4*)(a + L.off_pfrac);
   h->pnrm = keep ? (float4*)(a + L.off_pnrm) : nullptr;

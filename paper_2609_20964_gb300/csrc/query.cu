@@ -256,10 +256,16 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
 // smallest float not below c, c - chi1 from c as a float-float pair, and the
 // dL/dc sum in float-float, so no node needs the FP64 pipe.
 
+// LIST = false: every node with a seed; a node whose closest triangle is a
+// sliver (its float32 weights would lose their digits) is appended to
+// `slivers` instead.  LIST = true: the listed nodes, weights and direction in
+// FP64.  Two passes, so the rare FP64 work does not stall whole warps.
+template <bool LIST>
 __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int* __restrict__ ctri,
                                       const float* __restrict__ chi, const DevState* __restrict__ st,
                                       const Tri* __restrict__ tris, const float4* __restrict__ tris_s, QParams g,
-                                      double* __restrict__ dchi, double* __restrict__ partials) {
+                                      double* __restrict__ dchi, double* __restrict__ partials,
+                                      int* __restrict__ slivers, unsigned* __restrict__ nsliver) {
   __shared__ double red[32];
   __shared__ float s_ax[3][kMaxRes];
   const int n = g.res;
@@ -273,9 +279,10 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
   const float c_hi = (float)cd, c_lo = (float)(cd - (double)c_hi);
   const float hf = (float)g.h;
   const unsigned un = (unsigned)n;
-  const unsigned N = un * un * un;
+  const unsigned N = LIST ? *nsliver : un * un * un;
   float2 dcacc = make_float2(0.f, 0.f);   // dL/dc: terms of both signs that nearly cancel
-  for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < N; o += gridDim.x * blockDim.x) {
+  for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < N; it += gridDim.x * blockDim.x) {
+    const unsigned o = LIST ? (unsigned)slivers[it] : it;
     const double gphi64 = dphi[o];
     if (gphi64 == 0.0) continue;
     const int t = ctri[o];
@@ -286,21 +293,37 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
     const float3 p = make_float3(s_ax[0][i], s_ax[1][j], s_ax[2][k]);
     const float4* rec = tris_s + kTriRec * (int64_t)t;
     const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
-    const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
-    const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
-    const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
-    float v, w;
-    rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
-    const float rx = ap.x - v * r1.x - w * r2.x;
-    const float ry = ap.y - v * r1.y - w * r2.y;
-    const float rz = ap.z - v * r1.z - w * r2.z;
-    const float dd = rx * rx + ry * ry + rz * rz;
-    if (!(dd > 0.f)) continue;
-    const float invd = rsqrtf(dd);
-    const float sgn = (chi[o] >= cf) ? 1.f : -1.f;
-    const float u[3] = {rx * invd, ry * invd, rz * invd};
-    const float bw[3] = {fmaxf(1.f - v - w, 0.f), v, w};
+    float u[3], bw[3];
     const Tri tr = tris[t];
+    if (!LIST) {
+      if (!(r0.w * r2.w * r3.w < kSliverKappa)) {
+        slivers[atomicAdd(nsliver, 1u)] = (int)o;
+        continue;
+      }
+      const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+      const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
+      const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
+      float v, w;
+      rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
+      const float rx = ap.x - v * r1.x - w * r2.x;
+      const float ry = ap.y - v * r1.y - w * r2.y;
+      const float rz = ap.z - v * r1.z - w * r2.z;
+      const float dd = rx * rx + ry * ry + rz * rz;
+      if (!(dd > 0.f)) continue;
+      const float invd = rsqrtf(dd);
+      u[0] = rx * invd, u[1] = ry * invd, u[2] = rz * invd;
+      bw[0] = fmaxf(1.f - v - w, 0.f), bw[1] = v, bw[2] = w;
+    } else {
+      const double pd[3] = {p.x, p.y, p.z}, ad[3] = {tr.a.x, tr.a.y, tr.a.z}, bd[3] = {tr.b.x, tr.b.y, tr.b.z},
+                   cdv[3] = {tr.c.x, tr.c.y, tr.c.z};
+      double bw64[3], dir64[3];
+      if (!(closest_point_fp64(pd, ad, bd, cdv, bw64, dir64) > 0.0)) continue;
+      for (int q = 0; q < 3; ++q) {
+        bw[q] = (float)bw64[q];
+        u[q] = (float)dir64[q];
+      }
+    }
+    const float sgn = (chi[o] >= cf) ? 1.f : -1.f;
     const float gv[3] = {tr.a.w, tr.b.w, tr.c.w};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -379,8 +402,15 @@ __global__ void exact_adjoint_kernel(const float* __restrict__ q, int nq, const 
     const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
     float v, w;
     rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
-    const float bw[3] = {fmaxf(1.f - v - w, 0.f), v, w};
+    float bw[3] = {fmaxf(1.f - v - w, 0.f), v, w};
     const Tri tr = tris[t];
+    if (!(r0.w * r2.w * r3.w < kSliverKappa)) {
+      const double pd[3] = {p.x, p.y, p.z}, ad[3] = {tr.a.x, tr.a.y, tr.a.z}, bd[3] = {tr.b.x, tr.b.y, tr.b.z},
+                   cdv[3] = {tr.c.x, tr.c.y, tr.c.z};
+      double bw64[3], dir64[3];
+      closest_point_fp64(pd, ad, bd, cdv, bw64, dir64);
+      for (int q = 0; q < 3; ++q) bw[q] = (float)bw64[q];
+    }
     const float gv[3] = {tr.a.w, tr.b.w, tr.c.w};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -636,10 +666,19 @@ int backward_grid_seeds(wgeo_handle* h, const float* d_sdf_grid, const float* d_
 int backward_mesh_nodes(wgeo_handle* h, cudaStream_t s) {
   const int64_t N = (int64_t)h->res * h->res * h->res;
   const int nb = grid_blocks(N, 256, kPartials);
-  sdf_mc_adjoint_kernel<<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, h->tris_s, qparams(h),
-                                           h->dchi64, h->partials);
+  const int nb2 = 152 * 4;
+  // the solver's correction buffer is idle until the adjoint solve: it holds
+  // the sliver nodes between the two passes
+  int* slivers = reinterpret_cast<int*>(h->e32);
+  WGEO_CUDA_TRY(cudaMemsetAsync(&h->dstate->nsliver, 0, sizeof(unsigned), s));
+  sdf_mc_adjoint_kernel<false><<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, h->tris_s,
+                                                  qparams(h), h->dchi64, h->partials, slivers, &h->dstate->nsliver);
   WGEO_LAUNCH_CHECK();
-  dc_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, nb, h->dstate);
+  sdf_mc_adjoint_kernel<true><<<nb2, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, h->tris_s,
+                                                  qparams(h), h->dchi64, h->partials + nb, slivers,
+                                                  &h->dstate->nsliver);
+  WGEO_LAUNCH_CHECK();
+  dc_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, nb + nb2, h->dstate);
   WGEO_LAUNCH_CHECK();
   return WGEO_OK;
 }

@@ -444,7 +444,7 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks
     const double rel = (bn > 0.0) ? rn / bn : 0.0;
     ss->rel = rel;
     ss->iter = step;
-    if (bn <= 0.0 || rel <= tol) {
+    if (bn <= 0.0 || (rel <= tol && step >= ss->min_steps)) {
       ss->done = 1;
     } else if (last) {
       atomicOr(&st->status, WGEO_STATUS_NOT_CONVERGED);
@@ -453,7 +453,7 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks
     if (cond) cudaGraphSetConditional(hc, ss->done ? 0u : 1u);
   }
 }
-__global__ void solve_begin_kernel(SolveState* ss, int cold, int max_steps, int body_launches) {
+__global__ void solve_begin_kernel(SolveState* ss, int cold, int max_steps, int min_steps, int body_launches) {
   ss->done = 0;
   ss->iter = 0;
   ss->rel = 0.0;
@@ -461,6 +461,7 @@ __global__ void solve_begin_kernel(SolveState* ss, int cold, int max_steps, int 
   ss->rmean32 = 0.f;
   ss->cold = cold;
   ss->max_steps = max_steps;
+  ss->min_steps = min(min_steps, max_steps);
   ss->body_launches = body_launches;
 }
 
@@ -915,6 +916,203 @@ int vcycle(wgeo_handle* h, int l, float* x0, const float* b0, const float* shift
   return WGEO_OK;
 }
 
+// ---------------------------------------------------------------- spectral correction
+// With the walls mirrored, both operators are diagonal in the cosine basis
+// c_k(i) = cos(pi k (i + 1/2) / n) per axis: the 7-point L has eigenvalue
+// -(s_x + s_y + s_z), s = 4 sin^2(pi k / 2n), and the scaled Galerkin L' has
+// -12 (s_x m_y m_z + m_x s_y m_z + m_x m_y s_z), m = 1 - s / 6.  So a
+// correction L e = r - mean(r) is solved directly: the (unnormalised)
+// DCT-II along x, y and z, a division by the eigenvalue (the zero mode, the
+// mean, dropped), and the exact inverse transform along z, y and x.  Five
+// in-place passes over the grid (the z pass divides and transforms back).
+//
+// Each one-dimensional DCT-II of n = 2^p points goes through an n-point
+// complex FFT (Makhoul, IEEE TASSP 1980): v_m = x_{2m}, v_{n-1-m} = x_{2m+1},
+// X_k = Re(e^{-i pi k / 2n} V_k).  Its inverse: V_k = e^{i pi k / 2n} (X_k -
+// i X_{n-k}) (X_n = 0), v = IFFT(V), taken as conj(FFT(conj V)) / n.  The FFT
+// is the radix-2 Stockham form (self-sorting, two buffers), 16 lines per
+// block in shared memory, twiddles from tables built in double.
+constexpr int kDctLines = 16;
+constexpr int kDctThreads = 256;
+
+bool use_spectral(const wgeo_handle* h, int n) {
+  return h->opt.spectral && n >= 16 && n <= 512 && (n & (n - 1)) == 0;
+}
+
+__global__ void dct_tables_kernel(int n, float2* __restrict__ tw, float2* __restrict__ wm, float* __restrict__ sk) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi((double)k / (2.0 * n), &sn, &cs);      // angle pi k / 2n
+    wm[k] = make_float2((float)cs, (float)-sn);
+    sk[k] = (float)(4.0 * sn * sn);
+    if (k < n / 2) {
+      sincospi(2.0 * k / n, &sn, &cs);              // angle 2 pi k / n
+      tw[k] = make_float2((float)cs, (float)-sn);
+    }
+  }
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Forward FFT (e^{-2 pi i jk / n}) of the kDctLines lines of a (n points each,
+// line l at a + l n); returns the buffer that holds the result.
+__device__ float2* fft_lines(float2* a, float2* b, int n, int logn, const float2* __restrict__ tw) {
+  const int half = n >> 1;
+  for (int st = 0; st < logn; ++st) {
+    const int ns = 1 << st;
+    for (int t = threadIdx.x; t < kDctLines * half; t += blockDim.x) {
+      const int l = t >> (logn - 1), j = t & (half - 1);
+      const int k = j & (ns - 1);
+      const float2 v0 = a[l * n + j];
+      const float2 v1 = cmul(a[l * n + j + half], tw[k << (logn - 1 - st)]);
+      const int d = ((j >> st) << (st + 1)) + k;
+      b[l * n + d] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      b[l * n + d + ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+    }
+    __syncthreads();
+    float2* tmp = a;
+    a = b;
+    b = tmp;
+  }
+  return a;
+}
+
+// The position of x_i in Makhoul's reordered sequence v.
+__device__ __forceinline__ int dct_perm(int i, int n) { return (i & 1) ? n - 1 - (i >> 1) : (i >> 1); }
+
+// MODE 0: forward DCT-II along `axis`; 1: its inverse; 2 (axis z): forward,
+// division by the eigenvalue, inverse.  A block takes kDctLines lines: along
+// x, 16 rows of one plane; along y or z, 16 neighbouring x columns.
+template <int MODE>
+__global__ void __launch_bounds__(kDctThreads) dct_pass_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                               int n, int logn, int axis,
+                                                               const float2* __restrict__ tw,
+                                                               const float2* __restrict__ wm,
+                                                               const float* __restrict__ sk, int q1,
+                                                               const int* __restrict__ gate) {
+  if (*gate) return;
+  extern __shared__ float2 dsm[];
+  float2* A = dsm;
+  float2* B = dsm + kDctLines * n;
+  const int tpp = n / kDctLines;
+  const int fixed = blockIdx.x / tpp, t0 = (blockIdx.x - fixed * tpp) * kDctLines;
+  auto gidx = [&](int l, int i) -> int64_t {
+    if (axis == 0) return ((int64_t)fixed * n + t0 + l) * n + i;
+    if (axis == 1) return ((int64_t)fixed * n + i) * n + t0 + l;
+    return ((int64_t)i * n + fixed) * n + t0 + l;
+  };
+  auto lpos = [&](int q, int& l, int& i) {   // coalesced order: consecutive threads, consecutive addresses
+    if (axis == 0) {
+      l = q >> logn;
+      i = q & (n - 1);
+    } else {
+      l = q & (kDctLines - 1);
+      i = q / kDctLines;
+    }
+  };
+  const int total = kDctLines * n;
+  const float inv_n = 1.f / (float)n;
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    int l, i;
+    lpos(q, l, i);
+    const float x = in[gidx(l, i)];
+    if (MODE == 1)
+      B[l * n + i] = make_float2(x, 0.f);                 // X, to pair X_k with X_{n-k}
+    else
+      A[l * n + dct_perm(i, n)] = make_float2(x, 0.f);
+  }
+  __syncthreads();
+  if (MODE == 1) {
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int l = q >> logn, k = q & (n - 1);
+      const float xk = B[l * n + k].x, xnk = k ? B[l * n + n - k].x : 0.f;
+      A[l * n + k] = cmul(wm[k], make_float2(xk, xnk));  // e^{-i pi k/2n} conj(X_k - i X_{n-k})
+    }
+    __syncthreads();
+  }
+  float2* R = fft_lines(A, B, n, logn, tw);
+  float2* F = (R == A) ? B : A;
+  if (MODE == 2) {
+    // X_k, divided by the eigenvalue of mode (kx, ky, kz) = (t0 + l, fixed, k)
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int l = q >> logn, k = q & (n - 1);
+      const float2 w = wm[k], v = R[l * n + k];
+      const float X = v.x * w.x - v.y * w.y;
+      const float sx = sk[t0 + l], sy = sk[fixed], sz = sk[k];
+      float lam;
+      if (q1) {
+        const float mx = 1.f - sx * (1.f / 6.f), my = 1.f - sy * (1.f / 6.f), mz = 1.f - sz * (1.f / 6.f);
+        lam = -(float)kQ1Scale * (sx * my * mz + mx * sy * mz + mx * my * sz);
+      } else {
+        lam = -(sx + sy + sz);
+      }
+      const bool zero_mode = (t0 + l) == 0 && fixed == 0 && k == 0;
+      F[l * n + k] = make_float2(zero_mode ? 0.f : X / lam, 0.f);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int l = q >> logn, k = q & (n - 1);
+      const float xk = F[l * n + k].x, xnk = k ? F[l * n + n - k].x : 0.f;
+      R[l * n + k] = cmul(wm[k], make_float2(xk, xnk));
+    }
+    __syncthreads();
+    R = fft_lines(R, F, n, logn, tw);
+  }
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    int l, i;
+    lpos(q, l, i);
+    float y;
+    if (MODE == 0) {
+      const float2 w = wm[i], v = R[l * n + i];
+      y = v.x * w.x - v.y * w.y;                          // X_i (i the frequency here)
+    } else {
+      y = R[l * n + dct_perm(i, n)].x * inv_n;            // x_i from v
+    }
+    out[gidx(l, i)] = y;
+  }
+}
+
+// e = the solution of L e = r - mean(r) (L the handle's operator), zero mean.
+int spectral_solve(wgeo_handle* h, int n, float* e, const float* r, const int* gate, cudaStream_t s) {
+  int logn = 0;
+  while ((1 << logn) < n) ++logn;
+  const size_t smem = 2 * sizeof(float2) * kDctLines * n;
+  const int blocks = n * (n / kDctLines);
+  const int q1 = h->opt.galerkin ? 1 : 0;
+  dct_pass_kernel<0><<<blocks, kDctThreads, smem, s>>>(r, e, n, logn, 0, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
+  WGEO_LAUNCH_CHECK();
+  dct_pass_kernel<0><<<blocks, kDctThreads, smem, s>>>(e, e, n, logn, 1, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
+  WGEO_LAUNCH_CHECK();
+  dct_pass_kernel<2><<<blocks, kDctThreads, smem, s>>>(e, e, n, logn, 2, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
+  WGEO_LAUNCH_CHECK();
+  dct_pass_kernel<1><<<blocks, kDctThreads, smem, s>>>(e, e, n, logn, 1, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
+  WGEO_LAUNCH_CHECK();
+  dct_pass_kernel<1><<<blocks, kDctThreads, smem, s>>>(e, e, n, logn, 0, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
+  WGEO_LAUNCH_CHECK();
+  return WGEO_OK;
+}
+
+// The twiddle and eigenvalue tables for n, and the shared-memory opt-in of the
+// pass kernels (host calls, kept out of any capture).
+int spectral_setup(wgeo_handle* h, int n, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    const int mx = 2 * (int)sizeof(float2) * kDctLines * 512;
+    WGEO_CUDA_TRY(cudaFuncSetAttribute(dct_pass_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    WGEO_CUDA_TRY(cudaFuncSetAttribute(dct_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    WGEO_CUDA_TRY(cudaFuncSetAttribute(dct_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    attr = true;
+  }
+  if (h->dct_n != n) {
+    dct_tables_kernel<<<div_up(n, 256), 256, 0, s>>>(n, h->dct_tw, h->dct_wm, h->dct_s);
+    WGEO_LAUNCH_CHECK();
+    h->dct_n = n;
+  }
+  return WGEO_OK;
+}
+
 // One V-cycle for L' on level l, in place: damped Jacobi sweeps (ping-pong
 // through the level's t buffer; t0 on level 0), the same transfers, the
 // 8-colour small-grid kernel at 16^3 and below.
@@ -992,10 +1190,15 @@ int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGrap
   float* x32 = mode == 0 ? h->chi32 : h->lam32;
   if (part == 1) {
     // correction: V-cycles on L e = r - mean(r)
-    for (int v = 0; v < h->opt.vcycles_per_refine; ++v) {
-      int rc = h->opt.galerkin ? vcycle_q1(h, 0, h->e32, h->r32, &ss->rmean32, v == 0, x32, gate, s)
-                               : vcycle(h, 0, h->e32, h->r32, &ss->rmean32, v == 0, gate, s);
+    if (use_spectral(h, res)) {
+      int rc = spectral_solve(h, res, h->e32, h->r32, gate, s);
       if (rc) return rc;
+    } else {
+      for (int v = 0; v < h->opt.vcycles_per_refine; ++v) {
+        int rc = h->opt.galerkin ? vcycle_q1(h, 0, h->e32, h->r32, &ss->rmean32, v == 0, x32, gate, s)
+                                 : vcycle(h, 0, h->e32, h->r32, &ss->rmean32, v == 0, gate, s);
+        if (rc) return rc;
+      }
     }
   }
   const float* e = part == 0 ? nullptr : h->e32;
@@ -1143,6 +1346,11 @@ int build_levels(wgeo_handle* h, int res) {
 int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
   const int64_t N = (int64_t)res * res * res;
   SolveState* ss = mode == 0 ? &h->dstate->fwd : &h->dstate->bwd;
+  const bool fp32_plain = (mode == 0 && h->opt.precision == WGEO_PREC_FP32);
+  if (!fp32_plain && use_spectral(h, res)) {
+    int rc = spectral_setup(h, res, s);
+    if (rc) return rc;
+  }
   if (mode == 1) {
     const int rb = grid_blocks(N, kThreads, kPartials);
     if (h->opt.galerkin) {
@@ -1158,8 +1366,12 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   WGEO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
   const int steps = max_steps(h, mode);
+  // the direct correction reaches the float-float limit in two steps (the
+  // first is exact to FP32 rounding): always take both, so that chi, and the
+  // adjoint's right-hand side built from it, carry no solver error
+  const int min_steps = (!fp32_plain && use_spectral(h, res)) ? 2 : 0;
   if (!h->opt.use_graphs || cap != cudaStreamCaptureStatusNone) {
-    solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0, steps, 0);
+    solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0, steps, min_steps, 0);
     WGEO_LAUNCH_CHECK();
     return enqueue_solve(h, res, mode, s);
   }
@@ -1190,7 +1402,7 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
     g.launches = head;
     g.body_launches = body;
   }
-  solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0, steps, (int)g.body_launches);
+  solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0, steps, min_steps, (int)g.body_launches);
   WGEO_LAUNCH_CHECK();
   WGEO_CUDA_TRY(cudaGraphLaunch(g.exec, s));
   g_kernel_launches.fetch_add(g.launches, std::memory_order_relaxed);

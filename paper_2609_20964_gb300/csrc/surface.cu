@@ -983,6 +983,7 @@ __global__ void normals_kernel(const float* __restrict__ phi, int n, double h,
 // on the surface, infinite distance when the mesh is empty).
 template <bool SEEDS>
 __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* __restrict__ phi, SurfParams g,
+                                                                const Tri* __restrict__ tris,
                                                                 const float4* __restrict__ tris_s,
                                                                 const int* __restrict__ leaf_off, int64_t cap,
                                                                 const float4* __restrict__ pyr, PyrInfo pi,
@@ -1119,6 +1120,15 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
                                    ap.z - v * r1.z - wt * r2.z);
       const float len = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
       if (len > 0.f) dir = make_float3(r.x / len, r.y / len, r.z / len);
+      if (!(r0.w * r2.w * r3.w < kSliverKappa)) {
+        // a sliver: the closest point's direction in FP64
+        const Tri tr = tris[ct];
+        const double pd[3] = {p.x, p.y, p.z}, ad[3] = {tr.a.x, tr.a.y, tr.a.z}, bd[3] = {tr.b.x, tr.b.y, tr.b.z},
+                     cdv[3] = {tr.c.x, tr.c.y, tr.c.z};
+        double bw64[3], dir64[3];
+        closest_point_fp64(pd, ad, bd, cdv, bw64, dir64);
+        dir = make_float3((float)dir64[0], (float)dir64[1], (float)dir64[2]);
+      }
     }
     dist_out[idx] = ct >= 0 ? sqrtf(cd) : INFINITY;
     if (tri_out) tri_out[idx] = ct;
@@ -1466,10 +1476,10 @@ int launch_query_exact_chunk(wgeo_handle* h, const float* q, int nq, float* sdf_
   const int* total = h->dp_off + pg.ncell;
   const int nblk = grid_blocks((int64_t)nq, kWarps * 32, 152 * 8);
   if (ctri)
-    sdf_query_kernel<true><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris_s, h->leaf_off, h->mesh_cap, h->pyramid,
+    sdf_query_kernel<true><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris, h->tris_s, h->leaf_off, h->mesh_cap, h->pyramid,
                                                         pi, h->dp_sorted, total, ctri, sdf_q, nrm_q, tri);
   else
-    sdf_query_kernel<false><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris_s, h->leaf_off, h->mesh_cap,
+    sdf_query_kernel<false><<<nblk, kWarps * 32, 0, s>>>(h->phi, g, h->tris, h->tris_s, h->leaf_off, h->mesh_cap,
                                                          h->pyramid, pi, h->dp_sorted, total, nullptr, sdf_q, nrm_q,
                                                          tri);
   WGEO_LAUNCH_CHECK();

@@ -36,6 +36,7 @@ struct SolveState {
   int xidx;          // which of the two FP64 buffers holds the current iterate
   int cold;          // 1: start from x = 0 (the first refinement pass writes zeros)
   int max_steps;     // the last step allowed (refinement steps, or V-cycles in plain FP32)
+  int min_steps;     // the first step that may stop (2 with the spectral correction, else 0)
   int body_launches; // kernels of one iteration of the recorded loop body (launch accounting)
   double bnorm;      // || b - mean(b) ||
   double bmean;
@@ -57,6 +58,7 @@ struct DevState {
   SolveState bwd;
   unsigned long long sdf_cnt[4];   // octree nodes entered, leaves entered, lane point-triangle tests,
                                    // nodes re-decided in float-float
+  unsigned nsliver;                // backward: nodes whose closest triangle is a sliver (FP64 pass)
 };
 
 struct Tri {          // one marching-cubes triangle: vertex xyz + global edge id in .w
@@ -220,6 +222,76 @@ __device__ __forceinline__ void rec_weights(const float3 ap, float d1, float d2,
   }
 }
 
+// Closest point y = wa a + wb b + wc c of triangle (a, b, c) to p in FP64:
+// the face point when the projection falls inside (2 x 2 normal equations),
+// else the nearest of the three edge points (segments clamped); returns
+// |p - y|^2 and the unit direction (p - y) / |p - y| (zero when p is on the
+// triangle).  For the rare ill-conditioned (sliver) triangles, where float32
+// barycentric weights lose their digits while the distance does not.
+__device__ __forceinline__ double closest_point_fp64(const double p[3], const double a[3], const double b[3],
+                                                     const double c[3], double bw[3], double dir[3]) {
+  double ab[3], ac[3], ap[3];
+  for (int k = 0; k < 3; ++k) {
+    ab[k] = b[k] - a[k];
+    ac[k] = c[k] - a[k];
+    ap[k] = p[k] - a[k];
+  }
+  auto dot = [](const double* x, const double* y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+  double best = -1.0;
+  double bv = 0.0, bwv = 0.0;   // weights of b and c
+  const double d00 = dot(ab, ab), d01 = dot(ab, ac), d11 = dot(ac, ac);
+  const double r0 = dot(ab, ap), r1 = dot(ac, ap);
+  const double det = d00 * d11 - d01 * d01;
+  if (det > 0.0) {
+    const double v = (d11 * r0 - d01 * r1) / det, w = (d00 * r1 - d01 * r0) / det;
+    if (v >= 0.0 && w >= 0.0 && v + w <= 1.0) {
+      double r[3];
+      for (int k = 0; k < 3; ++k) r[k] = ap[k] - v * ab[k] - w * ac[k];
+      best = dot(r, r);
+      bv = v;
+      bwv = w;
+    }
+  }
+  if (best < 0.0) {
+    // edges ab (v = t), ac (w = t), bc (v = 1 - t, w = t)
+    const double* P0[3] = {a, a, b};
+    const double* P1[3] = {b, c, c};
+    for (int e = 0; e < 3; ++e) {
+      double d[3], q[3];
+      for (int k = 0; k < 3; ++k) {
+        d[k] = P1[e][k] - P0[e][k];
+        q[k] = p[k] - P0[e][k];
+      }
+      const double L2 = dot(d, d);
+      double t = L2 > 0.0 ? dot(q, d) / L2 : 0.0;
+      t = fmin(fmax(t, 0.0), 1.0);
+      double r[3];
+      for (int k = 0; k < 3; ++k) r[k] = q[k] - t * d[k];
+      const double dd = dot(r, r);
+      if (best < 0.0 || dd < best) {
+        best = dd;
+        bv = e == 0 ? t : (e == 2 ? 1.0 - t : 0.0);
+        bwv = e == 1 ? t : (e == 2 ? t : 0.0);
+      }
+    }
+  }
+  bw[0] = fmax(1.0 - bv - bwv, 0.0);
+  bw[1] = bv;
+  bw[2] = bwv;
+  double y[3], r[3];
+  for (int k = 0; k < 3; ++k) {
+    y[k] = bw[0] * a[k] + bw[1] * b[k] + bw[2] * c[k];
+    r[k] = p[k] - y[k];
+  }
+  const double len = sqrt(dot(r, r));
+  for (int k = 0; k < 3; ++k) dir[k] = len > 0.0 ? r[k] / len : 0.0;
+  return best;
+}
+
+// |ab|^2 |ac|^2 / |ab x ac|^2 (1 / sin^2 of the angle at a) from a search
+// record: above this the float32 weights are replaced by closest_point_fp64.
+constexpr float kSliverKappa = 1e3f;
+
 template <typename T>
 struct Vec3 {
   T x, y, z;
@@ -251,6 +323,10 @@ struct wgeo_handle {
   float2* lamff[2] = {nullptr, nullptr};   // adjoint solution, ping-pong like chiff
   float* lam32 = nullptr;
   float* level_pool = nullptr;
+  float2* dct_tw = nullptr;      // spectral solve: FFT twiddles e^{-2 pi i q / n} (q < n/2)
+  float2* dct_wm = nullptr;      //   e^{-i pi k / (2 n)} (k < n)
+  float* dct_s = nullptr;        //   4 sin^2(pi k / (2 n)) (k < n)
+  int dct_n = 0;                 // n the tables hold (0: none yet)
 
   // points
   int* pcell = nullptr;          // packed central cell per point (original order); -1 = skipped
