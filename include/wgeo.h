@@ -88,7 +88,7 @@ typedef struct {
                                 Needs WGEO_PREC_MIXED. */
   int32_t spectral;          /* MIXED mode: 1 (default) = each refinement step's correction is a
                                 direct spectral solve (the operator is diagonal in the cosine basis
-                                of the mirrored walls) when res is a power of two >= 16, else
+                                of the mirrored walls) when res is a power of two from 32 to 512, else
                                 multigrid; 0 = always multigrid V-cycles */
   int32_t reserved[3];
   double  tol_rel_adjoint;   /* adjoint solve: stop when ||g - A lambda|| <= tol * ||g|| (default 1e-7) */

@@ -58,7 +58,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   // x, b per coarse level (and a Jacobi buffer t for the unlumped operator)
   const size_t lev = (opt.galerkin ? 3 : 2) * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);
   L.off_levels = take(c, 4 * lev);
-  L.off_dct = take(c, 8 * 512 + 8 * 1024 + 4 * 1024);   // spectral tables for n <= 1024
+  L.off_dct = take(c, 8 * (512 + 160 + 512 + 16) + 4 * (512 + 512));   // spectral tables, n <= 512
   const size_t Pp = (size_t)(P > 0 ? P : 1);
   L.off_pcell = take(c, 4 * Pp);
   L.off_pfrac = take(c, 16 * Pp);
@@ -270,9 +270,12 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->lamff[1] = keep ? h->lamff[0] + N : nullptr;
   h->lam32 = keep ? (float*)(a + L.off_lam32) : nullptr;
   h->level_pool = (float*)(a + L.off_levels);
-  h->dct_tw = (float2*)(a + L.off_dct);
-  h->dct_wm = h->dct_tw + 512;
-  h->dct_s = (float*)(h->dct_wm + 1024);
+  h->dct_t1 = (float2*)(a + L.off_dct);
+  h->dct_w32 = h->dct_t1 + 512;
+  h->dct_wml = h->dct_w32 + 160;
+  h->dct_tr = h->dct_wml + 512;
+  h->dct_sk = (float*)(h->dct_tr + 16);
+  h->dct_skl = h->dct_sk + 512;
   h->pcell = (int*)(a + L.off_pcell);
   h->pfrac = (float4*)(a + L.off_pfrac);
   h->pnrm = keep ? (float4*)(a + L.off_pnrm) : nullptr;

@@ -926,28 +926,70 @@ int vcycle(wgeo_handle* h, int l, float* x0, const float* b0, const float* shift
 // mean, dropped), and the exact inverse transform along z, y and x.  Five
 // in-place passes over the grid (the z pass divides and transforms back).
 //
-// Each one-dimensional DCT-II of n = 2^p points goes through an n-point
-// complex FFT (Makhoul, IEEE TASSP 1980): v_m = x_{2m}, v_{n-1-m} = x_{2m+1},
-// X_k = Re(e^{-i pi k / 2n} V_k).  Its inverse: V_k = e^{i pi k / 2n} (X_k -
-// i X_{n-k}) (X_n = 0), v = IFFT(V), taken as conj(FFT(conj V)) / n.  The FFT
-// is the radix-2 Stockham form (self-sorting, two buffers), 16 lines per
-// block in shared memory, twiddles from tables built in double.
-constexpr int kDctLines = 16;
-constexpr int kDctThreads = 256;
+// Each one-dimensional DCT-II of n points goes through an n-point complex FFT
+// (Makhoul, IEEE TASSP 1980): v_m = x_{2m}, v_{n-1-m} = x_{2m+1}, X_k =
+// Re(e^{-i pi k / 2n} V_k).  Its inverse: V_k = e^{i pi k / 2n} (X_k - i
+// X_{n-k}) (X_n = 0), v = IFFT(V) = conj(FFT(conj V)) / n.  Two real lines
+// share one complex FFT (Z = v_a + i v_b; V_a, V_b from Z_k and conj Z_{n-k};
+// back, IFFT(V_a + i V_b) = v_a + i v_b), one warp per pair.
+//
+// The FFT of n = 32 R points in a warp (the four-step split n = R x 32): lane
+// j holds z_{j + 32 m} in register m; an R-point DFT over m in registers, the
+// twiddle e^{-2 pi i j a / n}, and a 32-point DFT across the lanes by xor
+// shuffles (decimation in frequency), after which lane j register a holds
+// Z_{a + R brev5(j)}.  The transposed sequence (decimation in time across the
+// lanes, twiddle, register DFT) takes that layout back to j + 32 m, so the z
+// pass never leaves registers.  Shared memory holds the block's 32 lines
+// (padded rows: the coalesced tile copies and the scattered lane accesses are
+// both free of bank conflicts) and the twiddle tables; power-of-two
+// 32 <= n <= 512.
+constexpr int kDctTile = 32;      // lines per block: 16 warps, two lines each
+constexpr int kDctThreads = 512;
+constexpr unsigned kFull = 0xffffffffu;
 
 bool use_spectral(const wgeo_handle* h, int n) {
-  return h->opt.spectral && n >= 16 && n <= 512 && (n & (n - 1)) == 0;
+  return h->opt.spectral && n >= 32 && n <= 512 && (n & (n - 1)) == 0;
 }
 
-__global__ void dct_tables_kernel(int n, float2* __restrict__ tw, float2* __restrict__ wm, float* __restrict__ sk) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+__host__ __device__ constexpr int dct_ls(int n) { return (n + n / 32) | 1; }   // odd row stride
+__device__ __forceinline__ int dct_at(int i) { return i + (i >> 5); }
+// Compiler-only fence between the FFT phases: the shared twiddle tables are
+// read again after it instead of being held in registers across phases.
+__device__ __forceinline__ void phase_fence() { asm volatile("" ::: "memory"); }
+__device__ __forceinline__ int brev5(int j) { return (int)(__brev((unsigned)j) >> 27); }
+
+template <int R>
+constexpr size_t dct_smem() {
+  return sizeof(float2) * (32 * R + 160 + 32 * R + 16) + sizeof(float) * 32 * R +
+         sizeof(float) * kDctTile * dct_ls(32 * R);
+}
+
+__global__ void dct_tables_kernel(int n, float2* __restrict__ t1, float2* __restrict__ w32,
+                                  float2* __restrict__ wml, float2* __restrict__ tr,
+                                  float* __restrict__ sk, float* __restrict__ skl) {
+  const int R = n / 32;
+  const int count = n > 160 ? n : 160;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
     double sn, cs;
-    sincospi((double)k / (2.0 * n), &sn, &cs);      // angle pi k / 2n
-    wm[k] = make_float2((float)cs, (float)-sn);
-    sk[k] = (float)(4.0 * sn * sn);
-    if (k < n / 2) {
-      sincospi(2.0 * k / n, &sn, &cs);              // angle 2 pi k / n
-      tw[k] = make_float2((float)cs, (float)-sn);
+    const int a = q >> 5, j = q & 31;
+    if (q < n) {
+      sincospi(2.0 * (double)(j * a) / n, &sn, &cs);
+      t1[q] = make_float2((float)cs, (float)-sn);
+      const int k = a + R * (int)(__brev((unsigned)j) >> 27);
+      sincospi((double)k / (2.0 * n), &sn, &cs);
+      wml[q] = make_float2((float)cs, (float)-sn);
+      skl[q] = (float)(4.0 * sn * sn);
+      sincospi((double)q / (2.0 * n), &sn, &cs);
+      sk[q] = (float)(4.0 * sn * sn);
+    }
+    if (q < 160) {
+      const int hh = 1 << a;                        // stage a combines pairs of hh-point DFTs
+      sincospi((double)(j & (hh - 1)) / hh, &sn, &cs);
+      w32[q] = make_float2((float)cs, (float)-sn);
+    }
+    if (q < R) {
+      sincospi(2.0 * q / R, &sn, &cs);
+      tr[q] = make_float2((float)cs, (float)-sn);
     }
   }
 }
@@ -955,143 +997,332 @@ __global__ void dct_tables_kernel(int n, float2* __restrict__ tw, float2* __rest
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-
-// Forward FFT (e^{-2 pi i jk / n}) of the kDctLines lines of a (n points each,
-// line l at a + l n); returns the buffer that holds the result.
-__device__ float2* fft_lines(float2* a, float2* b, int n, int logn, const float2* __restrict__ tw) {
-  const int half = n >> 1;
-  for (int st = 0; st < logn; ++st) {
-    const int ns = 1 << st;
-    for (int t = threadIdx.x; t < kDctLines * half; t += blockDim.x) {
-      const int l = t >> (logn - 1), j = t & (half - 1);
-      const int k = j & (ns - 1);
-      const float2 v0 = a[l * n + j];
-      const float2 v1 = cmul(a[l * n + j + half], tw[k << (logn - 1 - st)]);
-      const int d = ((j >> st) << (st + 1)) + k;
-      b[l * n + d] = make_float2(v0.x + v1.x, v0.y + v1.y);
-      b[l * n + d + ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
-    }
-    __syncthreads();
-    float2* tmp = a;
-    a = b;
-    b = tmp;
-  }
-  return a;
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(kFull, v.x, m), __shfl_xor_sync(kFull, v.y, m));
+}
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src));
 }
 
-// The position of x_i in Makhoul's reordered sequence v.
-__device__ __forceinline__ int dct_perm(int i, int n) { return (i & 1) ? n - 1 - (i >> 1) : (i >> 1); }
+template <int R>
+__host__ __device__ constexpr int rev_bits(int k) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) r = (r << 1) | ((k & b) ? 1 : 0);
+  return r;
+}
+
+// v <- DFT_R(v) (e^{-2 pi i q a / R}), natural order in and out: radix-2
+// decimation in frequency, then the bit reversal as a register renaming.
+template <int R>
+__device__ __forceinline__ void dft_regs(float2 (&v)[R], const float2* tr) {
+#pragma unroll
+  for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+    for (int g = 0; g < R; g += 2 * h) {
+#pragma unroll
+      for (int t = 0; t < h; ++t) {
+        const float2 x = v[g + t], y = v[g + t + h];
+        v[g + t] = cadd(x, y);
+        v[g + t + h] = t == 0 ? csub(x, y) : cmul(csub(x, y), tr[t * (R / (2 * h))]);
+      }
+    }
+  }
+  float2 w[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) w[k] = v[rev_bits<R>(k)];
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = w[k];
+}
+
+// Forward FFT of the warp's line: in, lane j register m = z_{j + 32 m}; out,
+// lane j register a = Z_{a + R brev5(j)}.
+template <int R>
+__device__ __forceinline__ void fft_warp_dif(float2 (&v)[R], const float2* t1, const float2* w32,
+                                             const float2* tr, int lane) {
+  dft_regs<R>(v, tr);
+#pragma unroll
+  for (int a = 1; a < R; ++a) v[a] = cmul(v[a], t1[a * 32 + lane]);
+#pragma unroll
+  for (int st = 4; st >= 0; --st) {
+    const int h = 1 << st;
+    const bool up = lane & h;
+    const float2 w = w32[st * 32 + lane];
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      const float2 p = shfl_xor2(v[a], h);
+      v[a] = up ? cmul(csub(p, v[a]), w) : cadd(v[a], p);
+    }
+  }
+}
+
+// Forward FFT with the layouts swapped: in, lane j register a = u_{a + R
+// brev5(j)}; out, lane j register m = U_{j + 32 m}.
+template <int R>
+__device__ __forceinline__ void fft_warp_dit(float2 (&v)[R], const float2* t1, const float2* w32,
+                                             const float2* tr, int lane) {
+#pragma unroll
+  for (int st = 0; st <= 4; ++st) {
+    const int h = 1 << st;
+    const bool up = lane & h;
+    const float2 w = w32[st * 32 + lane];
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      const float2 m = up ? cmul(v[a], w) : v[a];
+      const float2 p = shfl_xor2(m, h);
+      v[a] = up ? csub(p, m) : cadd(m, p);
+    }
+  }
+#pragma unroll
+  for (int a = 1; a < R; ++a) v[a] = cmul(v[a], t1[a * 32 + lane]);
+  dft_regs<R>(v, tr);
+}
+
+// v[a] <- f(a, v[a], c_a) for every register, c_a the value at index n - k
+// of the layout k = a + R brev5(lane) (index 0 maps to itself, or to zero
+// with ZERO_ORIGIN); the registers are taken in mirrored pairs (a, R - a), so
+// that only a pair's partners are live at a time.
+template <int R, bool ZERO_ORIGIN, class F>
+__device__ __forceinline__ void mirror_apply(float2 (&v)[R], int lane, F f) {
+  float2 c0 = shfl2(v[0], brev5((32 - brev5(lane)) & 31));
+  if (ZERO_ORIGIN && lane == 0) c0 = make_float2(0.f, 0.f);
+  if (R > 1) {
+    const float2 ch = shfl_xor2(v[R / 2], 31);
+#pragma unroll
+    for (int a = 1; a < R / 2; ++a) {
+      const float2 ca = shfl_xor2(v[R - a], 31), cb = shfl_xor2(v[a], 31);
+      v[a] = f(a, v[a], ca);
+      v[R - a] = f(R - a, v[R - a], cb);
+    }
+    v[R / 2] = f(R / 2, v[R / 2], ch);
+  }
+  v[0] = f(0, v[0], c0);
+}
+
+// The conjugate of the packed inverse input: for each line conj(V_k) =
+// e^{-i pi k/2n} (X_k + i X_{n-k}), and conj(V_a + i V_b) = conj V_a - i conj V_b.
+__device__ __forceinline__ float2 inverse_input(float2 w, float xa, float xan, float xb, float xbn) {
+  const float2 ca = cmul(w, make_float2(xa, xan)), cb = cmul(w, make_float2(xb, xbn));
+  return make_float2(ca.x + cb.y, ca.y - cb.x);
+}
+
+// Position of v_p in x: v_p = x_{2p} (p < n/2), x_{2(n-1-p)+1} (p >= n/2).
+__device__ __forceinline__ int dct_src(int p, int n) { return p < (n >> 1) ? 2 * p : 2 * (n - 1 - p) + 1; }
 
 // MODE 0: forward DCT-II along `axis`; 1: its inverse; 2 (axis z): forward,
-// division by the eigenvalue, inverse.  A block takes kDctLines lines: along
-// x, 16 rows of one plane; along y or z, 16 neighbouring x columns.
-template <int MODE>
-__global__ void __launch_bounds__(kDctThreads) dct_pass_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                               int n, int logn, int axis,
-                                                               const float2* __restrict__ tw,
-                                                               const float2* __restrict__ wm,
-                                                               const float* __restrict__ sk, int q1,
-                                                               const int* __restrict__ gate) {
+// division by the eigenvalue, inverse.  A block takes 32 lines: along x, 32
+// rows of one plane; along y or z, 32 neighbouring x columns.  `in` may be `out`
+// (each block reads and writes only its own lines).
+template <int R, int MODE>
+__global__ void __launch_bounds__(kDctThreads, R <= 8 ? 2 : 1)
+    dct_pass_kernel(const float* in, float* out, int axis, const float2* __restrict__ t1g,
+                    const float2* __restrict__ w32g, const float2* __restrict__ wmg,
+                    const float2* __restrict__ trg, const float* __restrict__ skg,
+                    const float* __restrict__ sklg, int q1, const int* __restrict__ gate) {
+  constexpr int n = 32 * R;
+  constexpr int LS = dct_ls(n);
+  constexpr int kVec = kDctTile * n / 4;                       // float4 per tile
+  constexpr int kIt = (kVec + kDctThreads - 1) / kDctThreads;
   if (*gate) return;
-  extern __shared__ float2 dsm[];
-  float2* A = dsm;
-  float2* B = dsm + kDctLines * n;
-  const int tpp = n / kDctLines;
-  const int fixed = blockIdx.x / tpp, t0 = (blockIdx.x - fixed * tpp) * kDctLines;
-  auto gidx = [&](int l, int i) -> int64_t {
-    if (axis == 0) return ((int64_t)fixed * n + t0 + l) * n + i;
-    if (axis == 1) return ((int64_t)fixed * n + i) * n + t0 + l;
-    return ((int64_t)i * n + fixed) * n + t0 + l;
-  };
-  auto lpos = [&](int q, int& l, int& i) {   // coalesced order: consecutive threads, consecutive addresses
-    if (axis == 0) {
-      l = q >> logn;
-      i = q & (n - 1);
-    } else {
-      l = q & (kDctLines - 1);
-      i = q / kDctLines;
+  extern __shared__ float4 dsm4[];
+  float2* t1 = reinterpret_cast<float2*>(dsm4);
+  float2* w32 = t1 + n;
+  float2* wm = w32 + 160;
+  float2* tr = wm + n;
+  float* skl = reinterpret_cast<float*>(tr + 16);
+  float* S = skl + n;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < n; q += kDctThreads) {
+    t1[q] = t1g[q];
+    wm[q] = wmg[q];
+    if (MODE == 2) skl[q] = sklg[q];
+  }
+  if (tid < 160) w32[tid] = w32g[tid];
+  if (tid < R) tr[tid] = trg[tid];
+
+  const int groups = n / kDctTile;
+  const int fixed = blockIdx.x / groups, t0 = (blockIdx.x - fixed * groups) * kDctTile;
+  // tile element (l, i) -> grid; along x the tile is 32 n contiguous floats,
+  // along y or z n rows of 32 contiguous floats
+  const int64_t nn = (int64_t)n * n;
+  const int64_t base = axis == 0 ? ((int64_t)fixed * n + t0) * n : axis == 1 ? fixed * nn + t0 : (int64_t)fixed * n + t0;
+  const int64_t rstride = axis == 1 ? n : nn;
+  {
+    float4 buf[kIt];
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int q = tid + it * kDctThreads;
+      if (q < kVec) {
+        const int64_t g = axis == 0 ? base + 4 * (int64_t)q : base + (q >> 3) * rstride + 4 * (q & 7);
+        buf[it] = *reinterpret_cast<const float4*>(in + g);
+      }
     }
-  };
-  const int total = kDctLines * n;
-  const float inv_n = 1.f / (float)n;
-  for (int q = threadIdx.x; q < total; q += blockDim.x) {
-    int l, i;
-    lpos(q, l, i);
-    const float x = in[gidx(l, i)];
-    if (MODE == 1)
-      B[l * n + i] = make_float2(x, 0.f);                 // X, to pair X_k with X_{n-k}
-    else
-      A[l * n + dct_perm(i, n)] = make_float2(x, 0.f);
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int q = tid + it * kDctThreads;
+      if (q < kVec) {
+        const float e[4] = {buf[it].x, buf[it].y, buf[it].z, buf[it].w};
+        if (axis == 0) {
+          const int l = (4 * q) / n, i = (4 * q) % n;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) S[l * LS + dct_at(i + c)] = e[c];
+        } else {
+          const int i = q >> 3, l = 4 * (q & 7);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) S[(l + c) * LS + dct_at(i)] = e[c];
+        }
+      }
+    }
   }
   __syncthreads();
+
+  const int warp = tid >> 5, lane = tid & 31;
+  float* Sa = S + (2 * warp) * LS;
+  float* Sb = Sa + LS;
+  const int bl = brev5(lane);
+  float2 v[R];
   if (MODE == 1) {
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int l = q >> logn, k = q & (n - 1);
-      const float xk = B[l * n + k].x, xnk = k ? B[l * n + n - k].x : 0.f;
-      A[l * n + k] = cmul(wm[k], make_float2(xk, xnk));  // e^{-i pi k/2n} conj(X_k - i X_{n-k})
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      const int k = a + R * bl;
+      const float xa = Sa[dct_at(k)], xb = Sb[dct_at(k)];
+      const float xan = k ? Sa[dct_at(n - k)] : 0.f, xbn = k ? Sb[dct_at(n - k)] : 0.f;
+      v[a] = inverse_input(wm[a * 32 + lane], xa, xan, xb, xbn);
     }
-    __syncthreads();
-  }
-  float2* R = fft_lines(A, B, n, logn, tw);
-  float2* F = (R == A) ? B : A;
-  if (MODE == 2) {
-    // X_k, divided by the eigenvalue of mode (kx, ky, kz) = (t0 + l, fixed, k)
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int l = q >> logn, k = q & (n - 1);
-      const float2 w = wm[k], v = R[l * n + k];
-      const float X = v.x * w.x - v.y * w.y;
-      const float sx = sk[t0 + l], sy = sk[fixed], sz = sk[k];
-      float lam;
-      if (q1) {
-        const float mx = 1.f - sx * (1.f / 6.f), my = 1.f - sy * (1.f / 6.f), mz = 1.f - sz * (1.f / 6.f);
-        lam = -(float)kQ1Scale * (sx * my * mz + mx * sy * mz + mx * my * sz);
-      } else {
-        lam = -(sx + sy + sz);
-      }
-      const bool zero_mode = (t0 + l) == 0 && fixed == 0 && k == 0;
-      F[l * n + k] = make_float2(zero_mode ? 0.f : X / lam, 0.f);
+  } else {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int s = dct_at(dct_src(lane + 32 * m, n));
+      v[m] = make_float2(Sa[s], Sb[s]);
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-      const int l = q >> logn, k = q & (n - 1);
-      const float xk = F[l * n + k].x, xnk = k ? F[l * n + n - k].x : 0.f;
-      R[l * n + k] = cmul(wm[k], make_float2(xk, xnk));
-    }
-    __syncthreads();
-    R = fft_lines(R, F, n, logn, tw);
-  }
-  for (int q = threadIdx.x; q < total; q += blockDim.x) {
-    int l, i;
-    lpos(q, l, i);
-    float y;
+    fft_warp_dif<R>(v, t1, w32, tr, lane);
+    phase_fence();
+    // X_k of both lines: V_a = (Z_k + conj Z_{n-k}) / 2, V_b = (Z_k - conj Z_{n-k}) / 2i
+    mirror_apply<R, false>(v, lane, [&](int a, float2 z, float2 c) {
+      const float2 va = make_float2(0.5f * (z.x + c.x), 0.5f * (z.y - c.y));
+      const float2 vb = make_float2(0.5f * (z.y + c.y), 0.5f * (c.x - z.x));
+      const float2 w = wm[a * 32 + lane];
+      return make_float2(w.x * va.x - w.y * va.y, w.x * vb.x - w.y * vb.y);
+    });
+    phase_fence();
     if (MODE == 0) {
-      const float2 w = wm[i], v = R[l * n + i];
-      y = v.x * w.x - v.y * w.y;                          // X_i (i the frequency here)
+      __syncwarp();
+#pragma unroll
+      for (int a = 0; a < R; ++a) {
+        const int s = dct_at(a + R * bl);
+        Sa[s] = v[a].x;
+        Sb[s] = v[a].y;
+      }
     } else {
-      y = R[l * n + dct_perm(i, n)].x * inv_n;            // x_i from v
+      // divide by the eigenvalue of mode (kx, ky, kz) = (t0 + line, fixed, k)
+      const float sxa = skg[t0 + 2 * warp], sxb = skg[t0 + 2 * warp + 1], sy = skg[fixed];
+#pragma unroll
+      for (int a = 0; a < R; ++a) {
+        const float sz = skl[a * 32 + lane];
+        float la, lb;
+        if (q1) {
+          const float my = 1.f - sy * (1.f / 6.f), mz = 1.f - sz * (1.f / 6.f);
+          const float mxa = 1.f - sxa * (1.f / 6.f), mxb = 1.f - sxb * (1.f / 6.f);
+          const float t = sy * mz + my * sz;
+          la = -(float)kQ1Scale * (sxa * my * mz + mxa * t);
+          lb = -(float)kQ1Scale * (sxb * my * mz + mxb * t);
+        } else {
+          la = -(sxa + sy + sz);
+          lb = -(sxb + sy + sz);
+        }
+        const bool zero_a = (t0 + 2 * warp) == 0 && fixed == 0 && a == 0 && lane == 0;
+        v[a] = make_float2(zero_a ? 0.f : v[a].x / la, v[a].y / lb);
+      }
+      phase_fence();
+      mirror_apply<R, true>(v, lane, [&](int a, float2 y, float2 c) {   // Y_n = 0
+        return inverse_input(wm[a * 32 + lane], y.x, c.x, y.y, c.y);
+      });
+      phase_fence();
     }
-    out[gidx(l, i)] = y;
   }
+  if (MODE != 0) {
+    fft_warp_dit<R>(v, t1, w32, tr, lane);
+    __syncwarp();
+    constexpr float inv_n = 1.f / (float)n;
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int s = dct_at(dct_src(lane + 32 * m, n));
+      Sa[s] = v[m].x * inv_n;
+      Sb[s] = -v[m].y * inv_n;
+    }
+  }
+  __syncthreads();
+  {
+    float4 buf[kIt];
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int q = tid + it * kDctThreads;
+      if (q < kVec) {
+        float e[4];
+        if (axis == 0) {
+          const int l = (4 * q) / n, i = (4 * q) % n;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) e[c] = S[l * LS + dct_at(i + c)];
+        } else {
+          const int i = q >> 3, l = 4 * (q & 7);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) e[c] = S[(l + c) * LS + dct_at(i)];
+        }
+        buf[it] = make_float4(e[0], e[1], e[2], e[3]);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int q = tid + it * kDctThreads;
+      if (q < kVec) {
+        const int64_t g = axis == 0 ? base + 4 * (int64_t)q : base + (q >> 3) * rstride + 4 * (q & 7);
+        *reinterpret_cast<float4*>(out + g) = buf[it];
+      }
+    }
+  }
+}
+
+template <int R>
+int spectral_passes(wgeo_handle* h, float* e, const float* r, const int* gate, cudaStream_t s) {
+  constexpr int n = 32 * R;
+  constexpr size_t smem = dct_smem<R>();
+  const int blocks = n * (n / kDctTile);
+  const int q1 = h->opt.galerkin ? 1 : 0;
+#define WGEO_DCT_PASS(MODE, SRC, AXIS)                                                                  \
+  dct_pass_kernel<R, MODE><<<blocks, kDctThreads, smem, s>>>(SRC, e, AXIS, h->dct_t1, h->dct_w32,     \
+                                                              h->dct_wml, h->dct_tr, h->dct_sk,      \
+                                                              h->dct_skl, q1, gate);                 \
+  WGEO_LAUNCH_CHECK();
+  WGEO_DCT_PASS(0, r, 0)
+  WGEO_DCT_PASS(0, e, 1)
+  WGEO_DCT_PASS(2, e, 2)
+  WGEO_DCT_PASS(1, e, 1)
+  WGEO_DCT_PASS(1, e, 0)
+#undef WGEO_DCT_PASS
+  return WGEO_OK;
 }
 
 // e = the solution of L e = r - mean(r) (L the handle's operator), zero mean.
 int spectral_solve(wgeo_handle* h, int n, float* e, const float* r, const int* gate, cudaStream_t s) {
-  int logn = 0;
-  while ((1 << logn) < n) ++logn;
-  const size_t smem = 2 * sizeof(float2) * kDctLines * n;
-  const int blocks = n * (n / kDctLines);
-  const int q1 = h->opt.galerkin ? 1 : 0;
-  dct_pass_kernel<0><<<blocks, kDctThreads, smem, s>>>(r, e, n, logn, 0, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
-  WGEO_LAUNCH_CHECK();
-  dct_pass_kernel<0><<<blocks, kDctThreads, smem, s>>>(e, e, n, logn, 1, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
-  WGEO_LAUNCH_CHECK();
-  dct_pass_kernel<2><<<blocks, kDctThreads, smem, s>>>(e, e, n, logn, 2, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
-  WGEO_LAUNCH_CHECK();
-  dct_pass_kernel<1><<<blocks, kDctThreads, smem, s>>>(e, e, n, logn, 1, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
-  WGEO_LAUNCH_CHECK();
-  dct_pass_kernel<1><<<blocks, kDctThreads, smem, s>>>(e, e, n, logn, 0, h->dct_tw, h->dct_wm, h->dct_s, q1, gate);
-  WGEO_LAUNCH_CHECK();
-  return WGEO_OK;
+  if ((reinterpret_cast<uintptr_t>(e) | reinterpret_cast<uintptr_t>(r)) & 15) return WGEO_ERR_INVALID_ARG;
+  switch (n) {
+    case 32: return spectral_passes<1>(h, e, r, gate, s);
+    case 64: return spectral_passes<2>(h, e, r, gate, s);
+    case 128: return spectral_passes<4>(h, e, r, gate, s);
+    case 256: return spectral_passes<8>(h, e, r, gate, s);
+    case 512: return spectral_passes<16>(h, e, r, gate, s);
+    default: return WGEO_ERR_INVALID_ARG;
+  }
+}
+
+template <int R>
+cudaError_t dct_attr() {
+  const int mx = (int)dct_smem<R>();
+  cudaError_t err = cudaFuncSetAttribute(dct_pass_kernel<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (err == cudaSuccess) err = cudaFuncSetAttribute(dct_pass_kernel<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (err == cudaSuccess) err = cudaFuncSetAttribute(dct_pass_kernel<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return err;
 }
 
 // The twiddle and eigenvalue tables for n, and the shared-memory opt-in of the
@@ -1099,14 +1330,16 @@ int spectral_solve(wgeo_handle* h, int n, float* e, const float* r, const int* g
 int spectral_setup(wgeo_handle* h, int n, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    const int mx = 2 * (int)sizeof(float2) * kDctLines * 512;
-    WGEO_CUDA_TRY(cudaFuncSetAttribute(dct_pass_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    WGEO_CUDA_TRY(cudaFuncSetAttribute(dct_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    WGEO_CUDA_TRY(cudaFuncSetAttribute(dct_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    WGEO_CUDA_TRY(dct_attr<1>());
+    WGEO_CUDA_TRY(dct_attr<2>());
+    WGEO_CUDA_TRY(dct_attr<4>());
+    WGEO_CUDA_TRY(dct_attr<8>());
+    WGEO_CUDA_TRY(dct_attr<16>());
     attr = true;
   }
   if (h->dct_n != n) {
-    dct_tables_kernel<<<div_up(n, 256), 256, 0, s>>>(n, h->dct_tw, h->dct_wm, h->dct_s);
+    dct_tables_kernel<<<div_up(n > 160 ? n : 160, 256), 256, 0, s>>>(n, h->dct_t1, h->dct_w32, h->dct_wml,
+                                                                     h->dct_tr, h->dct_sk, h->dct_skl);
     WGEO_LAUNCH_CHECK();
     h->dct_n = n;
   }

@@ -323,9 +323,13 @@ struct wgeo_handle {
   float2* lamff[2] = {nullptr, nullptr};   // adjoint solution, ping-pong like chiff
   float* lam32 = nullptr;
   float* level_pool = nullptr;
-  float2* dct_tw = nullptr;      // spectral solve: FFT twiddles e^{-2 pi i q / n} (q < n/2)
-  float2* dct_wm = nullptr;      //   e^{-i pi k / (2 n)} (k < n)
-  float* dct_s = nullptr;        //   4 sin^2(pi k / (2 n)) (k < n)
+  // spectral solve tables for n = 32 R (the lane layout: entry a * 32 + j for lane j, register a)
+  float2* dct_t1 = nullptr;      //   e^{-2 pi i j a / n} (a < R)
+  float2* dct_w32 = nullptr;     //   per lane-butterfly stage s (h = 2^s): e^{-i pi (j mod h) / h}
+  float2* dct_wml = nullptr;     //   e^{-i pi k / (2 n)} at k = a + R brev5(j)
+  float2* dct_tr = nullptr;      //   e^{-2 pi i q / R} (q < R)
+  float* dct_sk = nullptr;       //   4 sin^2(pi k / (2 n)) (k < n, natural order)
+  float* dct_skl = nullptr;      //   the same at k = a + R brev5(j)
   int dct_n = 0;                 // n the tables hold (0: none yet)
 
   // points
