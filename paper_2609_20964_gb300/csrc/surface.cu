@@ -470,7 +470,10 @@ __device__ __forceinline__ float puck_dist2(const float3 p, const float4 A, cons
   if (A.w < 0.f) return INFINITY;
   const float3 d = make_float3(p.x - A.x, p.y - A.y, p.z - A.z);
   const float z = d.x * B.x + d.y * B.y + d.z * B.z;
-  const float rho = sqrtf(fmaxf(d.x * d.x + d.y * d.y + d.z * d.z - z * z, 0.f));
+  // rho from the hardware reciprocal square root (a few ulp), scaled down by
+  // 1e-6 so that it stays below the exact value: a lower bound still
+  const float x2 = fmaxf(d.x * d.x + d.y * d.y + d.z * d.z - z * z, 0.f);
+  const float rho = x2 * rsqrtf(fmaxf(x2, 1e-30f)) * (1.f - 1e-6f);
   const float dz = fmaxf(fabsf(z) - B.w, 0.f);
   const float dr = fmaxf(rho - A.w, 0.f);
   return dz * dz + dr * dr;
@@ -608,6 +611,34 @@ __global__ void puck_finalize_kernel(float4* __restrict__ pyr, const float4* __r
   }
 }
 
+// Child-occupancy masks of the internal nodes (levels >= 1): bit q set when
+// child q (x + (q & 1), y + (q >> 1 & 1), z + (q >> 2), at twice the
+// coordinates) exists and holds triangles.  The mask sits in the low 8 bits of
+// the node's radius, rounded up first so that the stored radius never
+// shrinks (the bound stays conservative; at most 2^-14 relative).
+__global__ void puck_mask_kernel(float4* __restrict__ pyr, PyrInfo pi) {
+  const int64_t total = pi.off[pi.nlev - 1] + 1 - pi.off[1];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gi = pi.off[1] + t;
+    int l = 1;
+    while (l + 1 < pi.nlev && gi >= pi.off[l + 1]) ++l;
+    const float4 A = pyr[2 * gi];
+    if (A.w < 0.f) continue;
+    const int64_t r = gi - pi.off[l];
+    const int d = pi.dim[l], dc = pi.dim[l - 1];
+    const int x = (int)(r % d), y = (int)((r / d) % d), z = (int)(r / ((int64_t)d * d));
+    unsigned mask = 0;
+    for (int q = 0; q < 8; ++q) {
+      const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
+      if (cx >= dc || cy >= dc || cz >= dc) continue;
+      const int64_t cg = pi.off[l - 1] + ((int64_t)cz * dc + cy) * dc + cx;
+      if (pyr[2 * cg].w >= 0.f) mask |= 1u << q;
+    }
+    const unsigned up = (__float_as_uint(A.w) + 0xffu) & ~0xffu;
+    pyr[2 * gi].w = __uint_as_float(up | mask);
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -705,7 +736,7 @@ __device__ __forceinline__ unsigned pack_node(int lev, int x, int y, int z) {
 // every pass for its nodes): real triangle distances, so the cut is an upper
 // bound from the start and the search mostly has to certify.
 template <bool COUNT, bool TIES>
-__global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __restrict__ chi, SurfParams g,
+__global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __restrict__ chi, SurfParams g,
                                                           DevState* __restrict__ st,
                                                           const float4* __restrict__ tris_s,
                                                           const int* __restrict__ leaf_off, int64_t cap,
@@ -715,7 +746,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
                                                           int* __restrict__ tie_b, TieSlots tie_cd,
                                                           int* __restrict__ seed_ids, int stride) {
   __shared__ unsigned int s_node[kWarps][kStack];
-  __shared__ long long s_off[12];
+  __shared__ int s_off[12];
   __shared__ int s_dim[12];
   if (threadIdx.x < 12) {
     s_off[threadIdx.x] = pi.off[threadIdx.x];
@@ -805,8 +836,9 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
     const int lev = (int)(e >> 27);
     const int x = (int)(e & 511u), y = (int)((e >> 9) & 511u), z = (int)((e >> 18) & 511u);
     const int dp = s_dim[lev];
-    const int64_t gi = s_off[lev] + ((int64_t)z * dp + y) * dp + x;
-    const float lb = puck_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
+    const int gi = s_off[lev] + (z * dp + y) * dp + x;
+    const float4 An = pyr[2 * gi];
+    const float lb = puck_dist2(p, An, pyr[2 * gi + 1]);
     if (!__any_sync(0xffffffffu, lb < cut)) continue;
     if (COUNT) ++c_nodes;
     if (lev == 0) {
@@ -823,20 +855,19 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_kernel(const float* __rest
       continue;
     }
     const int dc = s_dim[lev - 1];
-    const int64_t cbase = s_off[lev - 1];
+    const int cbase = s_off[lev - 1];
     // children: visit if any lane may improve; order nearest-first by the warp's
     // smallest bound (pushed far-to-near)
     float key[8];
     unsigned ent[8];
     int nc = 0;
+    const unsigned cmask = __float_as_uint(An.w) & 0xffu;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+      if (!((cmask >> q) & 1u)) continue;
       const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
-      if (cx >= dc || cy >= dc || cz >= dc) continue;
-      const int64_t cg = cbase + ((int64_t)cz * dc + cy) * dc + cx;
-      const float4 A = pyr[2 * cg];
-      if (A.w < 0.f) continue;
-      const float d = puck_dist2(p, A, pyr[2 * cg + 1]);
+      const int cg = cbase + (cz * dc + cy) * dc + cx;
+      const float d = puck_dist2(p, pyr[2 * cg], pyr[2 * cg + 1]);
       if (!__any_sync(0xffffffffu, d < cut)) continue;
       const float dm = __shfl_sync(0xffffffffu, d, 0);   // ordering key: the first lane's bound
       int q2 = nc;
@@ -994,7 +1025,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
                                                                 float* __restrict__ dir_out,
                                                                 int* __restrict__ tri_out) {
   __shared__ unsigned int s_node[kWarps][kStack];
-  __shared__ long long s_off[12];
+  __shared__ int s_off[12];
   __shared__ int s_dim[12];
   if (threadIdx.x < 12) {
     s_off[threadIdx.x] = pi.off[threadIdx.x];
@@ -1064,8 +1095,9 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
       const int lev = (int)(en >> 27);
       const int x = (int)(en & 511u), y = (int)((en >> 9) & 511u), z = (int)((en >> 18) & 511u);
       const int dp = s_dim[lev];
-      const int64_t gi = s_off[lev] + ((int64_t)z * dp + y) * dp + x;
-      const float lb = puck_dist2(p, pyr[2 * gi], pyr[2 * gi + 1]);
+      const int gi = s_off[lev] + (z * dp + y) * dp + x;
+      const float4 An = pyr[2 * gi];
+      const float lb = puck_dist2(p, An, pyr[2 * gi + 1]);
       if (!__any_sync(0xffffffffu, lb < cut)) continue;
       if (lev == 0) {
         const int li = leaf_index(x, y, z, nb);
@@ -1075,18 +1107,17 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
         continue;
       }
       const int dc = s_dim[lev - 1];
-      const int64_t cbase = s_off[lev - 1];
+      const int cbase = s_off[lev - 1];
       float key[8];
       unsigned ent[8];
       int nc = 0;
+      const unsigned cmask = __float_as_uint(An.w) & 0xffu;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
+        if (!((cmask >> q) & 1u)) continue;
         const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
-        if (cx >= dc || cy >= dc || cz >= dc) continue;
-        const int64_t cg = cbase + ((int64_t)cz * dc + cy) * dc + cx;
-        const float4 A = pyr[2 * cg];
-        if (A.w < 0.f) continue;
-        const float d = puck_dist2(p, A, pyr[2 * cg + 1]);
+        const int cg = cbase + (cz * dc + cy) * dc + cx;
+        const float d = puck_dist2(p, pyr[2 * cg], pyr[2 * cg + 1]);
         if (!__any_sync(0xffffffffu, d < cut)) continue;
         const float dm = __shfl_sync(0xffffffffu, d, 0);
         int q2 = nc;
@@ -1397,6 +1428,8 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
     const int64_t naux = pi.off[pi.nlev - 1] + 1 - pi.off[1];
     puck_finalize_kernel<<<grid_blocks(naux, 256, 152 * 16), 256, 0, s>>>(h->pyramid, h->pyr_sums, h->pyr_rth,
                                                                           naux, pi.off[1]);
+    WGEO_LAUNCH_CHECK();
+    puck_mask_kernel<<<grid_blocks(naux, 256, 152 * 16), 256, 0, s>>>(h->pyramid, pi);
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStMC, slot, s);
