@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict
   __shared__ double red[32];   // per-warp sums (16 warps x 2)
   __shared__ int s_list[kList];
   __shared__ int s_cnt;
+  __shared__ int s_nb_start[27], s_nb_cnt[27], s_nb_off[28];
   const int tile = blockIdx.x;
   const int tx = tile % ntile, ty = (tile / ntile) % ntile, tz = tile / (ntile * ntile);
   const int T0[3] = {tx * kSplatTile, ty * kSplatTile, tz * kSplatTile};
@@ -199,31 +200,56 @@ __global__ void __launch_bounds__(512) splat_div_kernel(const float4* __restrict
   };
   // the points of the 27 neighbouring tiles whose stencil reaches this tile's
   // V region go to a shared list first (flushed when it could overflow), so
-  // the splatting is spread evenly over the block
-  for (int nt = 0; nt < 27; ++nt) {
+  // the splatting is spread evenly over the block.  The 27 point ranges are
+  // walked as one index space (a prefix over their counts), so a block takes
+  // ceil(total / blockDim) list rounds rather than one round per tile.
+  if (threadIdx.x < 27) {
+    const int nt = threadIdx.x;
     const int ux = tx + nt % 3 - 1, uy = ty + (nt / 3) % 3 - 1, uz = tz + nt / 9 - 1;
-    if (ux < 0 || uy < 0 || uz < 0 || ux >= ntile || uy >= ntile || uz >= ntile) continue;
-    const int t = (uz * ntile + uy) * ntile + ux;
-    const int s0 = tile_off[t], s1 = tile_off[t + 1];
-    for (int base = s0; base < s1; base += blockDim.x) {
-      const int k = base + threadIdx.x;
-      if (k < s1) {
-        const int c = __float_as_int(srec[2 * (int64_t)k].w);
-        const int bc[3] = {cell_x(c), cell_y(c), cell_z(c)};
-        bool rel = true;
+    int s0 = 0, c = 0;
+    if (ux >= 0 && uy >= 0 && uz >= 0 && ux < ntile && uy < ntile && uz < ntile) {
+      const int t = (uz * ntile + uy) * ntile + ux;
+      s0 = tile_off[t];
+      c = tile_off[t + 1] - s0;
+    }
+    s_nb_start[nt] = s0;
+    s_nb_cnt[nt] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int nt = 0; nt < 27; ++nt) {
+      s_nb_off[nt] = acc;
+      acc += s_nb_cnt[nt];
+    }
+    s_nb_off[27] = acc;
+  }
+  __syncthreads();
+  const int total = s_nb_off[27];
+  for (int base = 0; base < total; base += blockDim.x) {
+    const int q = base + threadIdx.x;
+    if (q < total) {
+      int lo = 0, hi = 26;   // the last range starting at or before q (empty ranges share starts)
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_nb_off[mid] <= q) lo = mid; else hi = mid - 1;
+      }
+      const int k = s_nb_start[lo] + (q - s_nb_off[lo]);
+      const int c = __float_as_int(srec[2 * (int64_t)k].w);
+      const int bc[3] = {cell_x(c), cell_y(c), cell_z(c)};
+      bool rel = true;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) rel &= (bc[a] >= T0[a] - 2) && (bc[a] <= T0[a] + kSplatTile + 1);
-        if (rel) s_list[atomicAdd(&s_cnt, 1)] = k;
-      }
+      for (int a = 0; a < 3; ++a) rel &= (bc[a] >= T0[a] - 2) && (bc[a] <= T0[a] + kSplatTile + 1);
+      if (rel) s_list[atomicAdd(&s_cnt, 1)] = k;
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    __syncthreads();   // every thread has read the count before the next appends
+    if (cnt > kList - (int)blockDim.x) {
+      for (int r = threadIdx.x; r < cnt; r += blockDim.x) splat_point(s_list[r]);
       __syncthreads();
-      const int cnt = s_cnt;
-      __syncthreads();   // every thread has read the count before the next appends
-      if (cnt > kList - (int)blockDim.x) {
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) splat_point(s_list[q]);
-        __syncthreads();
-        if (threadIdx.x == 0) s_cnt = 0;
-        __syncthreads();
-      }
+      if (threadIdx.x == 0) s_cnt = 0;
+      __syncthreads();
     }
   }
   {
