@@ -123,6 +123,22 @@ def dist_env():
     return ws, rank, local
 
 
+def job_time_ms(local_ms: float, ws: int, device) -> float:
+    """The whole job's time of a timed region: the slowest rank's (every rank
+    timed the same region between barriers; at N = 1, this rank's own)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, cells_per_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank's cells over the slowest rank's time."""
+    return ws * cells_per_step * steps / (total_ms / 1e3)
+
+
 # --------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -189,14 +205,10 @@ def run_ours(args):
     clocks.stop()
     st_timed = rec.stage_times(reset=True)
     timed_stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in st_timed.items()}
-    total_ms = e0.elapsed_time(e1)
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    t = torch.tensor([total_ms], device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = job_time_ms(e0.elapsed_time(e1), ws, "cuda")
     ms_per_step = total_ms / args.steps
-    value = ws * N * args.steps / (total_ms / 1e3)
+    value = job_rate(ws, N, args.steps, total_ms)
 
     # forward-only rates (mixed and plain FP32) on the same input
     def time_it(fn, k):
@@ -270,12 +282,13 @@ def run_ours(args):
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     ke = max(3, args.steps // 2)
+    barrier()
     a.record(stream)
     for _ in range(ke):
         e2e_step()
     b.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = a.elapsed_time(b) / ke
+    barrier()
+    e2e_ms = job_time_ms(a.elapsed_time(b), ws, "cuda") / ke
     h2d = (p.nbytes + n.nbytes + q.nbytes + g.nbytes)
     d2h = 2 * NPTS * 3 * 4
 
@@ -325,7 +338,7 @@ def run_ours(args):
                        "tri_tests_per_node": info_t["sdf_tri_tests"] / N,
                        "near_tie_nodes": info_t["sdf_tie_nodes"]},
         "stage_ms": stages,
-        "e2e": {"value": N / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(ws, N, 1, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps,
