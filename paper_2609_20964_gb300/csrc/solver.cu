@@ -1326,16 +1326,15 @@ cudaError_t dct_attr() {
 }
 
 // The twiddle and eigenvalue tables for n, and the shared-memory opt-in of the
-// pass kernels (host calls, kept out of any capture).
+// pass kernels on the handle's device (host calls, kept out of any capture).
 int spectral_setup(wgeo_handle* h, int n, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  if (!h->dct_attr) {
     WGEO_CUDA_TRY(dct_attr<1>());
     WGEO_CUDA_TRY(dct_attr<2>());
     WGEO_CUDA_TRY(dct_attr<4>());
     WGEO_CUDA_TRY(dct_attr<8>());
     WGEO_CUDA_TRY(dct_attr<16>());
-    attr = true;
+    h->dct_attr = true;
   }
   if (h->dct_n != n) {
     dct_tables_kernel<<<div_up(n > 160 ? n : 160, 256), 256, 0, s>>>(n, h->dct_t1, h->dct_w32, h->dct_wml,

@@ -331,6 +331,7 @@ struct wgeo_handle {
   float* dct_sk = nullptr;       //   4 sin^2(pi k / (2 n)) (k < n, natural order)
   float* dct_skl = nullptr;      //   the same at k = a + R brev5(j)
   int dct_n = 0;                 // n the tables hold (0: none yet)
+  bool dct_attr = false;         // shared-memory opt-in of the pass kernels done (per device)
 
   // points
   int* pcell = nullptr;          // packed central cell per point (original order); -1 = skipped
