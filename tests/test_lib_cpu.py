@@ -69,6 +69,11 @@ def test_null_and_bad_args_rejected_on_host(lib):
     assert lib.wgeo_query(None, None, 0, None, None, None) == 1
     assert lib.wgeo_backward(None, None, None, None, None, None, 0, None, None, None, None) == 1
     assert lib.wgeo_get_info(None, None) == 1
+    # the entry points of the NEXT rows reject a null handle before any device call
+    assert lib.wgeo_query_exact(None, None, 0, None, None, None) == 1
+    assert lib.wgeo_backward_exact(None, None, None, None, None, 0, None, None, None, None) == 1
+    assert lib.wgeo_estimate_normals(None, None, 0, None, 0.1, 1e-4, None, None, None) == 1
+    assert lib.wgeo_orient_normals(None, None, 0, None, 2.5, 2, None, None, None, None) == 1
 
 
 def test_library_mc_table_equals_oracle_golden(lib):
