@@ -25,7 +25,7 @@ def __getattr__(name):
     if name in ("Reconstructor", "sh_surface", "sh_surface_backward"):
         from . import api
         return getattr(api, name)
-    if name in ("sdf_query", "sdf_query_exact", "sdf_grid", "sh_points", "WgeoQueryFunction",
+    if name in ("sdf_query", "sdf_query_exact", "sdf_grid", "sh_points", "WgeoFunction", "WgeoQueryFunction",
                 "WgeoExactQueryFunction", "WgeoGridFunction", "SHSurfaceFunction"):
         from . import autograd
         return getattr(autograd, name)

@@ -90,6 +90,11 @@ class SHSurfaceFunction(torch.autograd.Function):
         return dth, None, None, None
 
 
+# The general entry: (points, normals, q) -> (phi(q), n(q)), differentiable in
+# all three.
+WgeoFunction = WgeoQueryFunction
+
+
 def sdf_query(points, normals, q, recon: Reconstructor, bbox, res: int):
     return WgeoQueryFunction.apply(points, normals, q, recon, bbox, res)
 

@@ -89,3 +89,12 @@ def test_library_mc_table_equals_oracle_golden(lib):
         got = tris[c, :counts[c]].reshape(-1).tolist()
         assert got == want, f"case {c}"
         assert np.all(tris[c, counts[c]:] == -1)
+
+
+def test_python_layer_names():
+    # the autograd entry and the serving loop are importable without a GPU
+    torch = pytest.importorskip("torch")
+    import paper_2609_20964_gb300 as W
+    assert issubclass(W.WgeoFunction, torch.autograd.Function)
+    assert W.WgeoFunction is W.WgeoQueryFunction
+    assert callable(W.Server) and hasattr(W.Server, "submit")
