@@ -21,7 +21,7 @@ struct Layout {
   size_t total = 0;
   size_t off_b32, off_chi32, off_chi64, off_r32, off_e32, off_phi, off_ctri, off_dphi64, off_dchi64,
       off_lam64, off_lam32, off_levels, off_dct, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
-      off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_tris_s, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
+      off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_tris_lo, off_tris_s, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
       off_scan, off_state, off_dp_cell, off_dp_count, off_dp_off, off_dp_cursor, off_dp_scan, off_dp_tmp,
       off_dp_sorted, off_dp_key, off_dp_gbox, off_or_scal;
   size_t n_partials, n_scan, n_dp_scan;
@@ -78,6 +78,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   if (cap < 4096) cap = 4096;
   L.cap = cap;
   L.off_tris = take(c, sizeof(Tri) * (size_t)cap);
+  L.off_tris_lo = take(c, keep ? sizeof(Tri) * (size_t)cap : 0);
   L.off_tris_s = take(c, sizeof(float4) * kTriRec * (size_t)cap);
   L.off_pyr = take(c, 32 * pyramid_nodes(nb));
   L.off_pyr_sums = take(c, 32 * pyramid_aux_nodes(nb));
@@ -288,6 +289,7 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->leaf_off = (int*)(a + L.off_leaf_off);
   h->mesh_cap = L.cap;
   h->tris = (Tri*)(a + L.off_tris);
+  h->tris_lo = keep ? (Tri*)(a + L.off_tris_lo) : nullptr;
   h->tris_s = (float4*)(a + L.off_tris_s);
   h->pyramid = (float4*)(a + L.off_pyr);
   h->pyr_sums = (float4*)(a + L.off_pyr_sums);

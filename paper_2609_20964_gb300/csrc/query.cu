@@ -254,7 +254,14 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
 // search record, as in the forward search; node coordinates from per-axis
 // tables (the forward's float positions), the sign test against the
 // smallest float not below c, c - chi1 from c as a float-float pair, and the
-// dL/dc sum in float-float, so no node needs the FP64 pipe.
+// dL/dc sum in float-float, so no node needs the FP64 pipe.  When the
+// forward kept the vertices' low parts (tris_lo) and solved in float-float
+// (chiff), the closest point is taken from p - a with a's low part, on the
+// search record whose edge vectors come from the ~48-bit vertices, and the
+// indicator values of each vertex's cube edge carry their float-float low
+// parts: the weights then follow the refined surface, not its float32
+// rounding, which a far node's closest point would amplify by distance over
+// edge length.
 
 // LIST = false: every node with a seed; a node whose closest triangle is a
 // sliver (its float32 weights would lose their digits) is appended to
@@ -262,8 +269,9 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
 // FP64.  Two passes, so the rare FP64 work does not stall whole warps.
 template <bool LIST>
 __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int* __restrict__ ctri,
-                                      const float* __restrict__ chi, const DevState* __restrict__ st,
-                                      const Tri* __restrict__ tris, const float4* __restrict__ tris_s, QParams g,
+                                      const float* __restrict__ chi, ChiFF chiff, const DevState* __restrict__ st,
+                                      const Tri* __restrict__ tris, const Tri* __restrict__ tris_lo,
+                                      const float4* __restrict__ tris_s, QParams g,
                                       double* __restrict__ dchi, double* __restrict__ partials,
                                       int* __restrict__ slivers, unsigned* __restrict__ nsliver) {
   __shared__ double red[32];
@@ -280,6 +288,7 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
   const float hf = (float)g.h;
   const unsigned un = (unsigned)n;
   const unsigned N = LIST ? *nsliver : un * un * un;
+  const float2* __restrict__ xff = chiff.p[0] ? chiff.p[st->fwd.xidx] : nullptr;
   float2 dcacc = make_float2(0.f, 0.f);   // dL/dc: terms of both signs that nearly cancel
   for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < N; it += gridDim.x * blockDim.x) {
     const unsigned o = LIST ? (unsigned)slivers[it] : it;
@@ -300,7 +309,11 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
         slivers[atomicAdd(nsliver, 1u)] = (int)o;
         continue;
       }
-      const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+      float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+      if (tris_lo) {
+        const float4 al = tris_lo[t].a;
+        ap = make_float3(ap.x - al.x, ap.y - al.y, ap.z - al.z);
+      }
       const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
       const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
       float v, w;
@@ -314,8 +327,14 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
       u[0] = rx * invd, u[1] = ry * invd, u[2] = rz * invd;
       bw[0] = fmaxf(1.f - v - w, 0.f), bw[1] = v, bw[2] = w;
     } else {
-      const double pd[3] = {p.x, p.y, p.z}, ad[3] = {tr.a.x, tr.a.y, tr.a.z}, bd[3] = {tr.b.x, tr.b.y, tr.b.z},
-                   cdv[3] = {tr.c.x, tr.c.y, tr.c.z};
+      double ad[3] = {tr.a.x, tr.a.y, tr.a.z}, bd[3] = {tr.b.x, tr.b.y, tr.b.z}, cdv[3] = {tr.c.x, tr.c.y, tr.c.z};
+      if (tris_lo) {
+        const Tri tl = tris_lo[t];
+        ad[0] += tl.a.x, ad[1] += tl.a.y, ad[2] += tl.a.z;
+        bd[0] += tl.b.x, bd[1] += tl.b.y, bd[2] += tl.b.z;
+        cdv[0] += tl.c.x, cdv[1] += tl.c.y, cdv[2] += tl.c.z;
+      }
+      const double pd[3] = {p.x, p.y, p.z};
       double bw64[3], dir64[3];
       if (!(closest_point_fp64(pd, ad, bd, cdv, bw64, dir64) > 0.0)) continue;
       for (int q = 0; q < 3; ++q) {
@@ -332,9 +351,17 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
       const int ax = (int)(gid % 3u);
       const unsigned pl = gid / 3u;
       const unsigned stv = (ax == 0) ? 1u : (ax == 1 ? un : un * un);
-      const float c1 = chi[pl], c2 = chi[pl + stv];
-      const float den = c2 - c1;                                   // neighbouring values: exact
-      const float cm = __fadd_rn(__fsub_rn(c_hi, c1), c_lo);       // c - chi1, keeping c's low bits
+      float den, cm;
+      if (xff) {
+        // the refined values: hi differences exact or within one rounding, lo parts added
+        const float2 f1 = xff[pl], f2 = xff[pl + stv];
+        den = __fadd_rn(__fsub_rn(f2.x, f1.x), __fsub_rn(f2.y, f1.y));
+        cm = __fadd_rn(__fsub_rn(__fsub_rn(c_hi, f1.x), f1.y), c_lo);
+      } else {
+        const float c1 = chi[pl], c2 = chi[pl + stv];
+        den = c2 - c1;                                             // neighbouring values: exact
+        cm = __fadd_rn(__fsub_rn(c_hi, c1), c_lo);                 // c - chi1, keeping c's low bits
+      }
       const float eta = cm / den;
       // dL/dP_v[ax] = -s dphi beta_v u[ax];  dP/deta = h e_ax
       const float deta = -sgn * gphi * bw[q] * u[ax] * hf;
@@ -373,8 +400,9 @@ __global__ void dc_add_kernel(const double* __restrict__ partials, int nblocks, 
 // distance or none (empty surface) contribute nothing.
 __global__ void exact_adjoint_kernel(const float* __restrict__ q, int nq, const float* __restrict__ g_sdf,
                                      const float* __restrict__ tsdf, const float* __restrict__ tgrad,
-                                     const int* __restrict__ ttri, const float* __restrict__ chi,
+                                     const int* __restrict__ ttri, const float* __restrict__ chi, ChiFF chiff,
                                      const DevState* __restrict__ st, const Tri* __restrict__ tris,
+                                     const Tri* __restrict__ tris_lo,
                                      const float4* __restrict__ tris_s, QParams g, double* __restrict__ dchi,
                                      double* __restrict__ partials, float* __restrict__ d_q) {
   __shared__ double red[32];
@@ -382,6 +410,7 @@ __global__ void exact_adjoint_kernel(const float* __restrict__ q, int nq, const 
   const float c_hi = (float)cd, c_lo = (float)(cd - (double)c_hi);
   const float hf = (float)g.h;
   const unsigned un = (unsigned)g.res;
+  const float2* __restrict__ xff = chiff.p[0] ? chiff.p[st->fwd.xidx] : nullptr;
   float2 dcacc = make_float2(0.f, 0.f);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
     const float gi = g_sdf[i], d = tsdf[i];
@@ -397,7 +426,11 @@ __global__ void exact_adjoint_kernel(const float* __restrict__ q, int nq, const 
     const float3 p = make_float3(q[3 * (int64_t)i], q[3 * (int64_t)i + 1], q[3 * (int64_t)i + 2]);
     const float4* rec = tris_s + kTriRec * (int64_t)t;
     const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
-    const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+    float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
+    if (tris_lo) {
+      const float4 al = tris_lo[t].a;
+      ap = make_float3(ap.x - al.x, ap.y - al.y, ap.z - al.z);
+    }
     const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
     const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
     float v, w;
@@ -405,8 +438,14 @@ __global__ void exact_adjoint_kernel(const float* __restrict__ q, int nq, const 
     float bw[3] = {fmaxf(1.f - v - w, 0.f), v, w};
     const Tri tr = tris[t];
     if (!(r0.w * r2.w * r3.w < kSliverKappa)) {
-      const double pd[3] = {p.x, p.y, p.z}, ad[3] = {tr.a.x, tr.a.y, tr.a.z}, bd[3] = {tr.b.x, tr.b.y, tr.b.z},
-                   cdv[3] = {tr.c.x, tr.c.y, tr.c.z};
+      double ad[3] = {tr.a.x, tr.a.y, tr.a.z}, bd[3] = {tr.b.x, tr.b.y, tr.b.z}, cdv[3] = {tr.c.x, tr.c.y, tr.c.z};
+      if (tris_lo) {
+        const Tri tl = tris_lo[t];
+        ad[0] += tl.a.x, ad[1] += tl.a.y, ad[2] += tl.a.z;
+        bd[0] += tl.b.x, bd[1] += tl.b.y, bd[2] += tl.b.z;
+        cdv[0] += tl.c.x, cdv[1] += tl.c.y, cdv[2] += tl.c.z;
+      }
+      const double pd[3] = {p.x, p.y, p.z};
       double bw64[3], dir64[3];
       closest_point_fp64(pd, ad, bd, cdv, bw64, dir64);
       for (int q = 0; q < 3; ++q) bw[q] = (float)bw64[q];
@@ -419,9 +458,16 @@ __global__ void exact_adjoint_kernel(const float* __restrict__ q, int nq, const 
       const int ax = (int)(gid % 3u);
       const unsigned pl = gid / 3u;
       const unsigned stv = (ax == 0) ? 1u : (ax == 1 ? un : un * un);
-      const float c1 = chi[pl], c2 = chi[pl + stv];
-      const float den = c2 - c1;
-      const float cm = __fadd_rn(__fsub_rn(c_hi, c1), c_lo);
+      float den, cm;
+      if (xff) {
+        const float2 f1 = xff[pl], f2 = xff[pl + stv];
+        den = __fadd_rn(__fsub_rn(f2.x, f1.x), __fsub_rn(f2.y, f1.y));
+        cm = __fadd_rn(__fsub_rn(__fsub_rn(c_hi, f1.x), f1.y), c_lo);
+      } else {
+        const float c1 = chi[pl], c2 = chi[pl + stv];
+        den = c2 - c1;
+        cm = __fadd_rn(__fsub_rn(c_hi, c1), c_lo);
+      }
       const float eta = cm / den;
       const float deta = -gi * bw[k] * us[ax] * hf;
       const float wq = deta / den;
@@ -671,12 +717,14 @@ int backward_mesh_nodes(wgeo_handle* h, cudaStream_t s) {
   // the sliver nodes between the two passes
   int* slivers = reinterpret_cast<int*>(h->e32);
   WGEO_CUDA_TRY(cudaMemsetAsync(&h->dstate->nsliver, 0, sizeof(unsigned), s));
-  sdf_mc_adjoint_kernel<false><<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, h->tris_s,
-                                                  qparams(h), h->dchi64, h->partials, slivers, &h->dstate->nsliver);
+  const ChiFF cff = chiff_of(h);
+  sdf_mc_adjoint_kernel<false><<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, cff, h->dstate, h->tris,
+                                                  h->tris_lo, h->tris_s, qparams(h), h->dchi64, h->partials,
+                                                  slivers, &h->dstate->nsliver);
   WGEO_LAUNCH_CHECK();
-  sdf_mc_adjoint_kernel<true><<<nb2, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, h->dstate, h->tris, h->tris_s,
-                                                  qparams(h), h->dchi64, h->partials + nb, slivers,
-                                                  &h->dstate->nsliver);
+  sdf_mc_adjoint_kernel<true><<<nb2, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, cff, h->dstate, h->tris,
+                                                  h->tris_lo, h->tris_s, qparams(h), h->dchi64, h->partials + nb,
+                                                  slivers, &h->dstate->nsliver);
   WGEO_LAUNCH_CHECK();
   dc_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, nb + nb2, h->dstate);
   WGEO_LAUNCH_CHECK();
@@ -754,9 +802,9 @@ int launch_backward_exact(wgeo_handle* h, const float* d_sdf_grid, const float* 
     rc = launch_query_exact_chunk(h, q + 3 * c0, nq, tsdf, tgrad, ttri, s);
     if (rc) return rc;
     const int nb = grid_blocks(nq, 256, kPartials);
-    exact_adjoint_kernel<<<nb, 256, 0, s>>>(q + 3 * c0, nq, d_sdf_q + c0, tsdf, tgrad, ttri, h->chi32, h->dstate,
-                                            h->tris, h->tris_s, qparams(h), h->dchi64, h->partials,
-                                            d_q ? d_q + 3 * c0 : nullptr);
+    exact_adjoint_kernel<<<nb, 256, 0, s>>>(q + 3 * c0, nq, d_sdf_q + c0, tsdf, tgrad, ttri, h->chi32,
+                                            chiff_of(h), h->dstate, h->tris, h->tris_lo, h->tris_s, qparams(h),
+                                            h->dchi64, h->partials, d_q ? d_q + 3 * c0 : nullptr);
     WGEO_LAUNCH_CHECK();
     dc_add_kernel<<<1, 1024, 0, s>>>(h->partials, nb, h->dstate);
     WGEO_LAUNCH_CHECK();

@@ -313,11 +313,19 @@ __device__ __forceinline__ void edge_lower_offset(int e, int& ox, int& oy, int& 
 }
 
 // Emits each brick's triangles contiguously (Morton cube order) and the
-// triangle offset of each of its 8 sub-bricks (octree leaves).
-__global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ chi, SurfParams g,
+// triangle offset of each of its 8 sub-bricks (octree leaves).  A vertex is
+// placed in FP64 from the cube edge's two indicator values (Eq. 28); with
+// `chiff` (the refined float-float indicator, current buffer chosen by the
+// solve's index) those values carry the float-float low parts, so the vertex
+// follows the refined solution rather than its float32 copy.  tris holds the
+// vertices rounded to float32; tris_lo (may be null) their residuals
+// (double vertex - float vertex, rounded to float), so that hi + lo keeps
+// about 48 bits: near-tie decisions and the adjoint's closest points use it.
+__global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ chi, ChiFF chiff, SurfParams g,
                                                      const DevState* __restrict__ st,
                                                      const int* __restrict__ brick_off, int64_t cap,
-                                                     Tri* __restrict__ tris, int* __restrict__ leaf_off) {
+                                                     Tri* __restrict__ tris, Tri* __restrict__ tris_lo,
+                                                     int* __restrict__ leaf_off) {
   const int br = blockIdx.x;
   const int base = brick_off[br];
   if (brick_off[br + 1] == base) {
@@ -347,11 +355,13 @@ __global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ c
   __syncthreads();
   const int excl = incl - cnt + (w ? wt[0] : 0);
   if ((threadIdx.x & 7) == 0) leaf_off[8 * (int64_t)br + (threadIdx.x >> 3)] = base + excl;
+  const float2* __restrict__ xff = chiff.p[0] ? chiff.p[st->fwd.xidx] : nullptr;
   for (int q = 0; q < cnt; ++q) {
     const int64_t idx = (int64_t)base + excl + q;
     if (idx >= cap) break;
-    Tri tr;
+    Tri tr, tl;
     float4* out[3] = {&tr.a, &tr.b, &tr.c};
+    float4* outl[3] = {&tl.a, &tl.b, &tl.c};
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
       const int e = c_mc_tris[code][q][v];
@@ -360,15 +370,27 @@ __global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ c
       const int pi = i + ox, pj = j + oy, pk = k + oz;
       const int64_t p = lin3(pi, pj, pk, n);
       const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
-      const double c1 = (double)chi[p], c2 = (double)chi[p + stride];
+      double c1, c2;
+      if (xff) {
+        const float2 f1 = xff[p], f2 = xff[p + stride];
+        c1 = (double)f1.x + (double)f1.y;
+        c2 = (double)f2.x + (double)f2.y;
+      } else {
+        c1 = (double)chi[p];
+        c2 = (double)chi[p + stride];
+      }
       const double eta = (c - c1) / (c2 - c1);
       double pos[3] = {g.lo[0] + (pi + 0.5) * g.h, g.lo[1] + (pj + 0.5) * g.h,
                        g.lo[2] + (pk + 0.5) * g.h};
       pos[ax] += eta * g.h;
       const int gid = (int)(3 * p + ax);
-      *out[v] = make_float4((float)pos[0], (float)pos[1], (float)pos[2], __int_as_float(gid));
+      const float hx = (float)pos[0], hy = (float)pos[1], hz = (float)pos[2];
+      *out[v] = make_float4(hx, hy, hz, __int_as_float(gid));
+      *outl[v] = make_float4((float)(pos[0] - (double)hx), (float)(pos[1] - (double)hy),
+                             (float)(pos[2] - (double)hz), 0.f);
     }
     tris[idx] = tr;
+    if (tris_lo) tris_lo[idx] = tl;
   }
 }
 
@@ -395,24 +417,45 @@ __device__ __forceinline__ int leaf_index(int lx, int ly, int lz, int nb) {
 
 constexpr float kPuckPad = 1e-5f;   // relative inflation: rounding of the bound stays conservative
 
+// 10-bit hash of a marching-cubes vertex (its global edge id).
+__device__ __forceinline__ unsigned vertex_hash10(float gid_bits) {
+  return (__float_as_uint(gid_bits) * 0x9E3779B1u) >> 22;
+}
+
 // Search record of a triangle for the distance search: vertex a and the edge
-// vectors ab, ac with their Gram entries, and the reciprocals the Voronoi
-// regions divide by (0 for a zero-length edge or a collapsed triangle).
-__device__ __forceinline__ void write_search_record(const Tri& tr, float4* __restrict__ rec) {
+// vectors ab, ac with the Gram entries |ab|^2 and |ac|^2 (ab.ac is formed
+// where it is used), the reciprocals the Voronoi regions divide by (0 for a
+// zero-length edge or a collapsed triangle), and in the slot of ab.ac the
+// 10-bit hashes of the three vertices (bits 0-9 a, 10-19 b, 20-29 c), which
+// name a closest vertex or edge without another memory access.
+// With the vertices' low parts (lo, may be null) the edge vectors are the
+// float32 roundings of the differences of the ~48-bit vertices, not the
+// differences of the float32 vertices: their directions then carry float32
+// rounding (~6e-8 relative) instead of the vertices' absolute rounding,
+// which a far node's closest point would amplify by distance / edge length.
+__device__ __forceinline__ void write_search_record(const Tri& tr, const Tri* lo, float4* __restrict__ rec) {
   const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
-  const float3 ab = sub3(b, a), ac = sub3(c, a), bc = sub3(c, b);
-  const float e00 = dot3(ab, ab), e01 = dot3(ab, ac), e11 = dot3(ac, ac), ebc = dot3(bc, bc);
+  float3 ab = sub3(b, a), ac = sub3(c, a), bc = sub3(c, b);
+  if (lo) {
+    const float3 al = f3(lo->a), bl = f3(lo->b), cl = f3(lo->c);
+    ab = make_float3(ab.x + (bl.x - al.x), ab.y + (bl.y - al.y), ab.z + (bl.z - al.z));
+    ac = make_float3(ac.x + (cl.x - al.x), ac.y + (cl.y - al.y), ac.z + (cl.z - al.z));
+    bc = make_float3(bc.x + (cl.x - bl.x), bc.y + (cl.y - bl.y), bc.z + (cl.z - bl.z));
+  }
+  const float e00 = dot3(ab, ab), e11 = dot3(ac, ac), ebc = dot3(bc, bc);
   const float3 cr = cross3(ab, ac);
-  const float det = dot3(cr, cr);   // = e00 e11 - e01^2, without the cancellation
+  const float det = dot3(cr, cr);   // = |ab|^2 |ac|^2 - (ab.ac)^2, without the cancellation
   rec[0] = make_float4(a.x, a.y, a.z, e00);
-  rec[1] = make_float4(ab.x, ab.y, ab.z, e01);
+  const unsigned vk = vertex_hash10(tr.a.w) | (vertex_hash10(tr.b.w) << 10) | (vertex_hash10(tr.c.w) << 20);
+  rec[1] = make_float4(ab.x, ab.y, ab.z, __uint_as_float(vk));
   rec[2] = make_float4(ac.x, ac.y, ac.z, e11);
   rec[3] = make_float4(e00 > 0.f ? 1.f / e00 : 0.f, e11 > 0.f ? 1.f / e11 : 0.f, ebc > 0.f ? 1.f / ebc : 0.f,
                        det > 0.f ? 1.f / det : 0.f);
 }
 
-__global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const int* __restrict__ leaf_off, int nb,
-                                 int64_t cap, float4* __restrict__ pyr, float4* __restrict__ tris_s) {
+__global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const Tri* __restrict__ tris_lo,
+                                 const int* __restrict__ leaf_off, int nb, int64_t cap, float4* __restrict__ pyr,
+                                 float4* __restrict__ tris_s) {
   const int nl = 2 * nb;
   const int64_t nleaf = (int64_t)nl * nl * nl;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
@@ -429,7 +472,12 @@ __global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const int* __rest
     float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
     for (int64_t q = s0; q < s1; ++q) {
       const Tri tr = tris[q];
-      write_search_record(tr, tris_s + kTriRec * q);
+      if (tris_lo) {
+        const Tri tl = tris_lo[q];
+        write_search_record(tr, &tl, tris_s + kTriRec * q);
+      } else {
+        write_search_record(tr, nullptr, tris_s + kTriRec * q);
+      }
       const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
       cs.x += a.x + b.x + c.x;
       cs.y += a.y + b.y + c.y;
@@ -666,17 +714,44 @@ struct TieSlots {
 // p - y = ap - v ab - w ac is formed relative to a, so its rounding scales
 // with the distance and the edge length rather than with the coordinates.
 
-__device__ __forceinline__ float tri_dist2_rec(const float3 p, const float4* __restrict__ rec) {
+__device__ __forceinline__ float tri_dist2_rec(const float3 p, const float4* __restrict__ rec, float& v, float& w,
+                                               unsigned& vk) {
   const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
   const float3 ap = make_float3(p.x - r0.x, p.y - r0.y, p.z - r0.z);
   const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;   // ab . ap
   const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;   // ac . ap
-  float v, w;
   rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
+  vk = __float_as_uint(r1.w);
   const float rx = ap.x - v * r1.x - w * r2.x;
   const float ry = ap.y - v * r1.y - w * r2.y;
   const float rz = ap.z - v * r1.z - w * r2.z;
   return rx * rx + ry * ry + rz * rz;
+}
+__device__ __forceinline__ float tri_dist2_rec(const float3 p, const float4* __restrict__ rec) {
+  float v, w;
+  unsigned vk;
+  return tri_dist2_rec(p, rec, v, w, vk);
+}
+
+// Key (32-bit hash; callers keep its top bits) of a node's closest feature on triangle t, from the weights
+// (v, w) of its closest point y = a + v ab + w ac and the record's vertex
+// hashes: a vertex (weights 0 / 1) by its hash, an edge (one weight 0, or
+// v = 1 - w) by its two, a face by the triangle.  Triangles that share the
+// closest vertex or edge give the same key.
+__device__ __forceinline__ unsigned feature_key(float v, float w, unsigned vk, int t) {
+  const unsigned ha = vk & 1023u, hb = (vk >> 10) & 1023u, hc = (vk >> 20) & 1023u;
+  unsigned x;
+  auto edge = [](unsigned p, unsigned q) { return (1u << 20) | (min(p, q) << 10) | max(p, q); };
+  if (w == 0.f) {
+    x = (v == 0.f) ? ha : (v == 1.f ? hb : edge(ha, hb));
+  } else if (v == 0.f) {
+    x = (w == 1.f) ? hc : edge(ha, hc);
+  } else if (v == 1.f - w) {
+    x = edge(hb, hc);
+  } else {
+    x = (2u << 20) ^ (unsigned)t;
+  }
+  return ((x * 0x9E3779B1u) ^ 0x7F4A7C15u) * 0x85EBCA6Bu;
 }
 
 // The same distance in float-float for the near-tie decisions.  Only ap and
@@ -702,6 +777,32 @@ __device__ __forceinline__ Ff tri_dist2_rec_ff(const Vec3<Ff> p, const float4* _
   const Ff rx = apx - (two_prod_ff(v, r1.x) + two_prod_ff(w, r2.x));
   const Ff ry = apy - (two_prod_ff(v, r1.y) + two_prod_ff(w, r2.y));
   const Ff rz = apz - (two_prod_ff(v, r1.z) + two_prod_ff(w, r2.z));
+  return rx * rx + ry * ry + rz * rz;
+}
+
+// The same on the ~48-bit vertices (float32 vertex + its low part, see
+// mc_emit_kernel): a, ab and ac in float-float, so the distance is that of
+// the refined surface to ~1e-14 relative and two candidates are ranked as
+// the exact (FP64) mesh ranks them unless they tie to that level.  The region
+// and the weights still come from the float32 record (second-order effect).
+__device__ __forceinline__ Ff tri_dist2_ff_exact(const Vec3<Ff> p, const float4* __restrict__ rec, const Tri& hi,
+                                                 const Tri& lo) {
+  const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
+  const Ff ax = Ff(hi.a.x) + Ff(lo.a.x), ay = Ff(hi.a.y) + Ff(lo.a.y), az = Ff(hi.a.z) + Ff(lo.a.z);
+  const Ff abx = (Ff(hi.b.x) + Ff(lo.b.x)) - ax, aby = (Ff(hi.b.y) + Ff(lo.b.y)) - ay,
+           abz = (Ff(hi.b.z) + Ff(lo.b.z)) - az;
+  const Ff acx = (Ff(hi.c.x) + Ff(lo.c.x)) - ax, acy = (Ff(hi.c.y) + Ff(lo.c.y)) - ay,
+           acz = (Ff(hi.c.z) + Ff(lo.c.z)) - az;
+  const Ff apx = p.x - ax, apy = p.y - ay, apz = p.z - az;
+  const float3 ap = make_float3(apx.hi, apy.hi, apz.hi);
+  const float d1 = r1.x * ap.x + r1.y * ap.y + r1.z * ap.z;
+  const float d2 = r2.x * ap.x + r2.y * ap.y + r2.z * ap.z;
+  float v, w;
+  rec_weights(ap, d1, d2, r0, r1, r2, r3, v, w);
+  const Ff fv(v), fw(w);
+  const Ff rx = apx - (fv * abx + fw * acx);
+  const Ff ry = apy - (fv * aby + fw * acy);
+  const Ff rz = apz - (fv * abz + fw * acz);
   return rx * rx + ry * ry + rz * rz;
 }
 
@@ -738,7 +839,7 @@ __device__ __forceinline__ unsigned pack_node(int lev, int x, int y, int z) {
 template <bool COUNT, bool TIES>
 __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __restrict__ chi, SurfParams g,
                                                           DevState* __restrict__ st,
-                                                          const float4* __restrict__ tris_s,
+                                                          const float4* __restrict__ tris_s, int id_bits,
                                                           const int* __restrict__ leaf_off, int64_t cap,
                                                           const float4* __restrict__ pyr, PyrInfo pi,
                                                           float* __restrict__ phi, float* __restrict__ sdf_out,
@@ -783,17 +884,48 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
     ct[q] = -1;
   }
   float cut = valid ? INFINITY : -INFINITY;   // a lane without a node never asks for a subtree
+  // With id_bits > 0 (near-tie handles; triangle ids below 2^id_bits - 1,
+  // id_bits <= 24) each list entry carries the top 32 - id_bits bits of its
+  // closest feature's key (feature_key) above the id, and the list holds one
+  // entry per closest feature:
+  // triangles sharing the closest vertex (often six of them) or edge tie
+  // exactly and would otherwise fill the list and push out a distinct surface
+  // point at the same distance (a node on the medial axis), which the tie
+  // pass must see.  Entries merge when their keys match; both lie within the
+  // rounding margin of the best, so a key collision can at most leave a tie
+  // to the float32 ranking.
+  const bool keyed = TIES && id_bits > 0;
+  const int idmask = keyed ? (int)((1u << id_bits) - 1u) : -1;
+  auto margin2 = [&](float x) {
+    const float r = sqrtf(x) * (1.f + kTieRel) + mabs;
+    return r * r;
+  };
   // candidate list insertion (sorted, duplicates of a listed triangle ignored)
-  auto offer = [&](float d2, int t) {
+  auto offer = [&](float d2, int t, float v, float w, unsigned vk) {
     if (!(d2 < cut && d2 < cd[NC - 1])) return;
+    int e = t;
+    int at = NC - 1;
+    if (keyed) {
+      const unsigned key = feature_key(v, w, vk, t) >> id_bits;
+      e = t | (int)(key << id_bits);
 #pragma unroll
-    for (int q = 0; q < NC; ++q)
-      if (ct[q] == t) return;
-    cd[NC - 1] = d2;
-    ct[NC - 1] = t;
+      for (int q = 0; q < NC; ++q) {
+        if ((ct[q] & idmask) == t) return;
+        if (ct[q] != -1 && ((unsigned)ct[q] >> id_bits) == key) {
+          if (!(d2 < cd[q])) return;      // the listed entry of this feature stays
+          at = q;                         // replaced in place, then moved up
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+        if (ct[q] == t) return;
+    }
+    cd[at] = d2;
+    ct[at] = e;
 #pragma unroll
     for (int q = NC - 1; q > 0; --q) {
-      if (cd[q] < cd[q - 1]) {
+      if (q <= at && cd[q] < cd[q - 1]) {
         const float tf = cd[q];
         cd[q] = cd[q - 1];
         cd[q - 1] = tf;
@@ -803,8 +935,7 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
       }
     }
     if (TIES) {
-      const float r = sqrtf(cd[0]) * (1.f + kTieRel) + mabs;
-      cut = r * r;
+      cut = margin2(cd[0]);
     } else {
       cut = cd[0];
     }
@@ -818,7 +949,12 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
       const int ii = i0 + S2 * (q & 1), jj = j0 + S2 * ((q >> 1) & 1), kk = k0 + S2 * (q >> 2);
       if (ii >= n || jj >= n || kk >= n) continue;
       const int t = seed_ids[lin3(ii, jj, kk, n)];
-      if (t >= 0) offer(tri_dist2_rec(p, tris_s + kTriRec * (int64_t)t), t);
+      if (t >= 0) {
+        float v, w;
+        unsigned vk;
+        const float d2 = tri_dist2_rec(p, tris_s + kTriRec * (int64_t)t, v, w, vk);
+        offer(d2, t, v, w, vk);
+      }
     }
   }
   unsigned int* stk = s_node[w];
@@ -850,7 +986,10 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
         c_tests += 32ull * (unsigned long long)(s1 > s0 ? s1 - s0 : 0);
       }
       for (int64_t t = s0; t < s1; ++t) {
-        offer(tri_dist2_rec(p, tris_s + kTriRec * t), (int)t);
+        float v, w;
+        unsigned vk;
+        const float d2 = tri_dist2_rec(p, tris_s + kTriRec * t, v, w, vk);
+        offer(d2, (int)t, v, w, vk);
       }
       continue;
     }
@@ -886,7 +1025,7 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
     sp = min(sp + nc, kStack);
     __syncwarp();
   }
-  const bool tie = TIES && valid && ct[NC > 1 ? 1 : 0] >= 0 && cd[NC > 1 ? 1 : 0] <= cut;
+  const bool tie = TIES && valid && ct[NC > 1 ? 1 : 0] != -1 && cd[NC > 1 ? 1 : 0] <= cut;
   if (COUNT) {
     const unsigned long long nt = (unsigned long long)__popc(__ballot_sync(0xffffffffu, tie));
     if (lane == 0) {
@@ -898,7 +1037,7 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
   }
   if (!valid) return;
   const float val = sqrtf(cd[0]);
-  const int bt = ct[0];
+  const int bt = ct[0] == -1 ? -1 : (ct[0] & idmask);
   const int64_t o = lin3(i, j, k, n);
   const float sgn = (chi[o] >= st->c_up) ? 1.f : -1.f;
   phi[o] = sgn * val;
@@ -908,22 +1047,25 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
   if (TIES) {
     if (tie) {
       tie_a[o] = bt;
-      tie_cd.p[st->fwd.xidx ^ 1][o] = make_int2(cd[NC > 2 ? 2 : 0] <= cut ? ct[NC > 2 ? 2 : 0] : -1,
-                                                cd[NC > 3 ? 3 : 0] <= cut ? ct[NC > 3 ? 3 : 0] : -1);
+      const int c2 = ct[NC > 2 ? 2 : 0], c3 = ct[NC > 3 ? 3 : 0];
+      tie_cd.p[st->fwd.xidx ^ 1][o] = make_int2(cd[NC > 2 ? 2 : 0] <= cut && c2 != -1 ? (c2 & idmask) : -1,
+                                                cd[NC > 3 ? 3 : 0] <= cut && c3 != -1 ? (c3 & idmask) : -1);
     }
-    tie_b[o] = tie ? ct[NC > 1 ? 1 : 0] : -1;
+    tie_b[o] = tie ? (ct[NC > 1 ? 1 : 0] & idmask) : -1;
   }
 }
 
 // Float-float decision between the float32 near-tie candidates of a node:
-// distances (tri_dist2_rec_ff) from the node position rounded once from
-// double, the smaller wins; equal distances (a shared edge or vertex: the
+// distances (tri_dist2_ff_exact on the ~48-bit vertices when their low parts
+// exist, else tri_dist2_rec_ff on the float32 ones) from the node position
+// rounded once from double, the smaller wins; equal distances (a shared edge or vertex: the
 // same closest point) take the smaller triangle index.  The node coordinates come from per-axis
 // float-float tables built once per block, and chi >= c (c double) is tested
 // as chi >= the smallest float not below c, so no node needs FP64.
 
 __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, const DevState* __restrict__ st,
-                               const float4* __restrict__ tris_s, const int* __restrict__ tie_a,
+                               const float4* __restrict__ tris_s, const Tri* __restrict__ tris,
+                               const Tri* __restrict__ tris_lo, const int* __restrict__ tie_a,
                                const int* __restrict__ tie_b, TieSlots tie_cd, float* __restrict__ phi,
                                float* __restrict__ sdf_out, int* __restrict__ ctri) {
   __shared__ float2 s_ax[3][kMaxRes];
@@ -956,7 +1098,9 @@ __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, cons
 #pragma unroll 1
     for (int q = 0; q < kCand; ++q) {
       if (cand[q] < 0) continue;
-      const Ff d2 = tri_dist2_rec_ff(pf, tris_s + kTriRec * (int64_t)cand[q]);
+      const Ff d2 = tris_lo ? tri_dist2_ff_exact(pf, tris_s + kTriRec * (int64_t)cand[q], tris[cand[q]],
+                                                 tris_lo[cand[q]])
+                            : tri_dist2_rec_ff(pf, tris_s + kTriRec * (int64_t)cand[q]);
       if (bi < 0 || d2 < bd || (!(bd < d2) && cand[q] < bi)) {
         bd = d2;
         bi = cand[q];
@@ -1235,11 +1379,12 @@ __device__ float pt_tri_dist2(float3 p, float3 a, float3 b, float3 c) {
 // triangle, where |phi| is of rounding size.  Non-finite queries get NaN and a
 // zero gradient.
 __global__ void query_sign_kernel(const float* __restrict__ q, int64_t m, const float* __restrict__ chi,
-                                  SurfParams g, const DevState* __restrict__ st, float* __restrict__ sdf_q,
-                                  float* __restrict__ nrm_q) {
+                                  ChiFF chiff, SurfParams g, const DevState* __restrict__ st,
+                                  float* __restrict__ sdf_q, float* __restrict__ nrm_q) {
   const int n = g.res;
   const double c = st->c;
   const float c_up = st->c_up;
+  const float2* __restrict__ xff = chiff.p[0] ? chiff.p[st->fwd.xidx] : nullptr;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
     const float x0 = q[3 * t], x1 = q[3 * t + 1], x2 = q[3 * t + 2];
     if (!(isfinite(x0) && isfinite(x1) && isfinite(x2))) {
@@ -1288,7 +1433,15 @@ __global__ void query_sign_kernel(const float* __restrict__ q, int64_t m, const 
           const int pi = cc[0] + ox, pj = cc[1] + oy, pk = cc[2] + oz;
           const int64_t pl = lin3(pi, pj, pk, n);
           const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
-          const double c1 = (double)chi[pl], c2 = (double)chi[pl + stride];
+          double c1, c2;
+          if (xff) {
+            const float2 f1 = xff[pl], f2 = xff[pl + stride];
+            c1 = (double)f1.x + (double)f1.y;
+            c2 = (double)f2.x + (double)f2.y;
+          } else {
+            c1 = (double)chi[pl];
+            c2 = (double)chi[pl + stride];
+          }
           const double eta = (c - c1) / (c2 - c1);
           double pos[3] = {g.lo[0] + (pi + 0.5) * g.h, g.lo[1] + (pj + 0.5) * g.h, g.lo[2] + (pk + 0.5) * g.h};
           pos[ax] += eta * g.h;
@@ -1402,12 +1555,14 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   if (rc) return rc;
   mc_total_kernel<<<1, 1, 0, s>>>(h->brick_off, nbricks, h->mesh_cap, h->leaf_off, h->dstate);
   WGEO_LAUNCH_CHECK();
-  mc_emit_kernel<<<nbricks, 64, 0, s>>>(h->chi32, g, h->dstate, h->brick_off, h->mesh_cap, h->tris,
-                                        h->leaf_off);
+  // vertices from the refined float-float indicator (MIXED precision) and
+  // their low parts for the near-tie decisions and the adjoint (when kept)
+  mc_emit_kernel<<<nbricks, 64, 0, s>>>(h->chi32, chiff_of(h), g, h->dstate, h->brick_off, h->mesh_cap, h->tris,
+                                        h->tris_lo, h->leaf_off);
   WGEO_LAUNCH_CHECK();
   const PyrInfo pi = pyramid_info(2 * g.nb);
   const int64_t nleaf = (int64_t)pi.dim[0] * pi.dim[0] * pi.dim[0];
-  puck_leaf_kernel<<<grid_blocks(nleaf, 256, 152 * 16), 256, 0, s>>>(h->tris, h->leaf_off, g.nb,
+  puck_leaf_kernel<<<grid_blocks(nleaf, 256, 152 * 16), 256, 0, s>>>(h->tris, h->tris_lo, h->leaf_off, g.nb,
                                                                       h->mesh_cap, h->pyramid, h->tris_s);
   WGEO_LAUNCH_CHECK();
   {
@@ -1446,25 +1601,32 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   int* ctri = h->opt.keep_for_backward ? h->ctri : nullptr;
   // closest triangles of the coarser passes, read by the finer ones as seeds
   int* seed_ids = ctri ? ctri : tie_a;
+  // closest-feature keys of the near-tie candidates: the bits above the
+  // triangle ids (ids < cap <= 2^id_bits - 1; at least 8 key bits)
+  int id_bits = 0;
+  if (ctri) {
+    while (id_bits < 32 && ((int64_t)1 << id_bits) - 1 < h->mesh_cap) ++id_bits;
+    if (id_bits > 24) id_bits = 0;
+  }
   for (int stride = kSdfCoarse; stride >= 1; stride /= 2) {
     const int nl = (res + stride - 1) / stride;
     const int nblk = ((nl + 7) / 8) * ((nl + 7) / 8) * ((nl + 1) / 2);
     if (ctri) {
       if (h->opt.stage_timing == 2)
-        sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
+        sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, ctri,
                                                             tie_a, tie_b, tie_cd, seed_ids, stride);
       else
-        sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
+        sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                              h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, ctri,
                                                              tie_a, tie_b, tie_cd, seed_ids, stride);
     } else {
       if (h->opt.stage_timing == 2)
-        sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
+        sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                              h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
                                                              nullptr, nullptr, tie_cd, seed_ids, stride);
       else
-        sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->leaf_off,
+        sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                               h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
                                                               nullptr, nullptr, tie_cd, seed_ids, stride);
     }
@@ -1474,8 +1636,9 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   if (ctri) {
     slot = stage_begin(h, kStSDFTie, s);
     const int64_t N = (int64_t)res * res * res;
-    sdf_tie_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, tie_a, tie_b,
-                                                                 tie_cd, h->phi, sdf_out, ctri);
+    sdf_tie_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->tris,
+                                                                 h->tris_lo, tie_a, tie_b, tie_cd, h->phi, sdf_out,
+                                                                 ctri);
     WGEO_LAUNCH_CHECK();
     stage_end(h, kStSDFTie, slot, s);
   }
@@ -1516,7 +1679,8 @@ int launch_query_exact_chunk(wgeo_handle* h, const float* q, int nq, float* sdf_
                                                          h->pyramid, pi, h->dp_sorted, total, nullptr, sdf_q, nrm_q,
                                                          tri);
   WGEO_LAUNCH_CHECK();
-  query_sign_kernel<<<grid_blocks(nq, 128, 152 * 16), 128, 0, s>>>(q, nq, h->chi32, g, h->dstate, sdf_q, nrm_q);
+  query_sign_kernel<<<grid_blocks(nq, 128, 152 * 16), 128, 0, s>>>(q, nq, h->chi32, chiff_of(h), g, h->dstate,
+                                                                    sdf_q, nrm_q);
   WGEO_LAUNCH_CHECK();
   return WGEO_OK;
 }

@@ -65,6 +65,13 @@ struct Tri {          // one marching-cubes triangle: vertex xyz + global edge i
   float4 a, b, c;
 };
 
+// The two float-float indicator buffers of the forward solve (refinement
+// ping-pong; DevState::fwd.xidx selects the current one), or null pointers
+// when the handle solves in plain FP32.
+struct ChiFF {
+  const float2* p[2];
+};
+
 struct Level {
   int n;
   float* x;
@@ -180,14 +187,14 @@ __device__ __forceinline__ bool operator<=(Ff a, Ff b) { return !(b < a); }
 __device__ __forceinline__ bool operator>=(Ff a, Ff b) { return !(a < b); }
 
 // Closest-point weights (v, w) of y = a + v ab + w ac on a triangle given by
-// its search record (r0 = (a, |ab|^2), r1 = (ab, ab.ac), r2 = (ac, |ac|^2),
+// its search record (r0 = (a, |ab|^2), r1 = (ab, vertex keys), r2 = (ac, |ac|^2),
 // r3 = (1/|ab|^2, 1/|ac|^2, 1/|bc|^2, 1/|ab x ac|^2)), from ap = p - a,
 // d1 = ab.ap and d2 = ac.ap: Ericson's Voronoi-region case analysis with the
 // six dot products reduced to two through the Gram entries and the
 // divisions replaced by the reciprocals.
 __device__ __forceinline__ void rec_weights(const float3 ap, float d1, float d2, const float4 r0, const float4 r1,
                                             const float4 r2, const float4 r3, float& v, float& w) {
-  const float e00 = r0.w, e01 = r1.w, e11 = r2.w;
+  const float e00 = r0.w, e01 = r1.x * r2.x + r1.y * r2.y + r1.z * r2.z, e11 = r2.w;   // r1.w: vertex keys
   const float d3 = d1 - e00, d4 = d2 - e01;                  // ab . bp, ac . bp
   const float d5 = d1 - e01, d6 = d2 - e11;                  // ab . cp, ac . cp
   if (d1 <= 0.f && d2 <= 0.f) {
@@ -348,6 +355,8 @@ struct wgeo_handle {
   int* brick_off = nullptr;      // nbricks + 1
   int* leaf_off = nullptr;       // 8 * nbricks + 1: triangle offset of each 2^3 sub-brick
   wgeo::Tri* tris = nullptr;
+  wgeo::Tri* tris_lo = nullptr;  // keep_for_backward: per vertex the low part of its ~48-bit position
+                                 // (FP64 vertex - float32 vertex); null otherwise
   float4* tris_s = nullptr;      // per triangle: search record (a, |ab|^2), (ab, ab.ac), (ac, |ac|^2),
                                  // (1/|ab|^2, 1/|ac|^2, 1/|bc|^2, 1/|ab x ac|^2)
   float4* pyramid = nullptr;     // 2 float4 per node (puck: centre + radius, axis + half-thickness)
@@ -400,6 +409,17 @@ struct wgeo_handle {
 };
 
 namespace wgeo {
+// The forward's float-float indicator buffers when the handle solves in MIXED
+// precision (vertex placement, near-tie decisions, sign tests and the
+// adjoint's vertex weights read the current one), else null pointers.
+inline ChiFF chiff_of(const wgeo_handle* h) {
+  ChiFF c;
+  const bool mixed = h->opt.precision == WGEO_PREC_MIXED;
+  c.p[0] = mixed ? h->chiff[0] : nullptr;
+  c.p[1] = mixed ? h->chiff[1] : nullptr;
+  return c;
+}
+
 // Records the start / end of a stage on stream s (no-ops unless stage timing is on).
 int stage_begin(wgeo_handle* h, int stage, cudaStream_t s);
 void stage_end(wgeo_handle* h, int stage, int slot, cudaStream_t s);
