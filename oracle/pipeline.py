@@ -111,11 +111,54 @@ def sdf_at(rec: Reconstruction, lin):
     return sgn * d, d, tri
 
 
+def sdf_at_pool(rec: Reconstruction, lin, workers: int = 1):
+    """sdf_at, with the exact distance evaluated by `workers` processes."""
+    nodes = node_xyz(lin, rec.res, rec.lo, rec.h)
+    sgn = S.node_sign(rec.chi.reshape(-1)[lin], rec.c)
+    if rec.mesh["verts"].shape[0] == 0:
+        return sgn * np.inf, np.full(len(lin), np.inf), np.full(len(lin), -1)
+    d, tri = S.exact_distance_pool(nodes, rec.mesh["verts"], workers)
+    return sgn * d, d, tri
+
+
+def fill_nodes(rec: Reconstruction, lin, workers: int = 1):
+    """Evaluates phi, the distance and the closest triangle of a forward
+    (`forward_to_mesh`) at the linear node indices `lin` only (NaN / -1 at
+    every other node, no normals).  Enough for `backward` with grid or query
+    seeds of phi whose nodes (query corners included) all lie in `lin`; every
+    value it holds is the one `reconstruct` computes."""
+    res = rec.res
+    lin = np.unique(np.asarray(lin, dtype=np.int64))
+    N = res ** 3
+    phi = np.full(N, np.nan)
+    dist = np.full(N, np.nan)
+    tri = np.full(N, -1, dtype=np.int64)
+    phi[lin], dist[lin], tri[lin] = sdf_at_pool(rec, lin, workers)
+    rec.phi = phi.reshape(res, res, res)
+    rec.dist = dist.reshape(res, res, res)
+    rec.tri = tri.reshape(res, res, res)
+    rec.sign = S.node_sign(rec.chi, rec.c)
+    return rec
+
+
+def reconstruct_at_nodes(points, normals, bbox, res, lin, workers: int = 1, frozen_bins=None):
+    """`forward_to_mesh`, then `fill_nodes` at the linear node indices `lin`."""
+    return fill_nodes(forward_to_mesh(points, normals, bbox, res, frozen_bins), lin, workers)
+
+
+def query_corner_nodes(q, res, lo, h):
+    """Linear indices of the 8 trilinear corner nodes of every query point."""
+    corners, _, _ = I.trilinear(as_f64(q), lo, h, res)
+    return np.unique(((corners[..., 2] * res + corners[..., 1]) * res + corners[..., 0]).reshape(-1))
+
+
 def reconstruct(points, normals, bbox, res, with_normals: bool = True, frozen_bins=None,
-                operator: str = "lumped"):
+                operator: str = "lumped", workers: int = 1):
+    """The whole forward on the full grid (`workers` > 1: the exact distance
+    evaluated by a process pool, `sdf_at_pool`)."""
     rec = forward_to_mesh(points, normals, bbox, res, frozen_bins, operator)
     N = res ** 3
-    phi, d, tri = sdf_at(rec, np.arange(N))
+    phi, d, tri = sdf_at_pool(rec, np.arange(N), workers)
     rec.phi = phi.reshape(res, res, res)
     rec.dist = d.reshape(res, res, res)
     rec.tri = tri.reshape(res, res, res)

@@ -129,6 +129,27 @@ def exact_distance(nodes, verts, chunk: int = 16384):
     return d, tri
 
 
+def _exact_distance_part(args):
+    nodes, verts = args
+    return exact_distance(nodes, verts)
+
+
+def exact_distance_pool(nodes, verts, workers: int = 1, parts: int = 64):
+    """exact_distance, with the nodes split into contiguous parts evaluated by
+    a pool of `workers` processes (started with "spawn", so the pool may be
+    created in a process that already uses a GPU).  Every node's result is
+    computed by exact_distance itself; only the work is divided."""
+    N = nodes.shape[0]
+    if workers <= 1 or N < 4 * parts:
+        return exact_distance(nodes, verts)
+    import multiprocessing as mp
+    bounds = np.linspace(0, N, parts + 1).astype(np.int64)
+    jobs = [(nodes[bounds[i]:bounds[i + 1]], verts) for i in range(parts)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        out = pool.map(_exact_distance_part, jobs, chunksize=1)
+    return np.concatenate([o[0] for o in out]), np.concatenate([o[1] for o in out])
+
+
 def node_sign(chi, c):
     return np.where(chi >= c, 1.0, -1.0)
 
