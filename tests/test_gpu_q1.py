@@ -109,6 +109,8 @@ def test_q1_backward_parity(W, name):
         got = got.cpu().numpy().astype(np.float64)
         rel = np.linalg.norm(got - want) / np.linalg.norm(want)
         assert rel <= GRAD_TOL, f"{nm}: relative error {rel:.3e}"
+        pp = np.linalg.norm(got - want, axis=1).max() / np.linalg.norm(want, axis=1).max()
+        assert pp <= GRAD_TOL, f"{nm}: largest per-point error {pp:.3e} of the largest gradient"
     rec.close()
 
 

@@ -84,6 +84,7 @@ def test_spectral_adjoint_matches_the_oracle(W, galerkin):
     for got, want in ((dp, odp), (dn, odn)):
         got = got.cpu().numpy().astype(np.float64)
         assert np.linalg.norm(got - want) <= GRAD_TOL * np.linalg.norm(want)
+        assert np.linalg.norm(got - want, axis=1).max() <= GRAD_TOL * np.linalg.norm(want, axis=1).max()
     rec.close()
 
 
