@@ -270,11 +270,44 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // id of the context the address belongs to
+
+// Driver entry points for the id of the current context, looked up once
+// through the runtime (no link-time dependency on the driver library).
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+// Unique id of the calling thread's current context (the device's primary
+// context once the runtime has been used on it); 0 if it cannot be read.
+// Called with g_scratch_mu held.
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 // Device address of the scratch array on the current device.  The first call
-// per device resolves it (cudaGetSymbolAddress, which may also load the
-// module on that device) and checks the device is sm_103; later calls read
-// the cached pointer.
+// per device (and the first after the device's context was replaced, e.g. by
+// cudaDeviceReset) checks that the device is sm_103 and resolves the address
+// with cudaGetSymbolAddress, which may also load the module on that device;
+// later calls in the same context read the cached pointer.
 int noalloc_scratch(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -282,11 +315,19 @@ int noalloc_scratch(double** out) {
     return WGEO_ERR_CUDA;
   }
   if (dev < 0 || dev >= kMaxDevices) return WGEO_ERR_INVALID_ARG;
+  // 0 before the runtime has made a context current on this thread: then the
+  // address is resolved (which makes the primary context current) and the id
+  // read again afterwards
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  unsigned long long ctx = current_context_id();
+  if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
+    g_scratch_ptr[dev] = nullptr;
     int major = 0, minor = 0;
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return WGEO_ERR_CUDA;
+    }
     if (major * 10 + minor != 103) return WGEO_ERR_NOT_BUILT_FOR_DEVICE;
     void* p = nullptr;
     const cudaError_t rc = cudaGetSymbolAddress(&p, sh_noalloc_scratch);
@@ -295,6 +336,7 @@ int noalloc_scratch(double** out) {
       return WGEO_ERR_CUDA;
     }
     g_scratch_ptr[dev] = static_cast<double*>(p);
+    g_scratch_ctx[dev] = ctx ? ctx : current_context_id();
   }
   *out = g_scratch_ptr[dev];
   return WGEO_OK;

@@ -5,7 +5,9 @@ through the C ABI.
 Two calls in a row with different sizes (K = 81 with a grid at its block cap,
 then K = 49 with fewer blocks) must each equal the handle-based result: the
 same kernels reduce in the same fixed order, so the results are identical.
-K above the scratch limit of 81 is refused before anything is enqueued.
+The device's free memory is the same before and after the calls, n = 0
+zero-fills the output, and K above the scratch limit of 81 is refused before
+anything is enqueued.
 """
 import ctypes as C
 
@@ -54,16 +56,36 @@ def test_noalloc_adjoint_equals_handle_entry_point():
         want.append(out)
     torch.cuda.synchronize()
 
-    # two allocation-free calls in a row, on the default stream
-    got = [torch.full_like(c[0], float("nan")) for c in dev_cases]
-    for (theta, dirs, dpts, dnrm), out in zip(dev_cases, got):
-        L.check(lib.wgeo_sh_surface_backward_noalloc(_ptr(theta), theta.numel(), _ptr(dirs), dirs.shape[0], 0.3,
+    def noalloc(theta, dirs, dpts, dnrm, out, n=None):
+        L.check(lib.wgeo_sh_surface_backward_noalloc(_ptr(theta), theta.numel(), _ptr(dirs),
+                                                     dirs.shape[0] if n is None else n, 0.3,
                                                      _ptr(dpts), _ptr(dnrm), _ptr(out), None),
                 "wgeo_sh_surface_backward_noalloc")
+
+    # two allocation-free calls in a row, on the default stream; the device's
+    # free memory is read around them (after the outputs exist, and after one
+    # warm-up call that does the per-device set-up): unchanged, since the calls
+    # allocate nothing
+    got = [torch.full_like(c[0], float("nan")) for c in dev_cases]
+    warm = torch.empty_like(dev_cases[1][0])
+    noalloc(*dev_cases[1], warm)
     torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for c, out in zip(dev_cases, got):
+        noalloc(*c, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0, (free0, free1)
     for g, w in zip(got, want):
         assert torch.isfinite(g).all()
         assert torch.equal(g, w), float((g - w).abs().max())
+
+    # no points: d_theta is overwritten with zeros
+    theta, dirs, dpts, dnrm = dev_cases[1]
+    zero = torch.full_like(theta, 5.0)
+    noalloc(theta, dirs, dpts, dnrm, zero, n=0)
+    torch.cuda.synchronize()
+    assert (zero == 0).all()
 
     # K = 100 (lmax 9) exceeds the 81 coefficients the scratch holds: refused, output untouched
     theta, dirs, dpts, dnrm = dev_cases[1]
