@@ -22,7 +22,7 @@ from ._lib import (  # noqa: F401
 
 def __getattr__(name):
     # torch-dependent parts load lazily so that the CPU-only symbol checks need no torch import
-    if name in ("Reconstructor", "sh_surface", "sh_surface_backward"):
+    if name in ("Reconstructor", "sh_surface", "sh_surface_backward", "StaleForwardError"):
         from . import api
         return getattr(api, name)
     if name in ("sdf_query", "sdf_query_exact", "sdf_grid", "sh_points", "WgeoFunction", "WgeoQueryFunction",

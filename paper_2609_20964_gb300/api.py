@@ -11,6 +11,10 @@ import torch
 from . import _lib as L
 
 
+class StaleForwardError(RuntimeError):
+    """A backward was asked of a forward whose state the handle no longer holds."""
+
+
 def _stream(stream=None) -> int:
     s = stream if stream is not None else torch.cuda.current_stream()
     return int(s.cuda_stream)
@@ -48,6 +52,10 @@ class Reconstructor:
         self.h = h
         self.res = None
         self.n = 0
+        # forwards run on this handle so far: the handle keeps only the state
+        # of its last forward, so a backward saved against an older forward
+        # must be refused (see check_generation)
+        self.generation = 0
 
     @staticmethod
     def footprint(max_res: int, max_points: int, **options) -> int:
@@ -77,10 +85,20 @@ class Reconstructor:
         rc = self.lib.wgeo_reconstruct(self.h, _dev(points, "points", 3), _dev(normals, "normals", 3),
                                        n, _bbox(bbox), res, _dev(sdf_out, "sdf_out"),
                                        _dev(nrm_out, "nrm_out"), C.c_void_p(_stream(stream)))
+        self.generation += 1
         L.check(rc, "wgeo_reconstruct")
         self.res = res
         self.n = n
         return sdf_out, nrm_out
+
+    def check_generation(self, generation: int, what: str = "backward"):
+        """Raises StaleForwardError unless the handle's last forward is the one
+        numbered `generation` (its state is what a backward differentiates)."""
+        if generation != self.generation:
+            raise StaleForwardError(
+                f"{what}: this Reconstructor has run {self.generation - generation} forward(s) since the "
+                f"one being differentiated, and keeps only the last forward's state; give each "
+                f"differentiable call its own Reconstructor, or call backward before the next forward")
 
     def query(self, q: torch.Tensor, with_normals: bool = True, stream=None):
         m = int(q.shape[0])

@@ -1,7 +1,11 @@
 """torch.autograd wrapper: the forward runs wgeo_reconstruct + wgeo_query, the
 backward runs wgeo_backward (adjoint chain with one transposed Poisson solve,
 Sec. 2.5, Eqs. 35-39).  No solver iterate is saved; the handle keeps chi, c,
-the bins, the triangles and the closest-triangle ids of the forward."""
+the bins, the triangles and the closest-triangle ids of the forward.  A
+handle keeps only its last forward: each Function saves the forward's
+generation number, and its backward raises StaleForwardError if the same
+Reconstructor has run another forward since (rather than differentiate the
+wrong state)."""
 from __future__ import annotations
 
 import torch
@@ -18,12 +22,14 @@ class WgeoQueryFunction(torch.autograd.Function):
                           with_sdf=False, with_normals=False)
         sdf_q, nrm_q = recon.query(q.contiguous())
         ctx.recon = recon
+        ctx.generation = recon.generation
         ctx.save_for_backward(q)
         return sdf_q, nrm_q
 
     @staticmethod
     def backward(ctx, g_sdf_q, g_nrm_q):
         (q,) = ctx.saved_tensors
+        ctx.recon.check_generation(ctx.generation, "WgeoQueryFunction.backward")
         need_q = ctx.needs_input_grad[2]
         gs = g_sdf_q.contiguous() if g_sdf_q is not None else None
         gn = g_nrm_q.contiguous() if g_nrm_q is not None else None
@@ -42,12 +48,14 @@ class WgeoExactQueryFunction(torch.autograd.Function):
                           with_sdf=False, with_normals=False)
         sdf_q, _ = recon.query_exact(q.contiguous(), with_grad=False)
         ctx.recon = recon
+        ctx.generation = recon.generation
         ctx.save_for_backward(q)
         return sdf_q
 
     @staticmethod
     def backward(ctx, g_sdf_q):
         (q,) = ctx.saved_tensors
+        ctx.recon.check_generation(ctx.generation, "WgeoExactQueryFunction.backward")
         dp, dn, dq = ctx.recon.backward_exact(q.contiguous(), g_sdf_q.contiguous(),
                                               want_dq=ctx.needs_input_grad[2])
         return dp, dn, dq, None, None, None
@@ -60,10 +68,12 @@ class WgeoGridFunction(torch.autograd.Function):
     def forward(ctx, points, normals, recon: Reconstructor, bbox, res: int):
         sdf, nrm = recon.reconstruct(points.contiguous(), normals.contiguous(), bbox, res)
         ctx.recon = recon
+        ctx.generation = recon.generation
         return sdf, nrm
 
     @staticmethod
     def backward(ctx, g_sdf, g_nrm):
+        ctx.recon.check_generation(ctx.generation, "WgeoGridFunction.backward")
         dp, dn, _ = ctx.recon.backward(
             d_sdf_grid=g_sdf.contiguous() if g_sdf is not None else None,
             d_nrm_grid=g_nrm.contiguous() if g_nrm is not None else None)
