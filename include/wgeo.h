@@ -66,13 +66,19 @@ typedef enum {
 #define WGEO_STATUS_MESH_CAPACITY      (1u << 4) /* more triangles than mesh_capacity: sdf unspecified */
 
 /* Precision of the Poisson solve. */
-#define WGEO_PREC_MIXED 0  /* FP32 multigrid cycles inside FP64 iterative refinement (FP64 residual, FP64 dots) */
-#define WGEO_PREC_FP32  1  /* plain FP32 multigrid cycles, FP32 residual and dots */
+#define WGEO_PREC_MIXED 0  /* iterative refinement with a float-float iterate and residual (two-sum
+                              arithmetic on the FP32 pipe, ~48-bit significand) and FP64 norms and
+                              sums; each step's correction is one FP32 spectral (cosine-basis) solve
+                              on power-of-two grids of 32..512 with opt.spectral, else FP32
+                              multigrid V-cycles */
+#define WGEO_PREC_FP32  1  /* plain FP32, no refinement: one direct FP32 spectral solve on
+                              power-of-two grids of 32..512 with opt.spectral (set max_vcycles >= 1),
+                              else FP32 V-cycles on the iterate; FP32 residual and sums */
 
 typedef struct {
   double  tol_rel;           /* stop when ||b - A chi|| <= tol_rel * ||b|| (default 1e-6) */
-  int32_t max_vcycles;       /* FP32 mode: maximum V-cycles (default 40) */
-  int32_t max_refine;        /* MIXED mode: maximum FP64 refinement steps (default 10) */
+  int32_t max_vcycles;       /* FP32 mode: maximum V-cycles, or spectral solves (default 40) */
+  int32_t max_refine;        /* MIXED mode: maximum refinement steps (default 10) */
   int32_t vcycles_per_refine;/* MIXED mode: FP32 V-cycles per refinement step (default 2) */
   int32_t precision;         /* WGEO_PREC_MIXED (default) or WGEO_PREC_FP32 */
   int32_t warm_start;        /* start the solve from the previous chi on this handle when res matches (default 0) */
@@ -86,10 +92,11 @@ typedef struct {
                                 1-D stiffness S = {-1,2,-1}, mass M = {1,4,1}/6 and central
                                 difference D, the walls mirrored; Sec. 2.3, Eqs. 20-22 and 26).
                                 Needs WGEO_PREC_MIXED. */
-  int32_t spectral;          /* MIXED mode: 1 (default) = each refinement step's correction is a
-                                direct spectral solve (the operator is diagonal in the cosine basis
-                                of the mirrored walls) when res is a power of two from 32 to 512, else
-                                multigrid; 0 = always multigrid V-cycles */
+  int32_t spectral;          /* 1 (default): when res is a power of two from 32 to 512, MIXED mode
+                                takes each refinement step's correction from a direct spectral
+                                solve (the operator is diagonal in the cosine basis of the mirrored
+                                walls; always two steps), and FP32 mode solves once, directly;
+                                0: multigrid V-cycles on every grid */
   int32_t reserved[3];
   double  tol_rel_adjoint;   /* adjoint solve: stop when ||g - A lambda|| <= tol * ||g|| (default 1e-7) */
 } wgeo_options;
@@ -325,8 +332,11 @@ int wgeo_sh_surface_backward(wgeo_handle* h, const float* theta, int32_t K, cons
  *
  * Set-up: the first call on a device (with that device current) looks up the
  * array's device address and checks the device is sm_103 (else
- * WGEO_ERR_NOT_BUILT_FOR_DEVICE); later calls reuse the address.  Make that
- * first call before any stream capture.  No part of the array needs to start
+ * WGEO_ERR_NOT_BUILT_FOR_DEVICE); later calls in the same context reuse the
+ * address.  The first call after the device's context has been replaced (by
+ * cudaDeviceReset, for example) looks the address up again.  Make that first
+ * call before any stream capture.  If the device attributes or the address
+ * cannot be read, the call returns WGEO_ERR_CUDA.  No part of the array needs to start
  * at zero: each call writes every slot it reads.  The array is shared by all
  * calls on a device, so calls that may overlap in time (other streams or host
  * threads without ordering between them) race; order them on one stream or

@@ -17,7 +17,10 @@
 //   one-block kernel reduces the sums in a fixed order and tests
 //   ||r - mean r|| <= tol ||b - mean b||.  The correction solves
 //   L e = r - mean(r) with FP32 V-cycles.
-// Plain FP32 (comparator): V-cycles directly on x32 with an FP32 residual.
+// Plain FP32 (comparator): no refinement.  On power-of-two grids (with the
+//   spectral option) one direct FP32 spectral solve of L x = b - mean(b);
+//   elsewhere FP32 V-cycles directly on x32.  The residual and its norms are
+//   FP32.
 //
 // Multigrid: cell-centred, halving while even and larger than 8; red-black
 // Gauss-Seidel, 2 pre- and 2 post-sweeps; residual restricted with weight 1/2
@@ -1406,7 +1409,10 @@ int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGrap
   const int rb = grid_blocks(N, kThreads, kPartials);
   if (fp32) {
     if (part == 1) {
-      int rc = vcycle(h, 0, h->chi32, h->b32, &ss->bmean32, false, gate, s);
+      // plain FP32: on spectral grids one direct FP32 solve of L x = b - mean(b)
+      // (no refinement), else one FP32 V-cycle on x in place
+      int rc = use_spectral(h, res) ? spectral_solve(h, res, h->chi32, h->b32, gate, s)
+                                    : vcycle(h, 0, h->chi32, h->b32, &ss->bmean32, false, gate, s);
       if (rc) return rc;
     }
     residual32_kernel<<<rb, kThreads, 0, s>>>(h->chi32, h->b32, &ss->bmean32, res, h->partials, gate);
@@ -1579,7 +1585,7 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
   const int64_t N = (int64_t)res * res * res;
   SolveState* ss = mode == 0 ? &h->dstate->fwd : &h->dstate->bwd;
   const bool fp32_plain = (mode == 0 && h->opt.precision == WGEO_PREC_FP32);
-  if (!fp32_plain && use_spectral(h, res)) {
+  if (use_spectral(h, res)) {
     int rc = spectral_setup(h, res, s);
     if (rc) return rc;
   }
@@ -1601,7 +1607,8 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
   // the direct correction reaches the float-float limit in two steps (the
   // first is exact to FP32 rounding): always take both, so that chi, and the
   // adjoint's right-hand side built from it, carry no solver error
-  const int min_steps = (!fp32_plain && use_spectral(h, res)) ? 2 : 0;
+  // (plain FP32 takes its one direct solve)
+  const int min_steps = use_spectral(h, res) ? (fp32_plain ? 1 : 2) : 0;
   if (!h->opt.use_graphs || cap != cudaStreamCaptureStatusNone) {
     solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0, steps, min_steps, 0);
     WGEO_LAUNCH_CHECK();
