@@ -6,9 +6,17 @@ sizes and point counts.
   (then the point/normal gradients are returned too).
 * Admission: a request runs when a stream slot is free and its handle fits
   the device-memory budget.  Handles (library workspaces, sized by
-  ``wgeo_footprint_bytes``) are pooled per grid size and reused, so grids
-  and the warm-start solution stay resident; idle handles are evicted when a
-  new size needs room.
+  ``wgeo_footprint_bytes``) are pooled per (grid size, point-count bucket):
+  a request takes a handle of the smallest bucket that holds its cloud, so
+  small clouds do not reserve the workspace of the largest.  Handles are
+  reused, so grids and (with ``warm_start``, on by default) the previous
+  indicator stay resident and seed the next solve of that handle; idle
+  handles are evicted when a new size needs room.
+* Inputs may live on the host or the device.  Device inputs are read on the
+  request's stream after an event recorded on the caller's current stream at
+  submit(), so work the caller enqueued to produce them comes first; a
+  returned SDF grid is marked as used on the caller's stream, so freeing it
+  there cannot hand its memory to the request stream early.
 * Requests that arrive while others are on the GPU are admitted as soon as a
   slot and memory free up; each runs on its own CUDA stream, so the kernels of
   different requests overlap on the device.
@@ -40,6 +48,8 @@ class Request:
     want_grid: bool = False        # return the SDF grid (device tensor)
     arrival: float = field(default_factory=time.perf_counter)
     rid: int = 0
+    ready: object = None           # set by submit(): event on the caller's stream (device inputs)
+    caller_stream: object = None   # set by submit(): the caller's current stream
 
 
 @dataclass
@@ -51,6 +61,8 @@ class Result:
     sdf_grid: torch.Tensor | None
     info: dict
     latency_s: float
+    res: int = 0
+    done_event: object = None      # CUDA event after the request's last kernel
 
 
 class _Slot:
@@ -59,19 +71,33 @@ class _Slot:
         self.busy = False
 
 
+def _buckets(max_points: int):
+    """Point-count buckets: powers of four from 16,384 up to max_points."""
+    out, b = [], 16_384
+    while b < max_points:
+        out.append(b)
+        b *= 4
+    out.append(int(max_points))
+    return tuple(out)
+
+
 class Server:
     def __init__(self, budget_bytes: int, n_streams: int = 4, max_points: int = 500_000,
-                 device=None, **options):
+                 device=None, point_buckets=None, warm_start: int = 1, **options):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.budget = int(budget_bytes)
         self.max_points = max_points
-        self.options = options
+        self.buckets = tuple(sorted(point_buckets)) if point_buckets else _buckets(max_points)
+        if self.buckets[-1] < max_points:
+            raise ValueError("the largest point bucket must hold max_points")
+        self.options = dict(options, warm_start=warm_start)
         self.slots = [_Slot(self.device) for _ in range(n_streams)]
-        self.free_handles = collections.defaultdict(list)   # res -> [Reconstructor]
+        self.free_handles = collections.defaultdict(list)   # (res, bucket) -> [Reconstructor]
         self.used_bytes = 0
         self.pending = collections.deque()
         self.inflight = []
         self.latencies = []
+        self.latencies_by_res = collections.defaultdict(list)
         self.completed = 0
         self.lock = threading.Condition()
         self.stop_flag = False
@@ -81,10 +107,20 @@ class Server:
     # ---------------------------------------------------------------- public
     def submit(self, req: Request) -> Future:
         fut = Future()
-        if self.footprint(req.res) > self.budget:
-            fut.set_exception(MemoryError(
-                f"a {req.res}^3 workspace needs {self.footprint(req.res)} bytes, budget is {self.budget}"))
+        n = int(req.points.shape[0])
+        if n > self.buckets[-1]:
+            fut.set_exception(ValueError(f"{n} points exceed the server's max_points {self.buckets[-1]}"))
             return fut
+        need = self.footprint(req.res, self.bucket_of(n))
+        if need > self.budget:
+            fut.set_exception(MemoryError(
+                f"a {req.res}^3 workspace for {n} points needs {need} bytes, budget is {self.budget}"))
+            return fut
+        req.caller_stream = torch.cuda.current_stream(self.device)
+        if any(isinstance(a, torch.Tensor) and a.is_cuda
+               for a in (req.points, req.normals, req.queries, req.d_sdf_q)):
+            req.ready = torch.cuda.Event()
+            req.ready.record(req.caller_stream)
         with self.lock:
             self.pending.append((req, fut))
             self.lock.notify()
@@ -102,35 +138,46 @@ class Server:
 
     def stats(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        per = {r: {"count": len(v), "p50_ms": 1e3 * float(np.percentile(v, 50)),
+                   "p99_ms": 1e3 * float(np.percentile(v, 99))}
+               for r, v in sorted(self.latencies_by_res.items())}
         return {"completed": self.completed, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "used_bytes": self.used_bytes}
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "used_bytes": self.used_bytes,
+                "by_res": per}
 
     # ---------------------------------------------------------------- internals
-    def footprint(self, res: int) -> int:
-        return Reconstructor.footprint(res, self.max_points, **self.options)
+    def bucket_of(self, n: int) -> int:
+        return next(b for b in self.buckets if b >= n)
 
-    def _take_handle(self, res: int):
-        if self.free_handles[res]:
-            return self.free_handles[res].pop()
-        need = self.footprint(res)
-        # evict idle handles of other sizes until the new one fits
+    def footprint(self, res: int, bucket: int | None = None) -> int:
+        return Reconstructor.footprint(res, self.max_points if bucket is None else bucket, **self.options)
+
+    def _take_handle(self, res: int, n: int):
+        key = (res, self.bucket_of(n))
+        if self.free_handles[key]:
+            return self.free_handles[key].pop()
+        need = self.footprint(*key)
+        # evict idle handles of other kinds until the new one fits
         while self.used_bytes + need > self.budget:
             victim = None
-            for r, hs in self.free_handles.items():
+            for k, hs in self.free_handles.items():
                 if hs:
-                    victim = (r, hs.pop())
+                    victim = (k, hs.pop())
                     break
             if victim is None:
                 return None
             victim[1].close()
-            self.used_bytes -= self.footprint(victim[0])
+            self.used_bytes -= self.footprint(*victim[0])
         with torch.cuda.device(self.device):
-            h = Reconstructor(res, self.max_points, device=self.device.index, **self.options)
+            h = Reconstructor(res, key[1], device=self.device.index, **self.options)
+        h.pool_key = key
         self.used_bytes += need
         return h
 
     def _launch(self, req: Request, fut: Future, slot: _Slot, h: Reconstructor):
         dev = self.device
+        if req.ready is not None:
+            slot.stream.wait_event(req.ready)
         with torch.cuda.stream(slot.stream):
             def to_dev(a):
                 if a is None:
@@ -168,14 +215,18 @@ class Server:
             info = h.info()
             lat = time.perf_counter() - req.arrival
             self.latencies.append(lat)
+            self.latencies_by_res[req.res].append(lat)
             self.completed += 1
+            grid = out["sdf_grid"]
+            if grid is not None and req.caller_stream is not None:
+                grid.record_stream(req.caller_stream)
             res = Result(rid=req.rid,
                          sdf_q=out["sdf_q"].numpy() if out.get("sdf_q") is not None else None,
                          d_points=out["d_points"].numpy() if "d_points" in out else None,
                          d_normals=out["d_normals"].numpy() if "d_normals" in out else None,
-                         sdf_grid=out["sdf_grid"], info=info, latency_s=lat)
+                         sdf_grid=grid, info=info, latency_s=lat, res=req.res, done_event=ev)
             slot.busy = False
-            self.free_handles[req.res].append(h)
+            self.free_handles[h.pool_key].append(h)
             fut.set_result(res)
         return bool(done)
 
@@ -192,7 +243,7 @@ class Server:
                     if slot is None:
                         break
                     req, fut = self.pending[0]
-                    h = self._take_handle(req.res)
+                    h = self._take_handle(req.res, int(req.points.shape[0]))
                     if h is None:
                         break           # memory: wait for a running request to finish
                     self.pending.popleft()
@@ -201,7 +252,7 @@ class Server:
                         self._launch(req, fut, slot, h)
                     except Exception as exc:  # noqa: BLE001
                         slot.busy = False
-                        self.free_handles[req.res].append(h)
+                        self.free_handles[h.pool_key].append(h)
                         fut.set_exception(exc)
                     progressed = True
                 if not progressed:

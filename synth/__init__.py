@@ -16,6 +16,7 @@ from .shapes import (  # noqa: F401
     sphere_cloud,
     sh_body_cloud,
     sh_fixed_dirs_cloud,
+    random_sh_body_theta,
     wave_ellipsoid_cloud,
     uniform_queries,
     uniform_dirs,

@@ -19,6 +19,7 @@ Re/Im (x + i y)^m), so there is no pole singularity.
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -141,14 +142,21 @@ def uniform_dirs(n: int, rng: np.random.Generator) -> np.ndarray:
     return g / np.linalg.norm(g, axis=1, keepdims=True)
 
 
-def _fit_perturbation(theta: np.ndarray, base: float, rmax: float = 0.45,
-                      rmin: float = 0.1):
-    """Scale the perturbation so base + perturbation stays in [rmin, rmax]."""
-    th = np.linspace(0.0, math.pi, 256)
-    ph = np.linspace(0.0, 2 * math.pi, 512, endpoint=False)
+@functools.lru_cache(maxsize=8)
+def _grid_sh(lmax: int, grid: tuple):
+    """Real SH up to lmax on a (theta, phi) grid of directions."""
+    th = np.linspace(0.0, math.pi, grid[0])
+    ph = np.linspace(0.0, 2 * math.pi, grid[1], endpoint=False)
     T, P = np.meshgrid(th, ph, indexing="ij")
     u = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
-    pert = real_sh(_lmax_of(theta), u) @ theta
+    return real_sh(lmax, u)
+
+
+def _fit_perturbation(theta: np.ndarray, base: float, rmax: float = 0.45,
+                      rmin: float = 0.1, grid=(256, 512)):
+    """Scale the perturbation so base + perturbation stays in [rmin, rmax]
+    (checked on a (theta, phi) grid of the given size)."""
+    pert = _grid_sh(_lmax_of(theta), tuple(grid)) @ theta
     s = 1.0
     if pert.max() > rmax - base:
         s = min(s, (rmax - base) / pert.max())
@@ -167,6 +175,15 @@ def sphere_cloud(n: int = 4096, seed: int = CONFIG_SEEDS["sphere64"],
 
 def random_sh_theta(lmax: int, rng: np.random.Generator, std: float = 0.02):
     return rng.normal(0.0, std, sh_count(lmax))
+
+
+def random_sh_body_theta(lmax: int, rng: np.random.Generator, std: float = 0.02, base: float = 0.3,
+                         grid=(64, 128)):
+    """Coefficients of a random SH star body (N(0, std^2)), the perturbation
+    scaled into [0.1, 0.45] on a coarse direction grid (one body per request
+    of the serving mix)."""
+    theta, _ = _fit_perturbation(random_sh_theta(lmax, rng, std), base, grid=grid)
+    return theta
 
 
 def sh_body_cloud(n: int = 200_000, lmax: int = 8, seed: int = CONFIG_SEEDS["shbody256"],

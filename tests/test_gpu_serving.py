@@ -1,6 +1,9 @@
 """Serving loop on the GPU: every result is the same alone and in a mix of
-concurrent requests of different sizes; admission respects the memory budget;
-an oversized request is refused on the host."""
+concurrent requests of different sizes (bit for bit with cold solves; within
+the stated tolerances when each pooled handle warm-starts from whatever it
+solved last); admission respects the memory budget; an oversized request is
+refused on the host; device-resident inputs produced on the caller's stream
+are read after that stream's work."""
 import numpy as np
 import pytest
 
@@ -30,9 +33,9 @@ def lib():
     torch.cuda.set_device(0)
 
 
-def _run(reqs, budget, streams):
+def _run(reqs, budget, streams, warm_start=1):
     from paper_2609_20964_gb300.serving import Server
-    srv = Server(budget, n_streams=streams, max_points=20000)
+    srv = Server(budget, n_streams=streams, max_points=20000, warm_start=warm_start)
     futs = [srv.submit(r) for r in reqs]
     res = [f.result(timeout=120) for f in futs]
     st = srv.stats()
@@ -41,20 +44,65 @@ def _run(reqs, budget, streams):
 
 
 def test_alone_equals_mix(lib):
+    # cold solves: the forward is bit-reproducible, whatever ran before on the handle
+    reqs = _requests()
+    alone = []
+    for r in reqs:
+        out, _ = _run([r], 4 << 30, 1, warm_start=0)
+        alone.append(out[0])
+    mix, st = _run(reqs, 4 << 30, 4, warm_start=0)
+    assert st["completed"] == len(reqs)
+    for a, m in zip(alone, mix):
+        assert a.rid == m.rid
+        assert np.array_equal(a.sdf_q, m.sdf_q)
+        if a.d_points is not None:
+            rel = np.linalg.norm(a.d_points - m.d_points) / np.linalg.norm(a.d_points)
+            assert rel <= 1e-6                               # FP64-atomic accumulation order only
+        assert m.info["status"] == 0
+
+
+def test_alone_equals_mix_with_warm_start(lib):
+    # warm starts (the default): a handle's solve starts from the last body it
+    # solved, so results agree to the solver's tolerance, not bit for bit
     reqs = _requests()
     alone = []
     for r in reqs:
         out, _ = _run([r], 4 << 30, 1)
         alone.append(out[0])
-    mix, st = _run(reqs, 4 << 30, 4)
-    assert st["completed"] == len(reqs)
-    for a, m in zip(alone, mix):
-        assert a.rid == m.rid
-        assert np.array_equal(a.sdf_q, m.sdf_q)            # forward is bit-reproducible
+    mix, st = _run(reqs + reqs, 4 << 30, 4)      # every request twice: the second runs warm
+    assert st["completed"] == 2 * len(reqs)
+    for k, m in enumerate(mix):
+        a = alone[k % len(reqs)]
+        assert a.rid == m.rid and m.info["status"] == 0
+        assert np.abs(a.sdf_q - m.sdf_q).max() <= 1e-4      # 1e-4 of the unit box
         if a.d_points is not None:
-            rel = np.linalg.norm(a.d_points - m.d_points) / np.linalg.norm(a.d_points)
-            assert rel <= 1e-6                               # FP64-atomic accumulation order only
-        assert m.info["status"] == 0
+            for x, y in ((a.d_points, m.d_points), (a.d_normals, m.d_normals)):
+                assert np.linalg.norm(x - y) <= 1e-4 * np.linalg.norm(x)
+                assert np.linalg.norm(x - y, axis=1).max() <= 1e-4 * np.linalg.norm(x, axis=1).max()
+
+
+def test_device_inputs_follow_the_callers_stream(lib):
+    # inputs produced on the device by work enqueued on the caller's stream
+    # just before submit(): the request must read them after that work
+    from paper_2609_20964_gb300.serving import Request, Server
+    p, n, _ = synth.sh_body_cloud(8000, seed=901)
+    q = synth.uniform_queries(3000, seed=902)
+    srv = Server(4 << 30, n_streams=2, max_points=20000, warm_start=0)
+    want = srv.submit(Request(points=p, normals=n, res=48, queries=q, rid=0)).result(timeout=120)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        P = torch.zeros((len(p), 3), device="cuda")
+        N = torch.zeros((len(n), 3), device="cuda")
+        Q = torch.zeros((len(q), 3), device="cuda")
+        torch.cuda._sleep(20_000_000)                 # keep the stream busy before the copies
+        P.copy_(torch.from_numpy(p).cuda(non_blocking=True))
+        N.copy_(torch.from_numpy(n).cuda(non_blocking=True))
+        Q.copy_(torch.from_numpy(q).cuda(non_blocking=True))
+        fut = srv.submit(Request(points=P, normals=N, res=48, queries=Q, want_grid=True, rid=1))
+    got = fut.result(timeout=120)
+    srv.close()
+    assert np.array_equal(want.sdf_q, got.sdf_q)
+    assert got.sdf_grid is not None and got.done_event is not None
 
 
 def test_admission_under_small_budget(lib):
