@@ -1116,32 +1116,52 @@ __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, cons
 
 // n = grad phi / |grad phi|: central differences inside, second-order one-sided
 // on the first and last node of each axis; 0 where |grad| is 0 or not finite.
-__global__ void normals_kernel(const float* __restrict__ phi, int n, double h,
-                               float* __restrict__ nrm) {
-  const int64_t N = (int64_t)n * n * n;
+// One thread per (x, y) column marches kNrmZ planes in z, keeping the
+// column's previous, current and next phi in registers; x and y neighbours
+// come through L1 from the warp's own row and the block's neighbouring rows.
+// No index division, coalesced loads and stores of every plane.
+constexpr int kNrmZ = 16;
+__global__ void __launch_bounds__(256) normals_kernel(const float* __restrict__ phi, int n, double h,
+                                                      float* __restrict__ nrm) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const int k0 = blockIdx.z * kNrmZ;
+  if (i >= n || j >= n || k0 >= n) return;
+  const int64_t nn = (int64_t)n * n, N = nn * n;
   const float inv2h = (float)(0.5 / h);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int idx[3] = {(int)(t % n), (int)((t / n) % n), (int)(t / ((int64_t)n * n))};
-    const int64_t st[3] = {1, n, (int64_t)n * n};
+  const int k1 = min(k0 + kNrmZ, n);
+  int64_t t = (int64_t)k0 * nn + (int64_t)j * n + i;
+  float zm = k0 > 0 ? phi[t - nn] : 0.f;
+  float zc = phi[t];
+  for (int k = k0; k < k1; ++k, t += nn) {
+    const float zp = k + 1 < n ? phi[t + nn] : 0.f;
     float gr[3];
+    if (i == 0)
+      gr[0] = -3.f * zc + 4.f * phi[t + 1] - phi[t + 2];
+    else if (i == n - 1)
+      gr[0] = 3.f * zc - 4.f * phi[t - 1] + phi[t - 2];
+    else
+      gr[0] = phi[t + 1] - phi[t - 1];
+    if (j == 0)
+      gr[1] = -3.f * zc + 4.f * phi[t + n] - phi[t + 2 * n];
+    else if (j == n - 1)
+      gr[1] = 3.f * zc - 4.f * phi[t - n] + phi[t - 2 * n];
+    else
+      gr[1] = phi[t + n] - phi[t - n];
+    if (k == 0)
+      gr[2] = -3.f * zc + 4.f * zp - phi[t + 2 * nn];
+    else if (k == n - 1)
+      gr[2] = 3.f * zc - 4.f * zm + phi[t - 2 * nn];
+    else
+      gr[2] = zp - zm;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int i = idx[a];
-      float d;
-      if (i == 0)
-        d = -3.f * phi[t] + 4.f * phi[t + st[a]] - phi[t + 2 * st[a]];
-      else if (i == n - 1)
-        d = 3.f * phi[t] - 4.f * phi[t - st[a]] + phi[t - 2 * st[a]];
-      else
-        d = phi[t + st[a]] - phi[t - st[a]];
-      gr[a] = d * inv2h;
-    }
+    for (int a = 0; a < 3; ++a) gr[a] *= inv2h;
     const float m2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
     const bool ok = isfinite(m2) && m2 > 0.f;
     const float inv = ok ? rsqrtf(m2) : 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) nrm[a * N + t] = ok ? gr[a] * inv : 0.f;
+    zm = zc;
+    zc = zp;
   }
 }
 
@@ -1644,8 +1664,8 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   }
   if (nrm_out) {
     slot = stage_begin(h, kStNormals, s);
-    const int64_t N = (int64_t)res * res * res;
-    normals_kernel<<<grid_blocks(N, 256, 152 * 32), 256, 0, s>>>(h->phi, res, h->h, nrm_out);
+    normals_kernel<<<dim3(div_up(res, 32), div_up(res, 8), div_up(res, kNrmZ)), dim3(32, 8), 0, s>>>(
+        h->phi, res, h->h, nrm_out);
     WGEO_LAUNCH_CHECK();
     stage_end(h, kStNormals, slot, s);
   }
