@@ -74,13 +74,16 @@ typedef enum {
 #define WGEO_PREC_FP32  1  /* plain FP32, no refinement: one direct FP32 spectral solve on
                               power-of-two grids of 32..512 with opt.spectral (set max_vcycles >= 1),
                               else FP32 V-cycles on the iterate; FP32 residual and sums */
+#define WGEO_PREC_FP64  2  /* as MIXED with a native FP64 refinement iterate and residual (the FP64
+                              pipe) instead of float-float; the adjoint solve stays float-float.  A
+                              comparison point: same results to ~1e-12, slower on this GPU */
 
 typedef struct {
   double  tol_rel;           /* stop when ||b - A chi|| <= tol_rel * ||b|| (default 1e-6) */
   int32_t max_vcycles;       /* FP32 mode: maximum V-cycles, or spectral solves (default 40) */
   int32_t max_refine;        /* MIXED mode: maximum refinement steps (default 10) */
   int32_t vcycles_per_refine;/* MIXED mode: FP32 V-cycles per refinement step (default 2) */
-  int32_t precision;         /* WGEO_PREC_MIXED (default) or WGEO_PREC_FP32 */
+  int32_t precision;         /* WGEO_PREC_MIXED (default), WGEO_PREC_FP32 or WGEO_PREC_FP64 */
   int32_t warm_start;        /* start the solve from the previous chi on this handle when res matches (default 0) */
   int32_t keep_for_backward; /* keep what wgeo_backward needs (closest triangles, phi copy); default 1 */
   int64_t mesh_capacity;     /* maximum triangles; 0 = default 16 * max_res^2 */

@@ -8,6 +8,7 @@ does, and raises if it has not been built.
 """
 from ._lib import (  # noqa: F401
     PREC_FP32,
+    PREC_FP64,
     PREC_MIXED,
     STATUS_EMPTY_SURFACE,
     STATUS_MESH_CAPACITY,

@@ -29,6 +29,7 @@ STAGES = ("splat", "solve", "iso", "mc", "sdf", "normals", "query", "bwd_seed",
 
 PREC_MIXED = 0
 PREC_FP32 = 1
+PREC_FP64 = 2
 
 # every function the header declares, with (restype, argtypes)
 _vp = C.c_void_p

@@ -119,7 +119,8 @@ bool valid_opt(const wgeo_options& o) {
   return o.tol_rel >= 0.0 && o.tol_rel_adjoint >= 0.0 && o.max_vcycles >= 0 && o.max_vcycles <= 1000 &&
          o.max_refine >= 0 &&
          o.max_refine <= 200 && o.vcycles_per_refine >= 1 && o.vcycles_per_refine <= 20 &&
-         (o.precision == WGEO_PREC_MIXED || o.precision == WGEO_PREC_FP32) && o.mesh_capacity >= 0 &&
+         (o.precision == WGEO_PREC_MIXED || o.precision == WGEO_PREC_FP32 || o.precision == WGEO_PREC_FP64) &&
+         o.mesh_capacity >= 0 &&
          (o.galerkin == 0 || (o.galerkin == 1 && o.precision == WGEO_PREC_MIXED)) &&
          (o.spectral == 0 || o.spectral == 1) &&
          o.mesh_capacity < (int64_t)1 << 31;

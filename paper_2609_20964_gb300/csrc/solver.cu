@@ -55,6 +55,9 @@ __device__ __forceinline__ int64_t lin(int i, int j, int k, int n) {
 struct PairFF {
   float2* buf[2];
 };
+struct PairD {
+  double* buf[2];
+};
 
 __device__ __forceinline__ float rhs_hi(const float* b, int64_t t, float& lo) {
   lo = 0.f;
@@ -194,6 +197,130 @@ __global__ void __launch_bounds__(kSX * kSY) update_residual_kernel(PairFF xp, c
     const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     partials[2 * blk] = d1;
     partials[2 * blk + 1] = d2;
+  }
+}
+
+// The same refinement pass with a native FP64 iterate (WGEO_PREC_FP64): the
+// two iterate buffers hold doubles (8 bytes a cell, like a float-float pair),
+// x_new = x + e and r = b - L x_new are formed on the FP64 pipe, and r, r^2
+// are summed in FP64.  x32 = (float) x_new, r32 = (float) r.  A comparison
+// point for the float-float pass above, which needs no FP64 arithmetic per
+// cell.
+__global__ void __launch_bounds__(kSX * kSY) update_residual_f64_kernel(PairD xp, const float* __restrict__ e,
+                                                                        const float* __restrict__ b, int n,
+                                                                        float* __restrict__ r32,
+                                                                        float* __restrict__ x32,
+                                                                        double* __restrict__ partials,
+                                                                        SolveState* ss) {
+  if (ss->done) return;
+  __shared__ double red[2 * (kSX * kSY / 32)];
+  const int cur = ss->xidx;
+  const bool cold = ss->cold != 0;
+  const double* __restrict__ xin = xp.buf[cur];
+  double* __restrict__ xout = xp.buf[e ? cur ^ 1 : cur];
+  const int I = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y, k = blockIdx.z;
+  const int i0 = 2 * I;
+  const bool vec = (n & 1) == 0;
+  double s1 = 0.0, s2 = 0.0;
+  if (i0 < n && j < n) {
+    const bool has1 = i0 + 1 < n;
+    const int64_t nn = (int64_t)n * n;
+    const int64_t t0 = (int64_t)k * nn + (int64_t)j * n + i0;
+    auto one = [&](int64_t q) { return cold ? 0.0 : (e ? xin[q] + (double)e[q] : xin[q]); };
+    auto pair = [&](int64_t q, double& a, double& c) {
+      if (vec && !cold) {
+        const double2 v = *reinterpret_cast<const double2*>(xin + q);
+        a = v.x;
+        c = v.y;
+        if (e) {
+          const float2 ev = *reinterpret_cast<const float2*>(e + q);
+          a += (double)ev.x;
+          c += (double)ev.y;
+        }
+      } else {
+        a = one(q);
+        c = has1 ? one(q + 1) : 0.0;
+      }
+    };
+    double xc[2];
+    pair(t0, xc[0], xc[1]);
+    double acc[2] = {0.0, 0.0};
+    if (!cold) {
+      if (has1) {
+        acc[0] += xc[1] - xc[0];
+        acc[1] += xc[0] - xc[1];
+      }
+      if (i0 > 0) acc[0] += one(t0 - 1) - xc[0];
+      if (i0 + 2 < n) acc[1] += one(t0 + 2) - xc[1];
+      double a, c;
+      if (j > 0) { pair(t0 - n, a, c); acc[0] += a - xc[0]; acc[1] += c - xc[1]; }
+      if (j < n - 1) { pair(t0 + n, a, c); acc[0] += a - xc[0]; acc[1] += c - xc[1]; }
+      if (k > 0) { pair(t0 - nn, a, c); acc[0] += a - xc[0]; acc[1] += c - xc[1]; }
+      if (k < n - 1) { pair(t0 + nn, a, c); acc[0] += a - xc[0]; acc[1] += c - xc[1]; }
+    }
+    float rf[2] = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (q == 1 && !has1) break;
+      const double r = (double)b[t0 + q] - acc[q];
+      rf[q] = (float)r;
+      s1 += r;
+      s2 += r * r;
+    }
+    if (vec) {
+      if (e || cold) *reinterpret_cast<double2*>(xout + t0) = make_double2(xc[0], xc[1]);
+      *reinterpret_cast<float2*>(x32 + t0) = make_float2((float)xc[0], (float)xc[1]);
+      *reinterpret_cast<float2*>(r32 + t0) = make_float2(rf[0], rf[1]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (q == 1 && !has1) break;
+        if (e || cold) xout[t0 + q] = xc[q];
+        x32[t0 + q] = (float)xc[q];
+        r32[t0 + q] = rf[q];
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  const int lane = (threadIdx.y * kSX + threadIdx.x) & 31, wid = (threadIdx.y * kSX + threadIdx.x) >> 5;
+  if (lane == 0) {
+    red[2 * wid] = s1;
+    red[2 * wid + 1] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double d1 = 0.0, d2 = 0.0;
+    for (int q = 0; q < kSX * kSY / 32; ++q) {
+      d1 += red[2 * q];
+      d2 += red[2 * q + 1];
+    }
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    partials[2 * blk] = d1;
+    partials[2 * blk + 1] = d2;
+  }
+}
+
+// FP64 iterate <-> float-float pair, in place in the current buffer (the
+// solve's index on the device): the surface stages, the adjoint and a warm
+// start read the iterate as a float-float pair.
+__global__ void ff_from_f64_kernel(PairD xp, const SolveState* __restrict__ ss, int64_t N) {
+  double* x = xp.buf[ss->xidx];
+  float2* f = reinterpret_cast<float2*>(x);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[t];
+    const float hi = (float)v;
+    f[t] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+__global__ void f64_from_ff_kernel(PairD xp, const SolveState* __restrict__ ss, int64_t N) {
+  double* x = xp.buf[ss->xidx];
+  const float2* f = reinterpret_cast<const float2*>(x);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = f[t];
+    x[t] = (double)v.x + (double)v.y;
   }
 }
 
@@ -1449,6 +1576,11 @@ int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGrap
     else
       update_residual_q1_kernel<double><<<rg, dim3(kSX, kSY), 0, s>>>(xp, e, h->dchi64, res, h->r32, x32,
                                                                       h->partials, ss);
+  } else if (mode == 0 && h->opt.precision == WGEO_PREC_FP64) {
+    PairD xd;
+    xd.buf[0] = reinterpret_cast<double*>(xp.buf[0]);
+    xd.buf[1] = reinterpret_cast<double*>(xp.buf[1]);
+    update_residual_f64_kernel<<<rg, dim3(kSX, kSY), 0, s>>>(xd, e, h->b32, res, h->r32, x32, h->partials, ss);
   } else if (mode == 0) {
     update_residual_kernel<float><<<rg, dim3(kSX, kSY), 0, s>>>(xp, e, h->b32, res, h->r32, x32, h->partials, ss);
   } else {
@@ -1577,6 +1709,8 @@ int build_levels(wgeo_handle* h, int res) {
   return WGEO_OK;
 }
 
+int launch_solve_body(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s);
+
 // Enqueues one solve.  The launch sequence depends only on (res, mode,
 // options), and every pointer it uses is owned by the handle, so it is
 // recorded once as a CUDA graph and replayed; while the caller's stream is
@@ -1584,7 +1718,6 @@ int build_levels(wgeo_handle* h, int res) {
 int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
   const int64_t N = (int64_t)res * res * res;
   SolveState* ss = mode == 0 ? &h->dstate->fwd : &h->dstate->bwd;
-  const bool fp32_plain = (mode == 0 && h->opt.precision == WGEO_PREC_FP32);
   if (use_spectral(h, res)) {
     int rc = spectral_setup(h, res, s);
     if (rc) return rc;
@@ -1601,6 +1734,29 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
     rhs_stats_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss);
     WGEO_LAUNCH_CHECK();
   }
+  // native FP64 iterate: a warm start's float-float pair becomes a double
+  // first, and the solution becomes a pair again after the solve
+  const bool f64 = (mode == 0 && h->opt.precision == WGEO_PREC_FP64);
+  PairD xd;
+  xd.buf[0] = reinterpret_cast<double*>(h->chiff[0]);
+  xd.buf[1] = reinterpret_cast<double*>(h->chiff[1]);
+  if (f64 && !cold) {
+    f64_from_ff_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(xd, ss, N);
+    WGEO_LAUNCH_CHECK();
+  }
+  int rc = launch_solve_body(h, res, mode, cold, s);
+  if (rc) return rc;
+  if (f64) {
+    ff_from_f64_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(xd, ss, N);
+    WGEO_LAUNCH_CHECK();
+  }
+  return WGEO_OK;
+}
+
+// The solve proper (see launch_solve): the recorded graph or the fixed sequence.
+int launch_solve_body(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
+  SolveState* ss = mode == 0 ? &h->dstate->fwd : &h->dstate->bwd;
+  const bool fp32_plain = (mode == 0 && h->opt.precision == WGEO_PREC_FP32);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   WGEO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
   const int steps = max_steps(h, mode);
@@ -1615,7 +1771,7 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
     return enqueue_solve(h, res, mode, s);
   }
   SolverGraph& g = h->graphs[mode];
-  const int gmode = mode * 2 + (h->opt.precision == WGEO_PREC_FP32 ? 1 : 0);
+  const int gmode = mode * 3 + (mode == 0 ? h->opt.precision : 0);
   if (g.exec == nullptr || g.res != res || g.mode != gmode) {
     if (g.exec) {
       cudaGraphExecDestroy(g.exec);

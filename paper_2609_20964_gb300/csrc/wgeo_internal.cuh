@@ -409,12 +409,13 @@ struct wgeo_handle {
 };
 
 namespace wgeo {
-// The forward's float-float indicator buffers when the handle solves in MIXED
-// precision (vertex placement, near-tie decisions, sign tests and the
-// adjoint's vertex weights read the current one), else null pointers.
+// The forward's float-float indicator buffers when the handle refines its
+// solve (MIXED, or FP64 whose iterate is converted to a float-float pair after
+// the solve): vertex placement, near-tie decisions, sign tests and the
+// adjoint's vertex weights read the current one.  Null pointers in FP32 mode.
 inline ChiFF chiff_of(const wgeo_handle* h) {
   ChiFF c;
-  const bool mixed = h->opt.precision == WGEO_PREC_MIXED;
+  const bool mixed = h->opt.precision != WGEO_PREC_FP32;
   c.p[0] = mixed ? h->chiff[0] : nullptr;
   c.p[1] = mixed ? h->chiff[1] : nullptr;
   return c;

@@ -457,3 +457,36 @@ def test_sphere64_sampled_against_analytic_and_oracle(W):
     ophi, _, _ = OP.sdf_at(ref, lin)
     assert np.abs(phi.reshape(-1)[lin] - ophi).max() <= SDF_TOL
     rec.close()
+
+
+@pytest.mark.parametrize("name,res", [("shbody44", 44), ("sphere64", 64)])
+def test_fp64_refinement_mode(W, name, res):
+    """The native-FP64 refinement (WGEO_PREC_FP64) on a multigrid grid (44^3)
+    and a spectral one (64^3): the same SDF as the float-float refinement to
+    float32 rounding, within 1e-4 of the oracle, and gradient parity; a second
+    call on the handle warm-starts from the float-float pair it left."""
+    from paper_2609_20964_gb300 import PREC_FP64
+    if name == "sphere64":
+        p, n = synth.sphere_cloud(4096)
+        ref = oracle.reconstruct(p, n, BBOX, res, workers=max(1, min(16, os.cpu_count() or 1)))
+    else:
+        p, n, _ = CASES[name]
+        ref = _oracle(name)
+    mixed = W(res, len(p))
+    sm, _ = mixed.reconstruct(_t(p), _t(n), BBOX, res)
+    sm = sm.clone()
+    rec = W(res, len(p), precision=PREC_FP64, warm_start=1)
+    for _ in range(2):
+        s64, _ = rec.reconstruct(_t(p), _t(n), BBOX, res)
+        info = rec.info()
+        assert info["status"] == 0, info
+        assert float((s64 - sm).abs().max()) <= 1e-6
+        assert np.abs(s64.cpu().numpy().astype(np.float64) - ref.phi).max() <= SDF_TOL
+    q = synth.uniform_queries(2000, seed=35)
+    gs = np.random.default_rng(7).standard_normal(len(q)).astype(np.float32)
+    dp, dn, _ = rec.backward(q=_t(q), d_sdf_q=_t(gs))
+    odp, odn, _ = OP.backward(ref, q=q, d_sdf_q=gs.astype(np.float64))
+    _check_grad(dp, odp, "d_points")
+    _check_grad(dn, odn, "d_normals")
+    rec.close()
+    mixed.close()
