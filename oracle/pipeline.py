@@ -111,13 +111,14 @@ def sdf_at(rec: Reconstruction, lin):
     return sgn * d, d, tri
 
 
-def sdf_at_pool(rec: Reconstruction, lin, workers: int = 1):
-    """sdf_at, with the exact distance evaluated by `workers` processes."""
+def sdf_at_pool(rec: Reconstruction, lin, workers: int = 1, pool=None):
+    """sdf_at, with the exact distance evaluated by `workers` processes (or by
+    an existing process pool)."""
     nodes = node_xyz(lin, rec.res, rec.lo, rec.h)
     sgn = S.node_sign(rec.chi.reshape(-1)[lin], rec.c)
     if rec.mesh["verts"].shape[0] == 0:
         return sgn * np.inf, np.full(len(lin), np.inf), np.full(len(lin), -1)
-    d, tri = S.exact_distance_pool(nodes, rec.mesh["verts"], workers)
+    d, tri = S.exact_distance_pool(nodes, rec.mesh["verts"], workers, pool=pool)
     return sgn * d, d, tri
 
 

@@ -134,19 +134,23 @@ def _exact_distance_part(args):
     return exact_distance(nodes, verts)
 
 
-def exact_distance_pool(nodes, verts, workers: int = 1, parts: int = 64):
+def exact_distance_pool(nodes, verts, workers: int = 1, parts: int = 64, pool=None):
     """exact_distance, with the nodes split into contiguous parts evaluated by
     a pool of `workers` processes (started with "spawn", so the pool may be
-    created in a process that already uses a GPU).  Every node's result is
-    computed by exact_distance itself; only the work is divided."""
+    created in a process that already uses a GPU), or by `pool` when given.
+    Every node's result is computed by exact_distance itself; only the work is
+    divided."""
     N = nodes.shape[0]
-    if workers <= 1 or N < 4 * parts:
+    if (workers <= 1 and pool is None) or N < 4 * parts:
         return exact_distance(nodes, verts)
-    import multiprocessing as mp
     bounds = np.linspace(0, N, parts + 1).astype(np.int64)
     jobs = [(nodes[bounds[i]:bounds[i + 1]], verts) for i in range(parts)]
-    with mp.get_context("spawn").Pool(workers) as pool:
+    if pool is not None:
         out = pool.map(_exact_distance_part, jobs, chunksize=1)
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as own:
+            out = own.map(_exact_distance_part, jobs, chunksize=1)
     return np.concatenate([o[0] for o in out]), np.concatenate([o[1] for o in out])
 
 
