@@ -964,6 +964,27 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
   if (lane == 0) stk[0] = pack_node(top, 0, 0, 0);
   sp = 1;
   unsigned long long c_nodes = 0, c_leaves = 0, c_tests = 0;
+  // the warp's nodes' bounding box: centre and half-diagonal, widened so that
+  // float rounding keeps the box bound below every lane's exact bound
+  float bc[3], br;
+  {
+    const float pv[3] = {p.x, p.y, p.z};
+    float r2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float lo = pv[a], hi = pv[a];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      bc[a] = 0.5f * (lo + hi);
+      const float e = 0.5f * (hi - lo);
+      r2 += e * e;
+    }
+    br = sqrtf(r2) * (1.f + 1e-5f) + 1e-7f * coord;
+  }
+  const float3 pb = make_float3(bc[0], bc[1], bc[2]);
   __syncwarp();
   while (sp > 0) {
     --sp;
@@ -995,33 +1016,34 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
     }
     const int dc = s_dim[lev - 1];
     const int cbase = s_off[lev - 1];
-    // children: visit if any lane may improve; order nearest-first by the warp's
-    // smallest bound (pushed far-to-near)
-    float key[8];
-    unsigned ent[8];
-    int nc = 0;
+    // children, one per lane (lanes 0-7): kept when their bound from the
+    // warp's box (the puck's distance to the box centre less the box's
+    // half-diagonal, a lower bound for every node in it) beats the largest
+    // lane cut; pushed far-to-near by that bound.  Each lane's own bound is
+    // checked when a child is popped, so a child is bounded per lane once.
     const unsigned cmask = __float_as_uint(An.w) & 0xffu;
+    const float maxcut = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(cut, 0.f))));
+    bool keep = false;
+    float key = INFINITY;
+    unsigned ent = 0u;
+    if (lane < 8 && ((cmask >> lane) & 1u)) {
+      const int cx = 2 * x + (lane & 1), cy = 2 * y + ((lane >> 1) & 1), cz = 2 * z + (lane >> 2);
+      const int cg = cbase + (cz * dc + cy) * dc + cx;
+      const float dcen = sqrtf(puck_dist2(pb, pyr[2 * cg], pyr[2 * cg + 1])) * (1.f - 2e-6f) - br;
+      key = dcen > 0.f ? dcen * dcen : 0.f;
+      keep = key < maxcut;
+      ent = pack_node(lev - 1, cx, cy, cz);
+    }
+    const unsigned kept = __ballot_sync(0xffffffffu, keep);
+    const int nc = __popc(kept);
+    int rank = 0;   // kept children nearer than this one (ties by lane)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      if (!((cmask >> q) & 1u)) continue;
-      const int cx = 2 * x + (q & 1), cy = 2 * y + ((q >> 1) & 1), cz = 2 * z + (q >> 2);
-      const int cg = cbase + (cz * dc + cy) * dc + cx;
-      const float d = puck_dist2(p, pyr[2 * cg], pyr[2 * cg + 1]);
-      if (!__any_sync(0xffffffffu, d < cut)) continue;
-      const float dm = __shfl_sync(0xffffffffu, d, 0);   // ordering key: the first lane's bound
-      int q2 = nc;
-      while (q2 > 0 && key[q2 - 1] < dm) {
-        key[q2] = key[q2 - 1];
-        ent[q2] = ent[q2 - 1];
-        --q2;
-      }
-      key[q2] = dm;
-      ent[q2] = pack_node(lev - 1, cx, cy, cz);
-      ++nc;
+      const float kq = __shfl_sync(0xffffffffu, key, q);
+      if (((kept >> q) & 1u) && (kq < key || (kq == key && q < lane))) ++rank;
     }
-    if (lane == 0) {
-      for (int q = 0; q < nc && sp + q < kStack; ++q) stk[sp + q] = ent[q];
-    }
+    const int slot = sp + nc - 1 - rank;
+    if (keep && slot < kStack) stk[slot] = ent;
     sp = min(sp + nc, kStack);
     __syncwarp();
   }
