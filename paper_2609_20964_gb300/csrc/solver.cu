@@ -77,8 +77,16 @@ __device__ __forceinline__ float rhs_hi(const double* b, int64_t t, float& lo) {
 //   x_new = x + e (e may be null: no correction this step; cold: x := 0),
 //   x32 = hi(x_new), r32 = b - L x_new (each neighbour difference split
 //   exactly), per-thread sums of r and r^2 in FP32, per-block sums in FP64.
+// One x pair (i0 = 2 I, i0 + 1) of row j per thread, marching kResZ planes in
+// z: the pair's x_new below, at and above the current plane stay in
+// registers, so only the plane above is loaded per step (with the y
+// neighbours' pairs and the two x neighbours).  The neighbour differences
+// are summed in the same order as a one-plane-per-thread pass (x partner,
+// x - 1, x + 2, y - 1, y + 1, z - 1, z + 1), so x32 and r32 do not depend on
+// the marching.
+constexpr int kResZ = 8;
 template <typename TB>
-__global__ void __launch_bounds__(kSX * kSY) update_residual_kernel(PairFF xp, const float* __restrict__ e,
+__global__ void __launch_bounds__(kSX * kSY, 4) update_residual_kernel(PairFF xp, const float* __restrict__ e,
                                                                     const TB* __restrict__ b, int n,
                                                                     float* __restrict__ r32, float* __restrict__ x32,
                                                                     double* __restrict__ partials, SolveState* ss) {
@@ -88,17 +96,16 @@ __global__ void __launch_bounds__(kSX * kSY) update_residual_kernel(PairFF xp, c
   const bool cold = ss->cold != 0;
   const float2* __restrict__ xin = xp.buf[cur];
   float2* __restrict__ xout = xp.buf[e ? cur ^ 1 : cur];
-  // one x pair (i0 = 2 I, i0 + 1) of row j, plane k per thread; vector
-  // accesses need an even n (pairs then start on even cells); an odd n (only
-  // grids up to 15^3) takes scalar accesses and a last pair of one cell
-  const int I = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y, k = blockIdx.z;
+  // vector accesses need an even n (pairs then start on even cells); an odd
+  // n (only grids up to 15^3) takes scalar accesses and a last pair of one cell
+  const int I = blockIdx.x * kSX + threadIdx.x, j = blockIdx.y * kSY + threadIdx.y;
+  const int k0 = blockIdx.z * kResZ, k1 = min(k0 + kResZ, n);
   const int i0 = 2 * I;
   const bool vec = (n & 1) == 0;
   float s1 = 0.f, s2 = 0.f;
   if (i0 < n && j < n) {
     const bool has1 = i0 + 1 < n;
     const int64_t nn = (int64_t)n * n;
-    const int64_t t0 = (int64_t)k * nn + (int64_t)j * n + i0;
     auto pair = [&](int64_t q, float2& a, float2& c) {   // x_new at cells q, q + 1
       if (vec) {
         const float4 v = *reinterpret_cast<const float4*>(xin + q);
@@ -123,58 +130,71 @@ __global__ void __launch_bounds__(kSX * kSY) update_residual_kernel(PairFF xp, c
       const float2 v = xin[q];
       return e ? ff_add_f(v, e[q]) : v;
     };
-    float2 xc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const float2 zero2 = make_float2(0.f, 0.f);
+    // x_new of the pair on planes k - 1 (zm), k (zc) and k + 1 (zp)
+    float2 zm[2] = {zero2, zero2}, zc[2] = {zero2, zero2}, zp[2] = {zero2, zero2};
+    int64_t t0 = (int64_t)k0 * nn + (int64_t)j * n + i0;
     if (!cold) {
-      pair(t0, xc[0], xc[1]);
-      // L x = sum of (x_q - x_p): each hi difference split exactly by two-sum,
-      // the hi parts summed by a two-sum chain (rounding errors carried in
-      // `err`), the lo differences (each below ulp(hi)) summed in float
-      float sh[2] = {0.f, 0.f}, err[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
-      auto add = [&](int c, float2 v) {
-        const float2 d = two_sum(v.x, -xc[c].x);
-        const float2 q = two_sum(sh[c], d.x);
-        sh[c] = q.x;
-        err[c] = __fadd_rn(err[c], __fadd_rn(q.y, d.y));
-        lo[c] = __fadd_rn(lo[c], __fsub_rn(v.y, xc[c].y));
-      };
-      if (has1) {
-        add(0, xc[1]);                     // the pair's own cells are x neighbours
-        add(1, xc[0]);
+      if (k0 > 0) pair(t0 - nn, zm[0], zm[1]);
+      pair(t0, zc[0], zc[1]);
+    }
+    for (int k = k0; k < k1; ++k, t0 += nn) {
+      float2 acc[2] = {zero2, zero2};
+      if (!cold) {
+        if (k < n - 1) pair(t0 + nn, zp[0], zp[1]);
+        // L x = sum of (x_q - x_p): each hi difference split exactly by two-sum,
+        // the hi parts summed by a two-sum chain (rounding errors carried in
+        // `err`), the lo differences (each below ulp(hi)) summed in float
+        float sh[2] = {0.f, 0.f}, err[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
+        auto add = [&](int c, float2 v) {
+          const float2 d = two_sum(v.x, -zc[c].x);
+          const float2 q = two_sum(sh[c], d.x);
+          sh[c] = q.x;
+          err[c] = __fadd_rn(err[c], __fadd_rn(q.y, d.y));
+          lo[c] = __fadd_rn(lo[c], __fsub_rn(v.y, zc[c].y));
+        };
+        if (has1) {
+          add(0, zc[1]);                     // the pair's own cells are x neighbours
+          add(1, zc[0]);
+        }
+        if (i0 > 0) add(0, single(t0 - 1));
+        if (i0 + 2 < n) add(1, single(t0 + 2));
+        float2 a, c;
+        if (j > 0) { pair(t0 - n, a, c); add(0, a); add(1, c); }
+        if (j < n - 1) { pair(t0 + n, a, c); add(0, a); add(1, c); }
+        if (k > 0) { add(0, zm[0]); add(1, zm[1]); }
+        if (k < n - 1) { add(0, zp[0]); add(1, zp[1]); }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[q] = two_sum(sh[q], __fadd_rn(err[q], lo[q]));
       }
-      if (i0 > 0) add(0, single(t0 - 1));
-      if (i0 + 2 < n) add(1, single(t0 + 2));
-      float2 a, c;
-      if (j > 0) { pair(t0 - n, a, c); add(0, a); add(1, c); }
-      if (j < n - 1) { pair(t0 + n, a, c); add(0, a); add(1, c); }
-      if (k > 0) { pair(t0 - nn, a, c); add(0, a); add(1, c); }
-      if (k < n - 1) { pair(t0 + nn, a, c); add(0, a); add(1, c); }
-#pragma unroll
-      for (int q = 0; q < 2; ++q) acc[q] = two_sum(sh[q], __fadd_rn(err[q], lo[q]));
-    }
-    float rf[2] = {0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      if (q == 1 && !has1) break;
-      float blo;
-      const float bhi = rhs_hi(b, t0 + q, blo);
-      const float2 r = ff_sub(make_float2(bhi, blo), acc[q]);
-      rf[q] = r.x + r.y;
-      s1 += rf[q];
-      s2 += rf[q] * rf[q];
-    }
-    if (vec) {
-      if (e || cold) *reinterpret_cast<float4*>(xout + t0) = make_float4(xc[0].x, xc[0].y, xc[1].x, xc[1].y);
-      *reinterpret_cast<float2*>(x32 + t0) = make_float2(xc[0].x, xc[1].x);
-      *reinterpret_cast<float2*>(r32 + t0) = make_float2(rf[0], rf[1]);
-    } else {
+      float rf[2] = {0.f, 0.f};
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (q == 1 && !has1) break;
-        if (e || cold) xout[t0 + q] = xc[q];
-        x32[t0 + q] = xc[q].x;
-        r32[t0 + q] = rf[q];
+        float blo;
+        const float bhi = rhs_hi(b, t0 + q, blo);
+        const float2 r = ff_sub(make_float2(bhi, blo), acc[q]);
+        rf[q] = r.x + r.y;
+        s1 += rf[q];
+        s2 += rf[q] * rf[q];
       }
+      if (vec) {
+        if (e || cold) *reinterpret_cast<float4*>(xout + t0) = make_float4(zc[0].x, zc[0].y, zc[1].x, zc[1].y);
+        *reinterpret_cast<float2*>(x32 + t0) = make_float2(zc[0].x, zc[1].x);
+        *reinterpret_cast<float2*>(r32 + t0) = make_float2(rf[0], rf[1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (q == 1 && !has1) break;
+          if (e || cold) xout[t0 + q] = zc[q];
+          x32[t0 + q] = zc[q].x;
+          r32[t0 + q] = rf[q];
+        }
+      }
+      zm[0] = zc[0];
+      zm[1] = zc[1];
+      zc[0] = zp[0];
+      zc[1] = zp[1];
     }
   }
   // per-block sums of r and r^2: float within a warp, FP64 across the warps
@@ -1567,7 +1587,10 @@ int enqueue_part(wgeo_handle* h, int res, int mode, int part, int step, cudaGrap
     }
   }
   const float* e = part == 0 ? nullptr : h->e32;
-  const dim3 rg(div_up(div_up(res, 2), kSX), div_up(res, kSY), res);
+  // the lumped float-float pass marches kResZ planes per block in z; the
+  // unlumped and FP64 passes take one plane per block
+  const bool marching = !h->opt.galerkin && !(mode == 0 && h->opt.precision == WGEO_PREC_FP64);
+  const dim3 rg(div_up(div_up(res, 2), kSX), div_up(res, kSY), marching ? div_up(res, kResZ) : res);
   const int nrb = (int)(rg.x * rg.y * rg.z);
   if (h->opt.galerkin) {
     if (mode == 0)
