@@ -1197,12 +1197,18 @@ def main():
     # solver kernels inside graphs with device-side loops cannot be profiled
     # one by one: run the solves as plain launch sequences (profiler only)
     ap.add_argument("--no-graphs", action="store_true")
-    # profiler captures: only the warm-up and timed steps of the main handle
+    # profiler captures: only the warm-up and timed steps of the main handle,
+    # optionally with another solve precision
     ap.add_argument("--profile", action="store_true")
+    ap.add_argument("--precision", choices=["mixed", "fp32", "fp64"], default="mixed")
     args = ap.parse_args()
     globals().update(RES=args.res, NPTS=args.points, NQ=args.queries)
     if args.no_graphs:
         HANDLE_OPTS["use_graphs"] = 0
+    if args.precision != "mixed":
+        if not args.profile:
+            raise SystemExit("--precision applies to --profile runs only")
+        HANDLE_OPTS["precision"] = {"fp32": 1, "fp64": 2}[args.precision]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -20,6 +20,10 @@ sizes and point counts.
 * Requests that arrive while others are on the GPU are admitted as soon as a
   slot and memory free up; each runs on its own CUDA stream, so the kernels of
   different requests overlap on the device.
+* Order: when a slot frees, the pending request with the fewest grid cells
+  goes first (ties by arrival), unless the oldest has waited more than
+  ``max_wait_s``; then the oldest goes.  Small grids then do not queue behind
+  large ones, and no request waits without bound.
 * Completion is detected with CUDA events (host polling, no device spin);
   latency = completion - arrival, reported as p50 / p99.
 """
@@ -83,7 +87,8 @@ def _buckets(max_points: int):
 
 class Server:
     def __init__(self, budget_bytes: int, n_streams: int = 4, max_points: int = 500_000,
-                 device=None, point_buckets=None, warm_start: int = 1, **options):
+                 device=None, point_buckets=None, warm_start: int = 1, max_wait_s: float = 0.05,
+                 **options):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.budget = int(budget_bytes)
         self.max_points = max_points
@@ -91,6 +96,7 @@ class Server:
         if self.buckets[-1] < max_points:
             raise ValueError("the largest point bucket must hold max_points")
         self.options = dict(options, warm_start=warm_start)
+        self.max_wait_s = float(max_wait_s)
         self.slots = [_Slot(self.device) for _ in range(n_streams)]
         self.free_handles = collections.defaultdict(list)   # (res, bucket) -> [Reconstructor]
         self.used_bytes = 0
@@ -174,6 +180,19 @@ class Server:
         self.used_bytes += need
         return h
 
+    def _next_index(self) -> int:
+        """The pending request to run next: the oldest if it has waited more
+        than max_wait_s, else the one with the fewest grid cells (then the
+        earliest)."""
+        if time.perf_counter() - self.pending[0][0].arrival > self.max_wait_s:
+            return 0
+        best, key = 0, None
+        for i, (r, _) in enumerate(self.pending):
+            k = (r.res, r.arrival)
+            if key is None or k < key:
+                best, key = i, k
+        return best
+
     def _launch(self, req: Request, fut: Future, slot: _Slot, h: Reconstructor):
         dev = self.device
         if req.ready is not None:
@@ -242,11 +261,12 @@ class Server:
                     slot = next((s for s in self.slots if not s.busy), None)
                     if slot is None:
                         break
-                    req, fut = self.pending[0]
+                    pick = self._next_index()
+                    req, fut = self.pending[pick]
                     h = self._take_handle(req.res, int(req.points.shape[0]))
                     if h is None:
                         break           # memory: wait for a running request to finish
-                    self.pending.popleft()
+                    del self.pending[pick]
                     slot.busy = True
                     try:
                         self._launch(req, fut, slot, h)
