@@ -845,6 +845,7 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
                                                           float* __restrict__ phi, float* __restrict__ sdf_out,
                                                           int* __restrict__ ctri, int* __restrict__ tie_a,
                                                           int* __restrict__ tie_b, TieSlots tie_cd,
+                                                          int* __restrict__ tie_list,
                                                           int* __restrict__ seed_ids, int stride) {
   __shared__ unsigned int s_node[kWarps][kStack];
   __shared__ int s_off[12];
@@ -1057,23 +1058,33 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
       atomicAdd(&st->sdf_cnt[3], nt);
     }
   }
+  const int64_t o = lin3(i, j, k, n);
+  if (TIES) {
+    // near-tie nodes go to a compact list (one atomic per warp), so that the
+    // tie pass runs full warps over them alone
+    const unsigned m = __ballot_sync(0xffffffffu, tie);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(&st->ntie, (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (tie) tie_list[base + __popc(m & ((1u << lane) - 1u))] = (int)o;
+    }
+  }
   if (!valid) return;
   const float val = sqrtf(cd[0]);
   const int bt = ct[0] == -1 ? -1 : (ct[0] & idmask);
-  const int64_t o = lin3(i, j, k, n);
   const float sgn = (chi[o] >= st->c_up) ? 1.f : -1.f;
   phi[o] = sgn * val;
   if (sdf_out) sdf_out[o] = sgn * val;
   if (ctri) ctri[o] = bt;
   if (S > 1) seed_ids[o] = bt;
-  if (TIES) {
-    if (tie) {
-      tie_a[o] = bt;
-      const int c2 = ct[NC > 2 ? 2 : 0], c3 = ct[NC > 3 ? 3 : 0];
-      tie_cd.p[st->fwd.xidx ^ 1][o] = make_int2(cd[NC > 2 ? 2 : 0] <= cut && c2 != -1 ? (c2 & idmask) : -1,
-                                                cd[NC > 3 ? 3 : 0] <= cut && c3 != -1 ? (c3 & idmask) : -1);
-    }
-    tie_b[o] = tie ? (ct[NC > 1 ? 1 : 0] & idmask) : -1;
+  if (TIES && tie) {
+    tie_a[o] = bt;
+    tie_b[o] = ct[NC > 1 ? 1 : 0] & idmask;
+    const int c2 = ct[NC > 2 ? 2 : 0], c3 = ct[NC > 3 ? 3 : 0];
+    tie_cd.p[st->fwd.xidx ^ 1][o] = make_int2(cd[NC > 2 ? 2 : 0] <= cut && c2 != -1 ? (c2 & idmask) : -1,
+                                              cd[NC > 3 ? 3 : 0] <= cut && c3 != -1 ? (c3 & idmask) : -1);
   }
 }
 
@@ -1088,8 +1099,8 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
 __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, const DevState* __restrict__ st,
                                const float4* __restrict__ tris_s, const Tri* __restrict__ tris,
                                const Tri* __restrict__ tris_lo, const int* __restrict__ tie_a,
-                               const int* __restrict__ tie_b, TieSlots tie_cd, float* __restrict__ phi,
-                               float* __restrict__ sdf_out, int* __restrict__ ctri) {
+                               const int* __restrict__ tie_b, TieSlots tie_cd, const int* __restrict__ tie_list,
+                               float* __restrict__ phi, float* __restrict__ sdf_out, int* __restrict__ ctri) {
   __shared__ float2 s_ax[3][kMaxRes];
   const int n = g.res;
   for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
@@ -1101,11 +1112,11 @@ __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, cons
   __syncthreads();
   const float cf = st->c_up;
   const unsigned un = (unsigned)n;
-  const unsigned N = un * un * un;
+  const unsigned count = st->ntie;
   const int xi = st->fwd.xidx ^ 1;
-  for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < N; o += gridDim.x * blockDim.x) {
+  for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < count; it += gridDim.x * blockDim.x) {
+    const unsigned o = (unsigned)tie_list[it];
     const int t1 = tie_b[o];
-    if (t1 < 0) continue;
     const int t0 = tie_a[o];
     const int2 t23 = tie_cd.p[xi][o];
     const unsigned row = o / un;
@@ -1643,6 +1654,10 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   int* ctri = h->opt.keep_for_backward ? h->ctri : nullptr;
   // closest triangles of the coarser passes, read by the finer ones as seeds
   int* seed_ids = ctri ? ctri : tie_a;
+  // the near-tie list: nodes re-decided by the tie pass, in the adjoint's
+  // dL/dchi buffer, which is idle until a backward clears it
+  int* tie_list = ctri ? reinterpret_cast<int*>(h->dchi64) : nullptr;
+  if (ctri) WGEO_CUDA_TRY(cudaMemsetAsync(&h->dstate->ntie, 0, sizeof(unsigned), s));
   // closest-feature keys of the near-tie candidates: the bits above the
   // triangle ids (ids < cap <= 2^id_bits - 1; at least 8 key bits)
   int id_bits = 0;
@@ -1657,30 +1672,28 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
       if (h->opt.stage_timing == 2)
         sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, ctri,
-                                                            tie_a, tie_b, tie_cd, seed_ids, stride);
+                                                            tie_a, tie_b, tie_cd, tie_list, seed_ids, stride);
       else
         sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                              h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, ctri,
-                                                             tie_a, tie_b, tie_cd, seed_ids, stride);
+                                                             tie_a, tie_b, tie_cd, tie_list, seed_ids, stride);
     } else {
       if (h->opt.stage_timing == 2)
         sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                              h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
-                                                             nullptr, nullptr, tie_cd, seed_ids, stride);
+                                                             nullptr, nullptr, tie_cd, nullptr, seed_ids, stride);
       else
         sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                               h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
-                                                              nullptr, nullptr, tie_cd, seed_ids, stride);
+                                                              nullptr, nullptr, tie_cd, nullptr, seed_ids, stride);
     }
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStSDF, slot, s);
   if (ctri) {
     slot = stage_begin(h, kStSDFTie, s);
-    const int64_t N = (int64_t)res * res * res;
-    sdf_tie_kernel<<<grid_blocks(N, 256, 152 * 16), 256, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->tris,
-                                                                 h->tris_lo, tie_a, tie_b, tie_cd, h->phi, sdf_out,
-                                                                 ctri);
+    sdf_tie_kernel<<<152 * 8, 256, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, h->tris, h->tris_lo, tie_a, tie_b,
+                                           tie_cd, tie_list, h->phi, sdf_out, ctri);
     WGEO_LAUNCH_CHECK();
     stage_end(h, kStSDFTie, slot, s);
   }

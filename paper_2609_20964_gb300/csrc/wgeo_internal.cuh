@@ -59,6 +59,7 @@ struct DevState {
   unsigned long long sdf_cnt[4];   // octree nodes entered, leaves entered, lane point-triangle tests,
                                    // nodes re-decided in float-float
   unsigned nsliver;                // backward: nodes whose closest triangle is a sliver (FP64 pass)
+  unsigned ntie;                   // forward: nodes on the near-tie list (distance search)
 };
 
 struct Tri {          // one marching-cubes triangle: vertex xyz + global edge id in .w
