@@ -136,6 +136,7 @@ __global__ void reset_status_kernel(DevState* st) {
   st->sdf_cnt[1] = 0;
   st->sdf_cnt[2] = 0;
   st->sdf_cnt[3] = 0;
+  st->nmax_bits = 0;
 }
 
 void accumulate_slot(StageTimer& t, int slot) {
@@ -249,6 +250,11 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->max_points = max_points;
   h->opt = o;
   h->device = dev;
+  if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || h->num_sms < 1) {
+    cudaGetLastError();
+    delete h;
+    return WGEO_ERR_CUDA;
+  }
   if (cudaMalloc(&h->arena, L.total) != cudaSuccess) {
     cudaGetLastError();
     delete h;

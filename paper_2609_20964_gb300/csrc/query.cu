@@ -293,7 +293,8 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
   for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < N; it += gridDim.x * blockDim.x) {
     const unsigned o = LIST ? (unsigned)slivers[it] : it;
     const double gphi64 = dphi[o];
-    if (gphi64 == 0.0) continue;
+    // most nodes carry no seed: an integer test keeps them off the FP64 pipe
+    if ((__double_as_longlong(gphi64) << 1) == 0ll) continue;
     const int t = ctri[o];
     if (t < 0) continue;
     const float gphi = (float)gphi64;

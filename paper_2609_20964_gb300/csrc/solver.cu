@@ -64,10 +64,9 @@ __device__ __forceinline__ float rhs_hi(const float* b, int64_t t, float& lo) {
   return b[t];
 }
 __device__ __forceinline__ float rhs_hi(const double* b, int64_t t, float& lo) {
-  const double v = b[t];
-  const float hi = (float)v;
-  lo = (float)(v - (double)hi);
-  return hi;
+  const float2 p = split_f64(b[t]);
+  lo = p.y;
+  return p.x;
 }
 
 // ---------------------------------------------------------------- refinement pass
@@ -988,13 +987,17 @@ __global__ void scale64_kernel(double* __restrict__ v, int64_t N, double s) {
 __global__ void rhs_stats64_kernel(const double* __restrict__ b, int64_t N,
                                    double* __restrict__ partials) {
   __shared__ double red[32];
-  double s1 = 0.0, s2 = 0.0;
+  // per thread: the sum in float-float, the sum of squares in float (it only
+  // sets the tolerance's scale); FP64 from the block sums on
+  float2 f1 = make_float2(0.f, 0.f);
+  float f2 = 0.f;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const double v = b[t];
-    s1 += v;
-    s2 += v * v;
+    const float2 v = split_f64(b[t]);
+    f1 = ff_add_f(ff_add_f(f1, v.x), v.y);
+    f2 = fmaf(v.x, v.x, f2);
   }
+  double s1 = (double)f1.x + (double)f1.y, s2 = (double)f2;
   s1 = block_sum<kThreads>(s1, red);
   s2 = block_sum<kThreads>(s2, red);
   if (threadIdx.x == 0) {

@@ -271,23 +271,99 @@ __device__ __forceinline__ void brick_cube(int t, int& lx, int& ly, int& lz) {
   lz = ((t >> 2) & 1) | (((t >> 5) & 1) << 1);
 }
 
-// One CTA (64 threads) per 4^3 brick of cubes.
-__global__ void __launch_bounds__(64) mc_count_kernel(const float* __restrict__ chi, SurfParams g,
+// Inside bits of the nodes (chi < c, tested as chi < c_up), 32 per word
+// along x: word w of row (j, k) holds x = 32 w .. 32 w + 31 (bits past the
+// grid's edge clear), at bits[(k n + j) nw + w], nw = ceil(n / 32).  One warp
+// per word: coalesced reads of chi, one ballot.
+__global__ void __launch_bounds__(256) mc_bits_kernel(const float* __restrict__ chi, int n, int nw,
                                                       const DevState* __restrict__ st,
-                                                      int* __restrict__ brick_count) {
-  const int br = blockIdx.x;
-  const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
-  int lx, ly, lz;
-  brick_cube(threadIdx.x, lx, ly, lz);
-  const int i = bx * kBrick + lx, j = by * kBrick + ly, k = bz * kBrick + lz;
-  const int m = g.res - 1;
-  int cnt = 0;
-  if (i < m && j < m && k < m) cnt = c_mc_count[cube_code(chi, i, j, k, g.res, st->c_up)];
-  cnt = warp_sumi(cnt);
-  __shared__ int s[2];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) brick_count[br] = s[0] + s[1];
+                                                      unsigned* __restrict__ bits) {
+  // block (32, 8): warp y takes word blockIdx.x of row blockIdx.y * 8 + y
+  const int row = blockIdx.y * 8 + threadIdx.y;   // k n + j
+  if (row >= n * n) return;                       // whole warps
+  const int x = 32 * blockIdx.x + threadIdx.x;
+  const bool in = x < n && chi[(int64_t)row * n + x] < st->c_up;
+  const unsigned m = __ballot_sync(0xffffffffu, in);
+  if (threadIdx.x == 0) bits[row * nw + blockIdx.x] = m;
+}
+
+// Four 4^3 bricks of cubes per CTA (consecutive brick indices), 64 threads
+// (two warps) per brick.
+constexpr int kMcBricks = 4;
+
+// Triangles per 4^3 brick from the inside bits.  A thread takes 32 cubes
+// along x (one word) of one cube row: the cube's 8 corner bits are bit b and
+// bit b + 1 of the four node rows (j, k), (j + 1, k), (j, k + 1), (j + 1,
+// k + 1), so the cubes that the surface crosses (corners neither all inside
+// nor all outside) come out of eight word operations, and only those look up
+// their case.  The 16 threads of one word and brick row (j, k mod 4) are 16
+// consecutive lanes; their counts for the word's 8 bricks are summed by
+// shuffles (only where a cube is crossed) and written by the first.
+__global__ void mc_count_kernel(const unsigned* __restrict__ bits, SurfParams g, int nw,
+                                int* __restrict__ brick_count) {
+  const int n = g.res, m = n - 1, nb = g.nb;
+  const int cw = (m + 31) / 32;              // cube words per row
+  const int64_t groups = (int64_t)cw * nb * nb;
+  const int lane = threadIdx.x & 31, sub = lane & 15;
+  // warp-uniform trip count (two groups per warp): every lane reaches the shuffles
+  for (int64_t wb = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; 2 * wb < groups;
+       wb += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t gi = 2 * wb + (lane >> 4);   // (w, by, bz) of this half-warp
+    const bool ok = gi < groups;
+    const int w = ok ? (int)(gi % cw) : 0;
+    const int by = ok ? (int)((gi / cw) % nb) : 0, bz = ok ? (int)(gi / ((int64_t)cw * nb)) : 0;
+    const int j = 4 * by + (sub & 3), k = 4 * bz + (sub >> 2);
+    // triangle counts of the word's 8 bricks, 16 bits each (at most 320 per
+    // brick after the half-warp sum): bricks 0-3 in c03, 4-7 in c47
+    unsigned long long c03 = 0ull, c47 = 0ull;
+    bool any = false;
+    if (ok && j < m && k < m) {
+      unsigned A[4], B[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int64_t row = (int64_t)(k + (r >> 1)) * n + (j + (r & 1));
+        const unsigned lo = bits[row * nw + w];
+        const unsigned hi = (w + 1 < nw) ? bits[row * nw + w + 1] : 0u;
+        A[r] = lo;
+        B[r] = (lo >> 1) | (hi << 31);
+      }
+      const unsigned all_in = A[0] & A[1] & A[2] & A[3] & B[0] & B[1] & B[2] & B[3];
+      const unsigned all_out = ~(A[0] | A[1] | A[2] | A[3] | B[0] | B[1] | B[2] | B[3]);
+      const int xv = m - 32 * w;             // cubes of this word inside the grid
+      const unsigned valid = xv >= 32 ? 0xffffffffu : ((1u << xv) - 1u);
+      unsigned mixed = ~(all_in | all_out) & valid;
+      any = mixed != 0u;
+      while (mixed) {
+        const int b = __ffs(mixed) - 1;
+        mixed &= mixed - 1u;
+        // corner q = (x offset q & 1, y offset q >> 1 & 1, z offset q >> 2)
+        int code = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const unsigned word = (q & 1) ? B[q >> 1] : A[q >> 1];
+          code |= (int)((word >> b) & 1u) << q;
+        }
+        const unsigned long long add = (unsigned long long)c_mc_count[code] << (16 * ((b >> 2) & 3));
+        if (b < 16) c03 += add; else c47 += add;
+      }
+    }
+    // sum over the 16 lanes of the half-warp (both halves take part)
+    if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        c03 += __shfl_xor_sync(0xffffffffu, c03, o);
+        c47 += __shfl_xor_sync(0xffffffffu, c47, o);
+      }
+    }
+    if (ok && sub == 0) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int bx = 8 * w + q;
+        const unsigned long long v = q < 4 ? c03 : c47;
+        if (bx < nb) brick_count[((int64_t)bz * nb + by) * nb + bx] = (int)((v >> (16 * (q & 3))) & 0xffffull);
+      }
+    }
+  }
 }
 
 __global__ void mc_total_kernel(const int* __restrict__ brick_off, int nbricks, int64_t cap,
@@ -312,6 +388,26 @@ __device__ __forceinline__ void edge_lower_offset(int e, int& ox, int& oy, int& 
   oz = o[2];
 }
 
+// Edges of a brick's cubes, by the local coordinates (0..kBrick) of their
+// lower end node: along the edge's axis 0..kBrick-1, across it 0..kBrick.
+constexpr int kEdgesPerAxis = kBrick * (kBrick + 1) * (kBrick + 1);
+constexpr int kBrickEdges = 3 * kEdgesPerAxis;
+constexpr int div_up_c(int a, int b) { return (a + b - 1) / b; }
+__device__ __forceinline__ int brick_edge_slot(int ax, int ex, int ey, int ez) {
+  const int u = ax == 0 ? ex : (ax == 1 ? ey : ez);   // along the axis
+  const int v = ax == 0 ? ey : ex;                     // the first other axis
+  const int w = ax == 2 ? ey : ez;                     // the second
+  return ax * kEdgesPerAxis + (w * (kBrick + 1) + v) * kBrick + u;
+}
+__device__ __forceinline__ void brick_edge_of_slot(int sl, int& ax, int& ex, int& ey, int& ez) {
+  ax = sl / kEdgesPerAxis;
+  const int r = sl - ax * kEdgesPerAxis;
+  const int u = r % kBrick, v = (r / kBrick) % (kBrick + 1), w = r / (kBrick * (kBrick + 1));
+  ex = ax == 0 ? u : v;
+  ey = ax == 1 ? u : (ax == 0 ? v : w);
+  ez = ax == 2 ? u : w;
+}
+
 // Emits each brick's triangles contiguously (Morton cube order) and the
 // triangle offset of each of its 8 sub-bricks (octree leaves).  A vertex is
 // placed in FP64 from the cube edge's two indicator values (Eq. 28); with
@@ -321,53 +417,88 @@ __device__ __forceinline__ void edge_lower_offset(int e, int& ox, int& oy, int& 
 // vertices rounded to float32; tris_lo (may be null) their residuals
 // (double vertex - float vertex, rounded to float), so that hi + lo keeps
 // about 48 bits: near-tie decisions and the adjoint's closest points use it.
-__global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ chi, ChiFF chiff, SurfParams g,
-                                                     const DevState* __restrict__ st,
-                                                     const int* __restrict__ brick_off, int64_t cap,
-                                                     Tri* __restrict__ tris, Tri* __restrict__ tris_lo,
-                                                     int* __restrict__ leaf_off) {
-  const int br = blockIdx.x;
-  const int base = brick_off[br];
-  if (brick_off[br + 1] == base) {
-    if (threadIdx.x < 8) leaf_off[8 * (int64_t)br + threadIdx.x] = base;
-    return;
-  }
-  const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
-  int lx, ly, lz;
-  brick_cube(threadIdx.x, lx, ly, lz);
-  const int i = bx * kBrick + lx, j = by * kBrick + ly, k = bz * kBrick + lz;
+__global__ void __launch_bounds__(64 * kMcBricks) mc_emit_kernel(const float* __restrict__ chi, ChiFF chiff,
+                                                                 SurfParams g, const DevState* __restrict__ st,
+                                                                 const int* __restrict__ brick_off, int64_t cap,
+                                                                 Tri* __restrict__ tris, Tri* __restrict__ tris_lo,
+                                                                 int* __restrict__ leaf_off) {
+  const int nbr = g.nb * g.nb * g.nb;
+  const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int br = blockIdx.x * kMcBricks + grp;
+  // a brick without triangles only writes its leaf offsets (every thread
+  // still reaches the barrier below)
+  const int base = br < nbr ? brick_off[br] : 0;
+  const bool live = br < nbr && brick_off[br + 1] != base;
+  if (br < nbr && !live && t < 8) leaf_off[8 * (int64_t)br + t] = base;
+  int i = 0, j = 0, k = 0;
   const int n = g.res, m = n - 1;
-  const double c = st->c;
   int code = 0, cnt = 0;
-  if (i < m && j < m && k < m) {
-    code = cube_code(chi, i, j, k, n, st->c_up);
-    cnt = c_mc_count[code];
+  if (live) {
+    const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
+    int lx, ly, lz;
+    brick_cube(t, lx, ly, lz);
+    i = bx * kBrick + lx;
+    j = by * kBrick + ly;
+    k = bz * kBrick + lz;
+    if (i < m && j < m && k < m) {
+      code = cube_code(chi, i, j, k, n, st->c_up);
+      cnt = c_mc_count[code];
+    }
   }
+  const double c = st->c;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
+    const int tt = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += tt;
   }
-  __shared__ int wt[2];
+  __shared__ int wt[2 * kMcBricks];
+  // the brick's crossing edges (listed first, so that the FP64 placement
+  // runs on full warps), and its vertices, one per crossing edge (hi with
+  // the edge id in .w; lo)
+  __shared__ short s_cross[kMcBricks][kBrickEdges];
+  __shared__ int s_ncross[kMcBricks];
+  __shared__ float4 s_vh[kMcBricks][kBrickEdges], s_vl[kMcBricks][kBrickEdges];
   if (lane == 31) wt[w] = incl;
+  if (t == 0) s_ncross[grp] = 0;
   __syncthreads();
-  const int excl = incl - cnt + (w ? wt[0] : 0);
-  if ((threadIdx.x & 7) == 0) leaf_off[8 * (int64_t)br + (threadIdx.x >> 3)] = base + excl;
-  const float2* __restrict__ xff = chiff.p[0] ? chiff.p[st->fwd.xidx] : nullptr;
-  for (int q = 0; q < cnt; ++q) {
-    const int64_t idx = (int64_t)base + excl + q;
-    if (idx >= cap) break;
-    Tri tr, tl;
-    float4* out[3] = {&tr.a, &tr.b, &tr.c};
-    float4* outl[3] = {&tl.a, &tl.b, &tl.c};
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      const int e = c_mc_tris[code][q][v];
-      int ox, oy, oz, ax;
-      edge_lower_offset(e, ox, oy, oz, ax);
-      const int pi = i + ox, pj = j + oy, pk = k + oz;
+  const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
+  if (live) {
+    const float c_up = st->c_up;
+    for (int r = 0; r < div_up_c(kBrickEdges, 64); ++r) {   // the same trip count in both warps
+      const int e = t + 64 * r;
+      bool cross = false;
+      if (e < kBrickEdges) {
+        int ax, ex, ey, ez;
+        brick_edge_of_slot(e, ax, ex, ey, ez);
+        const int pi = bx * kBrick + ex, pj = by * kBrick + ey, pk = bz * kBrick + ez;
+        if (pi + (ax == 0) < n && pj + (ax == 1) < n && pk + (ax == 2) < n) {
+          const int64_t p = lin3(pi, pj, pk, n);
+          const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+          // crossing exactly when the two corner bits of the cube codes differ
+          cross = (chi[p] < c_up) != (chi[p + stride] < c_up);
+        }
+      }
+      const unsigned mk = __ballot_sync(0xffffffffu, cross);
+      if (mk) {
+        const int leader = __ffs(mk) - 1;
+        int at = 0;
+        if (lane == leader) at = atomicAdd(&s_ncross[grp], __popc(mk));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (cross) s_cross[grp][at + __popc(mk & ((1u << lane) - 1u))] = (short)e;
+      }
+    }
+  }
+  __syncthreads();
+  if (live) {
+    const float2* __restrict__ xff = chiff.p[0] ? chiff.p[st->fwd.xidx] : nullptr;
+    const int nc = s_ncross[grp];
+    for (int ci = t; ci < nc; ci += 64) {
+      const int e = s_cross[grp][ci];
+      int ax, ex, ey, ez;
+      brick_edge_of_slot(e, ax, ex, ey, ez);
+      const int pi = bx * kBrick + ex, pj = by * kBrick + ey, pk = bz * kBrick + ez;
       const int64_t p = lin3(pi, pj, pk, n);
       const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
       double c1, c2;
@@ -380,17 +511,33 @@ __global__ void __launch_bounds__(64) mc_emit_kernel(const float* __restrict__ c
         c2 = (double)chi[p + stride];
       }
       const double eta = (c - c1) / (c2 - c1);
-      double pos[3] = {g.lo[0] + (pi + 0.5) * g.h, g.lo[1] + (pj + 0.5) * g.h,
-                       g.lo[2] + (pk + 0.5) * g.h};
-      pos[ax] += eta * g.h;
+      // node centre, moved by eta h along the edge's axis
+      double px = fma(pi + 0.5, g.h, g.lo[0]), py = fma(pj + 0.5, g.h, g.lo[1]), pz = fma(pk + 0.5, g.h, g.lo[2]);
+      if (ax == 0) px = fma(eta, g.h, px);
+      else if (ax == 1) py = fma(eta, g.h, py);
+      else pz = fma(eta, g.h, pz);
       const int gid = (int)(3 * p + ax);
-      const float hx = (float)pos[0], hy = (float)pos[1], hz = (float)pos[2];
-      *out[v] = make_float4(hx, hy, hz, __int_as_float(gid));
-      *outl[v] = make_float4((float)(pos[0] - (double)hx), (float)(pos[1] - (double)hy),
-                             (float)(pos[2] - (double)hz), 0.f);
+      const float hx = (float)px, hy = (float)py, hz = (float)pz;
+      s_vh[grp][e] = make_float4(hx, hy, hz, __int_as_float(gid));
+      s_vl[grp][e] = make_float4((float)(px - (double)hx), (float)(py - (double)hy), (float)(pz - (double)hz), 0.f);
     }
-    tris[idx] = tr;
-    if (tris_lo) tris_lo[idx] = tl;
+  }
+  __syncthreads();
+  if (!live) return;
+  const int excl = incl - cnt + ((w & 1) ? wt[w - 1] : 0);
+  if ((t & 7) == 0) leaf_off[8 * (int64_t)br + (t >> 3)] = base + excl;
+  const int li = i - bx * kBrick, lj = j - by * kBrick, lk = k - bz * kBrick;
+  for (int q = 0; q < cnt; ++q) {
+    const int64_t idx = (int64_t)base + excl + q;
+    if (idx >= cap) break;
+    auto slot = [&](int v) {
+      int ox, oy, oz, ax;
+      edge_lower_offset(c_mc_tris[code][q][v], ox, oy, oz, ax);
+      return brick_edge_slot(ax, li + ox, lj + oy, lk + oz);
+    };
+    const int s0 = slot(0), s1 = slot(1), s2 = slot(2);
+    tris[idx] = Tri{s_vh[grp][s0], s_vh[grp][s1], s_vh[grp][s2]};
+    if (tris_lo) tris_lo[idx] = Tri{s_vl[grp][s0], s_vl[grp][s1], s_vl[grp][s2]};
   }
 }
 
@@ -453,22 +600,53 @@ __device__ __forceinline__ void write_search_record(const Tri& tr, const Tri* lo
                        det > 0.f ? 1.f / det : 0.f);
 }
 
-__global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const Tri* __restrict__ tris_lo,
-                                 const int* __restrict__ leaf_off, int nb, int64_t cap, float4* __restrict__ pyr,
-                                 float4* __restrict__ tris_s) {
+// Leaf pucks, pass 1 (every leaf): an empty leaf gets the empty puck; a
+// leaf with triangles goes to the list of live leaves (one atomic per warp),
+// which the fitting passes then take with full warps.
+__global__ void puck_leaf_scan_kernel(const int* __restrict__ leaf_off, int nb, int64_t cap,
+                                      float4* __restrict__ pyr, int* __restrict__ live, DevState* __restrict__ st) {
   const int nl = 2 * nb;
   const int64_t nleaf = (int64_t)nl * nl * nl;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count: every lane reaches the ballot
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nleaf; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = base + threadIdx.x;
+    bool full = false;
+    if (t < nleaf) {
+      const int lx = (int)(t % nl), ly = (int)((t / nl) % nl), lz = (int)(t / ((int64_t)nl * nl));
+      const int li = leaf_index(lx, ly, lz, nb);
+      full = min((int64_t)leaf_off[li + 1], cap) > (int64_t)leaf_off[li];
+      if (!full) {
+        pyr[2 * t] = make_float4(0.f, 0.f, 0.f, -1.f);
+        pyr[2 * t + 1] = make_float4(0.f, 0.f, 1.f, 0.f);
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, full);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned at = 0;
+      if (lane == leader) at = atomicAdd(&st->nleaf_live, (unsigned)__popc(m));
+      at = __shfl_sync(0xffffffffu, at, leader);
+      if (full) live[at + __popc(m & ((1u << lane) - 1u))] = (int)t;
+    }
+  }
+}
+
+// Leaf pucks, pass 2 (live leaves): the triangles' search records, then the
+// leaf's puck fitted to its vertices.
+__global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const Tri* __restrict__ tris_lo,
+                                 const int* __restrict__ leaf_off, int nb, int64_t cap,
+                                 const int* __restrict__ live, const DevState* __restrict__ st,
+                                 float4* __restrict__ pyr, float4* __restrict__ tris_s) {
+  const int nl = 2 * nb;
+  const int64_t nlive = st->nleaf_live;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nlive;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = live[it];
     const int lx = (int)(t % nl), ly = (int)((t / nl) % nl), lz = (int)(t / ((int64_t)nl * nl));
     const int li = leaf_index(lx, ly, lz, nb);
     const int64_t s0 = leaf_off[li];
     const int64_t s1 = min((int64_t)leaf_off[li + 1], cap);
-    if (s1 <= s0) {
-      pyr[2 * t] = make_float4(0.f, 0.f, 0.f, -1.f);
-      pyr[2 * t + 1] = make_float4(0.f, 0.f, 1.f, 0.f);
-      continue;
-    }
     float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
     for (int64_t q = s0; q < s1; ++q) {
       const Tri tr = tris[q];
@@ -590,14 +768,17 @@ __global__ void puck_sums_up_kernel(float4* __restrict__ sums, unsigned* __restr
 }
 
 __global__ void puck_rth_kernel(const Tri* __restrict__ tris, const int* __restrict__ leaf_off, int nb, int64_t cap,
-                                PyrInfo pi, const float4* __restrict__ sums, unsigned* __restrict__ rth) {
+                                PyrInfo pi, const int* __restrict__ live, const DevState* __restrict__ st,
+                                const float4* __restrict__ sums, unsigned* __restrict__ rth) {
   const int dl = pi.dim[0];
-  const int64_t nleaf = (int64_t)dl * dl * dl;
+  const int64_t nlive = st->nleaf_live;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // warp-uniform trip count: every lane reaches the warp-wide reductions
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nleaf; base += stride) {
-    const int64_t t = base + threadIdx.x;
-    const bool in = t < nleaf;
+  // the live leaves (list order keeps a warp's leaves together); warp-uniform
+  // trip count: every lane reaches the warp-wide reductions
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nlive; base += stride) {
+    const int64_t it = base + threadIdx.x;
+    const bool in = it < nlive;
+    const int64_t t = in ? live[it] : 0;
     const int lx = in ? (int)(t % dl) : 0, ly = in ? (int)((t / dl) % dl) : 0,
               lz = in ? (int)(t / ((int64_t)dl * dl)) : 0;
     int64_t q0 = 0, q1 = 0;
@@ -606,7 +787,6 @@ __global__ void puck_rth_kernel(const Tri* __restrict__ tris, const int* __restr
       q0 = leaf_off[li];
       q1 = min((int64_t)leaf_off[li + 1], cap);
     }
-    if (!__any_sync(0xffffffffu, q1 > q0)) continue;
 #pragma unroll 1
     for (int l = 1; l < pi.nlev; ++l) {
       const int d = pi.dim[l];
@@ -1020,8 +1200,11 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
     // children, one per lane (lanes 0-7): kept when their bound from the
     // warp's box (the puck's distance to the box centre less the box's
     // half-diagonal, a lower bound for every node in it) beats the largest
-    // lane cut; pushed far-to-near by that bound.  Each lane's own bound is
-    // checked when a child is popped, so a child is bounded per lane once.
+    // lane cut; pushed far-to-near by that bound in the unseeded pass, in
+    // child order in the seeded ones (their cuts start near their final
+    // values, so the order saves little and the ranking costs 8 shuffles).
+    // Each lane's own bound is checked when a child is popped, so a child is
+    // bounded per lane once.
     const unsigned cmask = __float_as_uint(An.w) & 0xffu;
     const float maxcut = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(cut, 0.f))));
     bool keep = false;
@@ -1038,10 +1221,14 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
     const unsigned kept = __ballot_sync(0xffffffffu, keep);
     const int nc = __popc(kept);
     int rank = 0;   // kept children nearer than this one (ties by lane)
+    if (seeded) {
+      rank = nc - 1 - __popc(kept & ((1u << lane) - 1u));
+    } else {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float kq = __shfl_sync(0xffffffffu, key, q);
-      if (((kept >> q) & 1u) && (kq < key || (kq == key && q < lane))) ++rank;
+      for (int q = 0; q < 8; ++q) {
+        const float kq = __shfl_sync(0xffffffffu, key, q);
+        if (((kept >> q) & 1u) && (kq < key || (kq == key && q < lane))) ++rank;
+      }
     }
     const int slot = sp + nc - 1 - rank;
     if (keep && slot < kStack) stk[slot] = ent;
@@ -1602,21 +1789,39 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   g.nb = div_up(res - 1, kBrick);
   const int nbricks = g.nb * g.nb * g.nb;
   int slot = stage_begin(h, kStMC, s);
-  mc_count_kernel<<<nbricks, 64, 0, s>>>(h->chi32, g, h->dstate, h->brick_count);
-  WGEO_LAUNCH_CHECK();
+  {
+    // inside bits of the nodes (in the solver's idle correction buffer), then
+    // the triangles per brick from them
+    const int nw = div_up(res, 32);
+    unsigned* bits = reinterpret_cast<unsigned*>(h->e32);
+    mc_bits_kernel<<<dim3(nw, div_up((int64_t)res * res, 8)), dim3(32, 8), 0, s>>>(h->chi32, res, nw, h->dstate,
+                                                                                    bits);
+    WGEO_LAUNCH_CHECK();
+    const int64_t groups = (int64_t)div_up(res - 1, 32) * g.nb * g.nb;
+    mc_count_kernel<<<grid_blocks(16 * groups, 256, h->num_sms * 16), 256, 0, s>>>(bits, g, nw, h->brick_count);
+    WGEO_LAUNCH_CHECK();
+  }
   int rc = exclusive_scan(h->brick_count, h->brick_off, nbricks, h->scan_tmp, s);
   if (rc) return rc;
   mc_total_kernel<<<1, 1, 0, s>>>(h->brick_off, nbricks, h->mesh_cap, h->leaf_off, h->dstate);
   WGEO_LAUNCH_CHECK();
   // vertices from the refined float-float indicator (MIXED precision) and
   // their low parts for the near-tie decisions and the adjoint (when kept)
-  mc_emit_kernel<<<nbricks, 64, 0, s>>>(h->chi32, chiff_of(h), g, h->dstate, h->brick_off, h->mesh_cap, h->tris,
-                                        h->tris_lo, h->leaf_off);
+  mc_emit_kernel<<<div_up(nbricks, kMcBricks), 64 * kMcBricks, 0, s>>>(h->chi32, chiff_of(h), g, h->dstate,
+                                                                         h->brick_off, h->mesh_cap, h->tris,
+                                                                         h->tris_lo, h->leaf_off);
   WGEO_LAUNCH_CHECK();
   const PyrInfo pi = pyramid_info(2 * g.nb);
   const int64_t nleaf = (int64_t)pi.dim[0] * pi.dim[0] * pi.dim[0];
-  puck_leaf_kernel<<<grid_blocks(nleaf, 256, 152 * 16), 256, 0, s>>>(h->tris, h->tris_lo, h->leaf_off, g.nb,
-                                                                      h->mesh_cap, h->pyramid, h->tris_s);
+  // the live leaves, listed in the correction buffer (its inside bits are consumed)
+  int* live = reinterpret_cast<int*>(h->e32);
+  WGEO_CUDA_TRY(cudaMemsetAsync(&h->dstate->nleaf_live, 0, sizeof(unsigned), s));
+  puck_leaf_scan_kernel<<<grid_blocks(nleaf, 256, h->num_sms * 16), 256, 0, s>>>(h->leaf_off, g.nb, h->mesh_cap,
+                                                                                 h->pyramid, live, h->dstate);
+  WGEO_LAUNCH_CHECK();
+  const int live_grid = grid_blocks(nleaf, 256, h->num_sms * 8);
+  puck_leaf_kernel<<<live_grid, 256, 0, s>>>(h->tris, h->tris_lo, h->leaf_off, g.nb, h->mesh_cap, live, h->dstate,
+                                             h->pyramid, h->tris_s);
   WGEO_LAUNCH_CHECK();
   {
     // levels >= 1: sums per brick, sums up the tree, vertex maxima, pucks
@@ -1630,8 +1835,8 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
           h->pyr_sums, h->pyr_rth, pi.off[l - 1] - pi.off[1], pi.dim[l - 1], pi.off[l] - pi.off[1], pi.dim[l]);
       WGEO_LAUNCH_CHECK();
     }
-    puck_rth_kernel<<<grid_blocks(nleaf, 256, 152 * 16), 256, 0, s>>>(h->tris, h->leaf_off, g.nb, h->mesh_cap, pi,
-                                                                      h->pyr_sums, h->pyr_rth);
+    puck_rth_kernel<<<live_grid, 256, 0, s>>>(h->tris, h->leaf_off, g.nb, h->mesh_cap, pi, live, h->dstate,
+                                              h->pyr_sums, h->pyr_rth);
     WGEO_LAUNCH_CHECK();
     const int64_t naux = pi.off[pi.nlev - 1] + 1 - pi.off[1];
     puck_finalize_kernel<<<grid_blocks(naux, 256, 152 * 16), 256, 0, s>>>(h->pyramid, h->pyr_sums, h->pyr_rth,

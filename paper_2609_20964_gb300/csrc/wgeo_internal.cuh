@@ -60,6 +60,10 @@ struct DevState {
                                    // nodes re-decided in float-float
   unsigned nsliver;                // backward: nodes whose closest triangle is a sliver (FP64 pass)
   unsigned ntie;                   // forward: nodes on the near-tie list (distance search)
+  unsigned splat_tiles;            // forward: splat tiles with a point in reach (the active list)
+  unsigned splat_next;             // forward: next active tile to be taken by a splat CTA
+  unsigned nleaf_live;             // forward: octree leaves holding triangles (the live list)
+  unsigned nmax_bits;              // forward: largest |normal component| of the points (float bits)
 };
 
 struct Tri {          // one marching-cubes triangle: vertex xyz + global edge id in .w
@@ -151,6 +155,27 @@ __device__ __forceinline__ float2 ff_sub(float2 a, float2 b) { return ff_add(a, 
 __device__ __forceinline__ float2 ff_add_f(float2 a, float b) {
   const float2 s = two_sum(a.x, b);
   return fast_two_sum(s.x, __fadd_rn(s.y, a.y));
+}
+
+// A double as hi + lo floats without the FP64 pipe (integer and FP32 work
+// only; the FP64 pipe of this GPU is a small fraction of its FP32 rate):
+// hi keeps the top 24 significand bits (truncated), lo the other 29 rounded
+// to float, so hi + lo equals v to 2^-47 relative, as a rounded pair does.  Zero and
+// FP64 subnormals give (signed zero, 0); magnitudes outside [2^-74, 2^127)
+// take the FP64 conversions.
+__device__ __forceinline__ float2 split_f64(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hw = (unsigned)(u >> 32);
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  if (e == 0) return make_float2(__uint_as_float(sign), 0.f);
+  if (e < 949 || e > 1150) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  }
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7fffffull));
+  const float lo = __uint2float_rn((unsigned)(u & 0x1fffffffull)) * __uint_as_float((unsigned)(e - 948) << 23);
+  return make_float2(hi, sign ? -lo : lo);
 }
 
 __device__ __forceinline__ float3 f3(const float4 v) { return make_float3(v.x, v.y, v.z); }
@@ -313,6 +338,7 @@ struct wgeo_handle {
   int64_t max_points = 0;
   wgeo_options opt{};
   int device = 0;
+  int num_sms = 1;   // the device's multiprocessor count (grids of persistent kernels)
 
   // arena
   char* arena = nullptr;

@@ -128,6 +128,34 @@ def test_forward_parity(W, name):
     rec.close()
 
 
+@pytest.mark.parametrize("scale", [1.0, 37.0])
+def test_splat_dense_and_sparse_tiles(W, scale):
+    # a sparse sphere plus a dense cap: tiles with short point lists sum in two
+    # 32-bit words, the dense ones (lists flushed) in 64-bit words; with
+    # normals scaled by 37 the two-word rule admits lists of at most 824
+    # points.  b must match the oracle either way (the integer sums are exact)
+    rng = np.random.default_rng(31)
+    p0, n0 = synth.sphere_cloud(400, seed=32)
+    d = rng.standard_normal((6000, 3))
+    d[:, 2] = np.abs(d[:, 2]) * 20.0          # directions near the +z pole
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    p1 = (0.5 + 0.3 * d).astype(np.float32)
+    p = np.concatenate([p0, p1]).astype(np.float32)
+    n = (np.concatenate([n0, d.astype(np.float32)]) * scale).astype(np.float32)
+    res = 40
+    ref = OP.forward_to_mesh(p, n, BBOX, res)
+    rec = W(res, len(p))
+    rec.reconstruct(_t(p), _t(n), BBOX, res)
+    b = rec.field("b").cpu().numpy().astype(np.float64)
+    assert rec.info()["status"] == 0
+    assert np.abs(b - ref.b).max() <= 2e-6 * np.abs(ref.b).max() + 1e-7
+    # the dense cap does put more points in one tile than one list holds
+    tiles = (np.asarray(rec.bins().cpu().numpy()) // 8)
+    _, counts = np.unique(tiles, axis=0, return_counts=True)
+    assert counts.max() > 3584
+    rec.close()
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_query_and_backward_parity(W, name):
     p, n, res = CASES[name]
