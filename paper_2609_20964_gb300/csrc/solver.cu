@@ -1136,9 +1136,12 @@ __global__ void dct_tables_kernel(int n, float2* __restrict__ t1, float2* __rest
       sk[q] = (float)(4.0 * sn * sn);
     }
     if (q < 160) {
-      const int hh = 1 << a;                        // stage a combines pairs of hh-point DFTs
+      // stage a combines pairs of hh-point DFTs; only the upper lane of a
+      // pair (j & hh) multiplies, the lower one holds 1 so that both run the
+      // same instructions
+      const int hh = 1 << a;
       sincospi((double)(j & (hh - 1)) / hh, &sn, &cs);
-      w32[q] = make_float2((float)cs, (float)-sn);
+      w32[q] = (j & hh) ? make_float2((float)cs, (float)-sn) : make_float2(1.f, 0.f);
     }
     if (q < R) {
       sincospi(2.0 * q / R, &sn, &cs);
@@ -1200,12 +1203,13 @@ __device__ __forceinline__ void fft_warp_dif(float2 (&v)[R], const float2* t1, c
 #pragma unroll
   for (int st = 4; st >= 0; --st) {
     const int h = 1 << st;
-    const bool up = lane & h;
+    // upper lane: (p - v) w; lower lane: (v + p) 1 (its table entry)
+    const float sg = (lane & h) ? -1.f : 1.f;
     const float2 w = w32[st * 32 + lane];
 #pragma unroll
     for (int a = 0; a < R; ++a) {
       const float2 p = shfl_xor2(v[a], h);
-      v[a] = up ? cmul(csub(p, v[a]), w) : cadd(v[a], p);
+      v[a] = cmul(make_float2(fmaf(sg, v[a].x, p.x), fmaf(sg, v[a].y, p.y)), w);
     }
   }
 }
@@ -1218,13 +1222,14 @@ __device__ __forceinline__ void fft_warp_dit(float2 (&v)[R], const float2* t1, c
 #pragma unroll
   for (int st = 0; st <= 4; ++st) {
     const int h = 1 << st;
-    const bool up = lane & h;
+    // upper lane: p - v w; lower lane: v 1 + p (its table entry is 1)
+    const float sg = (lane & h) ? -1.f : 1.f;
     const float2 w = w32[st * 32 + lane];
 #pragma unroll
     for (int a = 0; a < R; ++a) {
-      const float2 m = up ? cmul(v[a], w) : v[a];
+      const float2 m = cmul(v[a], w);
       const float2 p = shfl_xor2(m, h);
-      v[a] = up ? csub(p, m) : cadd(m, p);
+      v[a] = make_float2(fmaf(sg, m.x, p.x), fmaf(sg, m.y, p.y));
     }
   }
 #pragma unroll

@@ -1102,8 +1102,13 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
       for (int q = 0; q < NC; ++q)
         if (ct[q] == t) return;
     }
-    cd[at] = d2;
-    ct[at] = e;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {   // static indices: the list stays in registers
+      if (q == at) {
+        cd[q] = d2;
+        ct[q] = e;
+      }
+    }
 #pragma unroll
     for (int q = NC - 1; q > 0; --q) {
       if (q <= at && cd[q] < cd[q - 1]) {
