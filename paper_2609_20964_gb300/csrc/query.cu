@@ -28,6 +28,8 @@ struct QParams {
   double lo[3];
   double h;
   int res;
+  float lo_hi[3], lo_lo[3];   // lo and 1 / h as float-float pairs (trilinear cells off the FP64 pipe)
+  float ih_hi, ih_lo;
 };
 
 __device__ __forceinline__ int64_t lin3(int i, int j, int k, int n) {
@@ -35,19 +37,16 @@ __device__ __forceinline__ int64_t lin3(int i, int j, int k, int n) {
 }
 
 // Trilinear cell and weights of a query; dw[c][a] = d w_c / d q_a (0 on clamped axes).
+// The node coordinate is float-float (node_coord_ff): no FP64 arithmetic,
+// which this GPU runs at a small fraction of its FP32 rate.
 __device__ __forceinline__ void trilinear(const float* q, const QParams& g, int i0[3], float w[8],
                                           float dw[8][3]) {
   float t[3], dt[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double u = ((double)q[a] - g.lo[a]) / g.h - 0.5;
-    const bool cl = (u < 0.0) || (u > (double)(g.res - 1));
-    u = fmin(fmax(u, 0.0), (double)(g.res - 1));
-    int f = (int)floor(u);
-    f = min(f, g.res - 2);
-    i0[a] = f;
-    t[a] = (float)(u - f);
-    dt[a] = cl ? 0.f : (float)(1.0 / g.h);
+    const float2 u = node_coord_ff(q[a], g.lo_hi[a], g.lo_lo[a], g.ih_hi, g.ih_lo);
+    const bool cl = node_cell_ff(u, g.res, i0[a], t[a]);
+    dt[a] = cl ? 0.f : g.ih_hi;
   }
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -141,6 +140,10 @@ __global__ void query_kernel(const float* __restrict__ q, int64_t m, QParams g,
   }
 }
 
+// DN: the loss has a normal term (dnq != null).  Without it the kernel is the
+// trilinear part alone, at a fraction of the registers of the normal
+// adjoint's corner arrays.
+template <bool DN>
 __global__ void query_adjoint_kernel(const float* __restrict__ q, int64_t m, QParams g,
                                      const float* __restrict__ phi, const float* __restrict__ dsq,
                                      const float* __restrict__ dnq, double* __restrict__ dphi,
@@ -165,7 +168,7 @@ __global__ void query_adjoint_kernel(const float* __restrict__ q, int64_t m, QPa
         for (int a = 0; a < 3; ++a) dqa[a] += dw[c][a] * pv * gs;
       }
     }
-    if (dnq) {
+    if (DN && dnq) {
       // recompute the corner normals and the interpolated m
       float nc[8][3], gm[8];
       float mv[3] = {0.f, 0.f, 0.f};
@@ -627,6 +630,7 @@ __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4
       }
     }
     float S = 0.f, dS[3] = {0.f, 0.f, 0.f};
+#pragma unroll
     for (int q = 0; q < 27; ++q) {
       const int dx = q % 3, dy = (q / 3) % 3, dz = q / 9;
       if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
@@ -641,6 +645,7 @@ __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4
     }
     const float invS = 1.f / S;
     float gdn[3] = {0.f, 0.f, 0.f}, gdx[3] = {0.f, 0.f, 0.f};
+#pragma unroll
     for (int q = 0; q < 27; ++q) {
       const int dx = q % 3, dy = (q / 3) % 3, dz = q / 9;
       if (!(ing[0][dx] && ing[1][dy] && ing[2][dz])) continue;
@@ -678,9 +683,16 @@ __global__ void splat_adjoint_kernel(const int* __restrict__ pcell, const float4
 
 QParams qparams(const wgeo_handle* h) {
   QParams g;
-  for (int a = 0; a < 3; ++a) g.lo[a] = h->lo[a];
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = h->lo[a];
+    g.lo_hi[a] = (float)h->lo[a];
+    g.lo_lo[a] = (float)(h->lo[a] - (double)g.lo_hi[a]);
+  }
   g.h = h->h;
   g.res = h->res;
+  const double ih = 1.0 / h->h;
+  g.ih_hi = (float)ih;
+  g.ih_lo = (float)(ih - (double)g.ih_hi);
   return g;
 }
 
@@ -770,8 +782,12 @@ int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_
   int rc = backward_grid_seeds(h, d_sdf_grid, d_nrm_grid, s);
   if (rc) return rc;
   if (m > 0 && q && (d_sdf_q || d_nrm_q || d_q)) {
-    query_adjoint_kernel<<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, qparams(h), h->phi, d_sdf_q, d_nrm_q,
-                                                                       h->dphi64, d_q);
+    if (d_nrm_q)
+      query_adjoint_kernel<true><<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, qparams(h), h->phi, d_sdf_q,
+                                                                               d_nrm_q, h->dphi64, d_q);
+    else
+      query_adjoint_kernel<false><<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, qparams(h), h->phi, d_sdf_q,
+                                                                                nullptr, h->dphi64, d_q);
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStBwdSeed, slot, s);

@@ -105,9 +105,12 @@ __global__ void __launch_bounds__(kSX * kSY, 4) update_residual_kernel(PairFF xp
   if (i0 < n && j < n) {
     const bool has1 = i0 + 1 < n;
     const int64_t nn = (int64_t)n * n;
+    // a cold start reads x as 0: with no correction x_new = 0 and r = b; with
+    // one (the first iteration of a solve without a head) x_new = e
+    const bool stencil = !cold || e;
     auto pair = [&](int64_t q, float2& a, float2& c) {   // x_new at cells q, q + 1
       if (vec) {
-        const float4 v = *reinterpret_cast<const float4*>(xin + q);
+        const float4 v = cold ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(xin + q);
         a = make_float2(v.x, v.y);
         c = make_float2(v.z, v.w);
         if (e) {
@@ -116,30 +119,30 @@ __global__ void __launch_bounds__(kSX * kSY, 4) update_residual_kernel(PairFF xp
           c = ff_add_f(c, ev.y);
         }
       } else {
-        a = xin[q];
+        a = cold ? make_float2(0.f, 0.f) : xin[q];
         if (e) a = ff_add_f(a, e[q]);
         c = make_float2(0.f, 0.f);
         if (has1) {
-          c = xin[q + 1];
+          c = cold ? make_float2(0.f, 0.f) : xin[q + 1];
           if (e) c = ff_add_f(c, e[q + 1]);
         }
       }
     };
     auto single = [&](int64_t q) {
-      const float2 v = xin[q];
+      const float2 v = cold ? make_float2(0.f, 0.f) : xin[q];
       return e ? ff_add_f(v, e[q]) : v;
     };
     const float2 zero2 = make_float2(0.f, 0.f);
     // x_new of the pair on planes k - 1 (zm), k (zc) and k + 1 (zp)
     float2 zm[2] = {zero2, zero2}, zc[2] = {zero2, zero2}, zp[2] = {zero2, zero2};
     int64_t t0 = (int64_t)k0 * nn + (int64_t)j * n + i0;
-    if (!cold) {
+    if (stencil) {
       if (k0 > 0) pair(t0 - nn, zm[0], zm[1]);
       pair(t0, zc[0], zc[1]);
     }
     for (int k = k0; k < k1; ++k, t0 += nn) {
       float2 acc[2] = {zero2, zero2};
-      if (!cold) {
+      if (stencil) {
         if (k < n - 1) pair(t0 + nn, zp[0], zp[1]);
         // L x = sum of (x_q - x_p): each hi difference split exactly by two-sum,
         // the hi parts summed by a two-sum chain (rounding errors carried in
@@ -984,8 +987,10 @@ __global__ void scale64_kernel(double* __restrict__ v, int64_t N, double s) {
     v[t] *= s;
 }
 
+// out32 (may be null): b rounded to float, the first residual of a solve
+// from zero (its head skipped).
 __global__ void rhs_stats64_kernel(const double* __restrict__ b, int64_t N,
-                                   double* __restrict__ partials) {
+                                   double* __restrict__ partials, float* __restrict__ out32) {
   __shared__ double red[32];
   // per thread: the sum in float-float, the sum of squares in float (it only
   // sets the tolerance's scale); FP64 from the block sums on
@@ -996,6 +1001,7 @@ __global__ void rhs_stats64_kernel(const double* __restrict__ b, int64_t N,
     const float2 v = split_f64(b[t]);
     f1 = ff_add_f(ff_add_f(f1, v.x), v.y);
     f2 = fmaf(v.x, v.x, f2);
+    if (out32) out32[t] = __fadd_rn(v.x, v.y);
   }
   double s1 = (double)f1.x + (double)f1.y, s2 = (double)f2;
   s1 = block_sum<kThreads>(s1, red);
@@ -1629,8 +1635,8 @@ int max_steps(const wgeo_handle* h, int mode) {
 }
 
 // The fixed launch sequence: the head and max_steps gated iterations.
-int enqueue_solve(wgeo_handle* h, int res, int mode, cudaStream_t s) {
-  int rc = enqueue_part(h, res, mode, 0, 0, 0, 0, s);
+int enqueue_solve(wgeo_handle* h, int res, int mode, bool skip, cudaStream_t s) {
+  int rc = skip ? WGEO_OK : enqueue_part(h, res, mode, 0, 0, 0, 0, s);
   for (int it = 1; it <= max_steps(h, mode) && rc == WGEO_OK; ++it)
     rc = enqueue_part(h, res, mode, 1, it, 0, 0, s);
   return rc;
@@ -1640,21 +1646,27 @@ int enqueue_solve(wgeo_handle* h, int res, int mode, cudaStream_t s) {
 // body (one iteration) runs until the convergence test clears the condition,
 // so no launch happens after convergence.  Counts: the head's launches are
 // returned in *head, one body's in *body.
-int record_solve(wgeo_handle* h, int res, int mode, cudaGraph_t* out, long long* head, long long* body) {
+// skip: no head (see skip_head); the loop's condition then starts at 1.
+int record_solve(wgeo_handle* h, int res, int mode, bool skip, cudaGraph_t* out, long long* head,
+                 long long* body) {
   cudaStream_t cs = h->capture_stream;
   cudaGraph_t g = nullptr;
   WGEO_CUDA_TRY(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle hc;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&hc, g, 0, 0);
+  cudaError_t e = skip ? cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault)
+                       : cudaGraphConditionalHandleCreate(&hc, g, 0, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
     return WGEO_ERR_CUDA;
   }
   long long t0 = t_kernel_launches;
-  e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  int rc = e == cudaSuccess ? enqueue_part(h, res, mode, 0, 0, hc, 1, cs) : WGEO_ERR_CUDA;
+  int rc = WGEO_OK;
   std::vector<cudaGraphNode_t> deps;
-  if (e == cudaSuccess) {
+  if (!skip) {
+    e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    rc = e == cudaSuccess ? enqueue_part(h, res, mode, 0, 0, hc, 1, cs) : WGEO_ERR_CUDA;
+  }
+  if (!skip && e == cudaSuccess) {
     cudaStreamCaptureStatus st;
     const cudaGraphNode_t* d = nullptr;
     size_t nd = 0;
@@ -1742,6 +1754,16 @@ int build_levels(wgeo_handle* h, int res) {
 
 int launch_solve_body(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s);
 
+// A solve from zero with the lumped operator, the spectral correction and the
+// float-float iterate needs no head: its first residual is b itself, so the
+// first correction reads b (copied, or rounded from the adjoint's FP64 b, into
+// the residual buffer) and the first iteration's pass takes x as 0 (the cold
+// flag stays set until its test).  The iterations and their results are those
+// of the solve with the head.
+bool skip_head(const wgeo_handle* h, int res, int mode, bool cold) {
+  return cold && use_spectral(h, res) && !h->opt.galerkin && (mode == 1 || h->opt.precision == WGEO_PREC_MIXED);
+}
+
 // Enqueues one solve.  The launch sequence depends only on (res, mode,
 // options), and every pointer it uses is owned by the handle, so it is
 // recorded once as a CUDA graph and replayed; while the caller's stream is
@@ -1753,6 +1775,7 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
     int rc = spectral_setup(h, res, s);
     if (rc) return rc;
   }
+  const bool skip = skip_head(h, res, mode, cold);
   if (mode == 1) {
     const int rb = grid_blocks(N, kThreads, kPartials);
     if (h->opt.galerkin) {
@@ -1760,7 +1783,7 @@ int launch_solve(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t s) {
       scale64_kernel<<<grid_blocks(N, kThreads, 152 * 16), kThreads, 0, s>>>(h->dchi64, N, (double)kQ1Scale);
       WGEO_LAUNCH_CHECK();
     }
-    rhs_stats64_kernel<<<rb, kThreads, 0, s>>>(h->dchi64, N, h->partials);
+    rhs_stats64_kernel<<<rb, kThreads, 0, s>>>(h->dchi64, N, h->partials, skip ? h->r32 : nullptr);
     WGEO_LAUNCH_CHECK();
     rhs_stats_finalize_kernel<<<1, 1024, 0, s>>>(h->partials, rb, N, ss);
     WGEO_LAUNCH_CHECK();
@@ -1796,12 +1819,15 @@ int launch_solve_body(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t
   // adjoint's right-hand side built from it, carry no solver error
   // (plain FP32 takes its one direct solve)
   const int min_steps = use_spectral(h, res) ? (fp32_plain ? 1 : 2) : 0;
+  const bool skip = skip_head(h, res, mode, cold);
+  if (skip && mode == 0)
+    WGEO_CUDA_TRY(cudaMemcpyAsync(h->r32, h->b32, sizeof(float) * (size_t)res * res * res, cudaMemcpyDeviceToDevice, s));
   if (!h->opt.use_graphs || cap != cudaStreamCaptureStatusNone) {
     solve_begin_kernel<<<1, 1, 0, s>>>(ss, cold ? 1 : 0, steps, min_steps, 0);
     WGEO_LAUNCH_CHECK();
-    return enqueue_solve(h, res, mode, s);
+    return enqueue_solve(h, res, mode, skip, s);
   }
-  SolverGraph& g = h->graphs[mode];
+  SolverGraph& g = h->graphs[2 * mode + (skip ? 1 : 0)];
   const int gmode = mode * 3 + (mode == 0 ? h->opt.precision : 0);
   if (g.exec == nullptr || g.res != res || g.mode != gmode) {
     if (g.exec) {
@@ -1811,7 +1837,7 @@ int launch_solve_body(wgeo_handle* h, int res, int mode, bool cold, cudaStream_t
     if (!h->capture_stream) WGEO_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     long long head = 0, body = 0;
-    int rc = record_solve(h, res, mode, &graph, &head, &body);
+    int rc = record_solve(h, res, mode, skip, &graph, &head, &body);
     // recorded, not run: the head is counted at each replay, the body on the
     // device once per iteration
     t_kernel_launches -= head + body;

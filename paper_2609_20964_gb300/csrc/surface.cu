@@ -200,28 +200,33 @@ __global__ void isovalue_kernel(const float* __restrict__ pts, int64_t n, const 
   __shared__ double red[32];
   double s = 0.0, cnt = 0.0;
   const int res = g.res;
+  // lo and 1/h as float-float pairs: the cells and weights come from
+  // node_coord_ff, the FP64 pipe only sums
+  float lo_hi[3], lo_lo[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo_hi[a] = (float)g.lo[a];
+    lo_lo[a] = (float)(g.lo[a] - (double)lo_hi[a]);
+  }
+  const double ih = 1.0 / g.h;
+  const float ih_hi = (float)ih, ih_lo = (float)(ih - (double)ih_hi);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (pcell[i] < 0) continue;
     int i0[3];
-    double t[3];
+    float t[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double u = ((double)pts[3 * i + a] - g.lo[a]) / g.h - 0.5;
-      u = fmin(fmax(u, 0.0), (double)(res - 1));
-      int f = (int)floor(u);
-      f = min(f, res - 2);
-      i0[a] = f;
-      t[a] = u - f;
-    }
-    double v = 0.0;
+    for (int a = 0; a < 3; ++a)
+      node_cell_ff(node_coord_ff(pts[3 * i + a], lo_hi[a], lo_lo[a], ih_hi, ih_lo), res, i0[a], t[a]);
+    // the interpolated value in float-float (weights and products in float)
+    float2 v = make_float2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-      const double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dz ? t[2] : 1.0 - t[2]);
-      v += w * (double)chi[lin3(i0[0] + dx, i0[1] + dy, i0[2] + dz, res)];
+      const float w = (dx ? t[0] : 1.f - t[0]) * (dy ? t[1] : 1.f - t[1]) * (dz ? t[2] : 1.f - t[2]);
+      v = ff_add_f(v, w * chi[lin3(i0[0] + dx, i0[1] + dy, i0[2] + dz, res)]);
     }
-    s += v;
+    s += (double)v.x + (double)v.y;
     cnt += 1.0;
   }
   s = block_sum<256>(s, red);

@@ -157,6 +157,37 @@ __device__ __forceinline__ float2 ff_add_f(float2 a, float b) {
   return fast_two_sum(s.x, __fadd_rn(s.y, a.y));
 }
 
+// Node coordinate u = (x - lo) / h - 1/2 of a float position along one axis,
+// in float-float (x - lo by two-sum, the product with 1/h from its exact FMA
+// residual): about 2^-44 relative, so floor(u) and the fraction are those of
+// the exact quotient up to the fraction's final float rounding, with no FP64
+// arithmetic (lo and 1/h come as float-float pairs).
+__device__ __forceinline__ float2 node_coord_ff(float x, float lo_hi, float lo_lo, float ih_hi, float ih_lo) {
+  float2 d = two_sum(x, -lo_hi);
+  d = fast_two_sum(d.x, __fsub_rn(d.y, lo_lo));
+  const float ph = __fmul_rn(d.x, ih_hi);
+  const float pl = __fadd_rn(__fmaf_rn(d.x, ih_hi, -ph), __fadd_rn(__fmul_rn(d.x, ih_lo), __fmul_rn(d.y, ih_hi)));
+  const float2 u = fast_two_sum(ph, pl);
+  const float2 um = two_sum(u.x, -0.5f);
+  return fast_two_sum(um.x, __fadd_rn(um.y, u.y));
+}
+
+// Cell and fraction of a float-float node coordinate clamped to [0, top]
+// (top = n - 1): f = min(floor u, n - 2), t = u - f.  Returns whether u was
+// clamped.
+__device__ __forceinline__ bool node_cell_ff(float2 u, int n, int& f, float& t) {
+  const float top = (float)(n - 1);
+  const bool below = u.x < 0.f || (u.x == 0.f && u.y < 0.f);
+  const bool above = u.x > top || (u.x == top && u.y > 0.f);
+  if (below) u = make_float2(0.f, 0.f);
+  if (above) u = make_float2(top, 0.f);
+  float fl = floorf(u.x);
+  if (u.x == fl && u.y < 0.f) fl -= 1.f;
+  f = min((int)fl, n - 2);
+  t = __fadd_rn(__fsub_rn(u.x, (float)f), u.y);
+  return below || above;
+}
+
 // A double as hi + lo floats without the FP64 pipe (integer and FP32 work
 // only; the FP64 pipe of this GPU is a small fraction of its FP32 rate):
 // hi keeps the top 24 significand bits (truncated), lo the other 29 rounded
@@ -424,7 +455,7 @@ struct wgeo_handle {
   int warm_res = 0;
   cudaStream_t last_stream = nullptr;
   cudaStream_t capture_stream = nullptr;
-  wgeo::SolverGraph graphs[2];
+  wgeo::SolverGraph graphs[4];   // [2 mode + (the cold head skipped)]
 
   // multigrid hierarchy for the current res
   int nlevels = 0;
