@@ -58,7 +58,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   // x, b per coarse level (and a Jacobi buffer t for the unlumped operator)
   const size_t lev = (opt.galerkin ? 3 : 2) * (half * half * half * 8 / 7 + 64 * kMaxLevels + 64);
   L.off_levels = take(c, 4 * lev);
-  L.off_dct = take(c, 8 * (512 + 160 + 512 + 16) + 4 * (512 + 512));   // spectral tables, n <= 512
+  L.off_dct = take(c, 8 * (512 + 160 + 512 + 16 + 512 + 520) + 4 * (512 + 512));   // spectral tables, n <= 512
   const size_t Pp = (size_t)(P > 0 ? P : 1);
   L.off_pcell = take(c, 4 * Pp);
   L.off_pfrac = take(c, 16 * Pp);
@@ -284,6 +284,8 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->dct_tr = h->dct_wml + 512;
   h->dct_sk = (float*)(h->dct_tr + 16);
   h->dct_skl = h->dct_sk + 512;
+  h->dct_tw = reinterpret_cast<float2*>(h->dct_skl + 512);
+  h->dct_wq = h->dct_tw + 512;
   h->pcell = (int*)(a + L.off_pcell);
   h->pfrac = (float4*)(a + L.off_pfrac);
   h->pnrm = keep ? (float4*)(a + L.off_pnrm) : nullptr;

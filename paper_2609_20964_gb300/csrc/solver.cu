@@ -1125,11 +1125,20 @@ constexpr size_t dct_smem() {
 
 __global__ void dct_tables_kernel(int n, float2* __restrict__ t1, float2* __restrict__ w32,
                                   float2* __restrict__ wml, float2* __restrict__ tr,
-                                  float* __restrict__ sk, float* __restrict__ skl) {
+                                  float* __restrict__ sk, float* __restrict__ skl,
+                                  float2* __restrict__ tw, float2* __restrict__ wq) {
   const int R = n / 32;
-  const int count = n > 160 ? n : 160;
+  const int count = n > 160 ? n + 1 : 161;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
     double sn, cs;
+    if (q <= n) {
+      sincospi((double)q / (2.0 * n), &sn, &cs);
+      wq[q] = make_float2((float)cs, (float)-sn);   // e^{-i pi q / (2 n)}
+    }
+    if (q < n) {
+      sincospi(2.0 * (double)q / n, &sn, &cs);
+      tw[q] = make_float2((float)cs, (float)-sn);   // e^{-2 pi i q / n}
+    }
     const int a = q >> 5, j = q & 31;
     if (q < n) {
       sincospi(2.0 * (double)(j * a) / n, &sn, &cs);
@@ -1447,9 +1456,276 @@ __global__ void __launch_bounds__(kDctThreads, R <= 8 ? 2 : 1)
   }
 }
 
+// ---- n = 256: the same five passes with each complex FFT split 16 x 16
+// (Stockham through shared memory) instead of a warp-wide register FFT: 16
+// threads per FFT (two real lines), each holding 16 points, a DFT-16 in
+// registers, a twiddle, a transpose through the FFT's own two tile rows, and
+// a second DFT-16.  For p = t + 16 m and k = u + 16 k1,
+//   Z_k = sum_t W16^{t k1} W256^{t u} (sum_m z_p W16^{m u}),
+// so thread t forms the inner DFT over m, multiplies by W256^{t k2} and
+// stores it; thread u gathers the sixteen values for its k2 = u and forms the
+// outer DFT over t.  The transpose is XOR-swizzled (slot k2 * 16 + (t ^ k2)),
+// so neither its stores nor its loads conflict in the banks.  An FFT's
+// threads share a warp and only its own rows, so the phases need warp
+// barriers only; the block synchronises around the tile's global copies.
+// The DCT mapping around the FFT (Makhoul's permutation, two lines per
+// complex FFT, the post-twiddle of the forward transform and the pre-twiddle
+// of the inverse) is that of the warp-FFT passes.
+constexpr int kD2N = 256;
+constexpr int kD2Threads = 256;   // 16 FFTs (32 lines) x 16 threads
+
+__device__ __forceinline__ void dft4_f(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = make_float2(d02.x + d13.y, d02.y - d13.x);   // d02 - i d13
+  a3 = make_float2(d02.x - d13.y, d02.y + d13.x);   // d02 + i d13
+}
+
+// X_k = sum_n x_n e^{-2 pi i n k / 16}, natural order in and out: n = 4 n1 + n2,
+// k = k1 + 4 k2; DFT-4 over n1, twiddle W16^{n2 k1}, DFT-4 over n2.
+__device__ __forceinline__ void dft16_f(float2 (&x)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4_f(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+  // x[4 k1 + n2] = A[n2][k1]; A[n2][k1] *= W16^{n2 k1}
+  constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, r2 = 0.70710678118654752f;
+  const float2 w1 = make_float2(c1, -s1), w2 = make_float2(r2, -r2), w3 = make_float2(s1, -c1);
+  const float2 w6 = make_float2(-r2, -r2), w9 = make_float2(-c1, s1);
+  x[4 * 1 + 1] = cmul(x[4 * 1 + 1], w1);
+  x[4 * 1 + 2] = cmul(x[4 * 1 + 2], w2);
+  x[4 * 1 + 3] = cmul(x[4 * 1 + 3], w3);
+  x[4 * 2 + 1] = cmul(x[4 * 2 + 1], w2);
+  x[4 * 2 + 2] = make_float2(x[4 * 2 + 2].y, -x[4 * 2 + 2].x);   // W16^4 = -i
+  x[4 * 2 + 3] = cmul(x[4 * 2 + 3], w6);
+  x[4 * 3 + 1] = cmul(x[4 * 3 + 1], w3);
+  x[4 * 3 + 2] = cmul(x[4 * 3 + 2], w6);
+  x[4 * 3 + 3] = cmul(x[4 * 3 + 3], w9);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4_f(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+  // x[4 k1 + k2] = X[k1 + 4 k2]: back to natural order
+  float2 y[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = x[4 * k1 + k2];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = y[k];
+}
+
+// The 256-point FFT of the 16 points z[m] = z_{t + 16 m} of this thread's FFT:
+// on return z[k1] = Z_{t + 16 k1}.  sc: the FFT's scratch (256 float2).
+__device__ __forceinline__ void fft256_16x16(float2 (&z)[16], float2* sc, const float2* tw, int t) {
+  dft16_f(z);
+#pragma unroll
+  for (int k2 = 1; k2 < 16; ++k2) z[k2] = cmul(z[k2], tw[t * k2]);
+  __syncwarp();   // the FFT's rows are read before they hold the transpose
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) sc[k2 * 16 + (t ^ k2)] = z[k2];
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < 16; ++m) z[m] = sc[t * 16 + (m ^ t)];
+  dft16_f(z);
+}
+
+// MODE 0: forward DCT-II along `axis`; 1: its inverse; 2 (axis z): forward,
+// division by the eigenvalue, inverse.  Lines as in dct_pass_kernel; a block
+// takes 32 lines, `in` may be `out`.
+template <int MODE>
+__global__ void __launch_bounds__(kD2Threads, 3)
+    dct256_pass_kernel(const float* in, float* out, int axis, const float2* __restrict__ twg,
+                       const float2* __restrict__ wqg, const float* __restrict__ skg, int q1,
+                       const int* __restrict__ gate) {
+  constexpr int n = kD2N;
+  if (*gate) return;
+  __shared__ float2 tw[n];            // e^{-2 pi i j / n}
+  __shared__ float2 wq[n + 1];        // e^{-i pi k / (2 n)}
+  __shared__ float sk[n];             // 4 sin^2(pi k / (2 n))
+  __shared__ __align__(16) float S[kDctTile * 260];
+  const int tid = threadIdx.x;
+  for (int q = tid; q <= n; q += kD2Threads) {
+    if (q < n) {
+      tw[q] = twg[q];
+      if (MODE == 2) sk[q] = skg[q];
+    }
+    wq[q] = wqg[q];
+  }
+  // rows of 260 floats along x (float4-aligned copies), 257 across (the
+  // transposed copies then fall in distinct banks)
+  const int LS = axis == 0 ? 260 : 257;
+  const int groups = n / kDctTile;
+  const int fixed = blockIdx.x / groups, t0 = (blockIdx.x - fixed * groups) * kDctTile;
+  const int64_t nn = (int64_t)n * n;
+  const int64_t base = axis == 0 ? ((int64_t)fixed * n + t0) * n : axis == 1 ? fixed * nn + t0 : (int64_t)fixed * n + t0;
+  const int64_t rstride = axis == 1 ? n : nn;
+  constexpr int kVec = kDctTile * n / 4;
+  constexpr int kIt = kVec / kD2Threads;   // 8 float4 per thread
+  {
+    float4 buf[kIt];
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int q = tid + it * kD2Threads;
+      const int64_t g = axis == 0 ? base + 4 * (int64_t)q : base + (q >> 3) * rstride + 4 * (q & 7);
+      buf[it] = *reinterpret_cast<const float4*>(in + g);
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int q = tid + it * kD2Threads;
+      if (axis == 0) {
+        *reinterpret_cast<float4*>(&S[(q >> 6) * 260 + 4 * (q & 63)]) = buf[it];
+      } else {
+        const int i = q >> 3, l = 4 * (q & 7);
+        S[(l + 0) * 257 + i] = buf[it].x;
+        S[(l + 1) * 257 + i] = buf[it].y;
+        S[(l + 2) * 257 + i] = buf[it].z;
+        S[(l + 3) * 257 + i] = buf[it].w;
+      }
+    }
+  }
+  __syncthreads();
+
+  const int f = tid >> 4, t = tid & 15;   // FFT f: lines 2f, 2f + 1
+  float* ra = S + (2 * f) * LS;
+  float* rb = ra + LS;
+  float2* sc = reinterpret_cast<float2*>(ra);   // 256 float2 over the two rows
+  float2 z[16];
+  if (MODE != 1) {
+    // forward: z_p = v_a[p] + i v_b[p], v_p = x_{2p} (p < n/2), x_{2(n-1-p)+1}
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int p = t + 16 * m;
+      const int sp = p < n / 2 ? 2 * p : 2 * n - 1 - 2 * p;
+      z[m] = make_float2(ra[sp], rb[sp]);
+    }
+    fft256_16x16(z, sc, tw, t);
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) sc[t + 16 * k1] = z[k1];
+    __syncwarp();
+    // X_k = Re(e^{-i pi k / 2n} V_k) of both lines, in pairs (k, n - k):
+    // V_a = (Z_k + conj Z_{n-k}) / 2, V_b = (Z_k - conj Z_{n-k}) / 2i, and at
+    // n - k the conjugates
+    float xa[16], xb[16], xa128 = 0.f, xb128 = 0.f;
+#pragma unroll
+    for (int sidx = 0; sidx < 8; ++sidx) {
+      const int k = t + 16 * sidx;
+      const float2 zk = sc[k], zc = sc[(n - k) & (n - 1)];
+      const float2 va = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+      const float2 vb = make_float2(0.5f * (zk.y + zc.y), 0.5f * (zc.x - zk.x));
+      const float2 w = wq[k], wc = wq[n - k];
+      xa[sidx] = w.x * va.x - w.y * va.y;
+      xb[sidx] = w.x * vb.x - w.y * vb.y;
+      xa[8 + sidx] = wc.x * va.x + wc.y * va.y;
+      xb[8 + sidx] = wc.x * vb.x + wc.y * vb.y;
+    }
+    if (t == 0) {
+      const float2 zh = sc[n / 2];
+      xa128 = wq[n / 2].x * zh.x;
+      xb128 = wq[n / 2].x * zh.y;
+    }
+    if (MODE == 2) {
+      // divide by the eigenvalue of mode (kx, ky, kz) = (t0 + line, fixed, k)
+      const float sxa = sk[t0 + 2 * f], sxb = sk[t0 + 2 * f + 1], sy = sk[fixed];
+      auto lam = [&](float sx, float sz) {
+        if (q1) {
+          const float my = 1.f - sy * (1.f / 6.f), mz = 1.f - sz * (1.f / 6.f), mx = 1.f - sx * (1.f / 6.f);
+          return -(float)kQ1Scale * (sx * my * mz + mx * (sy * mz + my * sz));
+        }
+        return -(sx + sy + sz);
+      };
+#pragma unroll
+      for (int sidx = 0; sidx < 8; ++sidx) {
+        const int k = t + 16 * sidx;
+        const bool zero_a = (t0 + 2 * f) == 0 && fixed == 0 && k == 0;
+        xa[sidx] = zero_a ? 0.f : xa[sidx] / lam(sxa, sk[k]);
+        xb[sidx] = xb[sidx] / lam(sxb, sk[k]);
+        const float skc = sk[(n - k) & (n - 1)];   // at k = 0 the value is not used (n - k = n)
+        xa[8 + sidx] = xa[8 + sidx] / lam(sxa, skc);
+        xb[8 + sidx] = xb[8 + sidx] / lam(sxb, skc);
+      }
+      if (t == 0) {
+        xa128 = xa128 / lam(sxa, sk[n / 2]);
+        xb128 = xb128 / lam(sxb, sk[n / 2]);
+      }
+    }
+    __syncwarp();   // every thread has read its Z before the rows take X
+#pragma unroll
+    for (int sidx = 0; sidx < 8; ++sidx) {
+      const int k = t + 16 * sidx;
+      ra[k] = xa[sidx];
+      rb[k] = xb[sidx];
+      if (k) {
+        ra[n - k] = xa[8 + sidx];
+        rb[n - k] = xb[8 + sidx];
+      }
+    }
+    if (t == 0) {
+      ra[n / 2] = xa128;
+      rb[n / 2] = xb128;
+    }
+  }
+  if (MODE != 0) {
+    __syncwarp();
+    // inverse: the FFT of conj(V_a + i V_b), conj V_k = e^{-i pi k / 2n} (X_k + i X_{n-k})
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int p = t + 16 * m;
+      const float xa = ra[p], xb = rb[p];
+      const float xan = p ? ra[n - p] : 0.f, xbn = p ? rb[n - p] : 0.f;
+      z[m] = inverse_input(wq[p], xa, xan, xb, xbn);
+    }
+    fft256_16x16(z, sc, tw, t);
+    __syncwarp();
+    // v_a + i v_b = conj(Z) / n, back in place: x_{2q} = v_q, x_{2(n-1-q)+1} = v_q
+    constexpr float inv_n = 1.f / (float)n;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+      const int q = t + 16 * k1;
+      const int sq = q < n / 2 ? 2 * q : 2 * n - 1 - 2 * q;
+      ra[sq] = z[k1].x * inv_n;
+      rb[sq] = -z[k1].y * inv_n;
+    }
+  }
+  __syncthreads();
+  {
+    float4 buf[kIt];
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int q = tid + it * kD2Threads;
+      if (axis == 0) {
+        buf[it] = *reinterpret_cast<const float4*>(&S[(q >> 6) * 260 + 4 * (q & 63)]);
+      } else {
+        const int i = q >> 3, l = 4 * (q & 7);
+        buf[it] = make_float4(S[(l + 0) * 257 + i], S[(l + 1) * 257 + i], S[(l + 2) * 257 + i],
+                              S[(l + 3) * 257 + i]);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int q = tid + it * kD2Threads;
+      const int64_t g = axis == 0 ? base + 4 * (int64_t)q : base + (q >> 3) * rstride + 4 * (q & 7);
+      *reinterpret_cast<float4*>(out + g) = buf[it];
+    }
+  }
+}
+
 template <int R>
 int spectral_passes(wgeo_handle* h, float* e, const float* r, const int* gate, cudaStream_t s) {
   constexpr int n = 32 * R;
+  if (n == kD2N) {
+    const int blocks = n * (n / kDctTile);
+    const int q1 = h->opt.galerkin ? 1 : 0;
+#define WGEO_DCT256_PASS(MODE, SRC, AXIS)                                                                 \
+  dct256_pass_kernel<MODE><<<blocks, kD2Threads, 0, s>>>(SRC, e, AXIS, h->dct_tw, h->dct_wq, h->dct_sk, q1, \
+                                                         gate);                                          \
+  WGEO_LAUNCH_CHECK();
+    WGEO_DCT256_PASS(0, r, 0)
+    WGEO_DCT256_PASS(0, e, 1)
+    WGEO_DCT256_PASS(2, e, 2)
+    WGEO_DCT256_PASS(1, e, 1)
+    WGEO_DCT256_PASS(1, e, 0)
+#undef WGEO_DCT256_PASS
+    return WGEO_OK;
+  }
   constexpr size_t smem = dct_smem<R>();
   const int blocks = n * (n / kDctTile);
   const int q1 = h->opt.galerkin ? 1 : 0;
@@ -1501,8 +1777,9 @@ int spectral_setup(wgeo_handle* h, int n, cudaStream_t s) {
     h->dct_attr = true;
   }
   if (h->dct_n != n) {
-    dct_tables_kernel<<<div_up(n > 160 ? n : 160, 256), 256, 0, s>>>(n, h->dct_t1, h->dct_w32, h->dct_wml,
-                                                                     h->dct_tr, h->dct_sk, h->dct_skl);
+    dct_tables_kernel<<<div_up(n > 160 ? n + 1 : 161, 256), 256, 0, s>>>(n, h->dct_t1, h->dct_w32, h->dct_wml,
+                                                                         h->dct_tr, h->dct_sk, h->dct_skl,
+                                                                         h->dct_tw, h->dct_wq);
     WGEO_LAUNCH_CHECK();
     h->dct_n = n;
   }

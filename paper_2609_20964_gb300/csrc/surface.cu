@@ -280,16 +280,24 @@ __device__ __forceinline__ void brick_cube(int t, int& lx, int& ly, int& lz) {
 // along x: word w of row (j, k) holds x = 32 w .. 32 w + 31 (bits past the
 // grid's edge clear), at bits[(k n + j) nw + w], nw = ceil(n / 32).  One warp
 // per word: coalesced reads of chi, one ballot.
+constexpr int kBitRows = 8;   // rows per warp in mc_bits_kernel (loads in flight per lane)
 __global__ void __launch_bounds__(256) mc_bits_kernel(const float* __restrict__ chi, int n, int nw,
                                                       const DevState* __restrict__ st,
                                                       unsigned* __restrict__ bits) {
-  // block (32, 8): warp y takes word blockIdx.x of row blockIdx.y * 8 + y
-  const int row = blockIdx.y * 8 + threadIdx.y;   // k n + j
-  if (row >= n * n) return;                       // whole warps
+  // block (32, 8): warp y takes word blockIdx.x of kBitRows consecutive rows
+  // (k n + j), their loads issued together
+  const int row0 = (blockIdx.y * 8 + threadIdx.y) * kBitRows;
   const int x = 32 * blockIdx.x + threadIdx.x;
-  const bool in = x < n && chi[(int64_t)row * n + x] < st->c_up;
-  const unsigned m = __ballot_sync(0xffffffffu, in);
-  if (threadIdx.x == 0) bits[row * nw + blockIdx.x] = m;
+  const float c_up = st->c_up;
+  float v[kBitRows];
+#pragma unroll
+  for (int r = 0; r < kBitRows; ++r)
+    v[r] = (x < n && row0 + r < n * n) ? chi[(int64_t)(row0 + r) * n + x] : INFINITY;
+#pragma unroll
+  for (int r = 0; r < kBitRows; ++r) {
+    const unsigned m = __ballot_sync(0xffffffffu, v[r] < c_up);
+    if (threadIdx.x == 0 && row0 + r < n * n) bits[(row0 + r) * nw + blockIdx.x] = m;
+  }
 }
 
 // Four 4^3 bricks of cubes per CTA (consecutive brick indices), 64 threads
@@ -1804,8 +1812,8 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
     // the triangles per brick from them
     const int nw = div_up(res, 32);
     unsigned* bits = reinterpret_cast<unsigned*>(h->e32);
-    mc_bits_kernel<<<dim3(nw, div_up((int64_t)res * res, 8)), dim3(32, 8), 0, s>>>(h->chi32, res, nw, h->dstate,
-                                                                                    bits);
+    mc_bits_kernel<<<dim3(nw, div_up((int64_t)res * res, 8 * kBitRows)), dim3(32, 8), 0, s>>>(h->chi32, res, nw,
+                                                                                               h->dstate, bits);
     WGEO_LAUNCH_CHECK();
     const int64_t groups = (int64_t)div_up(res - 1, 32) * g.nb * g.nb;
     mc_count_kernel<<<grid_blocks(16 * groups, 256, h->num_sms * 16), 256, 0, s>>>(bits, g, nw, h->brick_count);

@@ -393,6 +393,8 @@ struct wgeo_handle {
   float2* dct_w32 = nullptr;     //   per lane-butterfly stage s (h = 2^s): e^{-i pi (j mod h) / h}
   float2* dct_wml = nullptr;     //   e^{-i pi k / (2 n)} at k = a + R brev5(j)
   float2* dct_tr = nullptr;      //   e^{-2 pi i q / R} (q < R)
+  float2* dct_tw = nullptr;      //   e^{-2 pi i q / n} (q < n)
+  float2* dct_wq = nullptr;      //   e^{-i pi q / (2 n)} (q <= n)
   float* dct_sk = nullptr;       //   4 sin^2(pi k / (2 n)) (k < n, natural order)
   float* dct_skl = nullptr;      //   the same at k = a + R brev5(j)
   int dct_n = 0;                 // n the tables hold (0: none yet)

@@ -88,13 +88,13 @@ def test_spectral_adjoint_matches_the_oracle(W, galerkin):
     rec.close()
 
 
-@pytest.mark.parametrize("galerkin", [0, 1])
-def test_spectral_at_512_agrees_with_multigrid(W, galerkin):
-    # 512^3 (16 values per lane in the warp FFT): too large for the oracle's
-    # dense solve, so the property that holds at any size: both corrections
-    # drive the same system to a tight residual (1e-9 of ||b||), so chi
-    # agrees far below the SDF tolerance; the spectral refinement needs few steps
-    res = 512
+@pytest.mark.parametrize("res,galerkin", [(256, 0), (256, 1), (512, 0), (512, 1)])
+def test_spectral_at_large_sizes_agrees_with_multigrid(W, res, galerkin):
+    # 256^3 (the 16 x 16 shared-memory FFT) and 512^3 (16 values per lane in
+    # the warp FFT): too large for the oracle's dense solve, so the property
+    # that holds at any size: both corrections drive the same system to a
+    # tight residual (1e-9 of ||b||), so chi agrees far below the SDF
+    # tolerance; the spectral refinement needs few steps
     p, n, _ = synth.sh_body_cloud(200_000, lmax=8)
     chis, steps = [], []
     for spectral in (1, 0):
@@ -111,3 +111,26 @@ def test_spectral_at_512_agrees_with_multigrid(W, galerkin):
     assert steps[0] <= 4 and steps[0] <= steps[1]
     del chis
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("galerkin", [0, 1])
+def test_spectral_adjoint_at_256_agrees_with_multigrid(W, galerkin):
+    # the adjoint solve through the 256-point passes (inverse and z passes)
+    # against the multigrid correction, both to a tight residual
+    res = 256
+    p, n, _ = synth.sh_body_cloud(100_000, lmax=8, seed=5)
+    q = synth.uniform_queries(20_000, seed=6)
+    g = np.random.default_rng(7).standard_normal(len(q)).astype(np.float32)
+    out = []
+    for spectral in (1, 0):
+        rec = W(res, len(p), galerkin=galerkin, spectral=spectral, tol_rel=1e-9, tol_rel_adjoint=1e-9)
+        rec.reconstruct(_t(p), _t(n), BBOX, res, with_normals=False)
+        rec.query(_t(q), with_normals=False)
+        dp, dn, _ = rec.backward(q=_t(q), d_sdf_q=_t(g))
+        info = rec.info()
+        assert info["status"] == 0, info
+        out.append((dp.cpu().numpy().astype(np.float64), info["backward_steps"]))
+        rec.close()
+    (a, sa), (b, sb) = out
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+    assert sa <= 4 and sa <= sb
