@@ -1632,19 +1632,21 @@ __global__ void __launch_bounds__(kD2Threads, 3)
         }
         return -(sx + sy + sz);
       };
+      // (times the correctly rounded reciprocal: the correction needs FP32
+      // accuracy, not the division's last bit)
 #pragma unroll
       for (int sidx = 0; sidx < 8; ++sidx) {
         const int k = t + 16 * sidx;
         const bool zero_a = (t0 + 2 * f) == 0 && fixed == 0 && k == 0;
-        xa[sidx] = zero_a ? 0.f : xa[sidx] / lam(sxa, sk[k]);
-        xb[sidx] = xb[sidx] / lam(sxb, sk[k]);
+        xa[sidx] = zero_a ? 0.f : xa[sidx] * __frcp_rn(lam(sxa, sk[k]));
+        xb[sidx] = xb[sidx] * __frcp_rn(lam(sxb, sk[k]));
         const float skc = sk[(n - k) & (n - 1)];   // at k = 0 the value is not used (n - k = n)
-        xa[8 + sidx] = xa[8 + sidx] / lam(sxa, skc);
-        xb[8 + sidx] = xb[8 + sidx] / lam(sxb, skc);
+        xa[8 + sidx] = xa[8 + sidx] * __frcp_rn(lam(sxa, skc));
+        xb[8 + sidx] = xb[8 + sidx] * __frcp_rn(lam(sxb, skc));
       }
       if (t == 0) {
-        xa128 = xa128 / lam(sxa, sk[n / 2]);
-        xb128 = xb128 / lam(sxb, sk[n / 2]);
+        xa128 = xa128 * __frcp_rn(lam(sxa, sk[n / 2]));
+        xb128 = xb128 * __frcp_rn(lam(sxb, sk[n / 2]));
       }
     }
     __syncwarp();   // every thread has read its Z before the rows take X
