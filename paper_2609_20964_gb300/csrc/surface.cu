@@ -430,42 +430,48 @@ __device__ __forceinline__ void brick_edge_of_slot(int sl, int& ax, int& ex, int
 // vertices rounded to float32; tris_lo (may be null) their residuals
 // (double vertex - float vertex, rounded to float), so that hi + lo keeps
 // about 48 bits: near-tie decisions and the adjoint's closest points use it.
+// The bricks with triangles, listed (one atomic per warp); an empty brick
+// writes its 8 leaf offsets here (all equal to its triangle offset).
+__global__ void mc_live_kernel(const int* __restrict__ brick_off, int nbr, int* __restrict__ leaf_off,
+                               int* __restrict__ list, unsigned* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count: every lane reaches the ballot
+  for (int b0 = blockIdx.x * blockDim.x; b0 < nbr; b0 += gridDim.x * blockDim.x) {
+    const int br = b0 + threadIdx.x;
+    bool live = false;
+    if (br < nbr) {
+      const int base = brick_off[br];
+      live = brick_off[br + 1] != base;
+      if (!live) {
+        int4* lo4 = reinterpret_cast<int4*>(leaf_off + 8 * (int64_t)br);
+        lo4[0] = make_int4(base, base, base, base);
+        lo4[1] = make_int4(base, base, base, base);
+      }
+    }
+    const unsigned mk = __ballot_sync(0xffffffffu, live);
+    if (mk) {
+      const int leader = __ffs(mk) - 1;
+      unsigned at = 0;
+      if (lane == leader) at = atomicAdd(count, (unsigned)__popc(mk));
+      at = __shfl_sync(0xffffffffu, at, leader);
+      if (live) list[at + __popc(mk & ((1u << lane) - 1u))] = br;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(64 * kMcBricks) mc_emit_kernel(const float* __restrict__ chi, ChiFF chiff,
                                                                  SurfParams g, const DevState* __restrict__ st,
                                                                  const int* __restrict__ brick_off, int64_t cap,
+                                                                 const int* __restrict__ live_list,
+                                                                 const unsigned* __restrict__ nlive,
                                                                  Tri* __restrict__ tris, Tri* __restrict__ tris_lo,
                                                                  int* __restrict__ leaf_off) {
-  const int nbr = g.nb * g.nb * g.nb;
   const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
-  const int br = blockIdx.x * kMcBricks + grp;
-  // a brick without triangles only writes its leaf offsets (every thread
-  // still reaches the barrier below)
-  const int base = br < nbr ? brick_off[br] : 0;
-  const bool live = br < nbr && brick_off[br + 1] != base;
-  if (br < nbr && !live && t < 8) leaf_off[8 * (int64_t)br + t] = base;
-  int i = 0, j = 0, k = 0;
-  const int n = g.res, m = n - 1;
-  int code = 0, cnt = 0;
-  if (live) {
-    const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
-    int lx, ly, lz;
-    brick_cube(t, lx, ly, lz);
-    i = bx * kBrick + lx;
-    j = by * kBrick + ly;
-    k = bz * kBrick + lz;
-    if (i < m && j < m && k < m) {
-      code = cube_code(chi, i, j, k, n, st->c_up);
-      cnt = c_mc_count[code];
-    }
-  }
-  const double c = st->c;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int tt = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += tt;
-  }
+  const int n = g.res, m = n - 1;
+  const double c = st->c;
+  const float c_up = st->c_up;
+  const float2* __restrict__ xff = chiff.p[0] ? chiff.p[st->fwd.xidx] : nullptr;
   __shared__ int wt[2 * kMcBricks];
   // the brick's crossing edges (listed first, so that the FP64 placement
   // runs on full warps), and its vertices, one per crossing edge (hi with
@@ -473,84 +479,111 @@ __global__ void __launch_bounds__(64 * kMcBricks) mc_emit_kernel(const float* __
   __shared__ short s_cross[kMcBricks][kBrickEdges];
   __shared__ int s_ncross[kMcBricks];
   __shared__ float4 s_vh[kMcBricks][kBrickEdges], s_vl[kMcBricks][kBrickEdges];
-  if (lane == 31) wt[w] = incl;
-  if (t == 0) s_ncross[grp] = 0;
-  __syncthreads();
-  const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
-  if (live) {
-    const float c_up = st->c_up;
-    for (int r = 0; r < div_up_c(kBrickEdges, 64); ++r) {   // the same trip count in both warps
-      const int e = t + 64 * r;
-      bool cross = false;
-      if (e < kBrickEdges) {
+  const unsigned count = *nlive;
+  // persistent: kMcBricks listed bricks per iteration (the same trip count in
+  // the whole CTA: every thread reaches the barriers)
+  for (unsigned b0 = blockIdx.x * kMcBricks; b0 < count; b0 += gridDim.x * kMcBricks) {
+    const bool live = b0 + grp < count;
+    const int br = live ? live_list[b0 + grp] : 0;
+    const int base = live ? brick_off[br] : 0;
+    const int bx = br % g.nb, by = (br / g.nb) % g.nb, bz = br / (g.nb * g.nb);
+    int i = 0, j = 0, k = 0;
+    int code = 0, cnt = 0;
+    if (live) {
+      int lx, ly, lz;
+      brick_cube(t, lx, ly, lz);
+      i = bx * kBrick + lx;
+      j = by * kBrick + ly;
+      k = bz * kBrick + lz;
+      if (i < m && j < m && k < m) {
+        code = cube_code(chi, i, j, k, n, c_up);
+        cnt = c_mc_count[code];
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int tt = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += tt;
+    }
+    if (lane == 31) wt[w] = incl;
+    if (t == 0) s_ncross[grp] = 0;
+    __syncthreads();
+    if (live) {
+      for (int r = 0; r < div_up_c(kBrickEdges, 64); ++r) {   // the same trip count in both warps
+        const int e = t + 64 * r;
+        bool cross = false;
+        if (e < kBrickEdges) {
+          int ax, ex, ey, ez;
+          brick_edge_of_slot(e, ax, ex, ey, ez);
+          const int pi = bx * kBrick + ex, pj = by * kBrick + ey, pk = bz * kBrick + ez;
+          if (pi + (ax == 0) < n && pj + (ax == 1) < n && pk + (ax == 2) < n) {
+            const int64_t p = lin3(pi, pj, pk, n);
+            const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+            // crossing exactly when the two corner bits of the cube codes differ
+            cross = (chi[p] < c_up) != (chi[p + stride] < c_up);
+          }
+        }
+        const unsigned mk = __ballot_sync(0xffffffffu, cross);
+        if (mk) {
+          const int leader = __ffs(mk) - 1;
+          int at = 0;
+          if (lane == leader) at = atomicAdd(&s_ncross[grp], __popc(mk));
+          at = __shfl_sync(0xffffffffu, at, leader);
+          if (cross) s_cross[grp][at + __popc(mk & ((1u << lane) - 1u))] = (short)e;
+        }
+      }
+    }
+    __syncthreads();
+    if (live) {
+      const int nc = s_ncross[grp];
+      for (int ci = t; ci < nc; ci += 64) {
+        const int e = s_cross[grp][ci];
         int ax, ex, ey, ez;
         brick_edge_of_slot(e, ax, ex, ey, ez);
         const int pi = bx * kBrick + ex, pj = by * kBrick + ey, pk = bz * kBrick + ez;
-        if (pi + (ax == 0) < n && pj + (ax == 1) < n && pk + (ax == 2) < n) {
-          const int64_t p = lin3(pi, pj, pk, n);
-          const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
-          // crossing exactly when the two corner bits of the cube codes differ
-          cross = (chi[p] < c_up) != (chi[p + stride] < c_up);
+        const int64_t p = lin3(pi, pj, pk, n);
+        const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+        double c1, c2;
+        if (xff) {
+          const float2 f1 = xff[p], f2 = xff[p + stride];
+          c1 = (double)f1.x + (double)f1.y;
+          c2 = (double)f2.x + (double)f2.y;
+        } else {
+          c1 = (double)chi[p];
+          c2 = (double)chi[p + stride];
         }
-      }
-      const unsigned mk = __ballot_sync(0xffffffffu, cross);
-      if (mk) {
-        const int leader = __ffs(mk) - 1;
-        int at = 0;
-        if (lane == leader) at = atomicAdd(&s_ncross[grp], __popc(mk));
-        at = __shfl_sync(0xffffffffu, at, leader);
-        if (cross) s_cross[grp][at + __popc(mk & ((1u << lane) - 1u))] = (short)e;
+        const double eta = (c - c1) / (c2 - c1);
+        // node centre, moved by eta h along the edge's axis
+        double px = fma(pi + 0.5, g.h, g.lo[0]), py = fma(pj + 0.5, g.h, g.lo[1]), pz = fma(pk + 0.5, g.h, g.lo[2]);
+        if (ax == 0) px = fma(eta, g.h, px);
+        else if (ax == 1) py = fma(eta, g.h, py);
+        else pz = fma(eta, g.h, pz);
+        const int gid = (int)(3 * p + ax);
+        const float hx = (float)px, hy = (float)py, hz = (float)pz;
+        s_vh[grp][e] = make_float4(hx, hy, hz, __int_as_float(gid));
+        s_vl[grp][e] = make_float4((float)(px - (double)hx), (float)(py - (double)hy), (float)(pz - (double)hz), 0.f);
       }
     }
-  }
-  __syncthreads();
-  if (live) {
-    const float2* __restrict__ xff = chiff.p[0] ? chiff.p[st->fwd.xidx] : nullptr;
-    const int nc = s_ncross[grp];
-    for (int ci = t; ci < nc; ci += 64) {
-      const int e = s_cross[grp][ci];
-      int ax, ex, ey, ez;
-      brick_edge_of_slot(e, ax, ex, ey, ez);
-      const int pi = bx * kBrick + ex, pj = by * kBrick + ey, pk = bz * kBrick + ez;
-      const int64_t p = lin3(pi, pj, pk, n);
-      const int64_t stride = (ax == 0) ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
-      double c1, c2;
-      if (xff) {
-        const float2 f1 = xff[p], f2 = xff[p + stride];
-        c1 = (double)f1.x + (double)f1.y;
-        c2 = (double)f2.x + (double)f2.y;
-      } else {
-        c1 = (double)chi[p];
-        c2 = (double)chi[p + stride];
+    __syncthreads();
+    if (live) {
+      const int excl = incl - cnt + ((w & 1) ? wt[w - 1] : 0);
+      if ((t & 7) == 0) leaf_off[8 * (int64_t)br + (t >> 3)] = base + excl;
+      const int li = i - bx * kBrick, lj = j - by * kBrick, lk = k - bz * kBrick;
+      for (int q = 0; q < cnt; ++q) {
+        const int64_t idx = (int64_t)base + excl + q;
+        if (idx >= cap) break;
+        auto slot = [&](int v) {
+          int ox, oy, oz, ax;
+          edge_lower_offset(c_mc_tris[code][q][v], ox, oy, oz, ax);
+          return brick_edge_slot(ax, li + ox, lj + oy, lk + oz);
+        };
+        const int s0 = slot(0), s1 = slot(1), s2 = slot(2);
+        tris[idx] = Tri{s_vh[grp][s0], s_vh[grp][s1], s_vh[grp][s2]};
+        if (tris_lo) tris_lo[idx] = Tri{s_vl[grp][s0], s_vl[grp][s1], s_vl[grp][s2]};
       }
-      const double eta = (c - c1) / (c2 - c1);
-      // node centre, moved by eta h along the edge's axis
-      double px = fma(pi + 0.5, g.h, g.lo[0]), py = fma(pj + 0.5, g.h, g.lo[1]), pz = fma(pk + 0.5, g.h, g.lo[2]);
-      if (ax == 0) px = fma(eta, g.h, px);
-      else if (ax == 1) py = fma(eta, g.h, py);
-      else pz = fma(eta, g.h, pz);
-      const int gid = (int)(3 * p + ax);
-      const float hx = (float)px, hy = (float)py, hz = (float)pz;
-      s_vh[grp][e] = make_float4(hx, hy, hz, __int_as_float(gid));
-      s_vl[grp][e] = make_float4((float)(px - (double)hx), (float)(py - (double)hy), (float)(pz - (double)hz), 0.f);
     }
-  }
-  __syncthreads();
-  if (!live) return;
-  const int excl = incl - cnt + ((w & 1) ? wt[w - 1] : 0);
-  if ((t & 7) == 0) leaf_off[8 * (int64_t)br + (t >> 3)] = base + excl;
-  const int li = i - bx * kBrick, lj = j - by * kBrick, lk = k - bz * kBrick;
-  for (int q = 0; q < cnt; ++q) {
-    const int64_t idx = (int64_t)base + excl + q;
-    if (idx >= cap) break;
-    auto slot = [&](int v) {
-      int ox, oy, oz, ax;
-      edge_lower_offset(c_mc_tris[code][q][v], ox, oy, oz, ax);
-      return brick_edge_slot(ax, li + ox, lj + oy, lk + oz);
-    };
-    const int s0 = slot(0), s1 = slot(1), s2 = slot(2);
-    tris[idx] = Tri{s_vh[grp][s0], s_vh[grp][s1], s_vh[grp][s2]};
-    if (tris_lo) tris_lo[idx] = Tri{s_vl[grp][s0], s_vl[grp][s1], s_vl[grp][s2]};
+    __syncthreads();   // the shared arrays are reused by the next bricks
   }
 }
 
@@ -1016,9 +1049,9 @@ __device__ __forceinline__ unsigned pack_node(int lev, int x, int y, int z) {
 // keeps its kCand smallest float32 distances (four: triangles sharing the
 // closest edge tie exactly, so candidates come in pairs) and prunes against
 // the best plus a rounding margin; when the second lies within that margin
-// the node is a near-tie: the ids of the candidates within the margin go to
-// tie_a, tie_b and tie_cd (-1 for none; tie_b = -1 marks a decided node) and
-// sdf_tie_kernel re-decides it in float-float.  Without TIES (no closest
+// the node is a near-tie: it is appended to tie_list, the ids of the
+// candidates within the margin go to tie_a, tie_b and tie_cd at the same list
+// position (-1 for none), and sdf_tie_kernel re-decides it in float-float.  Without TIES (no closest
 // triangle is kept) the search keeps the float32 minimum alone, which is
 // within the same rounding of the exact distance.
 //
@@ -1264,16 +1297,19 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
     }
   }
   const int64_t o = lin3(i, j, k, n);
+  int tie_at = 0;
   if (TIES) {
     // near-tie nodes go to a compact list (one atomic per warp), so that the
-    // tie pass runs full warps over them alone
+    // tie pass runs full warps over them alone; their candidates are stored
+    // at the same list position (read coalesced by the tie pass)
     const unsigned m = __ballot_sync(0xffffffffu, tie);
     if (m) {
       const int leader = __ffs(m) - 1;
       unsigned base = 0;
       if (lane == leader) base = atomicAdd(&st->ntie, (unsigned)__popc(m));
       base = __shfl_sync(0xffffffffu, base, leader);
-      if (tie) tie_list[base + __popc(m & ((1u << lane) - 1u))] = (int)o;
+      tie_at = (int)(base + __popc(m & ((1u << lane) - 1u)));
+      if (tie) tie_list[tie_at] = (int)o;
     }
   }
   if (!valid) return;
@@ -1285,11 +1321,11 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
   if (ctri) ctri[o] = bt;
   if (S > 1) seed_ids[o] = bt;
   if (TIES && tie) {
-    tie_a[o] = bt;
-    tie_b[o] = ct[NC > 1 ? 1 : 0] & idmask;
+    tie_a[tie_at] = bt;
+    tie_b[tie_at] = ct[NC > 1 ? 1 : 0] & idmask;
     const int c2 = ct[NC > 2 ? 2 : 0], c3 = ct[NC > 3 ? 3 : 0];
-    tie_cd.p[st->fwd.xidx ^ 1][o] = make_int2(cd[NC > 2 ? 2 : 0] <= cut && c2 != -1 ? (c2 & idmask) : -1,
-                                              cd[NC > 3 ? 3 : 0] <= cut && c3 != -1 ? (c3 & idmask) : -1);
+    tie_cd.p[st->fwd.xidx ^ 1][tie_at] = make_int2(cd[NC > 2 ? 2 : 0] <= cut && c2 != -1 ? (c2 & idmask) : -1,
+                                                   cd[NC > 3 ? 3 : 0] <= cut && c3 != -1 ? (c3 & idmask) : -1);
   }
 }
 
@@ -1321,9 +1357,9 @@ __global__ void sdf_tie_kernel(const float* __restrict__ chi, SurfParams g, cons
   const int xi = st->fwd.xidx ^ 1;
   for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < count; it += gridDim.x * blockDim.x) {
     const unsigned o = (unsigned)tie_list[it];
-    const int t1 = tie_b[o];
-    const int t0 = tie_a[o];
-    const int2 t23 = tie_cd.p[xi][o];
+    const int t1 = tie_b[it];
+    const int t0 = tie_a[it];
+    const int2 t23 = tie_cd.p[xi][it];
     const unsigned row = o / un;
     const int i = (int)(o - row * un), j = (int)(row % un), k = (int)(row / un);
     const float2 px = s_ax[0][i], py = s_ax[1][j], pz = s_ax[2][k];
@@ -1823,11 +1859,17 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   if (rc) return rc;
   mc_total_kernel<<<1, 1, 0, s>>>(h->brick_off, nbricks, h->mesh_cap, h->leaf_off, h->dstate);
   WGEO_LAUNCH_CHECK();
+  // the bricks with triangles, listed in the solver's idle residual buffer
+  int* live_bricks = reinterpret_cast<int*>(h->r32);
+  WGEO_CUDA_TRY(cudaMemsetAsync(&h->dstate->nbrick_live, 0, sizeof(unsigned), s));
+  mc_live_kernel<<<grid_blocks(nbricks, 256, h->num_sms * 16), 256, 0, s>>>(h->brick_off, nbricks, h->leaf_off,
+                                                                            live_bricks, &h->dstate->nbrick_live);
+  WGEO_LAUNCH_CHECK();
   // vertices from the refined float-float indicator (MIXED precision) and
   // their low parts for the near-tie decisions and the adjoint (when kept)
-  mc_emit_kernel<<<div_up(nbricks, kMcBricks), 64 * kMcBricks, 0, s>>>(h->chi32, chiff_of(h), g, h->dstate,
-                                                                         h->brick_off, h->mesh_cap, h->tris,
-                                                                         h->tris_lo, h->leaf_off);
+  mc_emit_kernel<<<std::min(div_up(nbricks, kMcBricks), h->num_sms * 8), 64 * kMcBricks, 0, s>>>(
+      h->chi32, chiff_of(h), g, h->dstate, h->brick_off, h->mesh_cap, live_bricks, &h->dstate->nbrick_live,
+      h->tris, h->tris_lo, h->leaf_off);
   WGEO_LAUNCH_CHECK();
   const PyrInfo pi = pyramid_info(2 * g.nb);
   const int64_t nleaf = (int64_t)pi.dim[0] * pi.dim[0] * pi.dim[0];

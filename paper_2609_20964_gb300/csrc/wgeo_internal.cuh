@@ -63,6 +63,7 @@ struct DevState {
   unsigned splat_tiles;            // forward: splat tiles with a point in reach (the active list)
   unsigned splat_next;             // forward: next active tile to be taken by a splat CTA
   unsigned nleaf_live;             // forward: octree leaves holding triangles (the live list)
+  unsigned nbrick_live;            // forward: marching-cubes bricks holding triangles (the live list)
   unsigned nmax_bits;              // forward: largest |normal component| of the points (float bits)
 };
 
