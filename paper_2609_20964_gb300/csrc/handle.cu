@@ -19,7 +19,7 @@ constexpr size_t kAlign = 256;
 
 struct Layout {
   size_t total = 0;
-  size_t off_b32, off_chi32, off_chi64, off_r32, off_e32, off_phi, off_ctri, off_dphi64, off_dchi64,
+  size_t off_b32, off_chi32, off_chi64, off_r32, off_e32, off_phi, off_ctri, off_dphi, off_dchi64,
       off_lam64, off_lam32, off_levels, off_dct, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
       off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_tris_lo, off_tris_s, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
       off_scan, off_state, off_dp_cell, off_dp_count, off_dp_off, off_dp_cursor, off_dp_scan, off_dp_tmp,
@@ -50,7 +50,7 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.off_e32 = take(c, 4 * N);
   L.off_phi = take(c, 4 * N);
   L.off_ctri = take(c, keep ? 4 * N : 0);
-  L.off_dphi64 = take(c, keep ? 8 * N : 0);
+  L.off_dphi = take(c, keep ? 4 * N : 0);
   L.off_dchi64 = take(c, keep ? 8 * N : 0);
   L.off_lam64 = take(c, keep ? 16 * N : 0);
   L.off_lam32 = take(c, keep ? 4 * N : 0);
@@ -272,7 +272,7 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->e32 = (float*)(a + L.off_e32);
   h->phi = (float*)(a + L.off_phi);
   h->ctri = keep ? (int*)(a + L.off_ctri) : nullptr;
-  h->dphi64 = keep ? (double*)(a + L.off_dphi64) : nullptr;
+  h->dphi = keep ? (float*)(a + L.off_dphi) : nullptr;
   h->dchi64 = keep ? (double*)(a + L.off_dchi64) : nullptr;
   h->lamff[0] = keep ? (float2*)(a + L.off_lam64) : nullptr;
   h->lamff[1] = keep ? h->lamff[0] + N : nullptr;

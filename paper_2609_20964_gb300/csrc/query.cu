@@ -80,22 +80,22 @@ __device__ __forceinline__ void node_grad(const float* __restrict__ phi, int i, 
 }
 
 // Scatter dL/dg at node (i,j,k) through the transpose of the gradient stencil.
-__device__ __forceinline__ void scatter_grad_adjoint(double* __restrict__ dphi, int i, int j, int k,
-                                                     int n, double inv2h, const double dg[3]) {
+__device__ __forceinline__ void scatter_grad_adjoint(float* __restrict__ dphi, int i, int j, int k,
+                                                     int n, float inv2h, const float dg[3]) {
   const int idx[3] = {i, j, k};
   const int64_t t = lin3(i, j, k, n);
   const int64_t st[3] = {1, n, (int64_t)n * n};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double v = dg[a] * inv2h;
-    if (v == 0.0) continue;
+    const float v = dg[a] * inv2h;
+    if (v == 0.f) continue;
     if (idx[a] == 0) {
-      atomicAdd(&dphi[t], -3.0 * v);
-      atomicAdd(&dphi[t + st[a]], 4.0 * v);
+      atomicAdd(&dphi[t], -3.f * v);
+      atomicAdd(&dphi[t + st[a]], 4.f * v);
       atomicAdd(&dphi[t + 2 * st[a]], -v);
     } else if (idx[a] == n - 1) {
-      atomicAdd(&dphi[t], 3.0 * v);
-      atomicAdd(&dphi[t - st[a]], -4.0 * v);
+      atomicAdd(&dphi[t], 3.f * v);
+      atomicAdd(&dphi[t - st[a]], -4.f * v);
       atomicAdd(&dphi[t - 2 * st[a]], v);
     } else {
       atomicAdd(&dphi[t + st[a]], v);
@@ -146,7 +146,7 @@ __global__ void query_kernel(const float* __restrict__ q, int64_t m, QParams g,
 template <bool DN>
 __global__ void query_adjoint_kernel(const float* __restrict__ q, int64_t m, QParams g,
                                      const float* __restrict__ phi, const float* __restrict__ dsq,
-                                     const float* __restrict__ dnq, double* __restrict__ dphi,
+                                     const float* __restrict__ dnq, float* __restrict__ dphi,
                                      float* __restrict__ dq) {
   const int n = g.res;
   const float inv2h = (float)(0.5 / g.h);
@@ -162,7 +162,7 @@ __global__ void query_adjoint_kernel(const float* __restrict__ q, int64_t m, QPa
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int64_t o = lin3(i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + (c >> 2), n);
-        if (gs != 0.f) atomicAdd(&dphi[o], (double)(w[c] * gs));
+        if (gs != 0.f) atomicAdd(&dphi[o], w[c] * gs);
         const float pv = phi[o];
 #pragma unroll
         for (int a = 0; a < 3; ++a) dqa[a] += dw[c][a] * pv * gs;
@@ -202,11 +202,10 @@ __global__ void query_adjoint_kernel(const float* __restrict__ q, int64_t m, QPa
             // dn_c = w_c dm ; dg_c = (I - n n^T) dn_c / |g_c|
             const float wd[3] = {w[c] * dm[0], w[c] * dm[1], w[c] * dm[2]};
             const float pn = nc[c][0] * wd[0] + nc[c][1] * wd[1] + nc[c][2] * wd[2];
-            const double dg[3] = {(double)((wd[0] - nc[c][0] * pn) / gm[c]),
-                                  (double)((wd[1] - nc[c][1] * pn) / gm[c]),
-                                  (double)((wd[2] - nc[c][2] * pn) / gm[c])};
-            scatter_grad_adjoint(dphi, i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + (c >> 2), n,
-                                 0.5 / g.h, dg);
+            const float dg[3] = {(wd[0] - nc[c][0] * pn) / gm[c], (wd[1] - nc[c][1] * pn) / gm[c],
+                                 (wd[2] - nc[c][2] * pn) / gm[c]};
+            scatter_grad_adjoint(dphi, i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + (c >> 2), n, inv2h,
+                                 dg);
           }
         }
       }
@@ -219,7 +218,7 @@ __global__ void query_adjoint_kernel(const float* __restrict__ q, int64_t m, QPa
 }
 
 __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __restrict__ dng,
-                                 const float* __restrict__ phi, QParams g, double* __restrict__ dphi) {
+                                 const float* __restrict__ phi, QParams g, float* __restrict__ dphi) {
   const int n = g.res;
   const int64_t N = (int64_t)n * n * n;
   const float inv2h = (float)(0.5 / g.h);
@@ -227,7 +226,7 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
        t += (int64_t)gridDim.x * blockDim.x) {
     if (dsg) {
       const float v = dsg[t];
-      if (v != 0.f) atomicAdd(&dphi[t], (double)v);
+      if (v != 0.f) atomicAdd(&dphi[t], v);
     }
     if (dng) {
       const float dn[3] = {dng[t], dng[N + t], dng[2 * N + t]};
@@ -240,9 +239,8 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
       const float gm = sqrtf(m2);
       const float nv[3] = {gr[0] / gm, gr[1] / gm, gr[2] / gm};
       const float pn = nv[0] * dn[0] + nv[1] * dn[1] + nv[2] * dn[2];
-      const double dg[3] = {(double)((dn[0] - nv[0] * pn) / gm), (double)((dn[1] - nv[1] * pn) / gm),
-                            (double)((dn[2] - nv[2] * pn) / gm)};
-      scatter_grad_adjoint(dphi, i, j, k, n, 0.5 / g.h, dg);
+      const float dg[3] = {(dn[0] - nv[0] * pn) / gm, (dn[1] - nv[1] * pn) / gm, (dn[2] - nv[2] * pn) / gm};
+      scatter_grad_adjoint(dphi, i, j, k, n, inv2h, dg);
     }
   }
 }
@@ -271,7 +269,7 @@ __global__ void grid_seed_kernel(const float* __restrict__ dsg, const float* __r
 // `slivers` instead.  LIST = true: the listed nodes, weights and direction in
 // FP64.  Two passes, so the rare FP64 work does not stall whole warps.
 template <bool LIST>
-__global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int* __restrict__ ctri,
+__global__ void sdf_mc_adjoint_kernel(const float* __restrict__ dphi, const int* __restrict__ ctri,
                                       const float* __restrict__ chi, ChiFF chiff, const DevState* __restrict__ st,
                                       const Tri* __restrict__ tris, const Tri* __restrict__ tris_lo,
                                       const float4* __restrict__ tris_s, QParams g,
@@ -295,12 +293,10 @@ __global__ void sdf_mc_adjoint_kernel(const double* __restrict__ dphi, const int
   float2 dcacc = make_float2(0.f, 0.f);   // dL/dc: terms of both signs that nearly cancel
   for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < N; it += gridDim.x * blockDim.x) {
     const unsigned o = LIST ? (unsigned)slivers[it] : it;
-    const double gphi64 = dphi[o];
-    // most nodes carry no seed: an integer test keeps them off the FP64 pipe
-    if ((__double_as_longlong(gphi64) << 1) == 0ll) continue;
+    const float gphi = dphi[o];
+    if (gphi == 0.f) continue;   // most nodes carry no seed
     const int t = ctri[o];
     if (t < 0) continue;
-    const float gphi = (float)gphi64;
     const unsigned row = o / un;
     const int i = (int)(o - row * un), j = (int)(row % un), k = (int)(row / un);
     const float3 p = make_float3(s_ax[0][i], s_ax[1][j], s_ax[2][k]);
@@ -707,14 +703,14 @@ int launch_query(wgeo_handle* h, const float* q, int64_t m, float* sdf_q, float*
 
 namespace {
 
-// Seeds on the grid (phi and normal seeds): dphi64 cleared and filled.
+// Seeds on the grid (phi and normal seeds): dphi cleared and filled.
 int backward_grid_seeds(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_grid, cudaStream_t s) {
   const int64_t N = (int64_t)h->res * h->res * h->res;
-  WGEO_CUDA_TRY(cudaMemsetAsync(h->dphi64, 0, sizeof(double) * N, s));
+  WGEO_CUDA_TRY(cudaMemsetAsync(h->dphi, 0, sizeof(float) * N, s));
   WGEO_CUDA_TRY(cudaMemsetAsync(h->dchi64, 0, sizeof(double) * N, s));
   if (d_sdf_grid || d_nrm_grid) {
     grid_seed_kernel<<<grid_blocks(N, 256, 152 * 32), 256, 0, s>>>(d_sdf_grid, d_nrm_grid, h->phi, qparams(h),
-                                                                   h->dphi64);
+                                                                   h->dphi);
     WGEO_LAUNCH_CHECK();
   }
   return WGEO_OK;
@@ -731,11 +727,11 @@ int backward_mesh_nodes(wgeo_handle* h, cudaStream_t s) {
   int* slivers = reinterpret_cast<int*>(h->e32);
   WGEO_CUDA_TRY(cudaMemsetAsync(&h->dstate->nsliver, 0, sizeof(unsigned), s));
   const ChiFF cff = chiff_of(h);
-  sdf_mc_adjoint_kernel<false><<<nb, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, cff, h->dstate, h->tris,
+  sdf_mc_adjoint_kernel<false><<<nb, 256, 0, s>>>(h->dphi, h->ctri, h->chi32, cff, h->dstate, h->tris,
                                                   h->tris_lo, h->tris_s, qparams(h), h->dchi64, h->partials,
                                                   slivers, &h->dstate->nsliver);
   WGEO_LAUNCH_CHECK();
-  sdf_mc_adjoint_kernel<true><<<nb2, 256, 0, s>>>(h->dphi64, h->ctri, h->chi32, cff, h->dstate, h->tris,
+  sdf_mc_adjoint_kernel<true><<<nb2, 256, 0, s>>>(h->dphi, h->ctri, h->chi32, cff, h->dstate, h->tris,
                                                   h->tris_lo, h->tris_s, qparams(h), h->dchi64, h->partials + nb,
                                                   slivers, &h->dstate->nsliver);
   WGEO_LAUNCH_CHECK();
@@ -784,10 +780,10 @@ int launch_backward(wgeo_handle* h, const float* d_sdf_grid, const float* d_nrm_
   if (m > 0 && q && (d_sdf_q || d_nrm_q || d_q)) {
     if (d_nrm_q)
       query_adjoint_kernel<true><<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, qparams(h), h->phi, d_sdf_q,
-                                                                               d_nrm_q, h->dphi64, d_q);
+                                                                               d_nrm_q, h->dphi, d_q);
     else
       query_adjoint_kernel<false><<<grid_blocks(m, 256, 152 * 32), 256, 0, s>>>(q, m, qparams(h), h->phi, d_sdf_q,
-                                                                                nullptr, h->dphi64, d_q);
+                                                                                nullptr, h->dphi, d_q);
     WGEO_LAUNCH_CHECK();
   }
   stage_end(h, kStBwdSeed, slot, s);
@@ -857,7 +853,7 @@ int launch_export_adjoint(wgeo_handle* h, int which, float* out, cudaStream_t s)
   const int64_t N = (int64_t)h->res * h->res * h->res;
   const int gb = grid_blocks(N, 256, 152 * 32);
   if (which == 3)
-    export_f64_kernel<<<gb, 256, 0, s>>>(h->dphi64, N, out);
+    WGEO_CUDA_TRY(cudaMemcpyAsync(out, h->dphi, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
   else if (which == 4)
     export_f64_kernel<<<gb, 256, 0, s>>>(h->dchi64, N, out);
   else

@@ -384,7 +384,7 @@ struct wgeo_handle {
   float* e32 = nullptr;
   float* phi = nullptr;
   int* ctri = nullptr;
-  double* dphi64 = nullptr;
+  float* dphi = nullptr;         // backward: dL/dphi per node (float: its atomics stay in L2)
   double* dchi64 = nullptr;
   float2* lamff[2] = {nullptr, nullptr};   // adjoint solution, ping-pong like chiff
   float* lam32 = nullptr;

@@ -42,10 +42,10 @@ def test_default_options_and_footprint(lib):
     f128 = _lib.footprint_bytes(128, 10_000, o)
     f256 = _lib.footprint_bytes(256, 200_000, o)
     assert 0 < f64 < f128 < f256
-    # dominated by the res^3 fields, 76 bytes per cell when gradients are kept
-    # (b, chi32, float-float chi pair, r, e, phi, closest triangle, dphi, dchi,
-    # float-float lambda pair, lambda32), plus triangles, pucks and points
-    assert 76 * 256 ** 3 < f256 < 110 * 256 ** 3
+    # dominated by the res^3 fields, 72 bytes per cell when gradients are kept
+    # (b, chi32, float-float chi pair, r, e, phi, closest triangle, dphi (4),
+    # dchi (8), float-float lambda pair, lambda32), plus triangles, pucks and points
+    assert 72 * 256 ** 3 < f256 < 110 * 256 ** 3
     o2 = _lib.default_options(keep_for_backward=0)
     assert _lib.footprint_bytes(256, 200_000, o2) < f256
     # invalid bounds -> 0
