@@ -21,7 +21,7 @@ struct Layout {
   size_t total = 0;
   size_t off_b32, off_chi32, off_chi64, off_r32, off_e32, off_phi, off_ctri, off_dphi, off_dchi64,
       off_lam64, off_lam32, off_levels, off_dct, off_pcell, off_pfrac, off_pnrm, off_srec, off_tile_count,
-      off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_tris, off_tris_lo, off_tris_s, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
+      off_tile_off, off_tile_cursor, off_brick_count, off_brick_off, off_leaf_off, off_leaf_cnt, off_tris, off_tris_lo, off_tris_s, off_cell_pyr, off_pyr, off_pyr_sums, off_pyr_rth, off_partials,
       off_scan, off_state, off_dp_cell, off_dp_count, off_dp_off, off_dp_cursor, off_dp_scan, off_dp_tmp,
       off_dp_sorted, off_dp_key, off_dp_gbox, off_or_scal;
   size_t n_partials, n_scan, n_dp_scan;
@@ -74,12 +74,14 @@ Layout make_layout(int R, int64_t P, const wgeo_options& opt) {
   L.off_brick_count = take(c, 4 * (nbricks + 1));
   L.off_brick_off = take(c, 4 * (nbricks + 2));
   L.off_leaf_off = take(c, 4 * (8 * nbricks + 2));
+  L.off_leaf_cnt = take(c, 4 * 8 * nbricks);
   int64_t cap = opt.mesh_capacity > 0 ? opt.mesh_capacity : (int64_t)16 * R * R;
   if (cap < 4096) cap = 4096;
   L.cap = cap;
   L.off_tris = take(c, sizeof(Tri) * (size_t)cap);
   L.off_tris_lo = take(c, keep ? sizeof(Tri) * (size_t)cap : 0);
   L.off_tris_s = take(c, sizeof(float4) * kTriRec * (size_t)cap);
+  L.off_cell_pyr = take(c, 2 * sizeof(float4) * (size_t)cap);
   L.off_pyr = take(c, 32 * pyramid_nodes(nb));
   L.off_pyr_sums = take(c, 32 * pyramid_aux_nodes(nb));
   L.off_pyr_rth = take(c, 8 * pyramid_aux_nodes(nb));
@@ -296,10 +298,12 @@ int wgeo_create(wgeo_handle** out, int32_t max_res, int64_t max_points, const wg
   h->brick_count = (int*)(a + L.off_brick_count);
   h->brick_off = (int*)(a + L.off_brick_off);
   h->leaf_off = (int*)(a + L.off_leaf_off);
+  h->leaf_cnt = (unsigned*)(a + L.off_leaf_cnt);
   h->mesh_cap = L.cap;
   h->tris = (Tri*)(a + L.off_tris);
   h->tris_lo = keep ? (Tri*)(a + L.off_tris_lo) : nullptr;
   h->tris_s = (float4*)(a + L.off_tris_s);
+  h->cell_pyr = (float4*)(a + L.off_cell_pyr);
   h->pyramid = (float4*)(a + L.off_pyr);
   h->pyr_sums = (float4*)(a + L.off_pyr_sums);
   h->pyr_rth = (unsigned*)(a + L.off_pyr_rth);

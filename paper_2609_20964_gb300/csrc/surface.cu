@@ -465,7 +465,8 @@ __global__ void __launch_bounds__(64 * kMcBricks) mc_emit_kernel(const float* __
                                                                  const int* __restrict__ live_list,
                                                                  const unsigned* __restrict__ nlive,
                                                                  Tri* __restrict__ tris, Tri* __restrict__ tris_lo,
-                                                                 int* __restrict__ leaf_off) {
+                                                                 int* __restrict__ leaf_off,
+                                                                 unsigned* __restrict__ leaf_cnt) {
   const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = g.res, m = n - 1;
@@ -506,6 +507,12 @@ __global__ void __launch_bounds__(64 * kMcBricks) mc_emit_kernel(const float* __
       const int tt = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += tt;
     }
+    // the 8 cubes' triangle counts of each leaf (8 consecutive threads), 4 bits each
+    unsigned pk = (unsigned)cnt << (4 * (t & 7));
+    pk |= __shfl_xor_sync(0xffffffffu, pk, 1);
+    pk |= __shfl_xor_sync(0xffffffffu, pk, 2);
+    pk |= __shfl_xor_sync(0xffffffffu, pk, 4);
+    if (live && leaf_cnt && (t & 7) == 0) leaf_cnt[8 * (int64_t)br + (t >> 3)] = pk;
     if (lane == 31) wt[w] = incl;
     if (t == 0) s_ncross[grp] = 0;
     __syncthreads();
@@ -678,12 +685,55 @@ __global__ void puck_leaf_scan_kernel(const int* __restrict__ leaf_off, int nb, 
   }
 }
 
-// Leaf pucks, pass 2 (live leaves): the triangles' search records, then the
-// leaf's puck fitted to its vertices.
+// Puck (centre + radius, axis + half-thickness) fitted to the vertices of
+// triangles [q0, q1): centroid and mean area normal, then the largest radial
+// and axial vertex offsets in that frame, padded so the bound stays
+// conservative under float rounding.
+__device__ __forceinline__ void fit_puck(const Tri* __restrict__ tris, int64_t q0, int64_t q1, float4& A, float4& B) {
+  float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
+  for (int64_t q = q0; q < q1; ++q) {
+    const Tri tr = tris[q];
+    const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
+    cs.x += a.x + b.x + c.x;
+    cs.y += a.y + b.y + c.y;
+    cs.z += a.z + b.z + c.z;
+    const float3 cr = cross3(sub3(b, a), sub3(c, a));
+    ns.x += cr.x;
+    ns.y += cr.y;
+    ns.z += cr.z;
+  }
+  const float inv = 1.f / (3.f * (float)(q1 - q0));
+  const float3 cc = make_float3(cs.x * inv, cs.y * inv, cs.z * inv);
+  const float nn = sqrtf(dot3(ns, ns));
+  const float3 nv = nn > 0.f ? make_float3(ns.x / nn, ns.y / nn, ns.z / nn) : make_float3(0.f, 0.f, 1.f);
+  float r = 0.f, th = 0.f;
+  for (int64_t q = q0; q < q1; ++q) {
+    const Tri tr = tris[q];
+    const float4 vv[3] = {tr.a, tr.b, tr.c};
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const float3 d = sub3(f3(vv[v]), cc);
+      const float z = dot3(d, nv);
+      const float rho2 = fmaxf(dot3(d, d) - z * z, 0.f);
+      th = fmaxf(th, fabsf(z));
+      r = fmaxf(r, sqrtf(rho2));
+    }
+  }
+  const float pad = kPuckPad * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cc.z) + r + th) + 1e-7f;
+  A = make_float4(cc.x, cc.y, cc.z, r * (1.f + kPuckPad) + pad);
+  B = make_float4(nv.x, nv.y, nv.z, th * (1.f + kPuckPad) + pad);
+}
+
+// Leaf pucks, pass 2 (live leaves): the triangles' search records, the
+// leaf's puck fitted to its vertices, and (cell_pyr non-null) one puck per
+// cube of the leaf that holds triangles, stored at the slot of the cube's
+// first triangle (cell_pyr[2 q0], [2 q0 + 1]); leaf_cnt packs the cubes'
+// triangle counts, 4 bits per cube in the leaf's cube order.
 __global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const Tri* __restrict__ tris_lo,
-                                 const int* __restrict__ leaf_off, int nb, int64_t cap,
-                                 const int* __restrict__ live, const DevState* __restrict__ st,
-                                 float4* __restrict__ pyr, float4* __restrict__ tris_s) {
+                                 const int* __restrict__ leaf_off, const unsigned* __restrict__ leaf_cnt, int nb,
+                                 int64_t cap, const int* __restrict__ live, const DevState* __restrict__ st,
+                                 float4* __restrict__ pyr, float4* __restrict__ tris_s,
+                                 float4* __restrict__ cell_pyr) {
   const int nl = 2 * nb;
   const int64_t nlive = st->nleaf_live;
   for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nlive;
@@ -693,7 +743,6 @@ __global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const Tri* __rest
     const int li = leaf_index(lx, ly, lz, nb);
     const int64_t s0 = leaf_off[li];
     const int64_t s1 = min((int64_t)leaf_off[li + 1], cap);
-    float3 cs = make_float3(0.f, 0.f, 0.f), ns = make_float3(0.f, 0.f, 0.f);
     for (int64_t q = s0; q < s1; ++q) {
       const Tri tr = tris[q];
       if (tris_lo) {
@@ -702,35 +751,24 @@ __global__ void puck_leaf_kernel(const Tri* __restrict__ tris, const Tri* __rest
       } else {
         write_search_record(tr, nullptr, tris_s + kTriRec * q);
       }
-      const float3 a = f3(tr.a), b = f3(tr.b), c = f3(tr.c);
-      cs.x += a.x + b.x + c.x;
-      cs.y += a.y + b.y + c.y;
-      cs.z += a.z + b.z + c.z;
-      const float3 cr = cross3(sub3(b, a), sub3(c, a));
-      ns.x += cr.x;
-      ns.y += cr.y;
-      ns.z += cr.z;
     }
-    const float inv = 1.f / (3.f * (float)(s1 - s0));
-    const float3 cc = make_float3(cs.x * inv, cs.y * inv, cs.z * inv);
-    const float nn = sqrtf(dot3(ns, ns));
-    const float3 nv = nn > 0.f ? make_float3(ns.x / nn, ns.y / nn, ns.z / nn) : make_float3(0.f, 0.f, 1.f);
-    float r = 0.f, th = 0.f;
-    for (int64_t q = s0; q < s1; ++q) {
-      const Tri tr = tris[q];
-      const float4 vv[3] = {tr.a, tr.b, tr.c};
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        const float3 d = sub3(f3(vv[v]), cc);
-        const float z = dot3(d, nv);
-        const float rho2 = fmaxf(dot3(d, d) - z * z, 0.f);
-        th = fmaxf(th, fabsf(z));
-        r = fmaxf(r, sqrtf(rho2));
+    float4 A, B;
+    fit_puck(tris, s0, s1, A, B);
+    pyr[2 * t] = A;
+    pyr[2 * t + 1] = B;
+    if (cell_pyr) {
+      unsigned cn = leaf_cnt[li];
+      int64_t q0 = s0;
+      for (; cn != 0u; cn >>= 4) {
+        const int64_t q1 = min(q0 + (int64_t)(cn & 15u), s1);
+        if (q0 < q1) {
+          fit_puck(tris, q0, q1, A, B);
+          cell_pyr[2 * q0] = A;
+          cell_pyr[2 * q0 + 1] = B;
+        }
+        q0 += cn & 15u;
       }
     }
-    const float pad = kPuckPad * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cc.z) + r + th) + 1e-7f;
-    pyr[2 * t] = make_float4(cc.x, cc.y, cc.z, r * (1.f + kPuckPad) + pad);
-    pyr[2 * t + 1] = make_float4(nv.x, nv.y, nv.z, th * (1.f + kPuckPad) + pad);
   }
 }
 
@@ -1072,7 +1110,9 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
                                                           int* __restrict__ ctri, int* __restrict__ tie_a,
                                                           int* __restrict__ tie_b, TieSlots tie_cd,
                                                           int* __restrict__ tie_list,
-                                                          int* __restrict__ seed_ids, int stride) {
+                                                          int* __restrict__ seed_ids, int stride,
+                                                          const unsigned* __restrict__ leaf_cnt,
+                                                          const float4* __restrict__ cell_pyr) {
   __shared__ unsigned int s_node[kWarps][kStack];
   __shared__ int s_off[12];
   __shared__ int s_dim[12];
@@ -1232,17 +1272,26 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
     if (COUNT) ++c_nodes;
     if (lev == 0) {
       const int li = leaf_index(x, y, z, nb);
-      const int64_t s0 = leaf_off[li];
-      const int64_t s1 = min((int64_t)leaf_off[li + 1], cap);
-      if (COUNT) {
-        ++c_leaves;
-        c_tests += 32ull * (unsigned long long)(s1 > s0 ? s1 - s0 : 0);
-      }
-      for (int64_t t = s0; t < s1; ++t) {
-        float v, w;
-        unsigned vk;
-        const float d2 = tri_dist2_rec(p, tris_s + kTriRec * t, v, w, vk);
-        offer(d2, (int)t, v, w, vk);
+      const int s1 = (int)min((int64_t)leaf_off[li + 1], cap);
+      if (COUNT) ++c_leaves;
+      // the leaf's cubes in order; a cube's triangles are tested when its
+      // own puck beats the cut of at least one lane
+      unsigned cn = leaf_cnt[li];
+      int q0 = leaf_off[li];
+#pragma unroll 1
+      for (; cn != 0u; cn >>= 4) {
+        const int q1 = min(q0 + (int)(cn & 15u), s1);
+        if (q0 < q1 &&
+            __any_sync(0xffffffffu, puck_dist2(p, cell_pyr[2 * q0], cell_pyr[2 * q0 + 1]) < cut)) {
+          if (COUNT) c_tests += 32ull * (unsigned long long)(q1 - q0);
+          for (int t = q0; t < q1; ++t) {
+            float v, w;
+            unsigned vk;
+            const float d2 = tri_dist2_rec(p, tris_s + kTriRec * t, v, w, vk);
+            offer(d2, t, v, w, vk);
+          }
+        }
+        q0 += (int)(cn & 15u);
       }
       continue;
     }
@@ -1869,7 +1918,7 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
   // their low parts for the near-tie decisions and the adjoint (when kept)
   mc_emit_kernel<<<std::min(div_up(nbricks, kMcBricks), h->num_sms * 8), 64 * kMcBricks, 0, s>>>(
       h->chi32, chiff_of(h), g, h->dstate, h->brick_off, h->mesh_cap, live_bricks, &h->dstate->nbrick_live,
-      h->tris, h->tris_lo, h->leaf_off);
+      h->tris, h->tris_lo, h->leaf_off, h->leaf_cnt);
   WGEO_LAUNCH_CHECK();
   const PyrInfo pi = pyramid_info(2 * g.nb);
   const int64_t nleaf = (int64_t)pi.dim[0] * pi.dim[0] * pi.dim[0];
@@ -1880,8 +1929,8 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
                                                                                  h->pyramid, live, h->dstate);
   WGEO_LAUNCH_CHECK();
   const int live_grid = grid_blocks(nleaf, 256, h->num_sms * 8);
-  puck_leaf_kernel<<<live_grid, 256, 0, s>>>(h->tris, h->tris_lo, h->leaf_off, g.nb, h->mesh_cap, live, h->dstate,
-                                             h->pyramid, h->tris_s);
+  puck_leaf_kernel<<<live_grid, 256, 0, s>>>(h->tris, h->tris_lo, h->leaf_off, h->leaf_cnt, g.nb, h->mesh_cap, live,
+                                             h->dstate, h->pyramid, h->tris_s, h->cell_pyr);
   WGEO_LAUNCH_CHECK();
   {
     // levels >= 1: sums per brick, sums up the tree, vertex maxima, pucks
@@ -1937,20 +1986,24 @@ int launch_mc_sdf_normals(wgeo_handle* h, int res, float* sdf_out, float* nrm_ou
       if (h->opt.stage_timing == 2)
         sdf_kernel<true, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                             h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, ctri,
-                                                            tie_a, tie_b, tie_cd, tie_list, seed_ids, stride);
+                                                            tie_a, tie_b, tie_cd, tie_list, seed_ids, stride,
+                                                            h->leaf_cnt, h->cell_pyr);
       else
         sdf_kernel<false, true><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                              h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, ctri,
-                                                             tie_a, tie_b, tie_cd, tie_list, seed_ids, stride);
+                                                             tie_a, tie_b, tie_cd, tie_list, seed_ids, stride,
+                                                            h->leaf_cnt, h->cell_pyr);
     } else {
       if (h->opt.stage_timing == 2)
         sdf_kernel<true, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                              h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
-                                                             nullptr, nullptr, tie_cd, nullptr, seed_ids, stride);
+                                                             nullptr, nullptr, tie_cd, nullptr, seed_ids, stride,
+                                                             h->leaf_cnt, h->cell_pyr);
       else
         sdf_kernel<false, false><<<nblk, kWarps * 32, 0, s>>>(h->chi32, g, h->dstate, h->tris_s, id_bits, h->leaf_off,
                                                               h->mesh_cap, h->pyramid, pi, h->phi, sdf_out, nullptr,
-                                                              nullptr, nullptr, tie_cd, nullptr, seed_ids, stride);
+                                                              nullptr, nullptr, tie_cd, nullptr, seed_ids, stride,
+                                                             h->leaf_cnt, h->cell_pyr);
     }
     WGEO_LAUNCH_CHECK();
   }

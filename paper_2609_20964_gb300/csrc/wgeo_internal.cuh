@@ -415,12 +415,14 @@ struct wgeo_handle {
   int* brick_count = nullptr;
   int* brick_off = nullptr;      // nbricks + 1
   int* leaf_off = nullptr;       // 8 * nbricks + 1: triangle offset of each 2^3 sub-brick
+  unsigned* leaf_cnt = nullptr;  // 8 * nbricks: the triangle counts of a sub-brick's 8 cubes, 4 bits each
   wgeo::Tri* tris = nullptr;
   wgeo::Tri* tris_lo = nullptr;  // keep_for_backward: per vertex the low part of its ~48-bit position
                                  // (FP64 vertex - float32 vertex); null otherwise
   float4* tris_s = nullptr;      // per triangle: search record (a, |ab|^2), (ab, ab.ac), (ac, |ac|^2),
                                  // (1/|ab|^2, 1/|ac|^2, 1/|bc|^2, 1/|ab x ac|^2)
   float4* pyramid = nullptr;     // 2 float4 per node (puck: centre + radius, axis + half-thickness)
+  float4* cell_pyr = nullptr;    // per cube with triangles: its puck, at the slot of its first triangle
   float4* pyr_sums = nullptr;    // levels >= 1: vertex sum + count, area-normal sum (puck construction)
   unsigned* pyr_rth = nullptr;   // levels >= 1: radius, half-thickness as float bits (atomic maxima)
   double* dP = nullptr;          // backward: dL/d(vertex) per triangle corner, 9 doubles
