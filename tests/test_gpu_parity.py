@@ -373,6 +373,26 @@ def test_empty_and_degenerate_inputs(W):
     rec.close()
 
 
+def test_mesh_capacity_overflow_is_flagged(W):
+    """More triangles than mesh_capacity: the forward flags it and stays inside
+    the capped triangle, record and cube-puck buffers; the same handle then
+    reconstructs a surface that fits exactly (SDF against the oracle)."""
+    from paper_2609_20964_gb300 import STATUS_MESH_CAPACITY
+    p, n, res = CASES["sphere24"]
+    rec = W(64, len(p), mesh_capacity=4096)
+    rec.reconstruct(_t(p), _t(n), BBOX, 64)
+    info = rec.info()
+    assert info["status"] & STATUS_MESH_CAPACITY, info
+    assert info["n_triangles"] > 4096, info
+    sdf, _ = rec.reconstruct(_t(p), _t(n), BBOX, res)
+    info = rec.info()
+    assert not info["status"] & STATUS_MESH_CAPACITY, info
+    assert 0 < info["n_triangles"] <= 4096, info
+    err = np.abs(sdf.cpu().numpy().astype(np.float64) - _oracle("sphere24").phi).max()
+    assert err <= SDF_TOL, err
+    rec.close()
+
+
 def test_host_errors(W):
     from paper_2609_20964_gb300 import WgeoError
     rec = W(32, 100)
