@@ -1071,7 +1071,10 @@ __device__ __forceinline__ Ff tri_dist2_ff_exact(const Vec3<Ff> p, const float4*
 }
 
 // Octree entries on the traversal stack: level in bits 27..31, node
-// coordinates (< 512 per axis) in bits 0..8 (x), 9..17 (y), 18..26 (z).
+// coordinates (< 512 per axis) in bits 0..8 (x), 9..17 (y), 18..26 (z).  The
+// search stacks this word with the node's pyramid index, so that a pop loads
+// the node's puck at once instead of first looking up its level's offset and
+// dimension.
 __device__ __forceinline__ unsigned pack_node(int lev, int x, int y, int z) {
   return ((unsigned)lev << 27) | ((unsigned)z << 18) | ((unsigned)y << 9) | (unsigned)x;
 }
@@ -1113,7 +1116,7 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
                                                           int* __restrict__ seed_ids, int stride,
                                                           const unsigned* __restrict__ leaf_cnt,
                                                           const float4* __restrict__ cell_pyr) {
-  __shared__ unsigned int s_node[kWarps][kStack];
+  __shared__ uint2 s_node[kWarps][kStack];   // (packed level and coordinates, pyramid index)
   __shared__ int s_off[12];
   __shared__ int s_dim[12];
   if (threadIdx.x < 12) {
@@ -1229,11 +1232,11 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
       }
     }
   }
-  unsigned int* stk = s_node[w];
+  uint2* stk = s_node[w];
   int sp = 0;
   const int top = pi.nlev - 1;
   const int nb = (s_dim[0] + 1) / 2;
-  if (lane == 0) stk[0] = pack_node(top, 0, 0, 0);
+  if (lane == 0) stk[0] = make_uint2(pack_node(top, 0, 0, 0), (unsigned)s_off[top]);
   sp = 1;
   unsigned long long c_nodes = 0, c_leaves = 0, c_tests = 0;
   // the warp's nodes' bounding box: centre and half-diagonal, widened so that
@@ -1260,12 +1263,12 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
   __syncwarp();
   while (sp > 0) {
     --sp;
-    const unsigned e = stk[sp];
+    const uint2 en = stk[sp];
     __syncwarp();
+    const unsigned e = en.x;
+    const int gi = (int)en.y;
     const int lev = (int)(e >> 27);
     const int x = (int)(e & 511u), y = (int)((e >> 9) & 511u), z = (int)((e >> 18) & 511u);
-    const int dp = s_dim[lev];
-    const int gi = s_off[lev] + (z * dp + y) * dp + x;
     const float4 An = pyr[2 * gi];
     const float lb = puck_dist2(p, An, pyr[2 * gi + 1]);
     if (!__any_sync(0xffffffffu, lb < cut)) continue;
@@ -1309,14 +1312,14 @@ __global__ void __launch_bounds__(kWarps * 32, 10) sdf_kernel(const float* __res
     const float maxcut = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(cut, 0.f))));
     bool keep = false;
     float key = INFINITY;
-    unsigned ent = 0u;
+    uint2 ent = make_uint2(0u, 0u);
     if (lane < 8 && ((cmask >> lane) & 1u)) {
       const int cx = 2 * x + (lane & 1), cy = 2 * y + ((lane >> 1) & 1), cz = 2 * z + (lane >> 2);
       const int cg = cbase + (cz * dc + cy) * dc + cx;
       const float dcen = sqrtf(puck_dist2(pb, pyr[2 * cg], pyr[2 * cg + 1])) * (1.f - 2e-6f) - br;
       key = dcen > 0.f ? dcen * dcen : 0.f;
       keep = key < maxcut;
-      ent = pack_node(lev - 1, cx, cy, cz);
+      ent = make_uint2(pack_node(lev - 1, cx, cy, cz), (unsigned)cg);
     }
     const unsigned kept = __ballot_sync(0xffffffffu, keep);
     const int nc = __popc(kept);
@@ -1511,7 +1514,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
                                                                 float* __restrict__ dist_out,
                                                                 float* __restrict__ dir_out,
                                                                 int* __restrict__ tri_out) {
-  __shared__ unsigned int s_node[kWarps][kStack];
+  __shared__ uint2 s_node[kWarps][kStack];   // (packed level and coordinates, pyramid index)
   __shared__ int s_off[12];
   __shared__ int s_dim[12];
   if (threadIdx.x < 12) {
@@ -1528,7 +1531,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
     coord = fmaxf(coord, (float)fmax(fabs(g.lo[a]), fabs(g.lo[a] + n * g.h)));
   const int top = pi.nlev - 1;
   const int nb = (s_dim[0] + 1) / 2;
-  unsigned int* stk = s_node[w];
+  uint2* stk = s_node[w];
   const int nwarps = gridDim.x * kWarps;
   for (int base = (blockIdx.x * kWarps + w) * 32; base < m; base += nwarps * 32) {
     const int k = base + lane;
@@ -1573,16 +1576,16 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
       }
     }
     int sp = 1;
-    if (lane == 0) stk[0] = pack_node(top, 0, 0, 0);
+    if (lane == 0) stk[0] = make_uint2(pack_node(top, 0, 0, 0), (unsigned)s_off[top]);
     __syncwarp();
     while (sp > 0) {
       --sp;
-      const unsigned en = stk[sp];
+      const uint2 ew = stk[sp];
       __syncwarp();
+      const unsigned en = ew.x;
+      const int gi = (int)ew.y;
       const int lev = (int)(en >> 27);
       const int x = (int)(en & 511u), y = (int)((en >> 9) & 511u), z = (int)((en >> 18) & 511u);
-      const int dp = s_dim[lev];
-      const int gi = s_off[lev] + (z * dp + y) * dp + x;
       const float4 An = pyr[2 * gi];
       const float lb = puck_dist2(p, An, pyr[2 * gi + 1]);
       if (!__any_sync(0xffffffffu, lb < cut)) continue;
@@ -1596,7 +1599,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
       const int dc = s_dim[lev - 1];
       const int cbase = s_off[lev - 1];
       float key[8];
-      unsigned ent[8];
+      uint2 ent[8];
       int nc = 0;
       const unsigned cmask = __float_as_uint(An.w) & 0xffu;
 #pragma unroll
@@ -1614,7 +1617,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) sdf_query_kernel(const float* 
           --q2;
         }
         key[q2] = dm;
-        ent[q2] = pack_node(lev - 1, cx, cy, cz);
+        ent[q2] = make_uint2(pack_node(lev - 1, cx, cy, cz), (unsigned)cg);
         ++nc;
       }
       if (lane == 0)
