@@ -1081,7 +1081,8 @@ __device__ __forceinline__ unsigned pack_node(int lev, int x, int y, int z) {
 
 // Warp-cooperative exact distance search: a warp owns a 4 x 4 x 2 patch of
 // nodes and walks the octree once for all of them (a subtree is entered when
-// its bound beats the current cut of at least one lane); leaves are tested
+// its bound beats the current cut of at least one lane); in a leaf, the
+// triangles of each MC cube whose own puck beats some lane's cut are tested
 // by every lane against its own node with the same (broadcast) triangle.
 //
 // Exactness at near-ties: two triangles whose distances differ by less than
